@@ -67,9 +67,12 @@ int or_grid_dims(const or_params *P, int64_t nc[3])
     return 0;
 }
 
-static int coord(double x, double x0, double cs, int64_t n, int64_t *c)
+/* Cell coordinate floor((x - x0) * (1/(2h))), with 1/(2h) rounded once.
+ * (Sec. 3.1 fixes cells of size 2h but not the arithmetic; this form is the
+ * reading both implementations share so that labels agree bit for bit.) */
+static int coord(double x, double x0, double inv_cs, int64_t n, int64_t *c)
 {
-    double t = (x - x0) / cs;
+    double t = (x - x0) * inv_cs;
     if (!(t >= 0.0) || !(t < (double)n)) return 0;   /* also rejects NaN */
     *c = (int64_t)floor(t);
     return 1;
@@ -83,14 +86,14 @@ int64_t or_cell_keys(const or_params *P, int64_t n, const double *x,
 {
     int64_t nc[3];
     or_grid_dims(P, nc);
-    const double cs = 2.0 * P->h;
+    const double inv_cs = 1.0 / (2.0 * P->h);
     const uint64_t ncells = (uint64_t)nc[0] * nc[1] * nc[2];
     int64_t nout = 0;
     for (int64_t i = 0; i < n; ++i) {
         int64_t cx, cy, cz;
-        if (coord(x[i], P->dmin[0], cs, nc[0], &cx) &&
-            coord(y[i], P->dmin[1], cs, nc[1], &cy) &&
-            coord(z[i], P->dmin[2], cs, nc[2], &cz)) {
+        if (coord(x[i], P->dmin[0], inv_cs, nc[0], &cx) &&
+            coord(y[i], P->dmin[1], inv_cs, nc[1], &cy) &&
+            coord(z[i], P->dmin[2], inv_cs, nc[2], &cz)) {
             key[i] = (uint32_t)(cx + nc[0] * (cy + nc[1] * cz));
         } else {
             key[i] = (uint32_t)ncells;
@@ -410,9 +413,9 @@ static int is_in(const or_params *P, const int64_t nc[3], double x, double y,
                  double z)
 {
     int64_t c;
-    const double cs = 2.0 * P->h;
-    return coord(x, P->dmin[0], cs, nc[0], &c) && coord(y, P->dmin[1], cs, nc[1], &c) &&
-           coord(z, P->dmin[2], cs, nc[2], &c);
+    const double inv_cs = 1.0 / (2.0 * P->h);
+    return coord(x, P->dmin[0], inv_cs, nc[0], &c) && coord(y, P->dmin[1], inv_cs, nc[1], &c) &&
+           coord(z, P->dmin[2], inv_cs, nc[2], &c);
 }
 
 /* Predictor half step (symplectic scheme):

@@ -98,9 +98,15 @@ def test_cell_keys_on_known_points():
                          (ncx // 2, 0, ncz - 1)]:
         pts.append((x0 + (ix + 0.5) * cs, y0 + (iy + 0.5) * cs, z0 + (iz + 0.5) * cs))
         want.append(ix + ncx * (iy + ncy * iz))
-    # exactly on a lower face belongs to that cell
+    # exactly on the domain's lower corner belongs to cell 0
     pts.append((x0, y0, z0))
     want.append(0)
+    # labels follow floor((x - x0) * (1/(2h))) with 1/(2h) rounded once
+    inv_cs = 1.0 / cs
+    for f in (1.0, 2.0):
+        x = x0 + f * cs
+        pts.append((x, y0 + 0.5 * cs, z0 + 0.5 * cs))
+        want.append(int(math.floor((x - x0) * inv_cs)))
     ncells = ncx * ncy * ncz
     for bad in [(x0 - 1e-9, y0 + cs, z0 + cs), (x0 + cs, y0 + cs, z0 + ncz * cs + 1e-6),
                 (np.nan, y0, z0), (np.inf, y0, z0)]:
