@@ -1,0 +1,344 @@
+"""Throughput of the GB300 WCSPH hot path on the 32M-fluid-particle dam break.
+
+One step = one full symplectic step of the method: two force evaluations,
+each preceded by a cell rebuild (labels, radix sort, offsets, reorder), the
+CFL reduction, predictor and corrector.  The metric is particle interactions
+per second: ordered neighbour pairs (i, j) with |r_ij| < 2h evaluated by the
+interaction kernel, both evaluations of each step counted.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload dam_break_32m|dam_break_obstacles_1m|dam_break_6k]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path has
+no exchange step on one GPU); value = pairs of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-interactions/s"
+UNIT = "pairs/s"
+# Algorithmic FP32 flops per unit of interaction work (FMA = 2): the
+# distance test of one 27-cell candidate, one pair with a fluid particle i
+# (kernel gradient, continuity, viscosity, momentum), one pair with a
+# boundary particle i (kernel gradient and continuity only).
+FLOP_CANDIDATE, FLOP_FLUID_PAIR, FLOP_BOUNDARY_PAIR = 8, 50, 12
+# FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+SMS, FP32_LANES, MAX_CLOCK_GHZ = 152, 128, 2.07
+
+
+def workload(name):
+    from paper_1210_1017_gb300 import cases
+    if name == "dam_break_32m":
+        return cases.c3_dam_break_32m()
+    if name == "dam_break_obstacles_1m":
+        return cases.c2_dam_break_obstacles()
+    if name == "dam_break_6k":
+        return cases.c1_dam_break()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(case, max_seconds=25.0):
+    """The FP64 oracle as it stands, on this host's cores: one interaction
+    evaluation (its own grid over all particles + the pair sums) for a
+    contiguous block of particles sized to a bounded amount of CPU work."""
+    import oracle
+    O = oracle.Oracle(case.params())
+    st = oracle.State.from_case(case)
+    cores = oracle.num_threads()
+    n = case.n
+    # calibrate on a small block, then size the measured block
+    i0 = case.n_bound
+    t = time.perf_counter()
+    r = O.interact(st, i0=i0, i1=i0 + min(200000, n - i0))
+    t_small = time.perf_counter() - t
+    per_pair = t_small / max(r["pairs"], 1)
+    want_pairs = max_seconds * 0.6 / per_pair
+    count = int(min(n - i0, max(200000, want_pairs / 76.0)))
+    t = time.perf_counter()
+    r = O.interact(st, i0=i0, i1=i0 + count)
+    el = time.perf_counter() - t
+    return {"value": r["pairs"] / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one oracle interaction evaluation (its neighbour grid over all "
+                       f"{n} particles plus the pair sums of {count} fluid particles, "
+                       f"{r['pairs']} pairs) of the {case.name} initial state, "
+                       f"{el:.1f} s wall")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = workload(args.workload)
+    import oracle
+    O = oracle.Oracle(case.params())
+    st = oracle.State.from_case(case)
+    cores = oracle.num_threads()
+    i0 = case.n_bound
+    count = min(case.n - i0, 400000)
+    for _ in range(args.warmup):
+        O.interact(st, i0=i0, i1=i0 + count // 8)
+    pairs = 0
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r = O.interact(st, i0=i0, i1=i0 + count)
+        pairs += r["pairs"]
+    el = time.perf_counter() - t
+    value = pairs / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case.name, "n_particles": case.n,
+                       "n_fluid": case.n_fluid, "dp": case.dp},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": (f"each step: one oracle interaction evaluation (grid over "
+                                        f"all {case.n} particles + pair sums of {count} fluid "
+                                        f"particles)")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1210_1017_gb300 import sph as S
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S.lib(build=True)
+    case = workload(args.workload)
+    sim = S.Simulation.from_case(case, device=local)
+    stream = sim.stream
+    sim.build_cells()
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.synchronize()
+    d0 = sim.diagnostics()
+
+    # --- timed region: K steps, device time with CUDA events ---------------
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    d1 = sim.diagnostics()
+    sim.check()
+    pairs = d1["pairs_total"] - d0["pairs_total"]
+    pf = d1["pairs_fluid_total"] - d0["pairs_fluid_total"]
+    pb = d1["pairs_boundary_total"] - d0["pairs_boundary_total"]
+    cand = d1["candidates_total"] - d0["candidates_total"]
+    t_max = ms
+    pairs_all = pairs
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        p = torch.tensor([pairs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        pairs_all = int(p.item())
+    value = pairs_all / (t_max * 1e-3)
+    steps_per_s = args.steps / (t_max * 1e-3)
+
+    # --- dominant kernel: the interaction, timed per launch with events ------
+    nlaunch = 2 * args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nlaunch)]
+    dsum = 0.0
+    kflop = 0.0
+    for k in range(nlaunch):
+        evs[2 * k].record(stream)
+        sim.interact()
+        evs[2 * k + 1].record(stream)
+    sim.synchronize()
+    dk = sim.diagnostics()
+    for k in range(nlaunch):
+        dsum += evs[2 * k].elapsed_time(evs[2 * k + 1])
+    t_int = dsum / nlaunch * 1e-3
+    flop = (FLOP_CANDIDATE * dk["candidates_last"] + FLOP_FLUID_PAIR * dk["pairs_fluid_last"]
+            + FLOP_BOUNDARY_PAIR * dk["pairs_boundary_last"])
+    peak_tflops = SMS * FP32_LANES * 2 * MAX_CLOCK_GHZ / 1e3
+    achieved = flop / t_int / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "interaction_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        if tr.get("workload") == case.name and tr.get("kernel_rev") == S.KERNEL_REV:
+            traffic = tr.get("bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
+                "kernel": "k_interact", "ms_per_launch": round(t_int * 1e3, 4),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+
+    # --- end to end through the C ABI with pinned host buffers ---------------
+    n = case.n
+    pin = dict(pos=torch.from_numpy(case.pos.copy()).pin_memory(),
+               vel=torch.from_numpy(case.vel.copy()).pin_memory(),
+               rho=torch.from_numpy(case.rho.copy()).pin_memory(),
+               ids=torch.from_numpy(case.ids.view(np.int32).copy()).pin_memory())
+    out = dict(pos=torch.empty((n, 3), dtype=torch.float64).pin_memory(),
+               vel=torch.empty((n, 3), dtype=torch.float32).pin_memory(),
+               rho=torch.empty(n, dtype=torch.float32).pin_memory(),
+               ids=torch.empty(n, dtype=torch.int32).pin_memory())
+    e2e_steps = max(1, min(args.steps, 5))
+    de0 = sim.diagnostics()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        S.sph_upload(sim.ctx, pin["pos"], pin["vel"], pin["rho"], pin["ids"])
+        S.sph_step(sim.ctx, 1)
+        S.sph_download(sim.ctx, out["pos"], out["vel"], out["rho"], out["ids"])
+    t_e2e = time.perf_counter() - t0
+    de1 = sim.diagnostics()
+    barrier()
+    e2e_pairs = de1["pairs_total"] - de0["pairs_total"]
+    bytes_h2d = n * (24 + 12 + 4 + 4)
+    e2e = {"value": e2e_pairs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_h2d,
+           "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
+           "note": "per step: sph_upload (pinned host) + sph_step(1) + sph_download (pinned host)"}
+
+    kps = sim.kernels_per_step()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": case.name, "n_particles": case.n, "n_fluid": case.n_fluid,
+                       "n_boundary": case.n_bound, "dp": case.dp,
+                       "kernel": "Wendland C2, h=1.3dp", "integrator": "symplectic, 2 evaluations/step",
+                       "position_dtype": "f64", "l2": "inputs larger than L2 (state ~9 GB)",
+                       "parallelism": f"replicas x{ws}"},
+            "steps_per_s": steps_per_s, "pairs_per_step": pairs / args.steps,
+            "fluid_pairs_per_step": pf / args.steps, "boundary_pairs_per_step": pb / args.steps,
+            "candidates_per_step": cand / args.steps,
+            "sim_time_per_step": (d1["t"] - d0["t"]) / args.steps,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": kps * args.steps,
+            "clocks": clocks}
+    pk, src = peaks()
+    line["peaks_source"] = src
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        line["cpu_baseline"] = cpu_baseline(case)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dam_break_32m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

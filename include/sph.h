@@ -1,0 +1,236 @@
+/*
+ * sph.h -- C ABI of libsph.so, the GB300 (sm_103a) weakly compressible SPH
+ * hot path: cell list, pair interaction, CFL time step and symplectic update
+ * of a set of particles (Valdez-Balderas, Dominguez, Rogers, Crespo,
+ * "Towards accelerating SPH simulations for free-surface flows on multi-GPU
+ * clusters", single-GPU pipeline of Sec. 3).
+ *
+ * Conventions for every entry point
+ *   - Return value: SPH_OK (0) or a negative SPH_ERR_* code.  The context's
+ *     sph_last_error() then holds a one-line message.  A failed call leaves
+ *     the context usable unless the code is SPH_ERR_CUDA.
+ *   - Device memory: the caller allocates ONE device workspace of the size
+ *     sph_query_sizes() reports and passes it to sph_init().  The library
+ *     carves all its device buffers from it and never allocates or frees
+ *     device memory.  The workspace must stay allocated until sph_destroy().
+ *   - Host memory: arrays passed to sph_upload/sph_download/sph_read_array
+ *     are owned by the caller and only touched during the call.
+ *   - Streams: all work runs on the stream given to sph_init (a cudaStream_t
+ *     passed as void*).  Calls marked "async" only enqueue work; calls marked
+ *     "sync" wait for the stream.  On the legacy default stream (NULL) the
+ *     step is launched kernel by kernel; on any other stream it is captured
+ *     once into a CUDA graph and replayed.
+ *   - Particle order: the library keeps particles sorted by (cell label,
+ *     id).  Downloads return that order; ids identify particles.
+ *   - Device-side faults of the data (non-finite rates, a bounded spin that
+ *     gave up, a capacity overflow) never trap: they set bits of a device
+ *     status word that sph_diagnostics() returns and sph_check() turns into
+ *     an error code.
+ *   - Sizes: n_particles < 2^26 (67,108,864); the cell grid must have fewer
+ *     than 2^31 cells.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_OK                 0
+#define SPH_ERR_INVALID_ARG   -1   /* bad pointer, size or parameter        */
+#define SPH_ERR_CUDA          -2   /* a CUDA runtime call failed            */
+#define SPH_ERR_WORKSPACE     -3   /* workspace too small or misaligned     */
+#define SPH_ERR_TIMEOUT       -4   /* a bounded device spin gave up         */
+#define SPH_ERR_NONFINITE     -5   /* NaN/Inf in the interaction results    */
+#define SPH_ERR_CAPACITY      -6   /* a cell held more particles than the
+                                      id tie-break handles (order within it
+                                      then follows the sort's stable order) */
+#define SPH_ERR_STATE         -7   /* call out of order (e.g. no state yet) */
+
+/* Bits of the device status word. */
+#define SPH_STATUS_TIMEOUT    1u
+#define SPH_STATUS_NONFINITE  2u
+#define SPH_STATUS_CAPACITY   4u
+
+/* Physical and numerical constants of one simulation (Sec. 2.2, 2.3, 3).
+ *   dp        particle spacing [m]; mass is given separately
+ *   h         smoothing length [m]; cells have size 2h (Sec. 3.1)
+ *   rho0      reference density [kg/m^3] (1000 in the paper)
+ *   gamma     Tait exponent; must be 7 (Sec. 2.2)
+ *   c0        reference speed of sound [m/s]; B = c0^2 rho0 / gamma
+ *   alpha     artificial-viscosity coefficient (Sec. 2.2)
+ *   eta2_coef eta^2 = eta2_coef * h^2 (eta = 0.1 h in the paper -> 0.01)
+ *   gravity   acceleration [m/s^2]
+ *   cfl       CFL number of the variable time step (Sec. 3.3)
+ *   mass      mass of every particle [kg]
+ *   dmin,dmax cell-grid domain; ncx = ceil((dmax-dmin)/(2h)) per axis.
+ *             Particles outside it are excluded from the interactions and
+ *             frozen (counted in sph_diag.n_out)
+ *   n_bound   particles with id < n_bound are dynamic boundary particles
+ *             (Sec. 2.3): density evolves, position and velocity never do
+ *   dt_fixed  > 0: use this step size; otherwise the CFL step */
+typedef struct sph_params {
+    double dp, h, rho0, gamma, c0, alpha, eta2_coef;
+    double gravity[3];
+    double cfl, mass;
+    double dmin[3], dmax[3];
+    uint32_t n_bound;
+    uint32_t reserved;
+    double dt_fixed;
+} sph_params;
+
+typedef struct sph_sizes {
+    uint64_t workspace_bytes;   /* device bytes sph_init needs            */
+    uint64_t ncells;            /* ncx * ncy * ncz                        */
+    uint32_t ncx, ncy, ncz;
+    uint32_t sort_passes;       /* 8-bit radix passes per cell sort        */
+} sph_sizes;
+
+typedef struct sph_diag {
+    double t;                   /* simulated time [s]                     */
+    double dt;                  /* step size of the last step             */
+    double mass;                /* total mass of in-domain particles      */
+    double momentum[3];         /* fluid momentum                         */
+    double kinetic;             /* fluid kinetic energy                   */
+    double potential;           /* fluid potential energy -m g.r          */
+    double internal;            /* sum m e(rho), e' = p/rho^2 (Tait)      */
+    uint64_t step;              /* steps taken                            */
+    uint64_t pairs_total;       /* neighbour pairs evaluated, all calls   */
+    uint64_t candidates_total;  /* 27-cell candidates tested, all calls   */
+    uint64_t pairs_last;        /* pairs of the last interaction          */
+    uint64_t candidates_last;
+    uint64_t pairs_fluid_last;      /* of which with a fluid particle i     */
+    uint64_t pairs_boundary_last;   /* of which with a boundary particle i  */
+    uint64_t pairs_fluid_total;
+    uint64_t pairs_boundary_total;
+    uint32_t n_out;             /* excluded particles                     */
+    uint32_t status;            /* SPH_STATUS_* bits                      */
+    float amax, cmax, mumax;    /* CFL terms of the last evaluation       */
+} sph_diag;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Bytes of device workspace for n particles under params (no side
+ * effects, no CUDA calls). */
+int sph_query_sizes(const sph_params *params, uint32_t n_particles,
+                    sph_sizes *out);
+
+/* Create a context over a caller-owned device workspace.  d_workspace must
+ * be 256-byte aligned and at least sizes.workspace_bytes long.  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Sync (zeroes a few
+ * counters).  *out is owned by the caller and freed with sph_destroy. */
+int sph_init(const sph_params *params, uint32_t n_particles,
+             void *d_workspace, uint64_t workspace_bytes, void *stream,
+             sph_ctx **out);
+
+/* Copy a particle state from host memory (any order): pos[3n] float64
+ * (x,y,z interleaved), vel[3n] float32, rho[n] float32, ids[n] uint32 (a
+ * permutation of 0..n-1 is not required, but ids must be distinct).  Sync.
+ * The state needs sph_build_cells before sph_interact. */
+int sph_upload(sph_ctx *ctx, const double *pos, const float *vel,
+               const float *rho, const uint32_t *ids);
+
+/* Sec. 3.1: cell label of every particle (FP64, x fastest), radix sort by
+ * (label, id), first index per cell, and reorder of all state arrays.
+ * Async. */
+int sph_build_cells(sph_ctx *ctx);
+
+/* Sec. 3.2: pair sums of Eq. 7 (density rate, every in-domain particle)
+ * and Eq. 9 (acceleration, gravity included, fluid particles; boundary
+ * particles get gravity only since Sec. 2.3 never moves them), in FP32 on
+ * cell-relative coordinates, plus the CFL reductions of Sec. 3.3 (sets the device-side
+ * step size unless params.dt_fixed > 0).  Requires built cells.  Async.
+ * flags: SPH_INTERACT_COUNTS also stores each particle's neighbour count
+ * (readable as SPH_ARRAY_NNB). */
+#define SPH_INTERACT_COUNTS 1u
+int sph_interact(sph_ctx *ctx, uint32_t flags);
+
+/* Predictor half step of the symplectic scheme from the current rates:
+ * fluid r += dt/2 v, v += dt/2 a; every in-domain particle rho += dt/2
+ * drho/dt (Sec. 2.3: boundary particles keep r and v).  Keeps the start
+ * state for sph_correct and recomputes the cell labels.  Async. */
+int sph_predict(sph_ctx *ctx);
+
+/* Corrector of the symplectic scheme, from the start state kept by
+ * sph_predict and the rates of the last sph_interact: fluid
+ * v = v0 + dt a, r = r0 + dt/2 (v + v0); rho = rho0 (2 - e)/(2 + e) with
+ * e = -dt (drho/dt) / rho_half.  Advances t and the step count.  Async. */
+int sph_correct(sph_ctx *ctx);
+
+/* nsteps full steps: interact, CFL step, predict, rebuild, interact,
+ * correct, rebuild (two force evaluations per step).  Builds the cells
+ * first if needed.  Async. */
+int sph_step(sph_ctx *ctx, uint32_t nsteps);
+
+/* Run nsteps steps; after every save_every steps (and at the end) wait for
+ * the stream and call cb(user, step, t), from which the caller may call
+ * sph_download or sph_diagnostics (the paper's "copy to the host only when
+ * saving", Sec. 3).  cb may be NULL.  A non-zero return from cb stops the
+ * rollout early (still SPH_OK).  Sync. */
+typedef int (*sph_snapshot_fn)(void *user, uint64_t step, double t);
+int sph_rollout(sph_ctx *ctx, uint32_t nsteps, uint32_t save_every,
+                sph_snapshot_fn cb, void *user);
+
+/* Copy the current state (sorted order) to host arrays laid out as in
+ * sph_upload.  Any pointer may be NULL to skip it.  Sync. */
+int sph_download(sph_ctx *ctx, double *pos, float *vel, float *rho,
+                 uint32_t *ids);
+
+/* Copy an internal device array to host memory for inspection.  bytes must
+ * equal the array's size (see sph_array_bytes).  Sync.
+ *   SPH_ARRAY_KEY      uint32[n]  cell label of each particle, sorted order
+ *   SPH_ARRAY_CELL_OFF uint32[ncells+2] first index of each cell (the last
+ *                      two entries: in-domain count, n)
+ *   SPH_ARRAY_ACE      float32[4n] (ax, ay, az, drho/dt) per particle
+ *   SPH_ARRAY_NNB      uint32[n]  neighbour counts (SPH_INTERACT_COUNTS)
+ *   SPH_ARRAY_NNB64    uint32[n]  neighbour counts with the FP64 predicate
+ *                      (sph_neighbour_counts_fp64)
+ *   SPH_ARRAY_POSC     float32[4n] cell-relative position and p/rho^2
+ *   SPH_ARRAY_DT       float64[1] current step size */
+#define SPH_ARRAY_KEY      0
+#define SPH_ARRAY_CELL_OFF 1
+#define SPH_ARRAY_ACE      2
+#define SPH_ARRAY_NNB      3
+#define SPH_ARRAY_NNB64    4
+#define SPH_ARRAY_POSC     5
+#define SPH_ARRAY_DT       6
+uint64_t sph_array_bytes(const sph_ctx *ctx, int which);
+int sph_read_array(sph_ctx *ctx, int which, void *host, uint64_t bytes);
+
+/* Sec. 3.2 neighbour counts with the FP64 predicate |r_ij|^2 < (2h)^2,
+ * |r|^2 = (dx*dx + dy*dy) + dz*dz without contraction, on the current
+ * cells (for bit-exact comparison; not used by the time step).  Async. */
+int sph_neighbour_counts_fp64(sph_ctx *ctx);
+
+/* FP64 conservation sums, counters and status.  Sync. */
+int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
+
+/* Map the device status word to an error code (SPH_OK if clear).  Sync. */
+int sph_check(sph_ctx *ctx);
+
+/* Number of kernels one sph_step(ctx, 1) launches. */
+uint32_t sph_kernels_per_step(const sph_ctx *ctx);
+
+const char *sph_last_error(const sph_ctx *ctx);
+void sph_destroy(sph_ctx *ctx);
+
+/* Sec. 3.1 / Sec. 4.3: stable LSD radix sort of (key, value) pairs by the
+ * low key_bits bits of the key (8 bits per pass, onesweep with decoupled
+ * look-back).  Equal keys keep their input order, so sorting labels whose
+ * values are ids in ascending order reproduces the (label, id) order of the
+ * paper's example.  d_vals_in may be NULL: values are then the input
+ * indices 0..n-1.  All arrays are device arrays of n uint32; outputs must
+ * not alias inputs.  d_scratch must hold sph_radix_sort_scratch_bytes(n)
+ * bytes (256-byte aligned).  Async on stream. */
+uint64_t sph_radix_sort_scratch_bytes(uint32_t n);
+int sph_radix_sort_pairs(const uint32_t *d_keys_in, const uint32_t *d_vals_in,
+                         uint32_t *d_keys_out, uint32_t *d_vals_out,
+                         uint32_t n, uint32_t key_bits, void *d_scratch,
+                         uint64_t scratch_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,140 @@
+// Private declarations shared by the CUDA translation units of libsph.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusNonFinite = 2u;
+constexpr uint32_t kStatusCapacity = 4u;
+
+// Largest particle count: list entries pack a 26-bit particle index with the
+// 6-bit cell offset of the neighbour (2 bits per axis).
+constexpr uint32_t kMaxParticles = 1u << 26;
+
+// Per-context constants handed to kernels by value.
+struct Dev {
+    double x0, y0, z0;     // domain origin
+    double inv_cs;         // 1 / (2h), rounded once (cell label arithmetic)
+    double cs;             // 2h
+    double r2max_d;        // (2h)^2 rounded once (FP64 neighbour predicate)
+    double h_d, cfl, dt_fixed;
+    int ncx, ncy, ncz;
+    uint32_t ncells;
+    uint32_t n;
+    uint32_t n_bound;
+    float csf;             // 2h
+    float h, inv_h;
+    float r2max;           // (2h)^2 in FP32
+    float eta2;            // eta^2
+    float fc;              // -5 aD / h^2 (Wendland C2 gradient factor)
+    float alpha, c0, rho0, inv_rho0, B, mass;
+    float gx, gy, gz;
+};
+
+// Stream-ordered launchers (defined in the .cu files).
+void launch_keys(const Dev& d, const double* x, const double* y, const double* z,
+                 uint32_t n, uint32_t* key, uint32_t* cnt, uint32_t* hist,
+                 int passes, cudaStream_t st);
+void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
+                       cudaStream_t st);
+uint32_t scan_bsum_count(uint64_t m);
+
+// Radix sort
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsThreads * kOsItems;
+inline uint32_t os_tiles(uint32_t n) { return (n + kOsTile - 1) / kOsTile; }
+void launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, int bits_total,
+                       uint32_t* hist, cudaStream_t st);
+void launch_onesweep_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                          uint32_t* vout, uint32_t n, int pass, int bits_total,
+                          const uint32_t* hist, uint32_t* status, uint32_t* tilectr,
+                          uint32_t* err, cudaStream_t st);
+
+struct ReorderArgs {
+    const uint32_t* skey;
+    const uint32_t* sval;
+    const uint32_t* off;
+    const double *sx, *sy, *sz;
+    const float4* svr;
+    const uint32_t* sid;
+    const double *spx, *spy, *spz;   // pre state (may be null)
+    const float4* spvr;
+    double *dx, *dy, *dz;
+    float4* dvr;
+    uint32_t* did;
+    double *dpx, *dpy, *dpz;
+    float4* dpvr;
+    float4* posc;
+    uint32_t* hist_to_zero;          // cleared for the next rebuild
+    uint32_t* status;
+};
+void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
+
+struct InteractArgs {
+    const float4* posc;
+    const float4* velrhop;
+    const uint32_t* key;
+    const uint32_t* id;
+    const uint32_t* off;
+    float4* ace;
+    uint32_t* nnb;        // may be null
+    float4* part_f;       // per block: max|a|^2, max c, max mu, 0
+    uint4* part_u;        // per block: fluid-i pairs, candidates, status bits,
+                          // boundary-i pairs
+};
+uint32_t interact_blocks(uint32_t n);
+void prepare_interact();   // once per process: opt in to the list's shared memory
+void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
+
+struct ReduceArgs {
+    const float4* part_f;
+    const uint4* part_u;
+    uint32_t nparts;
+    float4* lvl2_f;
+    unsigned long long* lvl2_q;     // 4 per block: fluid pairs, boundary pairs, cands, status
+    uint32_t* done;
+    double* dt;             // written if set_dt
+    float* terms;           // 3 floats: amax, cmax, mumax
+    // [0] pairs total, [1] candidates total, [2] pairs last, [3] candidates
+    // last, [4] fluid-i pairs last, [5] boundary-i pairs last, [6] fluid-i
+    // pairs total, [7] boundary-i pairs total
+    unsigned long long* counters;
+    uint32_t* status;
+};
+constexpr int kReduceBlocks = 152;
+void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st);
+
+struct IntegrateArgs {
+    const uint32_t* off;     // for the in-domain count
+    double *x, *y, *z;
+    float4* velrhop;
+    const uint32_t* id;
+    const float4* ace;
+    double *px, *py, *pz;    // pre state: written by predict, read by correct
+    float4* pvr;
+    const double* dt;
+    double* t;
+    unsigned long long* step;
+    uint32_t* key;
+    uint32_t* cnt;
+    uint32_t* hist;
+    int passes;
+};
+void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st);
+void launch_correct(const Dev& d, const IntegrateArgs& a, cudaStream_t st);
+
+void launch_counts_fp64(const Dev& d, const double* x, const double* y, const double* z,
+                        const uint32_t* key, const uint32_t* off, uint32_t* out,
+                        cudaStream_t st);
+
+// FP64 conservation sums: out[0..7] = mass, px, py, pz, kinetic, potential,
+// internal, n_out (as double).
+constexpr int kDiagBlocks = 152;
+void launch_diag(const Dev& d, const double* x, const double* y, const double* z,
+                 const float4* vr, const uint32_t* id, const uint32_t* off,
+                 double* partial, double* out, cudaStream_t st);
+
+}  // namespace sph

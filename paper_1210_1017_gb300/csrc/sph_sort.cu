@@ -1,0 +1,309 @@
+// Radix sort of (cell label, index) pairs and the scan that turns per-cell
+// counts into first-index-per-cell offsets (Sec. 3.1 of the paper: label,
+// radix sort, reorder, first index of each cell).
+//
+// The sort is a least-significant-digit radix sort with 8-bit digits in the
+// single-pass "onesweep" organisation: one histogram of all digit places up
+// front (fused into the label kernel on the SPH path), then one kernel per
+// digit place in which each 4096-key tile ranks its keys in shared memory,
+// publishes its per-digit counts, and finds its global offsets by a bounded
+// decoupled look-back over the tiles before it.  Equal digits keep their
+// input order, so the sort is stable.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kFlagAgg = 1u << 30;     // tile's own count published
+constexpr uint32_t kFlagPre = 2u << 30;     // inclusive prefix published
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 24;   // polls before giving up
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < 8 ? s_w[lane] : 0u;
+        uint32_t inc = t;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < 8) s_w[lane] = inc - t;
+    }
+    __syncthreads();
+    uint32_t r = x - v + s_w[w];
+    __syncthreads();
+    return r;
+}
+
+__host__ __device__ __forceinline__ uint32_t digit_mask(int pass, int bits_total) {
+    int b = bits_total - 8 * pass;
+    b = b > 8 ? 8 : (b < 0 ? 0 : b);
+    return (1u << b) - 1u;
+}
+
+__global__ void __launch_bounds__(256) k_digit_hist(const uint32_t* __restrict__ keys,
+                                                    uint32_t n, int passes, int bits_total,
+                                                    uint32_t* __restrict__ hist) {
+    __shared__ uint32_t sh[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & digit_mask(p, bits_total))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// One digit place.  hist holds the global count of each digit value for
+// this place; status holds one word per (tile, digit), zero on entry;
+// tilectr is a zeroed counter that hands out tiles in launch order, so every
+// tile a block waits on belongs to a block that is already running.
+__global__ void __launch_bounds__(kOsThreads) k_onesweep(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n, int shift,
+    uint32_t dmask, const uint32_t* __restrict__ hist, uint32_t* status,
+    uint32_t* tilectr, uint32_t* err) {
+    constexpr int W = kOsThreads / 32;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_wh[W][256];       // per-warp digit counts, then offsets
+    __shared__ uint32_t s_dstart[256];      // tile-local first slot per digit
+    __shared__ uint32_t s_gbase[256];       // global first slot of the tile's digit run
+    __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_keys[kOsTile];
+    __shared__ uint32_t s_vals[kOsTile];
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tilectr, 1u);
+    for (int i = tid; i < W * 256; i += kOsThreads) (&s_wh[0][0])[i] = 0;
+    const uint32_t gofs = block_excl_scan_256(hist[tid], s_w);   // also syncs
+    const uint32_t tile = s_tile;
+    const uint32_t base = tile * kOsTile + w * (kOsItems * 32);
+
+    uint32_t k[kOsItems], v[kOsItems], rk[kOsItems];
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        const uint32_t idx = base + r * 32 + lane;
+        const bool ok = idx < n;
+        k[r] = ok ? kin[idx] : 0u;
+        v[r] = ok ? (vin ? vin[idx] : idx) : 0u;
+        rk[r] = ok ? 0u : 0xffffffffu;
+    }
+    // Warp-level stable ranking: items r = 0..15 in order, lanes in order.
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        const bool ok = rk[r] == 0u;
+        const uint32_t d = ok ? ((k[r] >> shift) & dmask) : 256u + lane;
+        const uint32_t peers = __match_any_sync(kFull, d);
+        uint32_t prev = 0;
+        if (ok) prev = s_wh[w][d];
+        __syncwarp();
+        if (ok) {
+            rk[r] = prev + __popc(peers & lt);
+            if (lane == __ffs(peers) - 1) s_wh[w][d] = prev + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // Thread tid owns digit tid: per-warp exclusive offsets and tile count.
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+        const uint32_t c = s_wh[ww][tid];
+        s_wh[ww][tid] = run;
+        run += c;
+    }
+    const uint32_t cnt = run;
+    uint32_t* my = status + (size_t)tile * 256 + tid;
+    st_relaxed(my, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+    const uint32_t dstart = block_excl_scan_256(cnt, s_w);
+    s_dstart[tid] = dstart;
+    // Decoupled look-back for digit tid.
+    uint32_t excl = 0;
+    if (tile > 0) {
+        int64_t p = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        while (p >= 0) {
+            const uint32_t s = ld_relaxed(status + (size_t)p * 256 + tid);
+            const uint32_t flag = s & ~kValMask;
+            if (flag == 0u) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(err, kStatusTimeout);
+                    break;
+                }
+                continue;
+            }
+            excl += s & kValMask;
+            if (flag == kFlagPre) break;
+            --p;
+        }
+        st_relaxed(my, kFlagPre | (excl + cnt));
+    }
+    s_gbase[tid] = gofs + excl;
+    __syncthreads();
+    // Scatter into tile-sorted order in shared memory.
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        if (rk[r] != 0xffffffffu) {
+            const uint32_t d = (k[r] >> shift) & dmask;
+            const uint32_t pos = s_dstart[d] + s_wh[w][d] + rk[r];
+            s_keys[pos] = k[r];
+            s_vals[pos] = v[r];
+        }
+    }
+    __syncthreads();
+    const uint32_t t0 = tile * kOsTile;
+    const uint32_t nv = (n - t0) < (uint32_t)kOsTile ? (n - t0) : (uint32_t)kOsTile;
+    for (uint32_t i = tid; i < nv; i += kOsThreads) {
+        const uint32_t key = s_keys[i];
+        const uint32_t d = (key >> shift) & dmask;
+        const uint32_t g = s_gbase[d] + (i - s_dstart[d]);
+        kout[g] = key;
+        vout[g] = s_vals[i];
+    }
+}
+
+// --- exclusive scan of the per-cell counts into cell offsets --------------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              uint64_t m,
+                                                              uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t s_w[8];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint64_t i = b0 + (uint64_t)r * kScanThreads + threadIdx.x;
+        if (i < m) s += in[i];
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < 8; ++i) t += s_w[i];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the block sums in place (one block).
+__global__ void __launch_bounds__(256) k_scan_top(uint32_t* bsum, uint32_t nb) {
+    __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nb; c0 += 256) {
+        const uint32_t i = c0 + threadIdx.x;
+        const uint32_t v = i < nb ? bsum[i] : 0u;
+        const uint32_t ex = block_excl_scan_256(v, s_w);
+        const uint32_t carry = s_carry;
+        if (i < nb) bsum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 255) s_carry = carry + ex + v;
+        __syncthreads();
+    }
+}
+
+// out[i] = sum of in[0..i), i = 0..m (m + 1 outputs); clears in[] for the
+// next use.
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ in, uint64_t m,
+                                                            const uint32_t* __restrict__ bsum,
+                                                            uint32_t* __restrict__ out) {
+    __shared__ uint32_t s_w[8];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
+    const uint64_t t0 = b0 + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint64_t i = t0 + r;
+        v[r] = i < m ? in[i] : 0u;
+        tot += v[r];
+    }
+    const uint32_t ex = block_excl_scan_256(tot, s_w) + bsum[blockIdx.x];
+    uint32_t run = ex;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint64_t i = t0 + r;
+        if (i < m) {
+            out[i] = run;
+            in[i] = 0u;
+        }
+        if (i == m) out[m] = run;
+        run += v[r];
+    }
+}
+
+}  // namespace
+
+uint32_t scan_bsum_count(uint64_t m) {
+    // m + 1 outputs: the block that holds index m writes the total
+    return (uint32_t)((m + 1 + kScanChunk - 1) / kScanChunk);
+}
+
+void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
+                       cudaStream_t st) {
+    const uint64_t m = (uint64_t)d.ncells + 1;   // counts incl. the excluded bin
+    const uint32_t nb = scan_bsum_count(m);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(cnt, m, bsum);
+    k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(cnt, m, bsum, off);
+}
+
+void launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, int bits_total,
+                       uint32_t* hist, cudaStream_t st) {
+    uint32_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks == 0) blocks = 1;
+    k_digit_hist<<<blocks, 256, 0, st>>>(keys, n, passes, bits_total, hist);
+}
+
+void launch_onesweep_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                          uint32_t* vout, uint32_t n, int pass, int bits_total,
+                          const uint32_t* hist, uint32_t* status, uint32_t* tilectr,
+                          uint32_t* err, cudaStream_t st) {
+    const uint32_t tiles = os_tiles(n);
+    if (tiles == 0) return;
+    k_onesweep<<<tiles, kOsThreads, 0, st>>>(kin, vin, kout, vout, n, 8 * pass,
+                                             digit_mask(pass, bits_total), hist + 256 * pass,
+                                             status + (size_t)pass * tiles * 256,
+                                             tilectr + pass, err);
+}
+
+}  // namespace sph

@@ -1,0 +1,356 @@
+"""Python binding of libsph.so (the C ABI in include/sph.h).
+
+The functions below carry the C names and only marshal arguments; every
+step of the hot path runs in the library's CUDA kernels.  PyTorch supplies
+the device workspace (one ``torch.empty`` of the size the library asks for)
+and the CUDA stream.  There is no CPU fallback: if the library is missing
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+# Revision tag of the interaction kernel; DRAM-traffic figures captured with
+# ncu are only quoted while they were taken on this revision.
+KERNEL_REV = "interact-v1"
+
+SPH_OK = 0
+SPH_INTERACT_COUNTS = 1
+SPH_ARRAY_KEY, SPH_ARRAY_CELL_OFF, SPH_ARRAY_ACE, SPH_ARRAY_NNB = 0, 1, 2, 3
+SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT = 4, 5, 6
+ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
+          -4: "SPH_ERR_TIMEOUT", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_CAPACITY",
+          -7: "SPH_ERR_STATE"}
+
+EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells",
+            "sph_interact", "sph_predict", "sph_correct", "sph_step",
+            "sph_rollout", "sph_download", "sph_array_bytes", "sph_read_array",
+            "sph_neighbour_counts_fp64", "sph_diagnostics", "sph_check",
+            "sph_kernels_per_step", "sph_last_error", "sph_destroy",
+            "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs"]
+
+
+class SphParams(C.Structure):
+    _fields_ = [("dp", C.c_double), ("h", C.c_double), ("rho0", C.c_double),
+                ("gamma", C.c_double), ("c0", C.c_double), ("alpha", C.c_double),
+                ("eta2_coef", C.c_double), ("gravity", C.c_double * 3),
+                ("cfl", C.c_double), ("mass", C.c_double),
+                ("dmin", C.c_double * 3), ("dmax", C.c_double * 3),
+                ("n_bound", C.c_uint32), ("reserved", C.c_uint32),
+                ("dt_fixed", C.c_double)]
+
+
+class SphSizes(C.Structure):
+    _fields_ = [("workspace_bytes", C.c_uint64), ("ncells", C.c_uint64),
+                ("ncx", C.c_uint32), ("ncy", C.c_uint32), ("ncz", C.c_uint32),
+                ("sort_passes", C.c_uint32)]
+
+
+class SphDiag(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
+                ("momentum", C.c_double * 3), ("kinetic", C.c_double),
+                ("potential", C.c_double), ("internal", C.c_double),
+                ("step", C.c_uint64), ("pairs_total", C.c_uint64),
+                ("candidates_total", C.c_uint64), ("pairs_last", C.c_uint64),
+                ("candidates_last", C.c_uint64), ("pairs_fluid_last", C.c_uint64),
+                ("pairs_boundary_last", C.c_uint64), ("pairs_fluid_total", C.c_uint64),
+                ("pairs_boundary_total", C.c_uint64), ("n_out", C.c_uint32),
+                ("status", C.c_uint32), ("amax", C.c_float), ("cmax", C.c_float),
+                ("mumax", C.c_float)]
+
+    def as_dict(self):
+        return dict(t=self.t, dt=self.dt, mass=self.mass,
+                    momentum=list(self.momentum), kinetic=self.kinetic,
+                    potential=self.potential, internal=self.internal,
+                    step=int(self.step), pairs_total=int(self.pairs_total),
+                    candidates_total=int(self.candidates_total),
+                    pairs_last=int(self.pairs_last),
+                    candidates_last=int(self.candidates_last),
+                    pairs_fluid_last=int(self.pairs_fluid_last),
+                    pairs_boundary_last=int(self.pairs_boundary_last),
+                    pairs_fluid_total=int(self.pairs_fluid_total),
+                    pairs_boundary_total=int(self.pairs_boundary_total),
+                    n_out=int(self.n_out), status=int(self.status),
+                    amax=self.amax, cmax=self.cmax, mumax=self.mumax)
+
+
+SNAPSHOT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_double)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build: bool = False):
+    """Load libsph.so (building it first if asked).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsph.so not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+    P = C.POINTER(SphParams)
+    L.sph_query_sizes.argtypes = [P, u32, C.POINTER(SphSizes)]
+    L.sph_init.argtypes = [P, u32, vp, u64, vp, C.POINTER(vp)]
+    L.sph_upload.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_build_cells.argtypes = [vp]
+    L.sph_interact.argtypes = [vp, u32]
+    L.sph_predict.argtypes = [vp]
+    L.sph_correct.argtypes = [vp]
+    L.sph_step.argtypes = [vp, u32]
+    L.sph_rollout.argtypes = [vp, u32, u32, SNAPSHOT_FN, vp]
+    L.sph_download.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_array_bytes.argtypes = [vp, i32]
+    L.sph_array_bytes.restype = u64
+    L.sph_read_array.argtypes = [vp, i32, vp, u64]
+    L.sph_neighbour_counts_fp64.argtypes = [vp]
+    L.sph_diagnostics.argtypes = [vp, C.POINTER(SphDiag)]
+    L.sph_check.argtypes = [vp]
+    L.sph_kernels_per_step.argtypes = [vp]
+    L.sph_kernels_per_step.restype = u32
+    L.sph_last_error.argtypes = [vp]
+    L.sph_last_error.restype = C.c_char_p
+    L.sph_destroy.argtypes = [vp]
+    L.sph_destroy.restype = None
+    L.sph_radix_sort_scratch_bytes.argtypes = [u32]
+    L.sph_radix_sort_scratch_bytes.restype = u64
+    L.sph_radix_sort_pairs.argtypes = [vp, vp, vp, vp, u32, u32, vp, u64, vp]
+    _lib = L
+    return L
+
+
+class SphError(RuntimeError):
+    pass
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != SPH_OK:
+        msg = ""
+        if ctx:
+            m = lib().sph_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise SphError(f"{what}: {ERRORS.get(rc, rc)} {msg}".strip())
+
+
+def make_params(p: dict, dt_fixed: float = 0.0) -> SphParams:
+    s = SphParams()
+    s.dp, s.h, s.rho0, s.gamma = p["dp"], p["h"], p["rho0"], p["gamma"]
+    s.c0, s.alpha, s.eta2_coef = p["c0"], p["alpha"], p["eta2_coef"]
+    for a in range(3):
+        s.gravity[a] = p["gravity"][a]
+        s.dmin[a] = p["dmin"][a]
+        s.dmax[a] = p["dmax"][a]
+    s.cfl, s.mass = p["cfl"], p["mass"]
+    s.n_bound = int(p["n_bound"])
+    s.dt_fixed = float(p.get("dt_fixed", dt_fixed))
+    return s
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()      # torch tensor (host pinned or device)
+
+
+# --- C-named wrappers -------------------------------------------------------
+
+def sph_query_sizes(params: SphParams, n: int) -> SphSizes:
+    out = SphSizes()
+    _check(lib().sph_query_sizes(C.byref(params), n, C.byref(out)), what="sph_query_sizes")
+    return out
+
+
+def sph_init(params: SphParams, n: int, d_workspace: int, nbytes: int, stream: int):
+    ctx = C.c_void_p()
+    _check(lib().sph_init(C.byref(params), n, d_workspace, nbytes, stream, C.byref(ctx)),
+           what="sph_init")
+    return ctx
+
+
+def sph_upload(ctx, pos, vel, rho, ids):
+    _check(lib().sph_upload(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx, "sph_upload")
+
+
+def sph_build_cells(ctx):
+    _check(lib().sph_build_cells(ctx), ctx, "sph_build_cells")
+
+
+def sph_interact(ctx, flags: int = 0):
+    _check(lib().sph_interact(ctx, flags), ctx, "sph_interact")
+
+
+def sph_predict(ctx):
+    _check(lib().sph_predict(ctx), ctx, "sph_predict")
+
+
+def sph_correct(ctx):
+    _check(lib().sph_correct(ctx), ctx, "sph_correct")
+
+
+def sph_step(ctx, nsteps: int = 1):
+    _check(lib().sph_step(ctx, nsteps), ctx, "sph_step")
+
+
+def sph_rollout(ctx, nsteps: int, save_every: int = 0, cb=None):
+    """cb(step, t) -> truthy to stop; may call sph_download."""
+    fn = SNAPSHOT_FN(0) if cb is None else SNAPSHOT_FN(lambda u, s, t: int(bool(cb(s, t))))
+    _check(lib().sph_rollout(ctx, nsteps, save_every, fn, None), ctx, "sph_rollout")
+
+
+def sph_download(ctx, pos=None, vel=None, rho=None, ids=None):
+    _check(lib().sph_download(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx,
+           "sph_download")
+
+
+def sph_read_array(ctx, which: int, out: np.ndarray):
+    nbytes = lib().sph_array_bytes(ctx, which)
+    assert out.nbytes == nbytes, (out.nbytes, nbytes)
+    _check(lib().sph_read_array(ctx, which, _ptr(out), nbytes), ctx, "sph_read_array")
+    return out
+
+
+def sph_neighbour_counts_fp64(ctx):
+    _check(lib().sph_neighbour_counts_fp64(ctx), ctx, "sph_neighbour_counts_fp64")
+
+
+def sph_diagnostics(ctx) -> dict:
+    d = SphDiag()
+    _check(lib().sph_diagnostics(ctx, C.byref(d)), ctx, "sph_diagnostics")
+    return d.as_dict()
+
+
+def sph_check(ctx):
+    _check(lib().sph_check(ctx), ctx, "sph_check")
+
+
+def sph_kernels_per_step(ctx) -> int:
+    return int(lib().sph_kernels_per_step(ctx))
+
+
+def sph_destroy(ctx):
+    lib().sph_destroy(ctx)
+
+
+def sph_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, scratch,
+                         scratch_bytes, stream):
+    _check(lib().sph_radix_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                      _ptr(vals_out), n, key_bits, _ptr(scratch),
+                                      scratch_bytes, stream), what="sph_radix_sort_pairs")
+
+
+# --- convenience object ------------------------------------------------------
+
+class Simulation:
+    """One simulation on one GPU: workspace, stream and context.
+
+    ``params`` is the scalar dict of :meth:`cases.Case.params`.  Arrays go in
+    and out in the library's (cell, id)-sorted order; ``ids`` says which
+    particle is which.
+    """
+
+    def __init__(self, params: dict, n: int, device: int = 0, stream=None,
+                 dt_fixed: float = 0.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the SPH hot path needs a CUDA GPU")
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.n = int(n)
+        self.params = dict(params)
+        self.P = make_params(params, dt_fixed)
+        self.sizes = sph_query_sizes(self.P, self.n)
+        self.workspace = torch.empty(int(self.sizes.workspace_bytes), dtype=torch.uint8,
+                                     device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.ctx = sph_init(self.P, self.n, self.workspace.data_ptr(),
+                            int(self.sizes.workspace_bytes), self.stream.cuda_stream)
+
+    @classmethod
+    def from_case(cls, case, **kw):
+        sim = cls(case.params(), case.n, **kw)
+        sim.upload(case.pos, case.vel, case.rho, case.ids)
+        return sim
+
+    def upload(self, pos, vel, rho, ids):
+        pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
+        vel = np.ascontiguousarray(vel, dtype=np.float32) if isinstance(vel, np.ndarray) else vel
+        rho = np.ascontiguousarray(rho, dtype=np.float32) if isinstance(rho, np.ndarray) else rho
+        ids = np.ascontiguousarray(ids, dtype=np.uint32) if isinstance(ids, np.ndarray) else ids
+        sph_upload(self.ctx, pos, vel, rho, ids)
+
+    def build_cells(self):
+        sph_build_cells(self.ctx)
+
+    def interact(self, counts=False):
+        sph_interact(self.ctx, SPH_INTERACT_COUNTS if counts else 0)
+
+    def predict(self):
+        sph_predict(self.ctx)
+
+    def correct(self):
+        sph_correct(self.ctx)
+
+    def step(self, nsteps=1):
+        sph_step(self.ctx, nsteps)
+
+    def rollout(self, nsteps, save_every=0, cb=None):
+        sph_rollout(self.ctx, nsteps, save_every, cb)
+
+    def neighbour_counts_fp64(self):
+        sph_neighbour_counts_fp64(self.ctx)
+        return self.read(SPH_ARRAY_NNB64)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def download(self):
+        n = self.n
+        pos = np.empty((n, 3), np.float64)
+        vel = np.empty((n, 3), np.float32)
+        rho = np.empty(n, np.float32)
+        ids = np.empty(n, np.uint32)
+        sph_download(self.ctx, pos, vel, rho, ids)
+        return dict(pos=pos, vel=vel, rho=rho, ids=ids)
+
+    def read(self, which):
+        n = self.n
+        shapes = {SPH_ARRAY_KEY: ((n,), np.uint32),
+                  SPH_ARRAY_CELL_OFF: ((int(self.sizes.ncells) + 2,), np.uint32),
+                  SPH_ARRAY_ACE: ((n, 4), np.float32), SPH_ARRAY_NNB: ((n,), np.uint32),
+                  SPH_ARRAY_NNB64: ((n,), np.uint32), SPH_ARRAY_POSC: ((n, 4), np.float32),
+                  SPH_ARRAY_DT: ((1,), np.float64)}
+        shape, dt = shapes[which]
+        return sph_read_array(self.ctx, which, np.empty(shape, dt))
+
+    def diagnostics(self):
+        return sph_diagnostics(self.ctx)
+
+    def check(self):
+        sph_check(self.ctx)
+
+    def kernels_per_step(self):
+        return sph_kernels_per_step(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.synchronize()
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""The C ABI library builds, loads and exports what include/sph.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import __graft_entry__  # noqa: F401  (puts the repo root on sys.path)
+from paper_1210_1017_gb300 import _build, cases
+from paper_1210_1017_gb300 import sph as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sph.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return S.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", src)) - {"sph_snapshot_fn"})
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (sph_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+    assert sorted(S.EXPORTED) == names
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(sph_params),'
+                    ' sizeof(sph_sizes), sizeof(sph_diag), offsetof(sph_params, dt_fixed),'
+                    ' offsetof(sph_diag, n_out));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(S.SphParams), C.sizeof(S.SphSizes), C.sizeof(S.SphDiag),
+            S.SphParams.dt_fixed.offset, S.SphDiag.n_out.offset]
+    assert got == want
+
+
+def test_query_sizes_without_gpu(lib):
+    case = cases.c1_dam_break()
+    P = S.make_params(case.params())
+    sz = S.sph_query_sizes(P, case.n)
+    ncx = -(-(case.dmax[0] - case.dmin[0]) // (2 * case.h))
+    assert sz.ncx == int(ncx)
+    assert sz.ncells == sz.ncx * sz.ncy * sz.ncz
+    assert sz.sort_passes == (int(sz.ncells).bit_length() + 7) // 8
+    # about 260 bytes per particle plus the cell arrays
+    assert 200 * case.n < sz.workspace_bytes < 400 * case.n + 64 * sz.ncells + (1 << 20)
+
+
+def test_invalid_arguments_are_rejected(lib):
+    case = cases.c1_dam_break()
+    p = case.params()
+    bad = dict(p, gamma=5.0)
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(S.make_params(bad), case.n)
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(S.make_params(p), 0)
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(S.make_params(p), 1 << 26)
+    flat = dict(p, dmax=(p["dmin"][0], p["dmax"][1], p["dmax"][2]))
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(S.make_params(flat), case.n)
+    # init refuses a misaligned or short workspace before touching the GPU
+    ctx = C.c_void_p()
+    P = S.make_params(p)
+    assert lib.sph_init(C.byref(P), case.n, 0x1001, 1 << 30, None, C.byref(ctx)) == -3
+    assert lib.sph_init(C.byref(P), case.n, 0x1000, 16, None, C.byref(ctx)) == -3
+    assert lib.sph_radix_sort_pairs(None, None, None, None, 8, 8, None, 0, None) == -1
+
+
+def test_sort_scratch_size_grows_with_n(lib):
+    a = lib.sph_radix_sort_scratch_bytes(1000)
+    b = lib.sph_radix_sort_scratch_bytes(1000000)
+    assert 8000 <= a < b
+    assert b >= 8 * 1000000
