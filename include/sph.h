@@ -141,7 +141,9 @@ int sph_build_cells(sph_ctx *ctx);
  * and Eq. 9 (acceleration, gravity included, fluid particles; boundary
  * particles get gravity only since Sec. 2.3 never moves them), in FP32 on
  * cell-relative coordinates, plus the CFL reductions of Sec. 3.3 (sets the device-side
- * step size unless params.dt_fixed > 0).  Requires built cells.  Async.
+ * step size unless params.dt_fixed > 0, or a predictor step is pending:
+ * the half-step evaluation keeps the step size of the step's first
+ * evaluation).  Requires built cells.  Async.
  * flags: SPH_INTERACT_COUNTS also stores each particle's neighbour count
  * (readable as SPH_ARRAY_NNB). */
 #define SPH_INTERACT_COUNTS 1u

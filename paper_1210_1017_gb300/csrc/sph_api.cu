@@ -240,6 +240,10 @@ Dev make_dev(const sph_params* p, uint32_t n, const uint32_t nc[3], uint64_t nce
     d.inv_rho0 = (float)(1.0 / p->rho0);
     d.B = (float)(p->c0 * p->c0 * p->rho0 / p->gamma);
     d.mass = (float)p->mass;
+    d.mass_d = p->mass;
+    d.rho0_d = p->rho0;
+    d.B_d = p->c0 * p->c0 * p->rho0 / p->gamma;
+    for (int k = 0; k < 3; ++k) d.g_d[k] = p->gravity[k];
     d.gx = (float)p->gravity[0];
     d.gy = (float)p->gravity[1];
     d.gz = (float)p->gravity[2];
@@ -476,7 +480,9 @@ int sph_build_cells(sph_ctx* c) {
 int sph_interact(sph_ctx* c, uint32_t flags) {
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
-    enqueue_interact(c, (flags & SPH_INTERACT_COUNTS) != 0, true);
+    // at the half step (predictor pending) the step size stays the one set
+    // by the evaluation at the start of the step, as in sph_step
+    enqueue_interact(c, (flags & SPH_INTERACT_COUNTS) != 0, c->pre_state != 2);
     return post_launch(c, "interact");
 }
 

@@ -20,6 +20,8 @@ struct Dev {
     double cs;             // 2h
     double r2max_d;        // (2h)^2 rounded once (FP64 neighbour predicate)
     double h_d, cfl, dt_fixed;
+    double mass_d, rho0_d, B_d;      // FP64 copies for the conservation sums
+    double g_d[3];
     int ncx, ncy, ncz;
     uint32_t ncells;
     uint32_t n;

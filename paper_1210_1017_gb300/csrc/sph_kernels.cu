@@ -610,9 +610,9 @@ __global__ void __launch_bounds__(256) k_diag_part(const Dev d, const double* __
     __shared__ double s[256][8];
     const uint32_t n_in = off[d.ncells];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const double m = d.mass;
-    const double rho0 = d.rho0;
-    const double B = d.B;
+    const double m = d.mass_d;
+    const double rho0 = d.rho0_d;
+    const double B = d.B_d;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
         if (k >= n_in) {
             acc[7] += 1.0;
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256) k_diag_part(const Dev d, const double* __
             acc[2] += m * v.y;
             acc[3] += m * v.z;
             acc[4] += 0.5 * m * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-            acc[5] -= m * ((double)d.gx * x[k] + (double)d.gy * y[k] + (double)d.gz * z[k]);
+            acc[5] -= m * (d.g_d[0] * x[k] + d.g_d[1] * y[k] + d.g_d[2] * z[k]);
         }
     }
     for (int q = 0; q < 8; ++q) s[threadIdx.x][q] = acc[q];

@@ -223,6 +223,8 @@ def test_predictor_and_corrector_match_oracle():
     s1 = sim.download()
     oh = O.predict(o0.copy(), ace0[:, :3], ace0[:, 3], dt)
     disp = np.abs(oh.pos() - o0.pos()).max()
+    print("predict errors", np.abs(s1["pos"] - oh.pos()).max() / disp,
+          np.abs(s1["vel"] - oh.vel()).max(), np.abs(s1["rho"] - oh.rho).max())
     assert np.abs(s1["pos"] - oh.pos()).max() <= 1e-6 * disp + 1e-15
     assert np.abs(s1["vel"] - oh.vel()).max() <= 2e-7 * (np.abs(oh.vel()).max() + 1)
     assert np.abs(s1["rho"] - oh.rho).max() <= 1e-7 * oh.rho.max()
@@ -236,8 +238,11 @@ def test_predictor_and_corrector_match_oracle():
     pre = oracle.State(s0["pos"][idx], s0["vel"][idx], s0["rho"][idx], s0["ids"][idx])
     sim.correct()
     s2 = sim.download()
+    assert float(sim.read(S.SPH_ARRAY_DT)[0]) == dt
     on = O.correct(pre, oh2.copy(), ace1[:, :3], ace1[:, 3], dt)
     disp = np.abs(on.pos() - pre.pos()).max()
+    print("correct errors", np.abs(s2["pos"] - on.pos()).max() / disp,
+          np.abs(s2["vel"] - on.vel()).max(), np.abs(s2["rho"] - on.rho).max())
     assert np.abs(s2["pos"] - on.pos()).max() <= 1e-6 * disp + 1e-15
     assert np.abs(s2["vel"] - on.vel()).max() <= 2e-7 * (np.abs(on.vel()).max() + 1)
     assert np.abs(s2["rho"] - on.rho).max() <= 2e-7 * on.rho.max()
