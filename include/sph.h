@@ -48,6 +48,7 @@ extern "C" {
                                       id tie-break handles (order within it
                                       then follows the sort's stable order) */
 #define SPH_ERR_STATE         -7   /* call out of order (e.g. no state yet) */
+#define SPH_ERR_TOO_LARGE     -8   /* n above the fixed maximum of a call    */
 
 /* Bits of the device status word. */
 #define SPH_STATUS_TIMEOUT    1u
@@ -231,6 +232,30 @@ int sph_radix_sort_pairs(const uint32_t *d_keys_in, const uint32_t *d_vals_in,
                          uint32_t *d_keys_out, uint32_t *d_vals_out,
                          uint32_t n, uint32_t key_bits, void *d_scratch,
                          uint64_t scratch_bytes, void *stream);
+
+/* The same stable radix sort without caller scratch.  The paper has no
+ * counterpart: this is for callers that cannot give the library device
+ * memory -- C code with no device allocator of its own, a process whose
+ * device memory belongs to another allocator's pool, or a latency-critical
+ * loop that must not call cudaMalloc/cudaFree (they can synchronise the
+ * device).  The scratch lives in a fixed array inside libsph.so, about
+ * 9 MB per device, held until the process exits; nothing is allocated per
+ * call.  Limits and behaviour:
+ *   - n <= SPH_RADIX_SORT_STATIC_MAX_N, else SPH_ERR_TOO_LARGE (no work done)
+ *   - arrays as for sph_radix_sort_pairs (device, n uint32 each, outputs not
+ *     aliasing inputs, d_vals_in may be NULL for values 0..n-1)
+ *   - the first call with a given device current looks up the array's
+ *     device address (a CUDA runtime query): make that first call before
+ *     any stream capture
+ *   - all calls on one device share the array and it keeps the last call's
+ *     contents (each call clears what must start at zero); calls that overlap
+ *     on the GPU race, so serialise them (e.g. one stream)
+ * Async on stream. */
+#define SPH_RADIX_SORT_STATIC_MAX_N (1u << 20)
+int sph_radix_sort_pairs_static(const uint32_t *d_keys_in,
+                                const uint32_t *d_vals_in,
+                                uint32_t *d_keys_out, uint32_t *d_vals_out,
+                                uint32_t n, uint32_t key_bits, void *stream);
 
 #ifdef __cplusplus
 }

@@ -25,14 +25,16 @@ SPH_ARRAY_KEY, SPH_ARRAY_CELL_OFF, SPH_ARRAY_ACE, SPH_ARRAY_NNB = 0, 1, 2, 3
 SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT = 4, 5, 6
 ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
           -4: "SPH_ERR_TIMEOUT", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_CAPACITY",
-          -7: "SPH_ERR_STATE"}
+          -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE"}
+SPH_RADIX_SORT_STATIC_MAX_N = 1 << 20
 
 EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells",
             "sph_interact", "sph_predict", "sph_correct", "sph_step",
             "sph_rollout", "sph_download", "sph_array_bytes", "sph_read_array",
             "sph_neighbour_counts_fp64", "sph_diagnostics", "sph_check",
             "sph_kernels_per_step", "sph_last_error", "sph_destroy",
-            "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs"]
+            "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
+            "sph_radix_sort_pairs_static"]
 
 
 class SphParams(C.Structure):
@@ -124,6 +126,7 @@ def lib(build: bool = False):
     L.sph_radix_sort_scratch_bytes.argtypes = [u32]
     L.sph_radix_sort_scratch_bytes.restype = u64
     L.sph_radix_sort_pairs.argtypes = [vp, vp, vp, vp, u32, u32, vp, u64, vp]
+    L.sph_radix_sort_pairs_static.argtypes = [vp, vp, vp, vp, u32, u32, vp]
     _lib = L
     return L
 
@@ -248,6 +251,13 @@ def sph_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, scra
     _check(lib().sph_radix_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
                                       _ptr(vals_out), n, key_bits, _ptr(scratch),
                                       scratch_bytes, stream), what="sph_radix_sort_pairs")
+
+
+def sph_radix_sort_pairs_static(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream):
+    """The sort with the library's fixed scratch (no caller memory)."""
+    _check(lib().sph_radix_sort_pairs_static(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                             _ptr(vals_out), n, key_bits, stream),
+           what="sph_radix_sort_pairs_static")
 
 
 # --- convenience object ------------------------------------------------------
