@@ -256,12 +256,12 @@ def run_ours(args):
     peak_tflops = SMS * FP32_LANES * 2 * MAX_CLOCK_GHZ / 1e3
     achieved = flop / t_int / 1e12
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "interaction_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
-        if tr.get("workload") == case.name and tr.get("kernel_rev") == S.KERNEL_REV:
-            traffic = tr.get("bytes_per_launch")
+        if tr.get("kernel_rev") == S.KERNEL_REV:
+            traffic = tr.get("bytes_per_launch", {}).get(case.name)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
                 "kernel": "k_interact", "ms_per_launch": round(t_int * 1e3, 4),

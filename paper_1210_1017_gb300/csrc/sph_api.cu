@@ -15,6 +15,7 @@ using namespace sph;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr uint32_t kMaxGridBlocks = 4096;   // partials of the persistent interaction
 
 // Bump allocator over the caller's workspace (base may be null when only
 // the size is wanted).
@@ -76,6 +77,7 @@ struct sph_ctx {
     int bits = 0, passes = 0;
     uint32_t tiles = 0, nparts = 0;
     uint64_t ncells = 0;
+    uint32_t ncx_ = 1;        // cells per row (set before carving)
     // state, double-buffered for the reorder gather
     double *x[2], *y[2], *z[2];
     float4* vr[2];
@@ -89,6 +91,8 @@ struct sph_ctx {
     float* stage_vr;         // 4n floats (velocity, then density)
     uint32_t *key[2], *val[2];
     uint32_t *cnt, *off, *bsum, *hist, *tilectr, *os_status, *nnb, *nnb64;
+    uint32_t *ucnt, *uoff, *ubsum;   // work units of the interaction
+    uint2* units;
     float4 *part_f, *lvl2_f;
     uint4* part_u;
     unsigned long long* lvl2_q;
@@ -191,7 +195,12 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, uint64_t ncells, int passes) {
     c->os_bytes = 4 * sizeof(uint32_t) + (size_t)passes * tiles * 256 * sizeof(uint32_t);
     c->tilectr = cv.take<uint32_t>(c->os_bytes / sizeof(uint32_t));
     c->os_status = c->tilectr ? c->tilectr + 4 : nullptr;
-    const uint32_t np = interact_blocks(n);
+    const uint32_t nrows = (uint32_t)(ncells / c->ncx_);
+    c->ucnt = cv.take<uint32_t>(nrows + 1);
+    c->uoff = cv.take<uint32_t>(nrows + 2);
+    c->ubsum = cv.take<uint32_t>(scan_bsum_count(nrows + 1));
+    c->units = cv.take<uint2>(max_units(n, nrows, c->ncx_));
+    const uint32_t np = kMaxGridBlocks;
     c->part_f = cv.take<float4>(np);
     c->part_u = cv.take<uint4>(np);
     c->lvl2_f = cv.take<float4>(kReduceBlocks);
@@ -265,6 +274,7 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
         src = 1 - src;
     }
     c->skey = src;
+    launch_units(c->d, c->off, c->ucnt, c->ubsum, c->uoff, c->units, st);
     ReorderArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.skey = c->key[src];
@@ -300,6 +310,9 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
 
 void enqueue_interact(sph_ctx* c, bool counts, bool set_dt) {
     InteractArgs ia;
+    ia.units = c->units;
+    ia.n_units = c->uoff + (c->ncells / c->ncx_);
+    ia.status = c->status;
     ia.posc = c->posc;
     ia.velrhop = c->vr[c->cur];
     ia.key = c->key[c->skey];
@@ -389,6 +402,7 @@ int sph_query_sizes(const sph_params* params, uint32_t n, sph_sizes* out) {
     int rc = validate(params, n, &ncells, nc, &why);
     if (rc) return rc;
     sph_ctx tmp;
+    tmp.ncx_ = nc[0];
     const int bits = bit_length(ncells);
     const int passes = (bits + 7) / 8;
     out->workspace_bytes = carve(&tmp, nullptr, n, ncells, passes);
@@ -417,15 +431,20 @@ int sph_init(const sph_params* params, uint32_t n, void* ws, uint64_t ws_bytes, 
     c->ncells = ncells;
     c->bits = bit_length(ncells);
     c->passes = (c->bits + 7) / 8;
+    c->ncx_ = nc[0];
     const size_t need = carve(c, ws, n, ncells, c->passes);
     if (ws_bytes < need) {
         delete c;
         return SPH_ERR_WORKSPACE;
     }
     c->tiles = os_tiles(n);
-    c->nparts = interact_blocks(n);
-    c->d = make_dev(params, n, nc, ncells);
     prepare_interact();
+    c->nparts = interact_grid();
+    if (c->nparts == 0 || c->nparts > kMaxGridBlocks) {
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    c->d = make_dev(params, n, nc, ncells);
     cudaStream_t st = c->st;
     cudaMemsetAsync(c->cnt, 0, (ncells + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(c->hist, 0, 4 * 256 * sizeof(uint32_t), st);
@@ -691,8 +710,9 @@ int sph_check(sph_ctx* c) {
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
-    // 2 x (interact + reduce) + predict + correct + 2 x (3 scan + passes + reorder)
-    return 2u * 2u + 2u + 2u * (3u + (uint32_t)c->passes + 1u);
+    // 2 x (interact + reduce) + predict + correct
+    // + 2 x (3 cell scan + passes + 5 unit list + reorder)
+    return 2u * 2u + 2u + 2u * (3u + (uint32_t)c->passes + 5u + 1u);
 }
 
 const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

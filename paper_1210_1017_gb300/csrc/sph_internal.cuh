@@ -41,6 +41,8 @@ void launch_keys(const Dev& d, const double* x, const double* y, const double* z
                  int passes, cudaStream_t st);
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st);
+// out[i] = in[0] + ... + in[i-1] for i = 0..m (m + 1 outputs); clears in[].
+void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st);
 uint32_t scan_bsum_count(uint64_t m);
 
 // Radix sort
@@ -75,7 +77,15 @@ struct ReorderArgs {
 };
 void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 
+// Interaction work unit: up to kUnit consecutive particles of one row of
+// cells spanning at most kSpan cells (uint2: first particle, end).
+constexpr int kUnit = 128;
+constexpr int kSpan = 32;
+
 struct InteractArgs {
+    const uint2* units;
+    const uint32_t* n_units;
+    uint32_t* status;
     const float4* posc;
     const float4* velrhop;
     const uint32_t* key;
@@ -83,12 +93,17 @@ struct InteractArgs {
     const uint32_t* off;
     float4* ace;
     uint32_t* nnb;        // may be null
-    float4* part_f;       // per block: max|a|^2, max c, max mu, 0
+    float4* part_f;       // per block (persistent grid): max|a|^2, max c, max mu, 0
     uint4* part_u;        // per block: fluid-i pairs, candidates, status bits,
                           // boundary-i pairs
 };
-uint32_t interact_blocks(uint32_t n);
-void prepare_interact();   // once per process: opt in to the list's shared memory
+uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t ncx);   // bound on units
+uint32_t interact_grid();   // blocks of the persistent interaction launch
+void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
+                  uint32_t* uoff, uint2* units, cudaStream_t st);
+// Once per context (current device): opt in to the shared memory and size
+// the persistent grid from the device's SM count and occupancy.
+void prepare_interact();
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
 
 struct ReduceArgs {

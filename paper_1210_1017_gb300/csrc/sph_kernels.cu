@@ -172,130 +172,351 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
 
 // ----------------------------------------------------------- interaction --
 
-constexpr int kIWarps = 4;          // warps per block
-constexpr int kCap = 96;            // neighbour-list slots per lane
+constexpr int kIWarps = kUnit / 32;   // warps per block (one work unit)
+constexpr int kCap = 96;              // neighbour-list slots per lane
+constexpr int kStage = 2048;          // staged candidates per unit
 constexpr uint32_t kIdxMask = (1u << 26) - 1;
+// dynamic shared memory: staged posc and velrhop (kStage float4 each), then
+// the per-lane lists (16-bit entries); the fallback path reuses the staging
+// area for 32-bit list entries
+constexpr size_t kInteractSmem =
+    (size_t)kStage * 2 * sizeof(float4) + (size_t)kIWarps * kCap * 32 * sizeof(uint16_t);
+static_assert((size_t)kIWarps * kCap * 32 * sizeof(uint32_t) <= (size_t)kStage * 2 * sizeof(float4),
+              "fallback lists must fit in the staging area");
+constexpr uint32_t kWaitLimit = 1u << 22;
 
-// Sec. 3.2.  Each warp owns 32 consecutive (sorted) particles i.  For the
-// lanes that share a row of cells (same cy, cz) it walks the 9 neighbouring
-// rows; in each row the cells [min cx - 1, max cx + 1] are contiguous in the
-// sorted arrays.  Phase 1 tests every candidate j (one load, broadcast to
-// all lanes) against each lane's particle and appends hits (|r_ij| < 2h) to
-// the lane's list in shared memory, tagged with the cell offset between i
-// and j.  Phase 2 walks the lists with all lanes busy and accumulates the
-// pair terms of Eqs. 7 and 9.  Distances use positions relative to each
-// particle's own cell origin plus whole-cell offsets, in FP32.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on bar.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t k = 0; k < kWaitLimit; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+struct PairAcc {
+    float ax, ay, az, dr, mu;
+    uint32_t np;
+};
+
+// Pair terms of Eqs. 7 and 9 for i (pi, vi) and j (pj, vj) at offset
+// (dx, dy, dz) = r_i - r_j.  MOM: evaluate the momentum terms (a warp-uniform
+// choice); only fluid particles keep them, since boundary particles never
+// move (Sec. 2.3).  The pair j = i (all offsets zero) contributes exactly
+// nothing, which lets lists be padded with it.
+template <bool MOM>
+__device__ __forceinline__ void pair_terms(const Dev& d, bool fluid, const float4& pi,
+                                           const float4& vi, float ci, float dx, float dy, float dz,
+                                           const float4& pj, const float4& vj, PairAcc& s) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // Wendland C2: grad_i W = F r_ij, F = -5 aD/h^2 (1 - q/2)^3
+    const float q = sqrt_approx(d2) * d.inv_h;
+    const float wq = fmaf(-0.5f, q, 1.0f);
+    const float F = d.fc * (wq * wq * wq);
+    const float dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = vi.z - vj.z;
+    const float vr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
+    s.dr = fmaf(vr, F, s.dr);                                      // Eq. 7
+    if (MOM) {
+        const float nu = d.h * vr * rcp_approx(d2 + d.eta2);       // Sec. 2.2
+        const float rrj = vj.w * d.inv_rho0;
+        const float cj = d.c0 * rrj * rrj * rrj;
+        const float visc = vr < 0.f ? -d.alpha * (ci + cj) * nu * rcp_approx(vi.w + vj.w) : 0.f;
+        const float f = fluid ? (pi.w + pj.w + visc) * F : 0.f;    // Eq. 9
+        s.ax = fmaf(-f, dx, s.ax);
+        s.ay = fmaf(-f, dy, s.ay);
+        s.az = fmaf(-f, dz, s.az);
+        s.mu = fmaxf(s.mu, fluid ? fabsf(nu) : 0.f);
+    }
+}
+
+// Sec. 3.2.  One block = one work unit: up to kUnit consecutive sorted
+// particles of one row of cells (same cy, cz) spanning at most kSpan cells
+// with no more than two empty cells in a row, so the candidates of all of
+// them lie in 9 contiguous, compact runs of the sorted arrays (the
+// neighbouring rows, cells [first cx - 1, last cx + 1]).  Those runs are copied to shared
+// memory with bulk asynchronous copies; their y, z are then shifted into the
+// frame of the unit's row, so a candidate's offset from particle i only
+// needs i's own cell offset in x.  Each warp then tests every candidate of
+// its lanes' cells (one broadcast shared-memory load, all lanes), appends
+// hits (|r_ij| < 2h) to per-lane lists, and evaluates the pair terms from
+// the lists with all lanes busy.  Positions are relative to the particles'
+// own cell origins (FP32), plus whole-cell offsets.  A unit whose runs do
+// not fit the staging area reads its candidates from global memory instead.
 template <bool COUNTS>
-__global__ void __launch_bounds__(kIWarps * 32) k_interact(const Dev d, const InteractArgs a) {
-    extern __shared__ uint32_t s_dyn[];
+__global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const InteractArgs a) {
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    float4* s_p = reinterpret_cast<float4*>(s_raw);
+    float4* s_v = s_p + kStage;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_rs[9], s_rb[9], s_len[9], s_base[10];
+    __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
+    __shared__ int s_ok[9];
+    __shared__ int s_mode;
     __shared__ float s_rf[kIWarps][3];
     __shared__ uint32_t s_ru[kIWarps][4];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t* lst = s_dyn + w * (kCap * 32);
-    const uint32_t n_in = a.off[d.ncells];
-    const uint32_t i = (blockIdx.x * kIWarps + w) * 32 + lane;
-    const bool valid = i < n_in;
 
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    const uint32_t nunits = *a.n_units;
+    uint32_t phase = 0;
+    // CFL terms and counters over all units of this block
+    float t_am = 0.f, t_cm = 0.f, t_mm = 0.f;
+    uint32_t t_np = 0, t_nb = 0, t_nc = 0, t_bad = 0;
+    for (uint32_t ui = blockIdx.x; ui < nunits; ui += gridDim.x) {
+    const uint2 unit = a.units[ui];
+    const uint32_t i0 = unit.x, i1 = unit.y;
+    const uint32_t key0 = __ldg(a.key + i0);
+    const uint32_t row = key0 / (uint32_t)d.ncx;
+    const uint32_t rowbase = row * (uint32_t)d.ncx;
+    const int cy = (int)(row % (uint32_t)d.ncy), cz = (int)(row / (uint32_t)d.ncy);
+    const int xb = (int)(key0 - rowbase);
+    const int xe = (int)(__ldg(a.key + i1 - 1) - rowbase);
+    const int ulo = xb > 0 ? xb - 1 : 0;
+    const int uhi = xe + 1 < d.ncx ? xe + 1 : d.ncx - 1;
+    const int nce = uhi - ulo + 2;                 // offsets per neighbour row
+    if (tid < 9) {
+        const int yy = cy + tid % 3 - 1, zz = cz + tid / 3 - 1;
+        const bool ok = yy >= 0 && yy < d.ncy && zz >= 0 && zz < d.ncz;
+        s_ok[tid] = ok;
+        s_rb[tid] = ok ? (uint32_t)d.ncx * ((uint32_t)yy + (uint32_t)d.ncy * (uint32_t)zz) : 0u;
+    }
+    __syncthreads();
+    for (int q = tid; q < 9 * nce; q += kIWarps * 32) {
+        const int r = q / nce, c = q - r * nce;
+        s_off[r][c] = s_ok[r] ? __ldg(a.off + s_rb[r] + ulo + c) : 0u;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int r = 0; r < 9; ++r) {
+            s_base[r] = acc;
+            s_rs[r] = s_off[r][0];
+            s_len[r] = s_off[r][nce - 1] - s_off[r][0];
+            acc += s_len[r];
+        }
+        s_base[9] = acc;
+        const int mode = acc <= (uint32_t)kStage;
+        s_mode = mode;
+        if (mode) {
+            mbar_expect_tx(&s_bar, acc * 2u * (uint32_t)sizeof(float4));
+            for (int r = 0; r < 9; ++r) {
+                if (s_len[r] == 0) continue;
+                const uint32_t bytes = s_len[r] * (uint32_t)sizeof(float4);
+                bulk_g2s(s_p + s_base[r], a.posc + s_rs[r], bytes, &s_bar);
+                bulk_g2s(s_v + s_base[r], a.velrhop + s_rs[r], bytes, &s_bar);
+            }
+        }
+    }
+    // own particle, while the copies are in flight
+    const uint32_t i = i0 + tid;
+    const bool valid = i < i1;
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = make_float4(0.f, 0.f, 0.f, 1.f);
-    int cx = 0, cy = 0, cz = 0;
+    int cx = 0;
     bool fluid = false;
     if (valid) {
         pi = a.posc[i];
         vi = a.velrhop[i];
-        const uint32_t k = a.key[i];
-        cx = (int)(k % (uint32_t)d.ncx);
-        const uint32_t t = k / (uint32_t)d.ncx;
-        cy = (int)(t % (uint32_t)d.ncy);
-        cz = (int)(t / (uint32_t)d.ncy);
+        cx = (int)(__ldg(a.key + i) - rowbase);
         fluid = a.id[i] >= d.n_bound;
     }
     const float rri = vi.w * d.inv_rho0;
     const float ci = d.c0 * rri * rri * rri;
-    float ax = 0.f, ay = 0.f, az = 0.f, dr = 0.f, mu = 0.f;
-    uint32_t cnt = 0, npairs = 0, nbpairs = 0, ncand = 0;
-
-    auto flush = [&]() {
-        const uint32_t mx = __reduce_max_sync(kFull, cnt);
-        for (uint32_t t = 0; t < mx; ++t) {
-            if (t < cnt) {
-                const uint32_t e = lst[t * 32 + lane];
-                const uint32_t j = e & kIdxMask;
-                const float ox = (float)((int)((e >> 26) & 3u) - 1);
-                const float oy = (float)((int)((e >> 28) & 3u) - 1);
-                const float oz = (float)((int)(e >> 30) - 1);
-                const float4 pj = __ldg(a.posc + j);
-                const float4 vj = __ldg(a.velrhop + j);
-                const float dx = fmaf(ox, d.csf, pi.x) - pj.x;
-                const float dy = fmaf(oy, d.csf, pi.y) - pj.y;
-                const float dz = fmaf(oz, d.csf, pi.z) - pj.z;
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                // Wendland C2: grad_i W = F r_ij, F = -5 aD/h^2 (1 - q/2)^3
-                const float q = sqrt_approx(d2) * d.inv_h;
-                const float wq = fmaf(-0.5f, q, 1.0f);
-                const float F = d.fc * (wq * wq * wq);
-                const float dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = vi.z - vj.z;
-                const float vr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
-                dr = fmaf(vr, F, dr);                                  // Eq. 7
-                if (fluid) {
-                    // boundary particles never move (Sec. 2.3): their
-                    // acceleration is not needed
-                    const float nu = d.h * vr * rcp_approx(d2 + d.eta2);   // Sec. 2.2
-                    const float rrj = vj.w * d.inv_rho0;
-                    const float cj = d.c0 * rrj * rrj * rrj;
-                    const float visc =
-                        vr < 0.f ? -d.alpha * (ci + cj) * nu * rcp_approx(vi.w + vj.w) : 0.f;
-                    const float s = (pi.w + pj.w + visc) * F;              // Eq. 9
-                    ax = fmaf(-s, dx, ax);
-                    ay = fmaf(-s, dy, ay);
-                    az = fmaf(-s, dz, az);
-                    mu = fmaxf(mu, fabsf(nu));
-                    ++npairs;
-                } else {
-                    ++nbpairs;
+    PairAcc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    uint32_t ncand = 0;
+    __syncthreads();
+    const bool staged = s_mode != 0;
+    bool failed = false;
+    if (staged) {
+        const bool got = mbar_wait_bounded(&s_bar, phase);
+        failed = __syncthreads_or(!got) != 0;
+        if (failed) {
+            if (tid == 0) atomicOr(a.status, kStatusTimeout);
+            mbar_wait_bounded(&s_bar, phase);   // let copies in flight land first
+            break;
+        } else {
+            phase ^= 1u;
+            // shift the staged y, z into the frame of this unit's row
+            for (int r = 0; r < 9; ++r) {
+                const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
+                for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += kIWarps * 32) {
+                    s_p[k].y += oy;
+                    s_p[k].z += oz;
                 }
             }
+            __syncthreads();
         }
-        cnt = 0;
-    };
+    }
 
-    uint32_t todo = __ballot_sync(kFull, valid);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int myrow = cy + d.ncy * cz;
-        const int row = __shfl_sync(kFull, myrow, leader);
-        const bool inrow = valid && myrow == row;
-        todo &= ~__ballot_sync(kFull, inrow);
-        const int xmin = __reduce_min_sync(kFull, inrow ? cx : 0x7fffffff);
-        const int xmax = __reduce_max_sync(kFull, inrow ? cx : -1);
-        const int rcy = row % d.ncy, rcz = row / d.ncy;
-        const int xlo = xmin > 0 ? xmin - 1 : 0;
-        const int xhi = xmax + 1 < d.ncx ? xmax + 1 : d.ncx - 1;
-        for (int zz = rcz - 1; zz <= rcz + 1; ++zz) {
-            if (zz < 0 || zz >= d.ncz) continue;
-            for (int yy = rcy - 1; yy <= rcy + 1; ++yy) {
-                if (yy < 0 || yy >= d.ncy) continue;
-                const uint32_t rbase = (uint32_t)d.ncx * ((uint32_t)yy + (uint32_t)d.ncy * zz);
-                const float qy = fmaf((float)(cy - yy), d.csf, pi.y);
-                const float qz = fmaf((float)(cz - zz), d.csf, pi.z);
-                const uint32_t code_yz =
-                    ((uint32_t)(cy - yy + 1) << 28) | ((uint32_t)(cz - zz + 1) << 30);
+    const uint32_t act = __ballot_sync(kFull, valid);
+    if (act && !failed) {
+        const int wxmin = __reduce_min_sync(kFull, valid ? cx : 0x7fffffff);
+        const int wxmax = __reduce_max_sync(kFull, valid ? cx : -1);
+        const int xlo = wxmin > 0 ? wxmin - 1 : 0;
+        const int xhi = wxmax + 1 < d.ncx ? wxmax + 1 : d.ncx - 1;
+        uint32_t cnt = 0;
+        if (staged) {
+            uint16_t* lst = reinterpret_cast<uint16_t*>(s_v + kStage) + w * (kCap * 32) + lane;
+            const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
+            const uint32_t selfe = self | (1u << 14);      // the pair (i, i), x offset 0
+            const bool anyfluid = __any_sync(kFull, fluid);
+            // pair phase: two list entries per iteration, short lists padded
+            // with the zero-contribution pair (i, i)
+            auto flush = [&]() {
+                const uint32_t mx = __reduce_max_sync(kFull, cnt);
+                for (uint32_t t = 0; t < mx; t += 2) {
+                    const uint32_t e0 = t < cnt ? lst[t * 32] : selfe;
+                    const uint32_t e1 = t + 1 < cnt ? lst[(t + 1) * 32] : selfe;
+                    const uint32_t j0 = e0 & 0x3fffu, j1 = e1 & 0x3fffu;
+                    const float ox0 = (float)((int)(e0 >> 14) - 1);
+                    const float ox1 = (float)((int)(e1 >> 14) - 1);
+                    const float4 p0 = s_p[j0], v0 = s_v[j0];
+                    const float4 p1 = s_p[j1], v1 = s_v[j1];
+                    if (anyfluid) {
+                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
+                                         pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
+                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
+                                         pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
+                    } else {
+                        pair_terms<false>(d, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
+                                          pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
+                        pair_terms<false>(d, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
+                                          pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
+                    }
+                }
+                acc.np += cnt;
+                cnt = 0;
+            };
+            // candidate test: every candidate of the warp's cells against
+            // every lane (broadcast loads); the pair (i, i) is kept and its
+            // count removed at the end
+            for (int r = 0; r < 9; ++r) {
+                if (!s_ok[r]) continue;
+                const uint32_t rs = s_rs[r], sb = s_base[r];
                 for (int xx = xlo; xx <= xhi; ++xx) {
-                    const uint32_t s = __ldg(a.off + rbase + xx);
-                    const uint32_t e = __ldg(a.off + rbase + xx + 1);
-                    const bool adj = inrow && cx - xx <= 1 && xx - cx <= 1;
-                    if (adj) ncand += e - s;
-                    if (s == e) continue;
-                    const float qx = fmaf((float)(cx - xx), d.csf, pi.x);
-                    const uint32_t code = code_yz | ((uint32_t)(cx - xx + 1) << 26);
-                    for (uint32_t c0 = s; c0 < e; c0 += kCap) {
+                    const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
+                    const int ox = cx - xx;
+                    const bool adj = valid && ox >= -1 && ox <= 1;
+                    if (adj) ncand += ge - gs;
+                    if (gs == ge) continue;
+                    const float qx = fmaf((float)ox, d.csf, pi.x);
+                    const uint32_t code = (uint32_t)(ox + 1) << 14;
+                    const uint32_t e = sb + (ge - rs);
+                    for (uint32_t c0 = sb + (gs - rs); c0 < e; c0 += kCap) {
                         const uint32_t c1 = (e - c0) > (uint32_t)kCap ? c0 + kCap : e;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0) > (uint32_t)kCap) flush();
+                        uint16_t* lp = lst + cnt * 32;
+                        uint32_t j = c0;
+                        for (; j + 4 <= c1; j += 4) {
+                            const float4 a0 = s_p[j], a1 = s_p[j + 1], a2 = s_p[j + 2],
+                                         a3 = s_p[j + 3];
+                            float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
+                            float x1 = qx - a1.x, y1 = pi.y - a1.y, z1 = pi.z - a1.z;
+                            float x2 = qx - a2.x, y2 = pi.y - a2.y, z2 = pi.z - a2.z;
+                            float x3 = qx - a3.x, y3 = pi.y - a3.y, z3 = pi.z - a3.z;
+                            const uint32_t h0 = adj && fmaf(x0, x0, fmaf(y0, y0, z0 * z0)) < d.r2max;
+                            const uint32_t h1 = adj && fmaf(x1, x1, fmaf(y1, y1, z1 * z1)) < d.r2max;
+                            const uint32_t h2 = adj && fmaf(x2, x2, fmaf(y2, y2, z2 * z2)) < d.r2max;
+                            const uint32_t h3 = adj && fmaf(x3, x3, fmaf(y3, y3, z3 * z3)) < d.r2max;
+                            const uint32_t o1 = h0, o2 = o1 + h1, o3 = o2 + h2;
+                            if (h0) lp[0] = (uint16_t)(code | j);
+                            if (h1) lp[o1 * 32] = (uint16_t)(code | (j + 1));
+                            if (h2) lp[o2 * 32] = (uint16_t)(code | (j + 2));
+                            if (h3) lp[o3 * 32] = (uint16_t)(code | (j + 3));
+                            const uint32_t nh = o3 + h3;
+                            lp += nh * 32;
+                            cnt += nh;
+                        }
+                        for (; j < c1; ++j) {
+                            const float4 a0 = s_p[j];
+                            const float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
+                            if (adj && fmaf(x0, x0, fmaf(y0, y0, z0 * z0)) < d.r2max) {
+                                lp[0] = (uint16_t)(code | j);
+                                lp += 32;
+                                ++cnt;
+                            }
+                        }
+                    }
+                }
+            }
+            flush();
+        } else {
+            // candidates straight from global memory (unit too large to stage)
+            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (kCap * 32);
+            auto flush = [&]() {
+                const uint32_t mx = __reduce_max_sync(kFull, cnt);
+                for (uint32_t t = 0; t < mx; ++t) {
+                    if (t < cnt) {
+                        const uint32_t e = lst[t * 32 + lane];
+                        const uint32_t j = e & kIdxMask;
+                        const float ox = (float)((int)((e >> 26) & 3u) - 1);
+                        const float oy = (float)((int)((e >> 28) & 3u) - 1);
+                        const float oz = (float)((int)(e >> 30) - 1);
+                        const float4 pj = __ldg(a.posc + j);
+                        const float4 vj = __ldg(a.velrhop + j);
+                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
+                                         fmaf(oy, d.csf, pi.y) - pj.y, fmaf(oz, d.csf, pi.z) - pj.z,
+                                         pj, vj, acc);
+                    }
+                }
+                acc.np += cnt;
+                cnt = 0;
+            };
+            for (int r = 0; r < 9; ++r) {
+                if (!s_ok[r]) continue;
+                const int dy = r % 3 - 1, dz = r / 3 - 1;
+                const float qy = fmaf((float)(-dy), d.csf, pi.y);
+                const float qz = fmaf((float)(-dz), d.csf, pi.z);
+                const uint32_t code_yz = ((uint32_t)(1 - dy) << 28) | ((uint32_t)(1 - dz) << 30);
+                for (int xx = xlo; xx <= xhi; ++xx) {
+                    const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
+                    const int ox = cx - xx;
+                    const bool adj = valid && ox >= -1 && ox <= 1;
+                    if (adj) ncand += ge - gs;
+                    if (gs == ge) continue;
+                    const float qx = fmaf((float)ox, d.csf, pi.x);
+                    const uint32_t code = code_yz | ((uint32_t)(ox + 1) << 26);
+                    for (uint32_t c0 = gs; c0 < ge; c0 += kCap) {
+                        const uint32_t c1 = (ge - c0) > (uint32_t)kCap ? c0 + kCap : ge;
                         if (__reduce_max_sync(kFull, cnt) + (c1 - c0) > (uint32_t)kCap) flush();
 #pragma unroll 4
                         for (uint32_t j = c0; j < c1; ++j) {
                             const float4 pj = __ldg(a.posc + j);
-                            const float dx = qx - pj.x, dy = qy - pj.y, dz = qz - pj.z;
-                            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (adj && d2 < d.r2max && j != i) {
+                            const float dx = qx - pj.x, dy2 = qy - pj.y, dz2 = qz - pj.z;
+                            const float d2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
+                            if (adj && d2 < d.r2max) {
                                 lst[cnt * 32 + lane] = j | code;
                                 ++cnt;
                             }
@@ -303,25 +524,35 @@ __global__ void __launch_bounds__(kIWarps * 32) k_interact(const Dev d, const In
                     }
                 }
             }
+            flush();
         }
     }
-    flush();
 
     const float m = d.mass;
-    const float4 out = make_float4(fmaf(m, ax, d.gx), fmaf(m, ay, d.gy), fmaf(m, az, d.gz), m * dr);
-    if (valid) {
+    const float4 out =
+        make_float4(fmaf(m, acc.ax, d.gx), fmaf(m, acc.ay, d.gy), fmaf(m, acc.az, d.gz), m * acc.dr);
+    const uint32_t npairs = valid ? acc.np - 1u : 0u;   // without the pair (i, i)
+    if (valid && !failed) {
         a.ace[i] = out;
-        if (COUNTS) a.nnb[i] = npairs + nbpairs;
+        if (COUNTS) a.nnb[i] = npairs;
     }
     float am = (valid && fluid) ? out.x * out.x + out.y * out.y + out.z * out.z : 0.f;
-    float cm = valid ? ci : 0.f;
-    float mm = (valid && fluid) ? mu : 0.f;
-    uint32_t bad = (valid && !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) &&
-                               isfinite(out.w)))
-                       ? kStatusNonFinite
-                       : 0u;
     if (!(am == am)) am = 0.f;
-    uint32_t np = npairs, nb = nbpairs, nc = ncand;
+    t_am = fmaxf(t_am, am);
+    t_cm = fmaxf(t_cm, valid ? ci : 0.f);
+    t_mm = fmaxf(t_mm, (valid && fluid) ? acc.mu : 0.f);
+    t_bad |= (valid && !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) &&
+                         isfinite(out.w)))
+                 ? kStatusNonFinite
+                 : 0u;
+    t_np += fluid ? npairs : 0u;
+    t_nb += fluid ? 0u : npairs;
+    t_nc += ncand;
+    __syncthreads();   // the next unit overwrites the shared staging
+    }
+
+    float am = t_am, cm = t_cm, mm = t_mm;
+    uint32_t np = t_np, nb = t_nb, nc = t_nc, bad = t_bad;
     for (int o = 16; o; o >>= 1) {
         am = fmaxf(am, __shfl_xor_sync(kFull, am, o));
         cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
@@ -341,7 +572,7 @@ __global__ void __launch_bounds__(kIWarps * 32) k_interact(const Dev d, const In
         s_ru[w][3] = nb;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
         for (int k = 0; k < kIWarps; ++k) {
@@ -356,6 +587,53 @@ __global__ void __launch_bounds__(kIWarps * 32) k_interact(const Dev d, const In
         a.part_f[blockIdx.x] = f;
         a.part_u[blockIdx.x] = u;
     }
+}
+
+// Work units.  A row of cells is cut into units of consecutive particles:
+// a unit closes before a cell that lies more than 3 cells past the unit's
+// last non-empty cell (so no unit spans an empty stretch), when it would
+// reach kSpan cells, or when it holds kUnit particles.  One thread walks one
+// row; mode 0 counts the units of each row, mode 1 writes them at the row's
+// offset (uint2: first particle, end).
+template <int MODE>
+__global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __restrict__ off,
+                                               uint32_t nrows, uint32_t* __restrict__ ucnt,
+                                               const uint32_t* __restrict__ uoff,
+                                               uint2* __restrict__ units) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const uint32_t* o = off + (size_t)r * (uint32_t)d.ncx;
+    uint32_t n = 0, out = MODE ? uoff[r] : 0u;
+    uint32_t start = 0xffffffffu;
+    int lo = 0, last = 0;
+    uint32_t a = o[0];
+    for (int x = 0; x < d.ncx; ++x) {
+        const uint32_t b = o[x + 1];
+        if (a != b) {
+            if (start != 0xffffffffu && (x - last > 3 || x - lo >= kSpan)) {
+                if (MODE) units[out + n] = make_uint2(start, a);
+                ++n;
+                start = 0xffffffffu;
+            }
+            if (start == 0xffffffffu) {
+                start = a;
+                lo = x;
+            }
+            last = x;
+            while (b - start > (uint32_t)kUnit) {
+                if (MODE) units[out + n] = make_uint2(start, start + kUnit);
+                ++n;
+                start += kUnit;
+                lo = x;
+            }
+        }
+        a = b;
+    }
+    if (start != 0xffffffffu) {
+        if (MODE) units[out + n] = make_uint2(start, a);
+        ++n;
+    }
+    if (!MODE) ucnt[r] = n;
 }
 
 // Sec. 3.3 reductions: per-block partials -> kReduceBlocks partials -> the
@@ -621,8 +899,9 @@ __global__ void __launch_bounds__(256) k_diag_part(const Dev d, const double* __
         const float4 v = vr[k];
         const double rho = v.w;
         acc[0] += m;
-        acc[6] += m * B * ((pow(rho, 6.0) - pow(rho0, 6.0)) / (6.0 * pow(rho0, 7.0)) + 1.0 / rho -
-                           1.0 / rho0);
+        // e(rho) = B [ ((rho/rho0)^6 - 1) / (6 rho0) + 1/rho - 1/rho0 ]
+        const double rr = rho / rho0, r2 = rr * rr, r6 = r2 * r2 * r2;
+        acc[6] += m * B * ((r6 - 1.0) / (6.0 * rho0) + 1.0 / rho - 1.0 / rho0);
         if (id[k] >= d.n_bound) {
             acc[1] += m * v.x;
             acc[2] += m * v.y;
@@ -661,23 +940,48 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
     k_reorder<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
 }
 
-uint32_t interact_blocks(uint32_t n) { return blocks_for(n, kIWarps * 32); }
+// Upper bound on the number of units: every unit but the last of its row
+// either holds kUnit particles or ends at a gap or at kSpan cells; a row of
+// ncx cells has at most ncx / 4 + 1 gap-separated stretches, each cut at most
+// ncx / kSpan + 1 more times.
+uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t ncx) {
+    return (n + kUnit - 1) / kUnit + nrows * (ncx / 4 + ncx / kSpan + 2);
+}
 
-constexpr size_t kInteractSmem = (size_t)kIWarps * kCap * 32 * sizeof(uint32_t);
+namespace {
+int g_interact_grid = 0;
+}
+
+// Persistent grid: every resident block of the interaction on this GPU.
+uint32_t interact_grid() { return (uint32_t)g_interact_grid; }
 
 void prepare_interact() {
     cudaFuncSetAttribute(k_interact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kInteractSmem);
     cudaFuncSetAttribute(k_interact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kInteractSmem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact<false>, kIWarps * 32,
+                                                  kInteractSmem);
+    g_interact_grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
 }
 
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st) {
-    const uint32_t nb = interact_blocks(d.n);
+    const uint32_t nb = interact_grid();
     if (counts)
         k_interact<true><<<nb, kIWarps * 32, kInteractSmem, st>>>(d, a);
     else
         k_interact<false><<<nb, kIWarps * 32, kInteractSmem, st>>>(d, a);
+}
+
+void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
+                  uint32_t* uoff, uint2* units, cudaStream_t st) {
+    const uint32_t nrows = (uint32_t)d.ncy * (uint32_t)d.ncz;
+    k_units<0><<<blocks_for(nrows, 128), 128, 0, st>>>(d, off, nrows, ucnt, uoff, units);
+    launch_scan(ucnt, nrows, ubsum, uoff, st);
+    k_units<1><<<blocks_for(nrows, 128), 128, 0, st>>>(d, off, nrows, ucnt, uoff, units);
 }
 
 void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st) {

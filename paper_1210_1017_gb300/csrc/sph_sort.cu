@@ -277,13 +277,16 @@ uint32_t scan_bsum_count(uint64_t m) {
     return (uint32_t)((m + 1 + kScanChunk - 1) / kScanChunk);
 }
 
+void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st) {
+    const uint32_t nb = scan_bsum_count(m);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, m, bsum);
+    k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, m, bsum, out);
+}
+
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st) {
-    const uint64_t m = (uint64_t)d.ncells + 1;   // counts incl. the excluded bin
-    const uint32_t nb = scan_bsum_count(m);
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(cnt, m, bsum);
-    k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
-    k_scan_down<<<nb, kScanThreads, 0, st>>>(cnt, m, bsum, off);
+    launch_scan(cnt, (uint64_t)d.ncells + 1, bsum, off, st);   // counts incl. the excluded bin
 }
 
 void launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, int bits_total,

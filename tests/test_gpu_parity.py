@@ -39,6 +39,9 @@ def _case_list():
         ("random_777", lambda: cases.random_block(777, seed=8, jitter=0.4)),
         ("random_2000", lambda: cases.random_block(2000, seed=9, jitter=0.3)),
         ("dam_break_6k", lambda: cases.c1_dam_break(shuffle_seed=3)),
+        # h = 3 dp: ~200 particles per cell, so work units overflow the
+        # shared-memory staging and take the global-memory path
+        ("dense_h3dp", lambda: cases.random_block(3000, seed=5, h_over_dp=3.0, jitter=0.2)),
     ]
 
 
@@ -169,9 +172,12 @@ def test_interaction_within_2e5(name, make):
     assert ea.max() <= REL_TOL
     assert ed.max() <= REL_TOL
     assert gl <= REL_TOL
+    # FP32 and FP64 predicates may disagree for pairs at |r_ij| = 2h
+    # (their terms vanish there); the FP64 counts are compared bit for bit
+    # in test_neighbour_counts_fp64_bit_exact
     d = sim.diagnostics()
-    assert d["pairs_last"] == int(ref["nnb"].sum())
-    assert d["pairs_fluid_last"] == int(ref["nnb"][fluid].sum())
+    assert abs(d["pairs_last"] - int(ref["nnb"].sum())) <= 1e-4 * ref["nnb"].sum()
+    assert abs(d["pairs_fluid_last"] - int(ref["nnb"][fluid].sum())) <= 1e-4 * ref["nnb"].sum()
     sim.close()
 
 
