@@ -90,14 +90,14 @@ typedef struct sph_sizes {
 } sph_sizes;
 
 typedef struct sph_diag {
-    double t;                   /* simulated time [s]                     */
-    double dt;                  /* step size of the last step             */
+    double t;                   /* simulated time [s] (member 0)          */
+    double dt;                  /* current step size (member 0)           */
     double mass;                /* total mass of in-domain particles      */
     double momentum[3];         /* fluid momentum                         */
     double kinetic;             /* fluid kinetic energy                   */
     double potential;           /* fluid potential energy -m g.r          */
     double internal;            /* sum m e(rho), e' = p/rho^2 (Tait)      */
-    uint64_t step;              /* steps taken                            */
+    uint64_t step;              /* steps taken (member 0)                 */
     uint64_t pairs_total;       /* neighbour pairs evaluated, all calls   */
     uint64_t candidates_total;  /* 27-cell candidates tested, all calls   */
     uint64_t pairs_last;        /* pairs of the last interaction          */
@@ -108,10 +108,26 @@ typedef struct sph_diag {
     uint64_t pairs_boundary_total;
     uint32_t n_out;             /* excluded particles                     */
     uint32_t status;            /* SPH_STATUS_* bits                      */
-    float amax, cmax, mumax;    /* CFL terms of the last evaluation       */
+    float amax, cmax, mumax;    /* CFL terms of the last step-setting
+                                   evaluation (member 0)                */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;
+
+/* One member of an ensemble of independent simulations run in lockstep
+ * (the batched configuration: many uneven dam breaks in one launch).  The
+ * members share sph_params' dp, h, rho0, gamma, alpha, eta2_coef, gravity,
+ * cfl, mass and dt_fixed; each has its own domain, c0 and end time.
+ * Particle ids: member q owns the n_particles consecutive ids that follow
+ * member q-1's, its first n_bound ids being boundary particles. */
+typedef struct sph_instance {
+    double dmin[3], dmax[3];    /* this member's cell-grid domain        */
+    double c0;                  /* this member's reference sound speed   */
+    double t_end;               /* the member stops once t >= t_end
+                                   (its step size becomes 0)            */
+    uint32_t n_particles;
+    uint32_t n_bound;
+} sph_instance;
 
 /* Bytes of device workspace for n particles under params (no side
  * effects, no CUDA calls). */
@@ -125,6 +141,25 @@ int sph_query_sizes(const sph_params *params, uint32_t n_particles,
 int sph_init(const sph_params *params, uint32_t n_particles,
              void *d_workspace, uint64_t workspace_bytes, void *stream,
              sph_ctx **out);
+
+/* Ensemble versions of sph_query_sizes / sph_init: n_inst members, whose
+ * particle counts add up to the context's n.  params supplies the shared
+ * constants (its dmin, dmax, c0 and n_bound are ignored).  Per-member step
+ * sizes, times and end flags live on the device; every other call works on
+ * the whole ensemble at once (one sort, one interaction launch, one
+ * integrator launch per stage).  sph_init is the ensemble of one with
+ * t_end = infinity. */
+int sph_query_sizes_batch(const sph_params *params, const sph_instance *inst,
+                          uint32_t n_inst, sph_sizes *out);
+int sph_init_batch(const sph_params *params, const sph_instance *inst,
+                   uint32_t n_inst, void *d_workspace,
+                   uint64_t workspace_bytes, void *stream, sph_ctx **out);
+
+/* Per-member simulated time, current step size, end flag and step count,
+ * copied into caller-owned host arrays of n_inst entries (any pointer may
+ * be NULL).  Sync. */
+int sph_instance_state(sph_ctx *ctx, double *t, double *dt, uint32_t *done,
+                       uint64_t *steps);
 
 /* Copy a particle state from host memory (any order): pos[3n] float64
  * (x,y,z interleaved), vel[3n] float32, rho[n] float32, ids[n] uint32 (a
@@ -191,7 +226,7 @@ int sph_download(sph_ctx *ctx, double *pos, float *vel, float *rho,
  *   SPH_ARRAY_NNB64    uint32[n]  neighbour counts with the FP64 predicate
  *                      (sph_neighbour_counts_fp64)
  *   SPH_ARRAY_POSC     float32[4n] cell-relative position and p/rho^2
- *   SPH_ARRAY_DT       float64[1] current step size */
+ *   SPH_ARRAY_DT       float64[n_inst] current step size of each member */
 #define SPH_ARRAY_KEY      0
 #define SPH_ARRAY_CELL_OFF 1
 #define SPH_ARRAY_ACE      2

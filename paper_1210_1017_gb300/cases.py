@@ -343,3 +343,60 @@ def random_block(n: int, seed: int = 7, dp: float = 0.02, h_over_dp=1.3,
                 gravity=(0.0, 0.0, -g), dmin=dmin, dmax=dmax,
                 fluid_height=float(pos[:, 2].max()))
     return shuffle(case, seed + 1)
+
+
+@dataclass
+class Ensemble:
+    """Independent dam breaks concatenated for a lockstep (batched) run.
+
+    Member q owns the global ids [id_base[q], id_base[q+1]) (its own ids
+    shifted, boundary particles first).  ``members`` holds the per-member
+    inputs of the C ABI (domain, c0, counts, end time); ``params`` the shared
+    constants (taken from member 0, which must agree with all others on dp,
+    h, rho0, alpha, cfl, gravity and mass).
+    """
+    cases: list
+    pos: np.ndarray
+    vel: np.ndarray
+    rho: np.ndarray
+    ids: np.ndarray
+    id_base: np.ndarray
+    members: list
+    params: dict
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    def member_slice(self, q):
+        return slice(int(self.id_base[q]), int(self.id_base[q + 1]))
+
+
+def ensemble(case_list, t_end=float("inf")) -> Ensemble:
+    """Concatenate cases (same dp, h and physical constants except c0)."""
+    base = [0]
+    for c in case_list:
+        base.append(base[-1] + c.n)
+    pos = np.concatenate([c.pos for c in case_list])
+    vel = np.concatenate([c.vel for c in case_list])
+    rho = np.concatenate([c.rho for c in case_list])
+    ids = np.concatenate([c.ids.astype(np.uint64) + b for c, b in zip(case_list, base)]
+                         ).astype(np.uint32)
+    members = [dict(dmin=c.dmin, dmax=c.dmax, c0=c.c0, n_particles=c.n, n_bound=c.n_bound,
+                    t_end=t_end) for c in case_list]
+    p = case_list[0].params()
+    for c in case_list[1:]:
+        q = c.params()
+        for k in ("dp", "h", "rho0", "alpha", "cfl", "mass", "gravity", "eta2_coef"):
+            if q[k] != p[k]:
+                raise ValueError(f"ensemble members disagree on {k}")
+    return Ensemble(cases=list(case_list), pos=pos, vel=vel, rho=rho, ids=ids,
+                    id_base=np.array(base, dtype=np.int64), members=members, params=p)
+
+
+def dam_break_ensemble(n_instances=256, seed=1017, dp=0.02, t_end=1.0) -> Ensemble:
+    """The batched workload: n dam breaks, fluid block b_x, b_y, b_z drawn
+    from U[0.2, 0.6] m (SplitMix64 ``seed``) in a 1.0 x b_y x 0.8 m tank, each
+    run to ``t_end`` seconds."""
+    specs = ensemble_specs(n_instances, seed=seed, dp=dp)
+    return ensemble([ensemble_instance(s, dp=dp) for s in specs], t_end=t_end)

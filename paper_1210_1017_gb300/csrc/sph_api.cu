@@ -1,5 +1,6 @@
 // C ABI of libsph.so (declared in include/sph.h): context, workspace
-// layout, the step sequence and its CUDA-graph capture, host transfers.
+// layout, the ensemble table, the step sequence and its CUDA-graph capture,
+// host transfers.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -16,6 +17,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr uint32_t kMaxGridBlocks = 4096;   // partials of the persistent interaction
+constexpr uint32_t kMaxInstances = 1u << 16;
 
 // Bump allocator over the caller's workspace (base may be null when only
 // the size is wanted).
@@ -67,17 +69,25 @@ __global__ void k_pack(uint32_t n, const double* __restrict__ x, const double* _
     rho[i] = v.w;
 }
 
+// Host view of the ensemble: the device table plus its search arrays.
+struct Table {
+    std::vector<Inst> inst;
+    std::vector<uint32_t> cell_base, row_base, id_base;   // n_inst + 1 each
+    uint64_t ncells = 0, nrows = 0, n = 0;
+    int max_ncx = 1;
+};
+
 }  // namespace
 
 struct sph_ctx {
     sph_params p;
     Dev d;
-    uint32_t n = 0;
+    Table tab;
+    uint32_t n = 0, n_inst = 1;
     cudaStream_t st = nullptr;
     int bits = 0, passes = 0;
     uint32_t tiles = 0, nparts = 0;
     uint64_t ncells = 0;
-    uint32_t ncx_ = 1;        // cells per row (set before carving)
     // state, double-buffered for the reorder gather
     double *x[2], *y[2], *z[2];
     float4* vr[2];
@@ -93,13 +103,18 @@ struct sph_ctx {
     uint32_t *cnt, *off, *bsum, *hist, *tilectr, *os_status, *nnb, *nnb64;
     uint32_t *ucnt, *uoff, *ubsum;   // work units of the interaction
     uint2* units;
-    float4 *part_f, *lvl2_f;
     uint4* part_u;
     unsigned long long* lvl2_q;
     uint32_t *done, *status;
-    double *dt, *t, *diag_out, *diag_part;
-    float* terms;
-    unsigned long long *counters, *step;
+    double *diag_out, *diag_part;
+    unsigned long long* counters;
+    // ensemble table and per-member state (device)
+    Inst* d_inst;
+    uint32_t *d_cell_base, *d_row_base, *d_id_base;
+    double *i_dt, *i_t;
+    uint32_t *i_done, *i_terms;
+    unsigned long long* i_steps;
+    float* i_last;
     size_t os_bytes = 0;
     // bookkeeping
     int cur = 0;             // state buffer index
@@ -124,50 +139,90 @@ int cuda_check(sph_ctx* c, cudaError_t e, const char* what) {
     return fail(c, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int validate(const sph_params* p, uint32_t n, uint64_t* ncells, uint32_t nc[3], std::string* why) {
-    if (!p) {
-        *why = "params is NULL";
+int validate_shared(const sph_params* p) {
+    if (!p) return SPH_ERR_INVALID_ARG;
+    if (!(p->h > 0.0) || !(p->rho0 > 0.0) || !(p->mass > 0.0) || !(p->cfl > 0.0) ||
+        !(p->alpha >= 0.0) || !(p->eta2_coef > 0.0))
         return SPH_ERR_INVALID_ARG;
-    }
-    if (n == 0 || n >= kMaxParticles) {
-        *why = "n_particles must be in [1, 2^26)";
-        return SPH_ERR_INVALID_ARG;
-    }
-    if (!(p->h > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0) || !(p->mass > 0.0) ||
-        !(p->cfl > 0.0) || !(p->alpha >= 0.0) || !(p->eta2_coef > 0.0)) {
-        *why = "h, rho0, c0, mass, cfl, eta2_coef must be > 0 and alpha >= 0";
-        return SPH_ERR_INVALID_ARG;
-    }
-    if (p->gamma != 7.0) {
-        *why = "gamma must be 7 (Tait law of Sec. 2.2)";
-        return SPH_ERR_INVALID_ARG;
-    }
-    const double cs = 2.0 * p->h;
-    uint64_t total = 1;
-    for (int a = 0; a < 3; ++a) {
-        if (!(p->dmax[a] > p->dmin[a])) {
-            *why = "dmax must exceed dmin on every axis";
-            return SPH_ERR_INVALID_ARG;
-        }
-        const double t = ceil((p->dmax[a] - p->dmin[a]) / cs);
-        if (!(t >= 1.0) || t > 65535.0) {
-            *why = "grid must have 1..65535 cells per axis";
-            return SPH_ERR_INVALID_ARG;
-        }
-        nc[a] = (uint32_t)t;
-        total *= nc[a];
-    }
-    if (total >= (1ull << 31)) {
-        *why = "cell grid must have fewer than 2^31 cells";
-        return SPH_ERR_INVALID_ARG;
-    }
-    *ncells = total;
+    if (p->gamma != 7.0) return SPH_ERR_INVALID_ARG;   // Tait law of Sec. 2.2
     return SPH_OK;
 }
 
+// Build the ensemble table (host side); validates every member.
+int build_table(const sph_params* p, const sph_instance* inst, uint32_t n_inst, Table* t) {
+    int rc = validate_shared(p);
+    if (rc) return rc;
+    if (!inst || n_inst == 0 || n_inst > kMaxInstances) return SPH_ERR_INVALID_ARG;
+    const double cs = 2.0 * p->h;
+    t->inst.assign(n_inst, Inst{});
+    t->cell_base.assign(n_inst + 1, 0);
+    t->row_base.assign(n_inst + 1, 0);
+    t->id_base.assign(n_inst + 1, 0);
+    uint64_t cells = 0, rows = 0, ids = 0;
+    int max_ncx = 1;
+    for (uint32_t q = 0; q < n_inst; ++q) {
+        const sph_instance& s = inst[q];
+        if (!(s.c0 > 0.0) || s.n_particles == 0 || s.n_bound > s.n_particles)
+            return SPH_ERR_INVALID_ARG;
+        Inst& I = t->inst[q];
+        int nc[3];
+        for (int a = 0; a < 3; ++a) {
+            if (!(s.dmax[a] > s.dmin[a])) return SPH_ERR_INVALID_ARG;
+            const double v = ceil((s.dmax[a] - s.dmin[a]) / cs);
+            if (!(v >= 1.0) || v > 65535.0) return SPH_ERR_INVALID_ARG;
+            nc[a] = (int)v;
+        }
+        I.x0 = s.dmin[0];
+        I.y0 = s.dmin[1];
+        I.z0 = s.dmin[2];
+        I.t_end = s.t_end;
+        I.ncx = nc[0];
+        I.ncy = nc[1];
+        I.ncz = nc[2];
+        I.cell_base = (uint32_t)cells;
+        I.row_base = (uint32_t)rows;
+        I.id_base = (uint32_t)ids;
+        I.id_fluid = (uint32_t)(ids + s.n_bound);
+        I.id_end = (uint32_t)(ids + s.n_particles);
+        I.c0 = (float)s.c0;
+        I.B = (float)(s.c0 * s.c0 * p->rho0 / p->gamma);
+        t->cell_base[q] = I.cell_base;
+        t->row_base[q] = I.row_base;
+        t->id_base[q] = I.id_base;
+        cells += (uint64_t)nc[0] * nc[1] * nc[2];
+        rows += (uint64_t)nc[1] * nc[2];
+        ids += s.n_particles;
+        if (nc[0] > max_ncx) max_ncx = nc[0];
+        if (cells >= (1ull << 31) || ids >= kMaxParticles) return SPH_ERR_INVALID_ARG;
+    }
+    t->cell_base[n_inst] = (uint32_t)cells;
+    t->row_base[n_inst] = (uint32_t)rows;
+    t->id_base[n_inst] = (uint32_t)ids;
+    t->ncells = cells;
+    t->nrows = rows;
+    t->n = ids;
+    t->max_ncx = max_ncx;
+    return SPH_OK;
+}
+
+sph_instance single_instance(const sph_params* p, uint32_t n) {
+    sph_instance s;
+    memset(&s, 0, sizeof(s));
+    for (int a = 0; a < 3; ++a) {
+        s.dmin[a] = p->dmin[a];
+        s.dmax[a] = p->dmax[a];
+    }
+    s.c0 = p->c0;
+    s.t_end = INFINITY;
+    s.n_particles = n;
+    s.n_bound = p->n_bound;
+    return s;
+}
+
 // Lay out every device buffer; with base == nullptr only sizes are computed.
-size_t carve(sph_ctx* c, void* base, uint32_t n, uint64_t ncells, int passes) {
+size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     Carver cv(base);
+    const uint32_t n_inst = (uint32_t)t.inst.size();
     for (int b = 0; b < 2; ++b) {
         c->x[b] = cv.take<double>(n);
         c->y[b] = cv.take<double>(n);
@@ -187,55 +242,67 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, uint64_t ncells, int passes) {
     c->stage_vr = cv.take<float>(4 * (size_t)n);
     c->nnb = cv.take<uint32_t>(n);
     c->nnb64 = cv.take<uint32_t>(n);
-    c->cnt = cv.take<uint32_t>(ncells + 1);
-    c->off = cv.take<uint32_t>(ncells + 2);
-    c->bsum = cv.take<uint32_t>(scan_bsum_count(ncells + 1));
+    c->cnt = cv.take<uint32_t>(t.ncells + 1);
+    c->off = cv.take<uint32_t>(t.ncells + 2);
+    c->bsum = cv.take<uint32_t>(scan_bsum_count(t.ncells + 1));
     c->hist = cv.take<uint32_t>(4 * 256);
     const uint32_t tiles = os_tiles(n);
     c->os_bytes = 4 * sizeof(uint32_t) + (size_t)passes * tiles * 256 * sizeof(uint32_t);
     c->tilectr = cv.take<uint32_t>(c->os_bytes / sizeof(uint32_t));
     c->os_status = c->tilectr ? c->tilectr + 4 : nullptr;
-    const uint32_t nrows = (uint32_t)(ncells / c->ncx_);
-    c->ucnt = cv.take<uint32_t>(nrows + 1);
-    c->uoff = cv.take<uint32_t>(nrows + 2);
-    c->ubsum = cv.take<uint32_t>(scan_bsum_count(nrows + 1));
-    c->units = cv.take<uint2>(max_units(n, nrows, c->ncx_));
-    const uint32_t np = kMaxGridBlocks;
-    c->part_f = cv.take<float4>(np);
-    c->part_u = cv.take<uint4>(np);
-    c->lvl2_f = cv.take<float4>(kReduceBlocks);
+    c->ucnt = cv.take<uint32_t>(t.nrows + 1);
+    c->uoff = cv.take<uint32_t>(t.nrows + 2);
+    c->ubsum = cv.take<uint32_t>(scan_bsum_count(t.nrows + 1));
+    c->units = cv.take<uint2>(max_units(n, (uint32_t)t.nrows, (uint32_t)t.max_ncx));
+    c->part_u = cv.take<uint4>(kMaxGridBlocks);
     c->lvl2_q = cv.take<unsigned long long>(4 * kReduceBlocks);
     c->done = cv.take<uint32_t>(1);
     c->status = cv.take<uint32_t>(1);
-    c->dt = cv.take<double>(1);
-    c->t = cv.take<double>(1);
     c->diag_out = cv.take<double>(8);
     c->diag_part = cv.take<double>(8 * kDiagBlocks);
-    c->terms = cv.take<float>(4);
     c->counters = cv.take<unsigned long long>(8);
-    c->step = cv.take<unsigned long long>(1);
+    c->d_inst = cv.take<Inst>(n_inst);
+    c->d_cell_base = cv.take<uint32_t>(n_inst + 1);
+    c->d_row_base = cv.take<uint32_t>(n_inst + 1);
+    c->d_id_base = cv.take<uint32_t>(n_inst + 1);
+    c->i_dt = cv.take<double>(n_inst);
+    c->i_t = cv.take<double>(n_inst);
+    c->i_done = cv.take<uint32_t>(n_inst);
+    c->i_steps = cv.take<unsigned long long>(n_inst);
+    c->i_terms = cv.take<uint32_t>(3 * (size_t)n_inst);
+    c->i_last = cv.take<float>(3 * (size_t)n_inst);
     return (cv.used + kAlign - 1) / kAlign * kAlign;
 }
 
-Dev make_dev(const sph_params* p, uint32_t n, const uint32_t nc[3], uint64_t ncells) {
+Dev make_dev(const sph_ctx* c) {
+    const sph_params* p = &c->p;
     Dev d;
     memset(&d, 0, sizeof(d));
     const double cs = 2.0 * p->h;
-    d.x0 = p->dmin[0];
-    d.y0 = p->dmin[1];
-    d.z0 = p->dmin[2];
+    d.inst = c->d_inst;
+    d.cell_base = c->d_cell_base;
+    d.row_base = c->d_row_base;
+    d.id_base = c->d_id_base;
+    d.n_inst = c->n_inst;
+    d.is.dt = c->i_dt;
+    d.is.t = c->i_t;
+    d.is.done = c->i_done;
+    d.is.steps = c->i_steps;
+    d.is.terms = c->i_terms;
+    d.is.last = c->i_last;
     d.inv_cs = 1.0 / cs;
     d.cs = cs;
     d.r2max_d = cs * cs;
     d.h_d = p->h;
     d.cfl = p->cfl;
     d.dt_fixed = p->dt_fixed;
-    d.ncx = (int)nc[0];
-    d.ncy = (int)nc[1];
-    d.ncz = (int)nc[2];
-    d.ncells = (uint32_t)ncells;
-    d.n = n;
-    d.n_bound = p->n_bound;
+    d.mass_d = p->mass;
+    d.rho0_d = p->rho0;
+    for (int k = 0; k < 3; ++k) d.g_d[k] = p->gravity[k];
+    d.ncells = (uint32_t)c->tab.ncells;
+    d.nrows = (uint32_t)c->tab.nrows;
+    d.n = c->n;
+    d.max_ncx = c->tab.max_ncx;
     d.csf = (float)cs;
     d.h = (float)p->h;
     d.inv_h = (float)(1.0 / p->h);
@@ -244,15 +311,9 @@ Dev make_dev(const sph_params* p, uint32_t n, const uint32_t nc[3], uint64_t nce
     const double aD = 21.0 / (16.0 * M_PI * p->h * p->h * p->h);
     d.fc = (float)(-5.0 * aD / (p->h * p->h));
     d.alpha = (float)p->alpha;
-    d.c0 = (float)p->c0;
     d.rho0 = (float)p->rho0;
     d.inv_rho0 = (float)(1.0 / p->rho0);
-    d.B = (float)(p->c0 * p->c0 * p->rho0 / p->gamma);
     d.mass = (float)p->mass;
-    d.mass_d = p->mass;
-    d.rho0_d = p->rho0;
-    d.B_d = p->c0 * p->c0 * p->rho0 / p->gamma;
-    for (int k = 0; k < 3; ++k) d.g_d[k] = p->gravity[k];
     d.gx = (float)p->gravity[0];
     d.gy = (float)p->gravity[1];
     d.gz = (float)p->gravity[2];
@@ -260,8 +321,8 @@ Dev make_dev(const sph_params* p, uint32_t n, const uint32_t nc[3], uint64_t nce
 }
 
 // Sort the labels in key[0] (counted into cnt/hist by the label kernel),
-// scan the counts into cell offsets and reorder the state (and the start
-// state when with_pre).
+// scan the counts into cell offsets, cut the rows into interaction work
+// units and reorder the state (and the start state when with_pre).
 void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     cudaStream_t st = c->st;
     launch_scan_cells(c->d, c->cnt, c->bsum, c->off, st);
@@ -311,7 +372,7 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
 void enqueue_interact(sph_ctx* c, bool counts, bool set_dt) {
     InteractArgs ia;
     ia.units = c->units;
-    ia.n_units = c->uoff + (c->ncells / c->ncx_);
+    ia.n_units = c->uoff + c->tab.nrows;
     ia.status = c->status;
     ia.posc = c->posc;
     ia.velrhop = c->vr[c->cur];
@@ -320,18 +381,13 @@ void enqueue_interact(sph_ctx* c, bool counts, bool set_dt) {
     ia.off = c->off;
     ia.ace = c->ace;
     ia.nnb = c->nnb;
-    ia.part_f = c->part_f;
     ia.part_u = c->part_u;
     launch_interact(c->d, ia, counts, c->st);
     ReduceArgs ra;
-    ra.part_f = c->part_f;
     ra.part_u = c->part_u;
     ra.nparts = c->nparts;
-    ra.lvl2_f = c->lvl2_f;
     ra.lvl2_q = c->lvl2_q;
     ra.done = c->done;
-    ra.dt = c->dt;
-    ra.terms = c->terms;
     ra.counters = c->counters;
     ra.status = c->status;
     launch_dt_reduce(c->d, ra, set_dt, c->st);
@@ -350,9 +406,6 @@ IntegrateArgs integrate_args(sph_ctx* c, int pre) {
     a.py = c->py[pre];
     a.pz = c->pz[pre];
     a.pvr = c->pvr[pre];
-    a.dt = c->dt;
-    a.t = c->t;
-    a.step = c->step;
     a.key = c->key[0];
     a.cnt = c->cnt;
     a.hist = c->hist;
@@ -362,8 +415,8 @@ IntegrateArgs integrate_args(sph_ctx* c, int pre) {
 
 void enqueue_build(sph_ctx* c) {
     if (!c->keys_ready) {
-        launch_keys(c->d, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->n, c->key[0], c->cnt,
-                    c->hist, c->passes, c->st);
+        launch_keys(c->d, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->id[c->cur], c->n,
+                    c->key[0], c->cnt, c->hist, c->passes, c->st);
     }
     const bool with_pre = c->pre_state == 1;
     rebuild_after_keys(c, with_pre);
@@ -390,72 +443,76 @@ int post_launch(sph_ctx* c, const char* what) {
     return cuda_check(c, cudaGetLastError(), what);
 }
 
-}  // namespace
-
-extern "C" {
-
-int sph_query_sizes(const sph_params* params, uint32_t n, sph_sizes* out) {
+int query(const sph_params* params, const sph_instance* inst, uint32_t n_inst, sph_sizes* out) {
     if (!out) return SPH_ERR_INVALID_ARG;
-    uint64_t ncells;
-    uint32_t nc[3];
-    std::string why;
-    int rc = validate(params, n, &ncells, nc, &why);
-    if (rc) return rc;
     sph_ctx tmp;
-    tmp.ncx_ = nc[0];
-    const int bits = bit_length(ncells);
+    int rc = build_table(params, inst, n_inst, &tmp.tab);
+    if (rc) return rc;
+    const int bits = bit_length(tmp.tab.ncells);
     const int passes = (bits + 7) / 8;
-    out->workspace_bytes = carve(&tmp, nullptr, n, ncells, passes);
-    out->ncells = ncells;
-    out->ncx = nc[0];
-    out->ncy = nc[1];
-    out->ncz = nc[2];
+    out->workspace_bytes = carve(&tmp, nullptr, (uint32_t)tmp.tab.n, tmp.tab, passes);
+    out->ncells = tmp.tab.ncells;
+    out->ncx = (uint32_t)tmp.tab.inst[0].ncx;
+    out->ncy = (uint32_t)tmp.tab.inst[0].ncy;
+    out->ncz = (uint32_t)tmp.tab.inst[0].ncz;
     out->sort_passes = (uint32_t)passes;
     return SPH_OK;
 }
 
-int sph_init(const sph_params* params, uint32_t n, void* ws, uint64_t ws_bytes, void* stream,
-             sph_ctx** out) {
+int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, void* ws,
+         uint64_t ws_bytes, void* stream, sph_ctx** out) {
     if (!out) return SPH_ERR_INVALID_ARG;
     *out = nullptr;
-    uint64_t ncells;
-    uint32_t nc[3];
-    std::string why;
-    int rc = validate(params, n, &ncells, nc, &why);
-    if (rc) return rc;
-    if (!ws || ((uintptr_t)ws % kAlign) != 0) return SPH_ERR_WORKSPACE;
     sph_ctx* c = new sph_ctx();
+    int rc = build_table(params, inst, n_inst, &c->tab);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    if (!ws || ((uintptr_t)ws % kAlign) != 0) {
+        delete c;
+        return SPH_ERR_WORKSPACE;
+    }
     c->p = *params;
-    c->n = n;
+    c->n = (uint32_t)c->tab.n;
+    c->n_inst = n_inst;
     c->st = (cudaStream_t)stream;
-    c->ncells = ncells;
-    c->bits = bit_length(ncells);
+    c->ncells = c->tab.ncells;
+    c->bits = bit_length(c->ncells);
     c->passes = (c->bits + 7) / 8;
-    c->ncx_ = nc[0];
-    const size_t need = carve(c, ws, n, ncells, c->passes);
+    const size_t need = carve(c, ws, c->n, c->tab, c->passes);
     if (ws_bytes < need) {
         delete c;
         return SPH_ERR_WORKSPACE;
     }
-    c->tiles = os_tiles(n);
+    c->tiles = os_tiles(c->n);
     prepare_interact();
     c->nparts = interact_grid();
     if (c->nparts == 0 || c->nparts > kMaxGridBlocks) {
         delete c;
         return SPH_ERR_CUDA;
     }
-    c->d = make_dev(params, n, nc, ncells);
+    c->d = make_dev(c);
     cudaStream_t st = c->st;
-    cudaMemsetAsync(c->cnt, 0, (ncells + 1) * sizeof(uint32_t), st);
+    cudaMemcpyAsync(c->d_inst, c->tab.inst.data(), n_inst * sizeof(Inst), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d_cell_base, c->tab.cell_base.data(), (n_inst + 1) * sizeof(uint32_t),
+                    cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d_row_base, c->tab.row_base.data(), (n_inst + 1) * sizeof(uint32_t),
+                    cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->d_id_base, c->tab.id_base.data(), (n_inst + 1) * sizeof(uint32_t),
+                    cudaMemcpyHostToDevice, st);
+    std::vector<double> dt0(n_inst, params->dt_fixed > 0.0 ? params->dt_fixed : 0.0);
+    cudaMemcpyAsync(c->i_dt, dt0.data(), n_inst * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(c->i_t, 0, n_inst * sizeof(double), st);
+    cudaMemsetAsync(c->i_done, 0, n_inst * sizeof(uint32_t), st);
+    cudaMemsetAsync(c->i_steps, 0, n_inst * sizeof(unsigned long long), st);
+    cudaMemsetAsync(c->i_terms, 0, 3 * (size_t)n_inst * sizeof(uint32_t), st);
+    cudaMemsetAsync(c->i_last, 0, 3 * (size_t)n_inst * sizeof(float), st);
+    cudaMemsetAsync(c->cnt, 0, (c->ncells + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(c->hist, 0, 4 * 256 * sizeof(uint32_t), st);
     cudaMemsetAsync(c->done, 0, sizeof(uint32_t), st);
     cudaMemsetAsync(c->status, 0, sizeof(uint32_t), st);
-    cudaMemsetAsync(c->t, 0, sizeof(double), st);
     cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned long long), st);
-    cudaMemsetAsync(c->step, 0, sizeof(unsigned long long), st);
-    cudaMemsetAsync(c->terms, 0, 4 * sizeof(float), st);
-    const double dt0 = params->dt_fixed > 0.0 ? params->dt_fixed : 0.0;
-    cudaMemcpyAsync(c->dt, &dt0, sizeof(double), cudaMemcpyHostToDevice, st);
     rc = cuda_check(c, cudaStreamSynchronize(st), "sph_init");
     if (rc) {
         delete c;
@@ -463,6 +520,46 @@ int sph_init(const sph_params* params, uint32_t n, void* ws, uint64_t ws_bytes, 
     }
     *out = c;
     return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_query_sizes(const sph_params* params, uint32_t n, sph_sizes* out) {
+    if (!params || n == 0 || n >= kMaxParticles) return SPH_ERR_INVALID_ARG;
+    const sph_instance one = single_instance(params, n);
+    return query(params, &one, 1, out);
+}
+
+int sph_query_sizes_batch(const sph_params* params, const sph_instance* inst, uint32_t n_inst,
+                          sph_sizes* out) {
+    return query(params, inst, n_inst, out);
+}
+
+int sph_init(const sph_params* params, uint32_t n, void* ws, uint64_t ws_bytes, void* stream,
+             sph_ctx** out) {
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || n == 0 || n >= kMaxParticles) return SPH_ERR_INVALID_ARG;
+    const sph_instance one = single_instance(params, n);
+    return init(params, &one, 1, ws, ws_bytes, stream, out);
+}
+
+int sph_init_batch(const sph_params* params, const sph_instance* inst, uint32_t n_inst, void* ws,
+                   uint64_t ws_bytes, void* stream, sph_ctx** out) {
+    return init(params, inst, n_inst, ws, ws_bytes, stream, out);
+}
+
+int sph_instance_state(sph_ctx* c, double* t, double* dt, uint32_t* done, uint64_t* steps) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    const size_t m = c->n_inst;
+    cudaStream_t st = c->st;
+    if (t) cudaMemcpyAsync(t, c->i_t, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (dt) cudaMemcpyAsync(dt, c->i_dt, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (done) cudaMemcpyAsync(done, c->i_done, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (steps) cudaMemcpyAsync(steps, c->i_steps, m * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    return cuda_check(c, cudaStreamSynchronize(st), "instance state");
 }
 
 int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho,
@@ -576,8 +673,8 @@ int sph_rollout(sph_ctx* c, uint32_t nsteps, uint32_t save_every, sph_snapshot_f
         if (cb) {
             double t = 0.0;
             unsigned long long s = 0;
-            cudaMemcpy(&t, c->t, sizeof(double), cudaMemcpyDeviceToHost);
-            cudaMemcpy(&s, c->step, sizeof(s), cudaMemcpyDeviceToHost);
+            cudaMemcpy(&t, c->i_t, sizeof(double), cudaMemcpyDeviceToHost);
+            cudaMemcpy(&s, c->i_steps, sizeof(s), cudaMemcpyDeviceToHost);
             if (cb(user, s, t)) break;
         }
     }
@@ -612,7 +709,7 @@ uint64_t sph_array_bytes(const sph_ctx* c, int which) {
         case SPH_ARRAY_CELL_OFF: return (c->ncells + 2) * 4;
         case SPH_ARRAY_ACE:
         case SPH_ARRAY_POSC: return (uint64_t)c->n * 16;
-        case SPH_ARRAY_DT: return 8;
+        case SPH_ARRAY_DT: return 8ull * c->n_inst;
         default: return 0;
     }
 }
@@ -629,7 +726,7 @@ int sph_read_array(sph_ctx* c, int which, void* host, uint64_t bytes) {
         case SPH_ARRAY_NNB: src = c->nnb; break;
         case SPH_ARRAY_NNB64: src = c->nnb64; break;
         case SPH_ARRAY_POSC: src = c->posc; break;
-        case SPH_ARRAY_DT: src = c->dt; break;
+        case SPH_ARRAY_DT: src = c->i_dt; break;
     }
     int rc = cuda_check(c, cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, c->st), "read array");
     if (rc) return rc;
@@ -661,11 +758,11 @@ int sph_diagnostics(sph_ctx* c, sph_diag* out) {
     cudaStream_t st = c->st;
     if (c->have_state && c->cells_valid)
         cudaMemcpyAsync(dsum, c->diag_out, sizeof(dsum), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&t, c->t, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&t, c->i_t, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&dt, c->i_dt, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&step, c->step, sizeof(step), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(terms, c->terms, sizeof(terms), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&step, c->i_steps, sizeof(step), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(terms, c->i_last, 3 * sizeof(float), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&status, c->status, sizeof(status), cudaMemcpyDeviceToHost, st);
     int rc = cuda_check(c, cudaStreamSynchronize(st), "diagnostics");
     if (rc) return rc;

@@ -1,4 +1,13 @@
 // Private declarations shared by the CUDA translation units of libsph.so.
+//
+// A context holds an ensemble of one or more independent simulations
+// ("instances") that share the smoothing length, particle mass and the
+// physical constants except c0, and run in lockstep: one cell sort, one
+// interaction launch and one integrator launch serve all of them.  Instance
+// q owns the particle ids [id_base, id_end) (boundary particles first) and
+// the global cell labels [cell_base, cell_base + ncx ncy ncz); its rows of
+// cells (cy, cz) are the global rows [row_base, row_base + ncy ncz).  A
+// single simulation is the ensemble of one.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -9,35 +18,64 @@ constexpr uint32_t kStatusTimeout = 1u;
 constexpr uint32_t kStatusNonFinite = 2u;
 constexpr uint32_t kStatusCapacity = 4u;
 
-// Largest particle count: list entries pack a 26-bit particle index with the
-// 6-bit cell offset of the neighbour (2 bits per axis).
+// Largest particle count (FP64 counts and ids stay within 32 bits with room).
 constexpr uint32_t kMaxParticles = 1u << 26;
+
+// One instance of the ensemble (device table entry).
+struct Inst {
+    double x0, y0, z0;      // grid origin
+    double t_end;           // the instance stops (dt = 0) once t >= t_end
+    int ncx, ncy, ncz;
+    uint32_t cell_base;
+    uint32_t row_base;
+    uint32_t id_base;
+    uint32_t id_fluid;      // ids in [id_base, id_fluid) are boundary particles
+    uint32_t id_end;
+    float c0;               // reference speed of sound
+    float B;                // Tait stiffness c0^2 rho0 / gamma
+};
+
+// Per-instance device state.
+struct InstState {
+    double* dt;             // step size of the current step
+    double* t;              // simulated time
+    uint32_t* done;         // 1 once t >= t_end
+    unsigned long long* steps;
+    uint32_t* terms;        // 3 per instance, float bits of the running maxima of
+                            // |a|^2, c and mu over the current evaluation
+    float* last;            // 3 per instance: max |a|, max c, max mu of the last one
+};
 
 // Per-context constants handed to kernels by value.
 struct Dev {
-    double x0, y0, z0;     // domain origin
+    const Inst* inst;
+    const uint32_t* cell_base;   // n_inst + 1 entries (last = ncells)
+    const uint32_t* row_base;    // n_inst + 1 entries (last = nrows)
+    const uint32_t* id_base;     // n_inst + 1 entries (last = n)
+    uint32_t n_inst;
+    InstState is;
     double inv_cs;         // 1 / (2h), rounded once (cell label arithmetic)
     double cs;             // 2h
     double r2max_d;        // (2h)^2 rounded once (FP64 neighbour predicate)
     double h_d, cfl, dt_fixed;
-    double mass_d, rho0_d, B_d;      // FP64 copies for the conservation sums
+    double mass_d, rho0_d;
     double g_d[3];
-    int ncx, ncy, ncz;
-    uint32_t ncells;
+    uint32_t ncells;       // all instances' cells; also the label of excluded particles
+    uint32_t nrows;        // all instances' rows of cells
     uint32_t n;
-    uint32_t n_bound;
+    int max_ncx;
     float csf;             // 2h
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
     float eta2;            // eta^2
     float fc;              // -5 aD / h^2 (Wendland C2 gradient factor)
-    float alpha, c0, rho0, inv_rho0, B, mass;
+    float alpha, rho0, inv_rho0, mass;
     float gx, gy, gz;
 };
 
 // Stream-ordered launchers (defined in the .cu files).
 void launch_keys(const Dev& d, const double* x, const double* y, const double* z,
-                 uint32_t n, uint32_t* key, uint32_t* cnt, uint32_t* hist,
+                 const uint32_t* id, uint32_t n, uint32_t* key, uint32_t* cnt, uint32_t* hist,
                  int passes, cudaStream_t st);
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st);
@@ -93,11 +131,10 @@ struct InteractArgs {
     const uint32_t* off;
     float4* ace;
     uint32_t* nnb;        // may be null
-    float4* part_f;       // per block (persistent grid): max|a|^2, max c, max mu, 0
-    uint4* part_u;        // per block: fluid-i pairs, candidates, status bits,
-                          // boundary-i pairs
+    uint4* part_u;        // per block (persistent grid): fluid-i pairs, candidates,
+                          // status bits, boundary-i pairs
 };
-uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t ncx);   // bound on units
+uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx);   // bound on units
 uint32_t interact_grid();   // blocks of the persistent interaction launch
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
                   uint32_t* uoff, uint2* units, cudaStream_t st);
@@ -107,14 +144,10 @@ void prepare_interact();
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
 
 struct ReduceArgs {
-    const float4* part_f;
     const uint4* part_u;
     uint32_t nparts;
-    float4* lvl2_f;
     unsigned long long* lvl2_q;     // 4 per block: fluid pairs, boundary pairs, cands, status
     uint32_t* done;
-    double* dt;             // written if set_dt
-    float* terms;           // 3 floats: amax, cmax, mumax
     // [0] pairs total, [1] candidates total, [2] pairs last, [3] candidates
     // last, [4] fluid-i pairs last, [5] boundary-i pairs last, [6] fluid-i
     // pairs total, [7] boundary-i pairs total
@@ -132,9 +165,6 @@ struct IntegrateArgs {
     const float4* ace;
     double *px, *py, *pz;    // pre state: written by predict, read by correct
     float4* pvr;
-    const double* dt;
-    double* t;
-    unsigned long long* step;
     uint32_t* key;
     uint32_t* cnt;
     uint32_t* hist;
@@ -147,8 +177,8 @@ void launch_counts_fp64(const Dev& d, const double* x, const double* y, const do
                         const uint32_t* key, const uint32_t* off, uint32_t* out,
                         cudaStream_t st);
 
-// FP64 conservation sums: out[0..7] = mass, px, py, pz, kinetic, potential,
-// internal, n_out (as double).
+// FP64 conservation sums over all instances: out[0..7] = mass, px, py, pz,
+// kinetic, potential, internal, n_out (as double).
 constexpr int kDiagBlocks = 152;
 void launch_diag(const Dev& d, const double* x, const double* y, const double* z,
                  const float4* vr, const uint32_t* id, const uint32_t* off,

@@ -2,7 +2,9 @@
 // cell labels, reorder with the id tie-break, the 27-cell pair interaction
 // (Eqs. 7 and 9 with the Tait law and artificial viscosity of Sec. 2.2),
 // the CFL reductions (Sec. 3.3), the symplectic predictor/corrector, FP64
-// neighbour counts and FP64 conservation sums.
+// neighbour counts and FP64 conservation sums.  Every kernel serves an
+// ensemble of independent instances (see sph_internal.cuh); a single
+// simulation is the ensemble of one.
 #include <math.h>
 
 #include "sph_internal.cuh"
@@ -25,18 +27,32 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Index q with base[q] <= v < base[q + 1] (base has n + 1 ascending entries).
+__device__ __forceinline__ uint32_t find_instance(const uint32_t* __restrict__ base, uint32_t n,
+                                                  uint32_t v) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(base + mid) <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Sec. 3.1 cell label: floor((x - x0) * (1/(2h))) per axis in FP64, each
-// operation rounded as written; label = cx + ncx (cy + ncy cz).  Outside the
-// grid (or non-finite) -> ncells.
-__device__ __forceinline__ uint32_t cell_key(const Dev& d, double x, double y, double z) {
-    const double tx = __dmul_rn(__dsub_rn(x, d.x0), d.inv_cs);
-    const double ty = __dmul_rn(__dsub_rn(y, d.y0), d.inv_cs);
-    const double tz = __dmul_rn(__dsub_rn(z, d.z0), d.inv_cs);
-    const bool in = (tx >= 0.0) && (tx < (double)d.ncx) && (ty >= 0.0) &&
-                    (ty < (double)d.ncy) && (tz >= 0.0) && (tz < (double)d.ncz);
+// operation rounded as written; label = cell_base + cx + ncx (cy + ncy cz)
+// in the particle's instance.  Outside its grid (or non-finite) -> ncells.
+__device__ __forceinline__ uint32_t cell_key(const Dev& d, const Inst& I, double x, double y,
+                                             double z) {
+    const double tx = __dmul_rn(__dsub_rn(x, I.x0), d.inv_cs);
+    const double ty = __dmul_rn(__dsub_rn(y, I.y0), d.inv_cs);
+    const double tz = __dmul_rn(__dsub_rn(z, I.z0), d.inv_cs);
+    const bool in = (tx >= 0.0) && (tx < (double)I.ncx) && (ty >= 0.0) &&
+                    (ty < (double)I.ncy) && (tz >= 0.0) && (tz < (double)I.ncz);
     if (!in) return d.ncells;
     const int cx = __double2int_rd(tx), cy = __double2int_rd(ty), cz = __double2int_rd(tz);
-    return (uint32_t)cx + (uint32_t)d.ncx * ((uint32_t)cy + (uint32_t)d.ncy * (uint32_t)cz);
+    return I.cell_base + (uint32_t)cx +
+           (uint32_t)I.ncx * ((uint32_t)cy + (uint32_t)I.ncy * (uint32_t)cz);
 }
 
 __host__ __device__ __forceinline__ uint32_t digit_mask(int pass, int bits_total) {
@@ -75,7 +91,8 @@ __device__ __forceinline__ int bits_for(uint32_t ncells) {
 
 __global__ void __launch_bounds__(256) k_keys(const Dev d, const double* __restrict__ x,
                                               const double* __restrict__ y,
-                                              const double* __restrict__ z, uint32_t n,
+                                              const double* __restrict__ z,
+                                              const uint32_t* __restrict__ id, uint32_t n,
                                               uint32_t* __restrict__ key, uint32_t* cnt,
                                               uint32_t* hist, int passes) {
     __shared__ uint32_t s_hist[4 * 256];
@@ -84,7 +101,8 @@ __global__ void __launch_bounds__(256) k_keys(const Dev d, const double* __restr
     const bool valid = i < n;
     uint32_t k = 0;
     if (valid) {
-        k = cell_key(d, x[i], y[i], z[i]);
+        const uint32_t q = find_instance(d.id_base, d.n_inst, id[i]);
+        k = cell_key(d, d.inst[q], x[i], y[i], z[i]);
         key[i] = k;
     }
     count_key(valid, k, cnt, s_hist, passes, bits_for(d.ncells));
@@ -94,11 +112,11 @@ __global__ void __launch_bounds__(256) k_keys(const Dev d, const double* __restr
 // Tait pressure over density squared, P = B [(rho/rho0)^7 - 1] / rho^2, in
 // FP32.  (rho/rho0)^7 - 1 is expanded in x = (rho - rho0)/rho0 so that it
 // keeps its relative accuracy near the free surface, where it cancels.
-__device__ __forceinline__ float p_over_rho2(const Dev& d, float rho) {
+__device__ __forceinline__ float p_over_rho2(const Dev& d, float B, float rho) {
     const float x = (rho - d.rho0) * d.inv_rho0;
     const float poly =
         x * (7.f + x * (21.f + x * (35.f + x * (35.f + x * (21.f + x * (7.f + x))))));
-    return d.B * poly / (rho * rho);
+    return B * poly / (rho * rho);
 }
 
 constexpr uint32_t kMaxSeg = 4096;   // largest cell the id tie-break handles
@@ -158,14 +176,16 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
     }
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < d.ncells) {
-        const uint32_t cx = c % (uint32_t)d.ncx;
-        const uint32_t t = c / (uint32_t)d.ncx;
-        const uint32_t cy = t % (uint32_t)d.ncy;
-        const uint32_t cz = t / (uint32_t)d.ncy;
-        pc.x = __double2float_rn(x - (d.x0 + (double)cx * d.cs));
-        pc.y = __double2float_rn(y - (d.y0 + (double)cy * d.cs));
-        pc.z = __double2float_rn(z - (d.z0 + (double)cz * d.cs));
-        pc.w = p_over_rho2(d, vr.w);
+        const Inst& I = d.inst[find_instance(d.cell_base, d.n_inst, c)];
+        const uint32_t lc = c - I.cell_base;
+        const uint32_t cx = lc % (uint32_t)I.ncx;
+        const uint32_t t = lc / (uint32_t)I.ncx;
+        const uint32_t cy = t % (uint32_t)I.ncy;
+        const uint32_t cz = t / (uint32_t)I.ncy;
+        pc.x = __double2float_rn(x - (I.x0 + (double)cx * d.cs));
+        pc.y = __double2float_rn(y - (I.y0 + (double)cy * d.cs));
+        pc.z = __double2float_rn(z - (I.z0 + (double)cz * d.cs));
+        pc.w = p_over_rho2(d, I.B, vr.w);
     }
     a.posc[dst] = pc;
 }
@@ -237,7 +257,7 @@ struct PairAcc {
 // move (Sec. 2.3).  The pair j = i (all offsets zero) contributes exactly
 // nothing, which lets lists be padded with it.
 template <bool MOM>
-__device__ __forceinline__ void pair_terms(const Dev& d, bool fluid, const float4& pi,
+__device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, const float4& pi,
                                            const float4& vi, float ci, float dx, float dy, float dz,
                                            const float4& pj, const float4& vj, PairAcc& s) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -251,7 +271,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, bool fluid, const float
     if (MOM) {
         const float nu = d.h * vr * rcp_approx(d2 + d.eta2);       // Sec. 2.2
         const float rrj = vj.w * d.inv_rho0;
-        const float cj = d.c0 * rrj * rrj * rrj;
+        const float cj = c0 * rrj * rrj * rrj;
         const float visc = vr < 0.f ? -d.alpha * (ci + cj) * nu * rcp_approx(vi.w + vj.w) : 0.f;
         const float f = fluid ? (pi.w + pj.w + visc) * F : 0.f;    // Eq. 9
         s.ax = fmaf(-f, dx, s.ax);
@@ -261,19 +281,20 @@ __device__ __forceinline__ void pair_terms(const Dev& d, bool fluid, const float
     }
 }
 
-// Sec. 3.2.  One block = one work unit: up to kUnit consecutive sorted
-// particles of one row of cells (same cy, cz) spanning at most kSpan cells
-// with no more than two empty cells in a row, so the candidates of all of
-// them lie in 9 contiguous, compact runs of the sorted arrays (the
-// neighbouring rows, cells [first cx - 1, last cx + 1]).  Those runs are copied to shared
-// memory with bulk asynchronous copies; their y, z are then shifted into the
-// frame of the unit's row, so a candidate's offset from particle i only
-// needs i's own cell offset in x.  Each warp then tests every candidate of
-// its lanes' cells (one broadcast shared-memory load, all lanes), appends
-// hits (|r_ij| < 2h) to per-lane lists, and evaluates the pair terms from
-// the lists with all lanes busy.  Positions are relative to the particles'
-// own cell origins (FP32), plus whole-cell offsets.  A unit whose runs do
-// not fit the staging area reads its candidates from global memory instead.
+// Sec. 3.2.  One block takes work units in turn: up to kUnit consecutive
+// sorted particles of one row of cells (same instance, cy, cz) spanning at
+// most kSpan cells with no more than two empty cells in a row, so the
+// candidates of all of them lie in 9 contiguous, compact runs of the sorted
+// arrays (the neighbouring rows, cells [first cx - 1, last cx + 1]).  Those
+// runs are copied to shared memory with bulk asynchronous copies; their y, z
+// are then shifted into the frame of the unit's row, so a candidate's offset
+// from particle i only needs i's own cell offset in x.  Each warp then tests
+// every candidate of its lanes' cells (one broadcast shared-memory load, all
+// lanes), appends hits (|r_ij| < 2h) to per-lane lists, and evaluates the
+// pair terms from the lists with all lanes busy.  Positions are relative to
+// the particles' own cell origins (FP32), plus whole-cell offsets.  A unit
+// whose runs do not fit the staging area reads its candidates from global
+// memory instead.  Units of instances that are done are skipped.
 template <bool COUNTS>
 __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const InteractArgs a) {
     extern __shared__ __align__(128) unsigned char s_raw[];
@@ -284,7 +305,6 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
     __shared__ int s_ok[9];
     __shared__ int s_mode;
-    __shared__ float s_rf[kIWarps][3];
     __shared__ uint32_t s_ru[kIWarps][4];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -292,30 +312,35 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     __syncthreads();
     const uint32_t nunits = *a.n_units;
     uint32_t phase = 0;
-    // CFL terms and counters over all units of this block
-    float t_am = 0.f, t_cm = 0.f, t_mm = 0.f;
-    uint32_t t_np = 0, t_nb = 0, t_nc = 0, t_bad = 0;
+    uint32_t t_np = 0, t_nb = 0, t_nc = 0, t_bad = 0;   // counters over this block's units
     for (uint32_t ui = blockIdx.x; ui < nunits; ui += gridDim.x) {
     const uint2 unit = a.units[ui];
     const uint32_t i0 = unit.x, i1 = unit.y;
     const uint32_t key0 = __ldg(a.key + i0);
-    const uint32_t row = key0 / (uint32_t)d.ncx;
-    const uint32_t rowbase = row * (uint32_t)d.ncx;
-    const int cy = (int)(row % (uint32_t)d.ncy), cz = (int)(row / (uint32_t)d.ncy);
+    const uint32_t q = find_instance(d.cell_base, d.n_inst, key0);
+    if (__ldg(d.is.done + q)) continue;             // block-uniform
+    const Inst& I = d.inst[q];
+    const int ncx = I.ncx, ncy = I.ncy, ncz = I.ncz;
+    const float c0 = I.c0;
+    const uint32_t lkey0 = key0 - I.cell_base;
+    const uint32_t lrow = lkey0 / (uint32_t)ncx;
+    const uint32_t rowbase = I.cell_base + lrow * (uint32_t)ncx;   // global label of (0, cy, cz)
+    const int cy = (int)(lrow % (uint32_t)ncy), cz = (int)(lrow / (uint32_t)ncy);
     const int xb = (int)(key0 - rowbase);
     const int xe = (int)(__ldg(a.key + i1 - 1) - rowbase);
     const int ulo = xb > 0 ? xb - 1 : 0;
-    const int uhi = xe + 1 < d.ncx ? xe + 1 : d.ncx - 1;
+    const int uhi = xe + 1 < ncx ? xe + 1 : ncx - 1;
     const int nce = uhi - ulo + 2;                 // offsets per neighbour row
     if (tid < 9) {
         const int yy = cy + tid % 3 - 1, zz = cz + tid / 3 - 1;
-        const bool ok = yy >= 0 && yy < d.ncy && zz >= 0 && zz < d.ncz;
+        const bool ok = yy >= 0 && yy < ncy && zz >= 0 && zz < ncz;
         s_ok[tid] = ok;
-        s_rb[tid] = ok ? (uint32_t)d.ncx * ((uint32_t)yy + (uint32_t)d.ncy * (uint32_t)zz) : 0u;
+        s_rb[tid] = ok ? I.cell_base + (uint32_t)ncx * ((uint32_t)yy + (uint32_t)ncy * (uint32_t)zz)
+                       : 0u;
     }
     __syncthreads();
-    for (int q = tid; q < 9 * nce; q += kIWarps * 32) {
-        const int r = q / nce, c = q - r * nce;
+    for (int r9 = tid; r9 < 9 * nce; r9 += kIWarps * 32) {
+        const int r = r9 / nce, c = r9 - r * nce;
         s_off[r][c] = s_ok[r] ? __ldg(a.off + s_rb[r] + ulo + c) : 0u;
     }
     __syncthreads();
@@ -350,42 +375,39 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
         pi = a.posc[i];
         vi = a.velrhop[i];
         cx = (int)(__ldg(a.key + i) - rowbase);
-        fluid = a.id[i] >= d.n_bound;
+        fluid = a.id[i] >= I.id_fluid;
     }
     const float rri = vi.w * d.inv_rho0;
-    const float ci = d.c0 * rri * rri * rri;
+    const float ci = c0 * rri * rri * rri;
     PairAcc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0u};
     uint32_t ncand = 0;
     __syncthreads();
     const bool staged = s_mode != 0;
-    bool failed = false;
     if (staged) {
         const bool got = mbar_wait_bounded(&s_bar, phase);
-        failed = __syncthreads_or(!got) != 0;
-        if (failed) {
+        if (__syncthreads_or(!got) != 0) {
             if (tid == 0) atomicOr(a.status, kStatusTimeout);
             mbar_wait_bounded(&s_bar, phase);   // let copies in flight land first
             break;
-        } else {
-            phase ^= 1u;
-            // shift the staged y, z into the frame of this unit's row
-            for (int r = 0; r < 9; ++r) {
-                const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
-                for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += kIWarps * 32) {
-                    s_p[k].y += oy;
-                    s_p[k].z += oz;
-                }
-            }
-            __syncthreads();
         }
+        phase ^= 1u;
+        // shift the staged y, z into the frame of this unit's row
+        for (int r = 0; r < 9; ++r) {
+            const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
+            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += kIWarps * 32) {
+                s_p[k].y += oy;
+                s_p[k].z += oz;
+            }
+        }
+        __syncthreads();
     }
 
     const uint32_t act = __ballot_sync(kFull, valid);
-    if (act && !failed) {
+    if (act) {
         const int wxmin = __reduce_min_sync(kFull, valid ? cx : 0x7fffffff);
         const int wxmax = __reduce_max_sync(kFull, valid ? cx : -1);
         const int xlo = wxmin > 0 ? wxmin - 1 : 0;
-        const int xhi = wxmax + 1 < d.ncx ? wxmax + 1 : d.ncx - 1;
+        const int xhi = wxmax + 1 < ncx ? wxmax + 1 : ncx - 1;
         uint32_t cnt = 0;
         if (staged) {
             uint16_t* lst = reinterpret_cast<uint16_t*>(s_v + kStage) + w * (kCap * 32) + lane;
@@ -405,14 +427,14 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                     const float4 p0 = s_p[j0], v0 = s_v[j0];
                     const float4 p1 = s_p[j1], v1 = s_v[j1];
                     if (anyfluid) {
-                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
+                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
                                          pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
-                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
+                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
                                          pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
                     } else {
-                        pair_terms<false>(d, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
+                        pair_terms<false>(d, c0, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
                                           pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
-                        pair_terms<false>(d, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
+                        pair_terms<false>(d, c0, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
                                           pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
                     }
                 }
@@ -434,18 +456,18 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = (uint32_t)(ox + 1) << 14;
                     const uint32_t e = sb + (ge - rs);
-                    for (uint32_t c0 = sb + (gs - rs); c0 < e; c0 += kCap) {
-                        const uint32_t c1 = (e - c0) > (uint32_t)kCap ? c0 + kCap : e;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0) > (uint32_t)kCap) flush();
+                    for (uint32_t c0i = sb + (gs - rs); c0i < e; c0i += kCap) {
+                        const uint32_t c1 = (e - c0i) > (uint32_t)kCap ? c0i + kCap : e;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kCap) flush();
                         uint16_t* lp = lst + cnt * 32;
-                        uint32_t j = c0;
+                        uint32_t j = c0i;
                         for (; j + 4 <= c1; j += 4) {
                             const float4 a0 = s_p[j], a1 = s_p[j + 1], a2 = s_p[j + 2],
                                          a3 = s_p[j + 3];
-                            float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
-                            float x1 = qx - a1.x, y1 = pi.y - a1.y, z1 = pi.z - a1.z;
-                            float x2 = qx - a2.x, y2 = pi.y - a2.y, z2 = pi.z - a2.z;
-                            float x3 = qx - a3.x, y3 = pi.y - a3.y, z3 = pi.z - a3.z;
+                            const float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
+                            const float x1 = qx - a1.x, y1 = pi.y - a1.y, z1 = pi.z - a1.z;
+                            const float x2 = qx - a2.x, y2 = pi.y - a2.y, z2 = pi.z - a2.z;
+                            const float x3 = qx - a3.x, y3 = pi.y - a3.y, z3 = pi.z - a3.z;
                             const uint32_t h0 = adj && fmaf(x0, x0, fmaf(y0, y0, z0 * z0)) < d.r2max;
                             const uint32_t h1 = adj && fmaf(x1, x1, fmaf(y1, y1, z1 * z1)) < d.r2max;
                             const uint32_t h2 = adj && fmaf(x2, x2, fmaf(y2, y2, z2 * z2)) < d.r2max;
@@ -486,7 +508,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                         const float oz = (float)((int)(e >> 30) - 1);
                         const float4 pj = __ldg(a.posc + j);
                         const float4 vj = __ldg(a.velrhop + j);
-                        pair_terms<true>(d, fluid, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
+                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
                                          fmaf(oy, d.csf, pi.y) - pj.y, fmaf(oz, d.csf, pi.z) - pj.z,
                                          pj, vj, acc);
                     }
@@ -508,11 +530,11 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                     if (gs == ge) continue;
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = code_yz | ((uint32_t)(ox + 1) << 26);
-                    for (uint32_t c0 = gs; c0 < ge; c0 += kCap) {
-                        const uint32_t c1 = (ge - c0) > (uint32_t)kCap ? c0 + kCap : ge;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0) > (uint32_t)kCap) flush();
+                    for (uint32_t c0i = gs; c0i < ge; c0i += kCap) {
+                        const uint32_t c1 = (ge - c0i) > (uint32_t)kCap ? c0i + kCap : ge;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kCap) flush();
 #pragma unroll 4
-                        for (uint32_t j = c0; j < c1; ++j) {
+                        for (uint32_t j = c0i; j < c1; ++j) {
                             const float4 pj = __ldg(a.posc + j);
                             const float dx = qx - pj.x, dy2 = qy - pj.y, dz2 = qz - pj.z;
                             const float d2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
@@ -532,15 +554,25 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     const float4 out =
         make_float4(fmaf(m, acc.ax, d.gx), fmaf(m, acc.ay, d.gy), fmaf(m, acc.az, d.gz), m * acc.dr);
     const uint32_t npairs = valid ? acc.np - 1u : 0u;   // without the pair (i, i)
-    if (valid && !failed) {
+    if (valid) {
         a.ace[i] = out;
         if (COUNTS) a.nnb[i] = npairs;
     }
+    // this instance's CFL maxima (non-negative floats order like their bits)
     float am = (valid && fluid) ? out.x * out.x + out.y * out.y + out.z * out.z : 0.f;
     if (!(am == am)) am = 0.f;
-    t_am = fmaxf(t_am, am);
-    t_cm = fmaxf(t_cm, valid ? ci : 0.f);
-    t_mm = fmaxf(t_mm, (valid && fluid) ? acc.mu : 0.f);
+    float cm = valid ? ci : 0.f;
+    float mm = (valid && fluid) ? acc.mu : 0.f;
+    for (int o = 16; o; o >>= 1) {
+        am = fmaxf(am, __shfl_xor_sync(kFull, am, o));
+        cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
+        mm = fmaxf(mm, __shfl_xor_sync(kFull, mm, o));
+    }
+    if (lane == 0 && act) {
+        atomicMax(d.is.terms + 3 * q + 0, __float_as_uint(am));
+        atomicMax(d.is.terms + 3 * q + 1, __float_as_uint(cm));
+        atomicMax(d.is.terms + 3 * q + 2, __float_as_uint(mm));
+    }
     t_bad |= (valid && !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) &&
                          isfinite(out.w)))
                  ? kStatusNonFinite
@@ -551,21 +583,14 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     __syncthreads();   // the next unit overwrites the shared staging
     }
 
-    float am = t_am, cm = t_cm, mm = t_mm;
     uint32_t np = t_np, nb = t_nb, nc = t_nc, bad = t_bad;
     for (int o = 16; o; o >>= 1) {
-        am = fmaxf(am, __shfl_xor_sync(kFull, am, o));
-        cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
-        mm = fmaxf(mm, __shfl_xor_sync(kFull, mm, o));
         np += __shfl_xor_sync(kFull, np, o);
         nb += __shfl_xor_sync(kFull, nb, o);
         nc += __shfl_xor_sync(kFull, nc, o);
         bad |= __shfl_xor_sync(kFull, bad, o);
     }
     if (lane == 0) {
-        s_rf[w][0] = am;
-        s_rf[w][1] = cm;
-        s_rf[w][2] = mm;
         s_ru[w][0] = np;
         s_ru[w][1] = nc;
         s_ru[w][2] = bad;
@@ -573,18 +598,13 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     }
     __syncthreads();
     if (tid == 0) {
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
         for (int k = 0; k < kIWarps; ++k) {
-            f.x = fmaxf(f.x, s_rf[k][0]);
-            f.y = fmaxf(f.y, s_rf[k][1]);
-            f.z = fmaxf(f.z, s_rf[k][2]);
             u.x += s_ru[k][0];
             u.y += s_ru[k][1];
             u.z |= s_ru[k][2];
             u.w += s_ru[k][3];
         }
-        a.part_f[blockIdx.x] = f;
         a.part_u[blockIdx.x] = u;
     }
 }
@@ -593,21 +613,23 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
 // a unit closes before a cell that lies more than 3 cells past the unit's
 // last non-empty cell (so no unit spans an empty stretch), when it would
 // reach kSpan cells, or when it holds kUnit particles.  One thread walks one
-// row; mode 0 counts the units of each row, mode 1 writes them at the row's
-// offset (uint2: first particle, end).
+// (global) row; mode 0 counts the units of each row, mode 1 writes them at
+// the row's offset (uint2: first particle, end).
 template <int MODE>
 __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __restrict__ off,
-                                               uint32_t nrows, uint32_t* __restrict__ ucnt,
+                                               uint32_t* __restrict__ ucnt,
                                                const uint32_t* __restrict__ uoff,
                                                uint2* __restrict__ units) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const uint32_t* o = off + (size_t)r * (uint32_t)d.ncx;
+    if (r >= d.nrows) return;
+    const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
+    const int ncx = I.ncx;
+    const uint32_t* o = off + I.cell_base + (size_t)(r - I.row_base) * (uint32_t)ncx;
     uint32_t n = 0, out = MODE ? uoff[r] : 0u;
     uint32_t start = 0xffffffffu;
     int lo = 0, last = 0;
     uint32_t a = o[0];
-    for (int x = 0; x < d.ncx; ++x) {
+    for (int x = 0; x < ncx; ++x) {
         const uint32_t b = o[x + 1];
         if (a != b) {
             if (start != 0xffffffffu && (x - last > 3 || x - lo >= kSpan)) {
@@ -636,44 +658,34 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
     if (!MODE) ucnt[r] = n;
 }
 
-// Sec. 3.3 reductions: per-block partials -> kReduceBlocks partials -> the
-// last block to finish combines them in block order and sets the step size
-// dt = CFL min( sqrt(h / max|a|), h / (max c + max mu) ).  Maxima and integer
-// sums do not depend on the order, so the result is deterministic.
+// Sec. 3.3 reductions.  The interaction leaves per-block counters (pairs,
+// candidates, status) and per-instance maxima; the last block to finish here
+// combines the counters in block order and, per instance,
+//   dt = CFL min( sqrt(h / max|a|), h / (max c + max mu) )
+// (0 for instances that are done), then clears the maxima for the next
+// evaluation.  Maxima and integer sums do not depend on the order.
 __global__ void __launch_bounds__(256) k_dt_reduce(const Dev d, const ReduceArgs a, int set_dt) {
-    __shared__ float s_f[8][3];
     __shared__ unsigned long long s_u[8][3];
     __shared__ uint32_t s_b[8];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float am = 0.f, cm = 0.f, mm = 0.f;
     unsigned long long pf = 0, pb = 0, nc = 0;
     uint32_t bad = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nparts;
          i += gridDim.x * blockDim.x) {
-        const float4 f = a.part_f[i];
         const uint4 u = a.part_u[i];
-        am = fmaxf(am, f.x);
-        cm = fmaxf(cm, f.y);
-        mm = fmaxf(mm, f.z);
         pf += u.x;
         nc += u.y;
         bad |= u.z;
         pb += u.w;
     }
     for (int o = 16; o; o >>= 1) {
-        am = fmaxf(am, __shfl_xor_sync(kFull, am, o));
-        cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
-        mm = fmaxf(mm, __shfl_xor_sync(kFull, mm, o));
         pf += __shfl_xor_sync(kFull, pf, o);
         pb += __shfl_xor_sync(kFull, pb, o);
         nc += __shfl_xor_sync(kFull, nc, o);
         bad |= __shfl_xor_sync(kFull, bad, o);
     }
     if (lane == 0) {
-        s_f[w][0] = am;
-        s_f[w][1] = cm;
-        s_f[w][2] = mm;
         s_u[w][0] = pf;
         s_u[w][1] = pb;
         s_u[w][2] = nc;
@@ -681,19 +693,14 @@ __global__ void __launch_bounds__(256) k_dt_reduce(const Dev d, const ReduceArgs
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned long long q0 = 0, q1 = 0, q2 = 0;
         uint32_t b = 0;
         for (int k = 0; k < 8; ++k) {
-            f.x = fmaxf(f.x, s_f[k][0]);
-            f.y = fmaxf(f.y, s_f[k][1]);
-            f.z = fmaxf(f.z, s_f[k][2]);
             q0 += s_u[k][0];
             q1 += s_u[k][1];
             q2 += s_u[k][2];
             b |= s_b[k];
         }
-        a.lvl2_f[blockIdx.x] = f;
         a.lvl2_q[4 * blockIdx.x + 0] = q0;
         a.lvl2_q[4 * blockIdx.x + 1] = q1;
         a.lvl2_q[4 * blockIdx.x + 2] = q2;
@@ -703,51 +710,60 @@ __global__ void __launch_bounds__(256) k_dt_reduce(const Dev d, const ReduceArgs
         s_last = ticket == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    float fa = 0.f, fc = 0.f, fm = 0.f;
-    unsigned long long qf = 0, qb = 0, qc = 0;
-    uint32_t b = 0;
-    for (uint32_t k = 0; k < gridDim.x; ++k) {
-        const float4 f = __ldcg(a.lvl2_f + k);
-        fa = fmaxf(fa, f.x);
-        fc = fmaxf(fc, f.y);
-        fm = fmaxf(fm, f.z);
-        qf += __ldcg(a.lvl2_q + 4 * k + 0);
-        qb += __ldcg(a.lvl2_q + 4 * k + 1);
-        qc += __ldcg(a.lvl2_q + 4 * k + 2);
-        b |= (uint32_t)__ldcg(a.lvl2_q + 4 * k + 3);
-    }
-    const double amax = sqrt((double)fa);
-    a.terms[0] = (float)amax;
-    a.terms[1] = fc;
-    a.terms[2] = fm;
-    a.counters[0] += qf + qb;
-    a.counters[1] += qc;
-    a.counters[2] = qf + qb;
-    a.counters[3] = qc;
-    a.counters[4] = qf;
-    a.counters[5] = qb;
-    a.counters[6] += qf;
-    a.counters[7] += qb;
-    if (b) atomicOr(a.status, b);
-    if (set_dt) {
-        double dt;
-        if (d.dt_fixed > 0.0) {
-            dt = d.dt_fixed;
-        } else {
-            const double dtf = amax > 0.0 ? sqrt(d.h_d / amax) : INFINITY;
-            const double dtc = d.h_d / ((double)fc + (double)fm);
-            dt = d.cfl * (dtf < dtc ? dtf : dtc);
+    if (threadIdx.x == 0) {
+        unsigned long long qf = 0, qb = 0, qc = 0;
+        uint32_t b = 0;
+        for (uint32_t k = 0; k < gridDim.x; ++k) {
+            qf += __ldcg(a.lvl2_q + 4 * k + 0);
+            qb += __ldcg(a.lvl2_q + 4 * k + 1);
+            qc += __ldcg(a.lvl2_q + 4 * k + 2);
+            b |= (uint32_t)__ldcg(a.lvl2_q + 4 * k + 3);
         }
-        *a.dt = dt;
+        a.counters[0] += qf + qb;
+        a.counters[1] += qc;
+        a.counters[2] = qf + qb;
+        a.counters[3] = qc;
+        a.counters[4] = qf;
+        a.counters[5] = qb;
+        a.counters[6] += qf;
+        a.counters[7] += qb;
+        if (b) atomicOr(a.status, b);
+        *a.done = 0u;
     }
-    *a.done = 0u;
+    for (uint32_t q = threadIdx.x; q < d.n_inst; q += blockDim.x) {
+        uint32_t* tm = d.is.terms + 3 * q;
+        const float fa = __uint_as_float(__ldcg(tm + 0));
+        const float fc = __uint_as_float(__ldcg(tm + 1));
+        const float fm = __uint_as_float(__ldcg(tm + 2));
+        const double amax = sqrt((double)fa);
+        if (set_dt) {
+            double dt = 0.0;
+            if (!d.is.done[q]) {
+                if (d.dt_fixed > 0.0) {
+                    dt = d.dt_fixed;
+                } else {
+                    const double dtf = amax > 0.0 ? sqrt(d.h_d / amax) : INFINITY;
+                    const double dtc = d.h_d / ((double)fc + (double)fm);
+                    dt = d.cfl * (dtf < dtc ? dtf : dtc);
+                }
+            }
+            d.is.dt[q] = dt;
+            d.is.last[3 * q + 0] = (float)amax;
+            d.is.last[3 * q + 1] = fc;
+            d.is.last[3 * q + 2] = fm;
+        }
+        tm[0] = 0u;
+        tm[1] = 0u;
+        tm[2] = 0u;
+    }
 }
 
 // Symplectic predictor (half step) for sorted particle k, then its new
 // label.  Boundary particles keep r and v (Sec. 2.3); excluded particles
-// (k >= in-domain count) are left untouched.
+// (k >= in-domain count) are left untouched.  Each particle uses its
+// instance's step size (0 once the instance is done).
 __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArgs a) {
     __shared__ uint32_t s_hist[4 * 256];
     zero_hist(s_hist);
@@ -756,17 +772,20 @@ __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArg
     uint32_t key = 0;
     if (valid) {
         const uint32_t n_in = a.off[d.ncells];
-        const double dt = *a.dt;
-        const float hdt = (float)(0.5 * dt);
         double x = a.x[k], y = a.y[k], z = a.z[k];
         float4 vr = a.velrhop[k];
         a.px[k] = x;
         a.py[k] = y;
         a.pz[k] = z;
         a.pvr[k] = vr;
+        key = d.ncells;
         if (k < n_in) {
+            const uint32_t id = a.id[k];
+            const uint32_t q = find_instance(d.id_base, d.n_inst, id);
+            const Inst& I = d.inst[q];
+            const float hdt = (float)(0.5 * d.is.dt[q]);
             const float4 ac = a.ace[k];
-            if (a.id[k] >= d.n_bound) {
+            if (id >= I.id_fluid) {
                 x += (double)(hdt * vr.x);
                 y += (double)(hdt * vr.y);
                 z += (double)(hdt * vr.z);
@@ -779,8 +798,8 @@ __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArg
             }
             vr.w = fmaf(hdt, ac.w, vr.w);
             a.velrhop[k] = vr;
+            key = cell_key(d, I, x, y, z);
         }
-        key = cell_key(d, x, y, z);
         a.key[k] = key;
     }
     count_key(valid, key, a.cnt, s_hist, a.passes, bits_for(d.ncells));
@@ -788,24 +807,29 @@ __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArg
 }
 
 // Symplectic corrector from the start state (pre arrays, reordered like the
-// current state) and the half-step rates, then the new label.
+// current state) and the half-step rates, then the new label.  Threads
+// k < n_inst also advance instance k's time and step count.
 __global__ void __launch_bounds__(256) k_correct(const Dev d, const IntegrateArgs a) {
     __shared__ uint32_t s_hist[4 * 256];
     zero_hist(s_hist);
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = k < d.n;
     uint32_t key = 0;
-    const double dt = *a.dt;
     if (valid) {
         const uint32_t n_in = a.off[d.ncells];
-        const float dtf = (float)dt;
-        const float hdt = (float)(0.5 * dt);
-        double x = a.x[k], y = a.y[k], z = a.z[k];
+        key = d.ncells;
         if (k < n_in) {
+            const uint32_t id = a.id[k];
+            const uint32_t q = find_instance(d.id_base, d.n_inst, id);
+            const Inst& I = d.inst[q];
+            const double dt = d.is.dt[q];
+            const float dtf = (float)dt;
+            const float hdt = (float)(0.5 * dt);
+            double x = a.x[k], y = a.y[k], z = a.z[k];
             const float4 ac = a.ace[k];
             const float4 pv = a.pvr[k];
             float4 vr = a.velrhop[k];
-            if (a.id[k] >= d.n_bound) {
+            if (id >= I.id_fluid) {
                 const float ux = fmaf(dtf, ac.x, pv.x);
                 const float uy = fmaf(dtf, ac.y, pv.y);
                 const float uz = fmaf(dtf, ac.z, pv.z);
@@ -822,13 +846,15 @@ __global__ void __launch_bounds__(256) k_correct(const Dev d, const IntegrateArg
             const float eps = -(ac.w * dtf) / vr.w;
             vr.w = pv.w * ((2.f - eps) / (2.f + eps));
             a.velrhop[k] = vr;
+            key = cell_key(d, I, x, y, z);
         }
-        key = cell_key(d, x, y, z);
         a.key[k] = key;
     }
-    if (k == 0) {
-        *a.t += dt;
-        *a.step += 1ull;
+    if (k < d.n_inst && !d.is.done[k]) {
+        const double t = d.is.t[k] + d.is.dt[k];
+        d.is.t[k] = t;
+        d.is.steps[k] += 1ull;
+        if (t >= d.inst[k].t_end) d.is.done[k] = 1u;
     }
     count_key(valid, key, a.cnt, s_hist, a.passes, bits_for(d.ncells));
     flush_hist(s_hist, a.hist, a.passes);
@@ -850,17 +876,20 @@ __global__ void __launch_bounds__(256) k_counts_fp64(const Dev d, const double* 
         return;
     }
     const uint32_t k = key[i];
-    const int cx = (int)(k % (uint32_t)d.ncx);
-    const uint32_t t = k / (uint32_t)d.ncx;
-    const int cy = (int)(t % (uint32_t)d.ncy), cz = (int)(t / (uint32_t)d.ncy);
+    const Inst& I = d.inst[find_instance(d.cell_base, d.n_inst, k)];
+    const uint32_t lk = k - I.cell_base;
+    const int cx = (int)(lk % (uint32_t)I.ncx);
+    const uint32_t t = lk / (uint32_t)I.ncx;
+    const int cy = (int)(t % (uint32_t)I.ncy), cz = (int)(t / (uint32_t)I.ncy);
     const double xi = x[i], yi = y[i], zi = z[i];
-    const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < d.ncx ? cx + 1 : d.ncx - 1;
+    const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < I.ncx ? cx + 1 : I.ncx - 1;
     uint32_t c = 0;
     for (int zz = cz - 1; zz <= cz + 1; ++zz) {
-        if (zz < 0 || zz >= d.ncz) continue;
+        if (zz < 0 || zz >= I.ncz) continue;
         for (int yy = cy - 1; yy <= cy + 1; ++yy) {
-            if (yy < 0 || yy >= d.ncy) continue;
-            const uint32_t rb = (uint32_t)d.ncx * ((uint32_t)yy + (uint32_t)d.ncy * zz);
+            if (yy < 0 || yy >= I.ncy) continue;
+            const uint32_t rb =
+                I.cell_base + (uint32_t)I.ncx * ((uint32_t)yy + (uint32_t)I.ncy * zz);
             const uint32_t s = off[rb + xlo], e = off[rb + xhi + 1];
             for (uint32_t j = s; j < e; ++j) {
                 if (j == i) continue;
@@ -890,19 +919,21 @@ __global__ void __launch_bounds__(256) k_diag_part(const Dev d, const double* __
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const double m = d.mass_d;
     const double rho0 = d.rho0_d;
-    const double B = d.B_d;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
         if (k >= n_in) {
             acc[7] += 1.0;
             continue;
         }
+        const uint32_t pid = id[k];
+        const Inst& I = d.inst[find_instance(d.id_base, d.n_inst, pid)];
         const float4 v = vr[k];
         const double rho = v.w;
+        const double B = (double)I.c0 * (double)I.c0 * rho0 / 7.0;
         acc[0] += m;
         // e(rho) = B [ ((rho/rho0)^6 - 1) / (6 rho0) + 1/rho - 1/rho0 ]
         const double rr = rho / rho0, r2 = rr * rr, r6 = r2 * r2 * r2;
         acc[6] += m * B * ((r6 - 1.0) / (6.0 * rho0) + 1.0 / rho - 1.0 / rho0);
-        if (id[k] >= d.n_bound) {
+        if (pid >= I.id_fluid) {
             acc[1] += m * v.x;
             acc[2] += m * v.y;
             acc[3] += m * v.z;
@@ -929,11 +960,14 @@ __global__ void k_diag_final(const double* __restrict__ part, int nparts, double
 
 inline uint32_t blocks_for(uint32_t n, uint32_t t) { return n ? (n + t - 1) / t : 1; }
 
+int g_interact_grid = 0;
+
 }  // namespace
 
-void launch_keys(const Dev& d, const double* x, const double* y, const double* z, uint32_t n,
-                 uint32_t* key, uint32_t* cnt, uint32_t* hist, int passes, cudaStream_t st) {
-    k_keys<<<blocks_for(n, 256), 256, 0, st>>>(d, x, y, z, n, key, cnt, hist, passes);
+void launch_keys(const Dev& d, const double* x, const double* y, const double* z,
+                 const uint32_t* id, uint32_t n, uint32_t* key, uint32_t* cnt, uint32_t* hist,
+                 int passes, cudaStream_t st) {
+    k_keys<<<blocks_for(n, 256), 256, 0, st>>>(d, x, y, z, id, n, key, cnt, hist, passes);
 }
 
 void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
@@ -944,12 +978,8 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
 // either holds kUnit particles or ends at a gap or at kSpan cells; a row of
 // ncx cells has at most ncx / 4 + 1 gap-separated stretches, each cut at most
 // ncx / kSpan + 1 more times.
-uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t ncx) {
-    return (n + kUnit - 1) / kUnit + nrows * (ncx / 4 + ncx / kSpan + 2);
-}
-
-namespace {
-int g_interact_grid = 0;
+uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx) {
+    return (n + kUnit - 1) / kUnit + nrows * (max_ncx / 4 + max_ncx / kSpan + 2);
 }
 
 // Persistent grid: every resident block of the interaction on this GPU.
@@ -978,10 +1008,9 @@ void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStrea
 
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
                   uint32_t* uoff, uint2* units, cudaStream_t st) {
-    const uint32_t nrows = (uint32_t)d.ncy * (uint32_t)d.ncz;
-    k_units<0><<<blocks_for(nrows, 128), 128, 0, st>>>(d, off, nrows, ucnt, uoff, units);
-    launch_scan(ucnt, nrows, ubsum, uoff, st);
-    k_units<1><<<blocks_for(nrows, 128), 128, 0, st>>>(d, off, nrows, ucnt, uoff, units);
+    k_units<0><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, ucnt, uoff, units);
+    launch_scan(ucnt, d.nrows, ubsum, uoff, st);
+    k_units<1><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, ucnt, uoff, units);
 }
 
 void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st) {
@@ -993,7 +1022,8 @@ void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
 }
 
 void launch_correct(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
-    k_correct<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
+    const uint32_t n = d.n > d.n_inst ? d.n : d.n_inst;
+    k_correct<<<blocks_for(n, 256), 256, 0, st>>>(d, a);
 }
 
 void launch_counts_fp64(const Dev& d, const double* x, const double* y, const double* z,

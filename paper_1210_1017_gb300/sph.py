@@ -34,7 +34,8 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells",
             "sph_neighbour_counts_fp64", "sph_diagnostics", "sph_check",
             "sph_kernels_per_step", "sph_last_error", "sph_destroy",
             "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
-            "sph_radix_sort_pairs_static"]
+            "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
+            "sph_instance_state"]
 
 
 class SphParams(C.Structure):
@@ -45,6 +46,11 @@ class SphParams(C.Structure):
                 ("dmin", C.c_double * 3), ("dmax", C.c_double * 3),
                 ("n_bound", C.c_uint32), ("reserved", C.c_uint32),
                 ("dt_fixed", C.c_double)]
+
+
+class SphInstance(C.Structure):
+    _fields_ = [("dmin", C.c_double * 3), ("dmax", C.c_double * 3), ("c0", C.c_double),
+                ("t_end", C.c_double), ("n_particles", C.c_uint32), ("n_bound", C.c_uint32)]
 
 
 class SphSizes(C.Structure):
@@ -127,6 +133,10 @@ def lib(build: bool = False):
     L.sph_radix_sort_scratch_bytes.restype = u64
     L.sph_radix_sort_pairs.argtypes = [vp, vp, vp, vp, u32, u32, vp, u64, vp]
     L.sph_radix_sort_pairs_static.argtypes = [vp, vp, vp, vp, u32, u32, vp]
+    PI = C.POINTER(SphInstance)
+    L.sph_query_sizes_batch.argtypes = [P, PI, u32, C.POINTER(SphSizes)]
+    L.sph_init_batch.argtypes = [P, PI, u32, vp, u64, vp, C.POINTER(vp)]
+    L.sph_instance_state.argtypes = [vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -180,6 +190,45 @@ def sph_init(params: SphParams, n: int, d_workspace: int, nbytes: int, stream: i
     _check(lib().sph_init(C.byref(params), n, d_workspace, nbytes, stream, C.byref(ctx)),
            what="sph_init")
     return ctx
+
+
+def make_instances(members) -> "C.Array":
+    """members: sequence of dicts with dmin, dmax, c0, n_particles, n_bound
+    and optionally t_end (default: never stops)."""
+    arr = (SphInstance * len(members))()
+    for k, m in enumerate(members):
+        for a in range(3):
+            arr[k].dmin[a] = m["dmin"][a]
+            arr[k].dmax[a] = m["dmax"][a]
+        arr[k].c0 = m["c0"]
+        arr[k].t_end = float(m.get("t_end", float("inf")))
+        arr[k].n_particles = int(m["n_particles"])
+        arr[k].n_bound = int(m["n_bound"])
+    return arr
+
+
+def sph_query_sizes_batch(params: SphParams, inst) -> SphSizes:
+    out = SphSizes()
+    _check(lib().sph_query_sizes_batch(C.byref(params), inst, len(inst), C.byref(out)),
+           what="sph_query_sizes_batch")
+    return out
+
+
+def sph_init_batch(params: SphParams, inst, d_workspace: int, nbytes: int, stream: int):
+    ctx = C.c_void_p()
+    _check(lib().sph_init_batch(C.byref(params), inst, len(inst), d_workspace, nbytes, stream,
+                                C.byref(ctx)), what="sph_init_batch")
+    return ctx
+
+
+def sph_instance_state(ctx, n_inst: int):
+    t = np.zeros(n_inst, np.float64)
+    dt = np.zeros(n_inst, np.float64)
+    done = np.zeros(n_inst, np.uint32)
+    steps = np.zeros(n_inst, np.uint64)
+    _check(lib().sph_instance_state(ctx, _ptr(t), _ptr(dt), _ptr(done), _ptr(steps)), ctx,
+           "sph_instance_state")
+    return dict(t=t, dt=dt, done=done.astype(bool), steps=steps)
 
 
 def sph_upload(ctx, pos, vel, rho, ids):
@@ -271,7 +320,7 @@ class Simulation:
     """
 
     def __init__(self, params: dict, n: int, device: int = 0, stream=None,
-                 dt_fixed: float = 0.0):
+                 dt_fixed: float = 0.0, members=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the SPH hot path needs a CUDA GPU")
@@ -280,18 +329,37 @@ class Simulation:
         self.n = int(n)
         self.params = dict(params)
         self.P = make_params(params, dt_fixed)
-        self.sizes = sph_query_sizes(self.P, self.n)
+        self.members = make_instances(members) if members is not None else None
+        self.n_inst = len(members) if members is not None else 1
+        if self.members is not None:
+            self.sizes = sph_query_sizes_batch(self.P, self.members)
+        else:
+            self.sizes = sph_query_sizes(self.P, self.n)
         self.workspace = torch.empty(int(self.sizes.workspace_bytes), dtype=torch.uint8,
                                      device=self.device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.ctx = sph_init(self.P, self.n, self.workspace.data_ptr(),
-                            int(self.sizes.workspace_bytes), self.stream.cuda_stream)
+        if self.members is not None:
+            self.ctx = sph_init_batch(self.P, self.members, self.workspace.data_ptr(),
+                                      int(self.sizes.workspace_bytes), self.stream.cuda_stream)
+        else:
+            self.ctx = sph_init(self.P, self.n, self.workspace.data_ptr(),
+                                int(self.sizes.workspace_bytes), self.stream.cuda_stream)
 
     @classmethod
     def from_case(cls, case, **kw):
         sim = cls(case.params(), case.n, **kw)
         sim.upload(case.pos, case.vel, case.rho, case.ids)
         return sim
+
+    @classmethod
+    def from_ensemble(cls, ens, **kw):
+        """An ensemble built by cases.ensemble (members run in lockstep)."""
+        sim = cls(ens.params, ens.n, members=ens.members, **kw)
+        sim.upload(ens.pos, ens.vel, ens.rho, ens.ids)
+        return sim
+
+    def instance_state(self):
+        return sph_instance_state(self.ctx, self.n_inst)
 
     def upload(self, pos, vel, rho, ids):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
@@ -340,7 +408,7 @@ class Simulation:
                   SPH_ARRAY_CELL_OFF: ((int(self.sizes.ncells) + 2,), np.uint32),
                   SPH_ARRAY_ACE: ((n, 4), np.float32), SPH_ARRAY_NNB: ((n,), np.uint32),
                   SPH_ARRAY_NNB64: ((n,), np.uint32), SPH_ARRAY_POSC: ((n, 4), np.float32),
-                  SPH_ARRAY_DT: ((1,), np.float64)}
+                  SPH_ARRAY_DT: ((self.n_inst,), np.float64)}
         shape, dt = shapes[which]
         return sph_read_array(self.ctx, which, np.empty(shape, dt))
 
