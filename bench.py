@@ -39,6 +39,9 @@ FLOP_CANDIDATE, FLOP_FLUID_PAIR, FLOP_BOUNDARY_PAIR = 8, 50, 12
 SMS, FP32_LANES, MAX_CLOCK_GHZ = 152, 128, 2.07
 
 
+WORKLOADS = ("dam_break_32m", "dam_break_obstacles_1m", "dam_break_6k", "dam_break_ensemble_256")
+
+
 def workload(name):
     from paper_1210_1017_gb300 import cases
     if name == "dam_break_32m":
@@ -47,7 +50,13 @@ def workload(name):
         return cases.c2_dam_break_obstacles()
     if name == "dam_break_6k":
         return cases.c1_dam_break()
+    if name == "dam_break_ensemble_256":
+        return cases.dam_break_ensemble(256, t_end=1.0)
     raise SystemExit(f"unknown workload {name}")
+
+
+def is_ensemble(w):
+    return hasattr(w, "members")
 
 
 def peaks():
@@ -147,6 +156,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     case = workload(args.workload)
+    if is_ensemble(case):
+        case = case.cases[0]
     import oracle
     O = oracle.Oracle(case.params())
     st = oracle.State.from_case(case)
@@ -193,9 +204,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     S.lib(build=True)
     case = workload(args.workload)
-    sim = S.Simulation.from_case(case, device=local)
+    if is_ensemble(case):
+        sim = S.Simulation.from_ensemble(case, device=local)
+    else:
+        sim = S.Simulation.from_case(case, device=local)
     stream = sim.stream
     sim.build_cells()
+    variant, variant_ms = sim.autotune(reps=3, cache=False)
     for _ in range(args.warmup):
         sim.step(1)
     sim.synchronize()
@@ -261,7 +276,7 @@ def run_ours(args):
         with open(prof) as f:
             tr = json.load(f)
         if tr.get("kernel_rev") == S.KERNEL_REV:
-            traffic = tr.get("bytes_per_launch", {}).get(case.name)
+            traffic = tr.get("bytes_per_launch", {}).get(args.workload)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
                 "kernel": "k_interact", "ms_per_launch": round(t_int * 1e3, 4),
@@ -269,10 +284,15 @@ def run_ours(args):
 
     # --- end to end through the C ABI with pinned host buffers ---------------
     n = case.n
-    pin = dict(pos=torch.from_numpy(case.pos.copy()).pin_memory(),
-               vel=torch.from_numpy(case.vel.copy()).pin_memory(),
-               rho=torch.from_numpy(case.rho.copy()).pin_memory(),
-               ids=torch.from_numpy(case.ids.view(np.int32).copy()).pin_memory())
+    if is_ensemble(case):
+        st0 = sim.download()   # resume point: the e2e steps restart from here
+        case_pos, case_vel, case_rho, case_ids = st0["pos"], st0["vel"], st0["rho"], st0["ids"]
+    else:
+        case_pos, case_vel, case_rho, case_ids = case.pos, case.vel, case.rho, case.ids
+    pin = dict(pos=torch.from_numpy(np.ascontiguousarray(case_pos)).pin_memory(),
+               vel=torch.from_numpy(np.ascontiguousarray(case_vel)).pin_memory(),
+               rho=torch.from_numpy(np.ascontiguousarray(case_rho)).pin_memory(),
+               ids=torch.from_numpy(np.ascontiguousarray(case_ids).view(np.int32)).pin_memory())
     out = dict(pos=torch.empty((n, 3), dtype=torch.float64).pin_memory(),
                vel=torch.empty((n, 3), dtype=torch.float32).pin_memory(),
                rho=torch.empty(n, dtype=torch.float32).pin_memory(),
@@ -295,19 +315,30 @@ def run_ours(args):
            "note": "per step: sph_upload (pinned host) + sph_step(1) + sph_download (pinned host)"}
 
     kps = sim.kernels_per_step()
+    if is_ensemble(case):
+        ist = sim.instance_state()
+        cfg = {"workload": args.workload, "members": len(case.members), "n_particles": case.n,
+               "member_sizes": [int(min(c.n for c in case.cases)), int(max(c.n for c in case.cases))],
+               "dp": case.params["dp"], "t_end": 1.0,
+               "members_done_after_run": int(ist["done"].sum())}
+        base_case = case.cases[0]
+    else:
+        cfg = {"workload": case.name, "n_particles": case.n, "n_fluid": case.n_fluid,
+               "n_boundary": case.n_bound, "dp": case.dp}
+        base_case = case
+    cfg.update({"kernel": "Wendland C2, h=1.3dp", "integrator": "symplectic, 2 evaluations/step",
+                "position_dtype": "f64", "l2": "inputs larger than L2",
+                "parallelism": f"replicas x{ws}", "interaction_variant": variant,
+                "variant_ms": [round(float(v), 3) for v in variant_ms]})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": case.name, "n_particles": case.n, "n_fluid": case.n_fluid,
-                       "n_boundary": case.n_bound, "dp": case.dp,
-                       "kernel": "Wendland C2, h=1.3dp", "integrator": "symplectic, 2 evaluations/step",
-                       "position_dtype": "f64", "l2": "inputs larger than L2 (state ~9 GB)",
-                       "parallelism": f"replicas x{ws}"},
+            "dtype": "f32", "data": "synthetic", "config": cfg,
             "steps_per_s": steps_per_s, "pairs_per_step": pairs / args.steps,
             "fluid_pairs_per_step": pf / args.steps, "boundary_pairs_per_step": pb / args.steps,
             "candidates_per_step": cand / args.steps,
             "sim_time_per_step": (d1["t"] - d0["t"]) / args.steps,
+            "member_steps_per_s": steps_per_s * getattr(sim, "n_inst", 1),
             "roofline": roofline, "e2e": e2e, "gpu_launches": kps * args.steps,
             "clocks": clocks}
     pk, src = peaks()
@@ -316,7 +347,7 @@ def run_ours(args):
         sim.close()
         del sim
         torch.cuda.empty_cache()
-        line["cpu_baseline"] = cpu_baseline(case)
+        line["cpu_baseline"] = cpu_baseline(base_case)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -330,7 +361,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dam_break_32m")
+    ap.add_argument("--workload", default="dam_break_32m", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -248,6 +248,21 @@ int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
 /* Map the device status word to an error code (SPH_OK if clear).  Sync. */
 int sph_check(sph_ctx *ctx);
 
+/* Block shapes of the interaction kernel ("variants": particles per work
+ * unit, staged candidates per unit, neighbour-list slots per lane) and the
+ * autotuner that picks one.  Results do not depend on the variant beyond
+ * FP32 summation order within a particle's own sum, which is the same for
+ * every variant (each particle sums its neighbours in the sorted order).
+ * sph_autotune times `reps` interaction launches of every variant on the
+ * current cells (CUDA events on the context's stream), selects the fastest
+ * and writes the per-variant milliseconds to ms_per_variant (NULL allowed,
+ * else sph_num_variants() floats).  It leaves the state and step size
+ * untouched.  Sync. */
+uint32_t sph_num_variants(void);
+int sph_set_variant(sph_ctx *ctx, uint32_t variant);
+int sph_autotune(sph_ctx *ctx, uint32_t reps, float *ms_per_variant,
+                 uint32_t *best);
+
 /* Number of kernels one sph_step(ctx, 1) launches. */
 uint32_t sph_kernels_per_step(const sph_ctx *ctx);
 

@@ -117,6 +117,7 @@ struct sph_ctx {
     float* i_last;
     size_t os_bytes = 0;
     // bookkeeping
+    int variant = 0;         // interaction block shape (see sph_autotune)
     int cur = 0;             // state buffer index
     int skey = 0;            // key/val buffer holding the last sort result
     bool have_state = false;
@@ -303,6 +304,8 @@ Dev make_dev(const sph_ctx* c) {
     d.nrows = (uint32_t)c->tab.nrows;
     d.n = c->n;
     d.max_ncx = c->tab.max_ncx;
+    d.variant = c->variant;
+    d.unit = variant_unit(c->variant);
     d.csf = (float)cs;
     d.h = (float)p->h;
     d.inv_h = (float)(1.0 / p->h);
@@ -487,11 +490,13 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
     }
     c->tiles = os_tiles(c->n);
     prepare_interact();
-    c->nparts = interact_grid();
-    if (c->nparts == 0 || c->nparts > kMaxGridBlocks) {
-        delete c;
-        return SPH_ERR_CUDA;
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (interact_grid(v) == 0 || interact_grid(v) > kMaxGridBlocks) {
+            delete c;
+            return SPH_ERR_CUDA;
+        }
     }
+    c->nparts = interact_grid(c->variant);
     c->d = make_dev(c);
     cudaStream_t st = c->st;
     cudaMemcpyAsync(c->d_inst, c->tab.inst.data(), n_inst * sizeof(Inst), cudaMemcpyHostToDevice, st);
@@ -803,6 +808,71 @@ int sph_check(sph_ctx* c) {
     if (status & SPH_STATUS_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite interaction result");
     if (status & SPH_STATUS_CAPACITY) return fail(c, SPH_ERR_CAPACITY, "a cell exceeded the id tie-break capacity");
     return SPH_OK;
+}
+
+uint32_t sph_num_variants(void) { return (uint32_t)kNumVariants; }
+
+int sph_set_variant(sph_ctx* c, uint32_t v) {
+    if (!c || v >= (uint32_t)kNumVariants) return fail(c, SPH_ERR_INVALID_ARG, "bad variant");
+    if ((int)v == c->variant) return SPH_OK;
+    c->variant = (int)v;
+    c->nparts = interact_grid(c->variant);
+    c->d = make_dev(c);
+    for (int g = 0; g < 2; ++g) {
+        if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
+        c->graph[g] = nullptr;
+    }
+    // the work units depend on the block shape: recut them for the current cells
+    if (c->cells_valid) launch_units(c->d, c->off, c->ucnt, c->ubsum, c->uoff, c->units, c->st);
+    return post_launch(c, "set variant");
+}
+
+int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* best) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
+    if (reps == 0) reps = 3;
+    const int start = c->variant;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = INFINITY;
+    int best_v = start;
+    for (int v = 0; v < kNumVariants; ++v) {
+        int rc = sph_set_variant(c, (uint32_t)v);
+        if (rc) return rc;
+        InteractArgs ia;
+        ia.units = c->units;
+        ia.n_units = c->uoff + c->tab.nrows;
+        ia.status = c->status;
+        ia.posc = c->posc;
+        ia.velrhop = c->vr[c->cur];
+        ia.key = c->key[c->skey];
+        ia.id = c->id[c->cur];
+        ia.off = c->off;
+        ia.ace = c->ace;
+        ia.nnb = c->nnb;
+        ia.part_u = c->part_u;
+        launch_interact(c->d, ia, false, c->st);   // warm
+        cudaEventRecord(e0, c->st);
+        for (uint32_t r = 0; r < reps; ++r) launch_interact(c->d, ia, false, c->st);
+        cudaEventRecord(e1, c->st);
+        rc = cuda_check(c, cudaEventSynchronize(e1), "autotune");
+        if (rc) return rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (ms_per_variant) ms_per_variant[v] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing launches left running maxima behind; clear them
+    cudaMemsetAsync(c->i_terms, 0, 3 * (size_t)c->n_inst * sizeof(uint32_t), c->st);
+    if (best) *best = (uint32_t)best_v;
+    return sph_set_variant(c, (uint32_t)best_v);
 }
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {

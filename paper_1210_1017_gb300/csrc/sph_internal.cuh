@@ -64,6 +64,8 @@ struct Dev {
     uint32_t nrows;        // all instances' rows of cells
     uint32_t n;
     int max_ncx;
+    int variant;           // interaction variant (block shape) in use
+    int unit;              // its unit size in particles
     float csf;             // 2h
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
@@ -115,10 +117,12 @@ struct ReorderArgs {
 };
 void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 
-// Interaction work unit: up to kUnit consecutive particles of one row of
-// cells spanning at most kSpan cells (uint2: first particle, end).
-constexpr int kUnit = 128;
+// Interaction work unit: up to `unit` consecutive particles of one row of
+// cells spanning at most kSpan cells (uint2: first particle, end).  The unit
+// size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
+constexpr int kMinUnit = 64;
+constexpr int kNumVariants = 4;
 
 struct InteractArgs {
     const uint2* units;
@@ -135,7 +139,8 @@ struct InteractArgs {
                           // status bits, boundary-i pairs
 };
 uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx);   // bound on units
-uint32_t interact_grid();   // blocks of the persistent interaction launch
+int variant_unit(int variant);               // particles per unit of a variant
+uint32_t interact_grid(int variant);         // blocks of its persistent launch
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
                   uint32_t* uoff, uint2* units, cudaStream_t st);
 // Once per context (current device): opt in to the shared memory and size

@@ -192,18 +192,22 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
 
 // ----------------------------------------------------------- interaction --
 
-constexpr int kIWarps = kUnit / 32;   // warps per block (one work unit)
-constexpr int kCap = 96;              // neighbour-list slots per lane
-constexpr int kStage = 2048;          // staged candidates per unit
 constexpr uint32_t kIdxMask = (1u << 26) - 1;
-// dynamic shared memory: staged posc and velrhop (kStage float4 each), then
-// the per-lane lists (16-bit entries); the fallback path reuses the staging
-// area for 32-bit list entries
-constexpr size_t kInteractSmem =
-    (size_t)kStage * 2 * sizeof(float4) + (size_t)kIWarps * kCap * 32 * sizeof(uint16_t);
-static_assert((size_t)kIWarps * kCap * 32 * sizeof(uint32_t) <= (size_t)kStage * 2 * sizeof(float4),
-              "fallback lists must fit in the staging area");
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+// Shape of one interaction variant: W warps per block (units of W*32
+// particles), STAGE staged candidates, CAP list slots per lane.  Dynamic
+// shared memory: staged posc and velrhop (STAGE float4 each), then the 16-bit
+// per-lane lists; the global-memory fallback reuses the staging area for
+// 32-bit list entries.
+template <int W, int STAGE, int CAP>
+struct Shape {
+    static constexpr size_t smem =
+        (size_t)STAGE * 2 * sizeof(float4) + (size_t)W * CAP * 32 * sizeof(uint16_t);
+    static_assert((size_t)W * CAP * 32 * sizeof(uint32_t) <= (size_t)STAGE * 2 * sizeof(float4),
+                  "fallback lists must fit in the staging area");
+    static_assert(STAGE <= (1 << 14), "staged index must fit 14 bits");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -281,7 +285,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
     }
 }
 
-// Sec. 3.2.  One block takes work units in turn: up to kUnit consecutive
+// Sec. 3.2.  One block takes work units in turn: up to W*32 consecutive
 // sorted particles of one row of cells (same instance, cy, cz) spanning at
 // most kSpan cells with no more than two empty cells in a row, so the
 // candidates of all of them lie in 9 contiguous, compact runs of the sorted
@@ -295,17 +299,17 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
 // the particles' own cell origins (FP32), plus whole-cell offsets.  A unit
 // whose runs do not fit the staging area reads its candidates from global
 // memory instead.  Units of instances that are done are skipped.
-template <bool COUNTS>
-__global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const InteractArgs a) {
+template <int W, int STAGE, int CAP, int MINB, bool COUNTS>
+__global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     extern __shared__ __align__(128) unsigned char s_raw[];
     float4* s_p = reinterpret_cast<float4*>(s_raw);
-    float4* s_v = s_p + kStage;
+    float4* s_v = s_p + STAGE;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_rs[9], s_rb[9], s_len[9], s_base[10];
     __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
     __shared__ int s_ok[9];
     __shared__ int s_mode;
-    __shared__ uint32_t s_ru[kIWarps][4];
+    __shared__ uint32_t s_ru[W][4];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) mbar_init(&s_bar, 1);
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                        : 0u;
     }
     __syncthreads();
-    for (int r9 = tid; r9 < 9 * nce; r9 += kIWarps * 32) {
+    for (int r9 = tid; r9 < 9 * nce; r9 += W * 32) {
         const int r = r9 / nce, c = r9 - r * nce;
         s_off[r][c] = s_ok[r] ? __ldg(a.off + s_rb[r] + ulo + c) : 0u;
     }
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
             acc += s_len[r];
         }
         s_base[9] = acc;
-        const int mode = acc <= (uint32_t)kStage;
+        const int mode = acc <= (uint32_t)STAGE;
         s_mode = mode;
         if (mode) {
             mbar_expect_tx(&s_bar, acc * 2u * (uint32_t)sizeof(float4));
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
         // shift the staged y, z into the frame of this unit's row
         for (int r = 0; r < 9; ++r) {
             const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
-            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += kIWarps * 32) {
+            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += W * 32) {
                 s_p[k].y += oy;
                 s_p[k].z += oz;
             }
@@ -410,7 +414,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
         const int xhi = wxmax + 1 < ncx ? wxmax + 1 : ncx - 1;
         uint32_t cnt = 0;
         if (staged) {
-            uint16_t* lst = reinterpret_cast<uint16_t*>(s_v + kStage) + w * (kCap * 32) + lane;
+            uint16_t* lst = reinterpret_cast<uint16_t*>(s_v + STAGE) + w * (CAP * 32) + lane;
             const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
             const uint32_t selfe = self | (1u << 14);      // the pair (i, i), x offset 0
             const bool anyfluid = __any_sync(kFull, fluid);
@@ -456,9 +460,9 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = (uint32_t)(ox + 1) << 14;
                     const uint32_t e = sb + (ge - rs);
-                    for (uint32_t c0i = sb + (gs - rs); c0i < e; c0i += kCap) {
-                        const uint32_t c1 = (e - c0i) > (uint32_t)kCap ? c0i + kCap : e;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kCap) flush();
+                    for (uint32_t c0i = sb + (gs - rs); c0i < e; c0i += CAP) {
+                        const uint32_t c1 = (e - c0i) > (uint32_t)CAP ? c0i + CAP : e;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)CAP) flush();
                         uint16_t* lp = lst + cnt * 32;
                         uint32_t j = c0i;
                         for (; j + 4 <= c1; j += 4) {
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
             flush();
         } else {
             // candidates straight from global memory (unit too large to stage)
-            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (kCap * 32);
+            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (CAP * 32);
             auto flush = [&]() {
                 const uint32_t mx = __reduce_max_sync(kFull, cnt);
                 for (uint32_t t = 0; t < mx; ++t) {
@@ -530,9 +534,9 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
                     if (gs == ge) continue;
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = code_yz | ((uint32_t)(ox + 1) << 26);
-                    for (uint32_t c0i = gs; c0i < ge; c0i += kCap) {
-                        const uint32_t c1 = (ge - c0i) > (uint32_t)kCap ? c0i + kCap : ge;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kCap) flush();
+                    for (uint32_t c0i = gs; c0i < ge; c0i += CAP) {
+                        const uint32_t c1 = (ge - c0i) > (uint32_t)CAP ? c0i + CAP : ge;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)CAP) flush();
 #pragma unroll 4
                         for (uint32_t j = c0i; j < c1; ++j) {
                             const float4 pj = __ldg(a.posc + j);
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
     __syncthreads();
     if (tid == 0) {
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
-        for (int k = 0; k < kIWarps; ++k) {
+        for (int k = 0; k < W; ++k) {
             u.x += s_ru[k][0];
             u.y += s_ru[k][1];
             u.z |= s_ru[k][2];
@@ -612,7 +616,8 @@ __global__ void __launch_bounds__(kIWarps * 32, 2) k_interact(const Dev d, const
 // Work units.  A row of cells is cut into units of consecutive particles:
 // a unit closes before a cell that lies more than 3 cells past the unit's
 // last non-empty cell (so no unit spans an empty stretch), when it would
-// reach kSpan cells, or when it holds kUnit particles.  One thread walks one
+// reach kSpan cells, or when it holds d.unit particles (the block size of the
+// interaction variant in use).  One thread walks one
 // (global) row; mode 0 counts the units of each row, mode 1 writes them at
 // the row's offset (uint2: first particle, end).
 template <int MODE>
@@ -642,10 +647,10 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
                 lo = x;
             }
             last = x;
-            while (b - start > (uint32_t)kUnit) {
-                if (MODE) units[out + n] = make_uint2(start, start + kUnit);
+            while (b - start > (uint32_t)d.unit) {
+                if (MODE) units[out + n] = make_uint2(start, start + d.unit);
                 ++n;
-                start += kUnit;
+                start += d.unit;
                 lo = x;
             }
         }
@@ -960,8 +965,6 @@ __global__ void k_diag_final(const double* __restrict__ part, int nparts, double
 
 inline uint32_t blocks_for(uint32_t n, uint32_t t) { return n ? (n + t - 1) / t : 1; }
 
-int g_interact_grid = 0;
-
 }  // namespace
 
 void launch_keys(const Dev& d, const double* x, const double* y, const double* z,
@@ -975,35 +978,62 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
 }
 
 // Upper bound on the number of units: every unit but the last of its row
-// either holds kUnit particles or ends at a gap or at kSpan cells; a row of
-// ncx cells has at most ncx / 4 + 1 gap-separated stretches, each cut at most
-// ncx / kSpan + 1 more times.
+// either holds the unit size (at least kMinUnit) or ends at a gap or at kSpan
+// cells; a row of ncx cells has at most ncx / 4 + 1 gap-separated stretches,
+// each cut at most ncx / kSpan + 1 more times.
 uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx) {
-    return (n + kUnit - 1) / kUnit + nrows * (max_ncx / 4 + max_ncx / kSpan + 2);
+    return (n + kMinUnit - 1) / kMinUnit + nrows * (max_ncx / 4 + max_ncx / kSpan + 2);
 }
 
-// Persistent grid: every resident block of the interaction on this GPU.
-uint32_t interact_grid() { return (uint32_t)g_interact_grid; }
+namespace {
+
+using KernelPtr = void (*)(const Dev, const InteractArgs);
+
+struct Variant {
+    int warps;
+    KernelPtr plain, counted;
+    size_t smem;
+    int grid;   // persistent grid on this GPU (set by prepare_interact)
+};
+
+// (warps, staged candidates, list slots, resident blocks per SM that the
+// shared memory allows -- also the register budget hint)
+#define SPH_VARIANT(Wv, Sv, Cv, Bv)                                                    \
+    Variant {                                                                         \
+        Wv, k_interact<Wv, Sv, Cv, Bv, false>, k_interact<Wv, Sv, Cv, Bv, true>,      \
+            Shape<Wv, Sv, Cv>::smem, 0                                                \
+    }
+
+Variant g_variants[kNumVariants] = {
+    SPH_VARIANT(4, 2048, 96, 2),   // 128-particle units
+    SPH_VARIANT(2, 1280, 96, 4),   // 64-particle units
+    SPH_VARIANT(3, 1536, 64, 3),   // 96-particle units
+    SPH_VARIANT(8, 3072, 80, 1),   // 256-particle units
+};
+
+}  // namespace
+
+int variant_unit(int v) { return g_variants[v].warps * 32; }
+
+// Persistent grid: every resident block of the variant on this GPU.
+uint32_t interact_grid(int v) { return (uint32_t)g_variants[v].grid; }
 
 void prepare_interact() {
-    cudaFuncSetAttribute(k_interact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kInteractSmem);
-    cudaFuncSetAttribute(k_interact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kInteractSmem);
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact<false>, kIWarps * 32,
-                                                  kInteractSmem);
-    g_interact_grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    for (Variant& v : g_variants) {
+        cudaFuncSetAttribute(v.plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        cudaFuncSetAttribute(v.counted, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.plain, v.warps * 32, v.smem);
+        v.grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
 }
 
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st) {
-    const uint32_t nb = interact_grid();
-    if (counts)
-        k_interact<true><<<nb, kIWarps * 32, kInteractSmem, st>>>(d, a);
-    else
-        k_interact<false><<<nb, kIWarps * 32, kInteractSmem, st>>>(d, a);
+    const Variant& v = g_variants[d.variant];
+    (counts ? v.counted : v.plain)<<<v.grid, v.warps * 32, v.smem, st>>>(d, a);
 }
 
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,

@@ -35,7 +35,7 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells",
             "sph_kernels_per_step", "sph_last_error", "sph_destroy",
             "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
             "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
-            "sph_instance_state"]
+            "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune"]
 
 
 class SphParams(C.Structure):
@@ -137,6 +137,10 @@ def lib(build: bool = False):
     L.sph_query_sizes_batch.argtypes = [P, PI, u32, C.POINTER(SphSizes)]
     L.sph_init_batch.argtypes = [P, PI, u32, vp, u64, vp, C.POINTER(vp)]
     L.sph_instance_state.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_num_variants.argtypes = []
+    L.sph_num_variants.restype = u32
+    L.sph_set_variant.argtypes = [vp, u32]
+    L.sph_autotune.argtypes = [vp, u32, vp, vp]
     _lib = L
     return L
 
@@ -231,6 +235,23 @@ def sph_instance_state(ctx, n_inst: int):
     return dict(t=t, dt=dt, done=done.astype(bool), steps=steps)
 
 
+def sph_num_variants() -> int:
+    return int(lib().sph_num_variants())
+
+
+def sph_set_variant(ctx, v: int):
+    _check(lib().sph_set_variant(ctx, v), ctx, "sph_set_variant")
+
+
+def sph_autotune(ctx, reps: int = 3):
+    """Times every interaction variant on the current cells and selects the
+    fastest; returns (best, milliseconds per variant)."""
+    ms = np.zeros(sph_num_variants(), np.float32)
+    best = np.zeros(1, np.uint32)
+    _check(lib().sph_autotune(ctx, reps, _ptr(ms), _ptr(best)), ctx, "sph_autotune")
+    return int(best[0]), ms
+
+
 def sph_upload(ctx, pos, vel, rho, ids):
     _check(lib().sph_upload(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx, "sph_upload")
 
@@ -309,6 +330,41 @@ def sph_radix_sort_pairs_static(keys_in, vals_in, keys_out, vals_out, n, key_bit
            what="sph_radix_sort_pairs_static")
 
 
+# --- autotuner cache ----------------------------------------------------------
+
+def _cache_path():
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "paper_1210_1017_gb300", "autotune.json")
+
+
+def autotune_cached(sim, reps=3):
+    """Autotune once per (GPU, size bucket, member count) and reuse the choice."""
+    import json
+    import math
+    name = sim.torch.cuda.get_device_name(sim.device)
+    key = f"{name}|{KERNEL_REV}|n2^{int(math.log2(max(sim.n, 1)))}|m{sim.n_inst}"
+    path = _cache_path()
+    table = {}
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        table = {}
+    if key in table:
+        sim.set_variant(int(table[key]["variant"]))
+        return int(table[key]["variant"]), np.array(table[key]["ms"], np.float32)
+    best, ms = sph_autotune(sim.ctx, reps)
+    table[key] = {"variant": best, "ms": [float(v) for v in ms]}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+    return best, ms
+
+
 # --- convenience object ------------------------------------------------------
 
 class Simulation:
@@ -360,6 +416,15 @@ class Simulation:
 
     def instance_state(self):
         return sph_instance_state(self.ctx, self.n_inst)
+
+    def autotune(self, reps=3, cache=True):
+        """Pick the fastest interaction variant for this GPU and size (needs
+        built cells).  With cache=True the choice is kept in the user cache
+        directory per (GPU name, log2 particle count, member count)."""
+        return autotune_cached(self, reps) if cache else sph_autotune(self.ctx, reps)
+
+    def set_variant(self, v):
+        sph_set_variant(self.ctx, v)
 
     def upload(self, pos, vel, rho, ids):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos

@@ -348,3 +348,27 @@ def test_dam_break_200_steps_tracks_the_oracle():
     assert d["t"] == pytest.approx(t_ref, rel=1e-4)
     assert rms < 1e-3 * case.dp
     sim.close()
+
+
+def test_every_interaction_variant_is_within_2e5():
+    case = cases.c1_dam_break(shuffle_seed=4)
+    sim = S.Simulation.from_case(case)
+    sim.step(10)
+    st, ost = _state(sim)
+    ref = oracle.Oracle(case.params()).interact(ost)
+    fluid = st["ids"] >= case.n_bound
+    results = []
+    for v in range(S.sph_num_variants()):
+        sim.set_variant(v)
+        sim.interact()
+        ace = sim.read(S.SPH_ARRAY_ACE)
+        ea, ed, gl = _rates_ok(ace, ref, fluid)
+        print(f"variant {v}: {ea.max():.2e} {ed.max():.2e} {gl:.2e}")
+        assert ea.max() <= REL_TOL and ed.max() <= REL_TOL and gl <= REL_TOL
+        results.append(ace)
+    best, ms = S.sph_autotune(sim.ctx, 2)
+    assert 0 <= best < S.sph_num_variants() and np.all(ms > 0)
+    # the autotuner leaves the state alone
+    st2 = sim.download()
+    assert np.array_equal(st2["pos"], st["pos"])
+    sim.close()
