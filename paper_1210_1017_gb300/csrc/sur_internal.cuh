@@ -1,0 +1,51 @@
+// Private declarations of the surrogate network's CUDA code.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sur {
+
+enum Epilogue : int {
+    kEpiNone = 0,       // acc (+ bias)
+    kEpiRelu = 1,       // relu(acc + bias)
+    kEpiResidual = 2,   // res + acc + bias
+    kEpiEdge1 = 3,      // relu(acc + P[src] + Q[dst] + bias): factorised edge-MLP input
+    kEpiReluMask = 4,   // acc where res > 0, else 0 (backward through a ReLU)
+};
+
+struct LinearArgs {
+    const __nv_bfloat16* A;     // M x K, row-major
+    const __nv_bfloat16* Bt;    // N x K, row-major (the layer's weights transposed)
+    const float* bias;          // N or null
+    uint32_t M;
+    int epi;
+    const __nv_bfloat16* res;   // M x N (residual / ReLU mask source)
+    const __nv_bfloat16* gp;    // node x N gathered at src (kEpiEdge1)
+    const __nv_bfloat16* gq;    // node x N gathered at dst (kEpiEdge1)
+    const uint32_t* src;
+    const uint32_t* dst;
+    __nv_bfloat16* out_bf16;    // M x ldo (may be null)
+    float* out_f32;             // M x ldo (may be null)
+    uint32_t ldo;
+    uint32_t* status;           // bit 0: a bounded wait gave up
+};
+
+// D[128 x N] = P^T Q summed over rows [0, M): P is M x 128, Q is M x N (bf16,
+// row-major with the given leading dimensions); dW = scale * D.
+struct WgradArgs {
+    const __nv_bfloat16* X;     // P
+    const __nv_bfloat16* dY;    // Q
+    uint32_t M;
+    float* partial;             // nparts x 128 x N scratch
+    uint32_t nparts;
+    float* dW;                  // 128 x N
+    float scale;
+    uint32_t* status;
+};
+
+int num_sms();
+bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st);
+bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st);
+
+}  // namespace sur

@@ -1,0 +1,300 @@
+// Linear layers of the surrogate network on the tcgen05 tensor cores:
+//   out[m, :] = epilogue( A[m, :] * B^T + bias )     (A: M x K bf16, B: N x K bf16)
+// with the epilogues the message-passing network needs (bias, ReLU,
+// residual add, the factorised edge-MLP input with gathered node terms, the
+// ReLU mask of the backward pass) fused after the tcgen05.ld of the fp32
+// accumulator.  Also the weight gradient dW = X^T dY, reduced over rows in
+// TMEM per block and then across blocks in a fixed order.
+#include <cuda_bf16.h>
+
+#include "sur_gemm.cuh"
+#include "sur_internal.cuh"
+
+namespace sur {
+
+namespace {
+
+// Stage a (rows x K) bf16 tile, row-major in global memory starting at row
+// `row0` of a matrix with `nrows` rows, into the canonical K-major layout
+// (rows past nrows read as zero).  Each thread moves 16-byte pieces.
+template <int K>
+__device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src,
+                                           uint32_t row0, uint32_t nrows, int rows) {
+    const int pieces = rows * (K / 8);
+    for (int c = threadIdx.x; c < pieces; c += blockDim.x) {
+        const int r = c % rows, g = c / rows;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row0 + r < nrows)
+            v = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * K + g * 8);
+        *reinterpret_cast<uint4*>(dst + kmajor_offset(r, g * 8, K)) = v;
+    }
+}
+
+// Stage rows [row0, row0+128) of a (nrows x C) bf16 row-major matrix as the
+// TRANSPOSED operand: element (c, m - row0) of a (C x 128) K-major tile.
+template <int C>
+__device__ __forceinline__ void stage_transposed(unsigned char* dst, const __nv_bfloat16* src,
+                                                 uint32_t row0, uint32_t nrows) {
+    // each thread takes 8 consecutive rows of one column block of 8: reads
+    // eight 16-byte pieces and writes eight 16-byte core-matrix rows
+    const int jobs = (C / 8) * 16;   // (column block, 8-row group)
+    for (int j = threadIdx.x; j < jobs; j += blockDim.x) {
+        const int cb = j % (C / 8), rg = j / (C / 8);
+        __nv_bfloat16 t[8][8];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const uint32_t m = row0 + rg * 8 + rr;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < nrows) v = *reinterpret_cast<const uint4*>(src + (size_t)m * C + cb * 8);
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) t[cc][rr] = e[cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+            *reinterpret_cast<uint4*>(dst + kmajor_offset(cb * 8 + cc, rg * 8, 128)) =
+                *reinterpret_cast<const uint4*>(t[cc]);
+    }
+}
+
+__device__ __forceinline__ float bf(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
+
+template <int N>
+__device__ __forceinline__ constexpr uint32_t tmem_cols() {
+    return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+}
+
+// Forward-type GEMM with fused epilogue; persistent over 128-row tiles.
+template <int K, int N>
+__global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    unsigned char* sa = s_raw;                        // 128 x K
+    unsigned char* sb = s_raw + 128 * K * 2;          // N x K
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (w == 0) tmem_alloc(&s_tmem, tmem_cols<N>());
+    if (tid == 0) mbar_init1(&s_bar);
+    stage_rows<K>(sb, g.Bt, 0, N, N);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t ntiles = (g.M + 127) / 128;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const uint32_t m0 = tile * 128;
+        stage_rows<K>(sa, g.A, m0, g.M, 128);
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < K / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sa) + s * 256, kLBO, (K / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sb) + s * 256, kLBO, (K / 8) * 128);
+                tc_mma(tmem, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
+            }
+            tc_commit(&s_bar);
+        }
+        const bool got = mbar_wait(&s_bar, phase);
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) {
+            if (tid == 0 && g.status) atomicOr(g.status, 1u);
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        const uint32_t m = m0 + w * 32 + lane;
+        const bool valid = m < g.M;
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
+            if (!valid) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = c0 + i;
+                float x = v[i];
+                if (g.bias) x += g.bias[n];
+                switch (g.epi) {
+                    case kEpiEdge1:   // relu(acc + P[src] + Q[dst] + b)
+                        x += bf(g.gp, (size_t)g.src[m] * N + n) + bf(g.gq, (size_t)g.dst[m] * N + n);
+                        x = fmaxf(x, 0.f);
+                        break;
+                    case kEpiRelu: x = fmaxf(x, 0.f); break;
+                    case kEpiResidual: x += bf(g.res, (size_t)m * N + n); break;
+                    case kEpiReluMask:   // backward through a ReLU: keep where act > 0
+                        x = bf(g.res, (size_t)m * N + n) > 0.f ? x : 0.f;
+                        break;
+                    default: break;
+                }
+                v[i] = x;
+            }
+            if (g.out_f32) {
+                float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            if (g.out_bf16) {
+                __nv_bfloat162 h[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                uint4* o = reinterpret_cast<uint4*>(g.out_bf16 + (size_t)m * g.ldo + c0);
+                o[0] = *reinterpret_cast<uint4*>(&h[0]);
+                o[1] = *reinterpret_cast<uint4*>(&h[4]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, tmem_cols<N>());
+}
+
+// Weight gradient dW[C x N] = X^T dY over rows [0, M): X is M x C, dY is
+// M x N (bf16, row-major).  Block b accumulates the row tiles b, b + grid,
+// ... in TMEM (C = 128 rows of the MMA, one MMA chain per tile), then writes
+// its partial; k_wgrad_reduce adds the partials in block order.
+template <int N>
+__global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    unsigned char* sa = s_raw;                  // X^T tile: 128 x 128 (features x rows)
+    unsigned char* sb = s_raw + 128 * 128 * 2;  // dY^T tile: N x 128
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (w == 0) tmem_alloc(&s_tmem, tmem_cols<N>());
+    if (tid == 0) mbar_init1(&s_bar);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t ntiles = (g.M + 127) / 128;
+    uint32_t phase = 0, first = 1;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        stage_transposed<128>(sa, g.X, tile * 128, g.M);
+        stage_transposed<N>(sb, g.dY, tile * 128, g.M);
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 128 / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sa) + s * 256, kLBO, 16 * 128);
+                const uint64_t bd = smem_desc(sm_addr(sb) + s * 256, kLBO, 16 * 128);
+                tc_mma(tmem, ad, bd, idesc_bf16(N), (first && s == 0) ? 0u : 1u);
+            }
+            tc_commit(&s_bar);
+        }
+        first = 0;
+        const bool got = mbar_wait(&s_bar, phase);
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) {
+            if (tid == 0 && g.status) atomicOr(g.status, 1u);
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_after();
+    float* part = g.partial + (size_t)blockIdx.x * 128 * N;
+    const uint32_t r = w * 32 + lane;   // feature row of dW
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) part[(size_t)r * N + c0 + i] = (first || !ok) ? 0.f : v[i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, tmem_cols<N>());
+}
+
+__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, int count,
+                               float* __restrict__ out, float scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * count + i];
+    out[i] = s * scale;
+}
+
+template <int K, int N>
+size_t linear_smem() { return (size_t)128 * K * 2 + (size_t)N * K * 2; }
+
+template <int K, int N>
+void launch_linear_t(const LinearArgs& g, int sms, cudaStream_t st) {
+    static bool init = false;
+    const size_t smem = linear_smem<K, N>();
+    if (!init) {
+        cudaFuncSetAttribute(k_linear<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_linear<K, N>, 128, smem);
+    // keep every resident block's TMEM inside the SM's 512 columns
+    const int cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    if (per_sm * cols > 512) per_sm = 512 / cols;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t tiles = (g.M + 127) / 128;
+    uint32_t grid = (uint32_t)(sms * per_sm);
+    if (grid > tiles) grid = tiles ? tiles : 1;
+    k_linear<K, N><<<grid, 128, smem, st>>>(g);
+}
+
+template <int N>
+void launch_wgrad_t(const WgradArgs& g, int sms, cudaStream_t st) {
+    static bool init = false;
+    const size_t smem = (size_t)128 * 128 * 2 + (size_t)N * 128 * 2;
+    if (!init) {
+        cudaFuncSetAttribute(k_wgrad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init = true;
+    }
+    const uint32_t tiles = (g.M + 127) / 128;
+    uint32_t grid = (uint32_t)g.nparts;
+    if (grid > tiles) grid = tiles ? tiles : 1;
+    k_wgrad<N><<<grid, 128, smem, st>>>(g);
+    const int count = 128 * N;
+    k_wgrad_reduce<<<(count + 255) / 256, 256, 0, st>>>(g.partial, (int)grid, count, g.dW, g.scale);
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+int num_sms() {
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st) {
+    const int sms = num_sms();
+    if (g.M == 0) return true;
+    if (K == 16 && N == 128) launch_linear_t<16, 128>(g, sms, st);
+    else if (K == 128 && N == 128) launch_linear_t<128, 128>(g, sms, st);
+    else if (K == 256 && N == 128) launch_linear_t<256, 128>(g, sms, st);
+    else if (K == 128 && N == 16) launch_linear_t<128, 16>(g, sms, st);
+    else if (K == 16 && N == 16) launch_linear_t<16, 16>(g, sms, st);
+    else if (K == 128 && N == 256) launch_linear_t<128, 256>(g, sms, st);
+    else return false;
+    return true;
+}
+
+bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st) {
+    if (N == 128) launch_wgrad_t<128>(g, num_sms(), st);
+    else if (N == 16) launch_wgrad_t<16>(g, num_sms(), st);
+    else return false;
+    return true;
+}
+
+}  // namespace sur

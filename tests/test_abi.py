@@ -12,7 +12,7 @@ from paper_1210_1017_gb300 import _build, cases
 from paper_1210_1017_gb300 import sph as S
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sph.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("sph.h", "sur.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,9 +22,11 @@ def lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", src)) - {"sph_snapshot_fn"})
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b((?:sph|sur)_[a-z0-9_]+)\s*\(", src))
+    return sorted(names - {"sph_snapshot_fn"})
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -32,12 +34,13 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 15
     out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r" T (sph_[a-z0-9_]+)", out))
+    exported = set(re.findall(r" T ((?:sph|sur)_[a-z0-9_]+)", out))
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     for n in names:
         assert hasattr(lib, n)
-    assert sorted(S.EXPORTED) == names
+    from paper_1210_1017_gb300 import surrogate as U
+    assert sorted(S.EXPORTED + U.EXPORTED) == names
 
 
 def test_struct_layouts_match_the_header(tmp_path):

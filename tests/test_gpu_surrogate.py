@@ -1,0 +1,90 @@
+"""The surrogate's tensor-core kernels through the C ABI against numpy on
+the same bf16-rounded inputs (fp32 accumulation on both sides)."""
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+from paper_1210_1017_gb300 import surrogate as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    return t
+
+
+def _bf16(torch, a):
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("K,N", [(16, 128), (128, 128), (256, 128), (128, 16), (16, 16),
+                                 (128, 256)])
+@pytest.mark.parametrize("M", [1, 200, 1000, 70001])
+def test_linear_matches_numpy(torch, K, N, M):
+    rng = np.random.default_rng(K * 1000 + N + M)
+    A = _bf16(torch, rng.normal(size=(M, K)))
+    Bt = _bf16(torch, rng.normal(size=(N, K)) / np.sqrt(K))
+    bias = torch.tensor(rng.normal(size=N).astype(np.float32)).cuda()
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    U.sur_linear(A, Bt, bias, M, K, N, U.SUR_EPI_NONE, None, None, out, st.cuda_stream)
+    st.synchronize()
+    a, b = _np(A), _np(Bt)
+    ref = a @ b.T + bias.cpu().numpy()
+    scale = np.abs(a) @ np.abs(b).T + 1.0
+    err = np.abs(out.cpu().numpy() - ref) / scale
+    assert err.max() < 1e-5, err.max()
+
+
+def test_linear_epilogues(torch):
+    rng = np.random.default_rng(3)
+    M, K, N = 3000, 128, 128
+    A = _bf16(torch, rng.normal(size=(M, K)))
+    Bt = _bf16(torch, rng.normal(size=(N, K)) / 11.3)
+    bias = torch.tensor(rng.normal(size=N).astype(np.float32)).cuda()
+    res = _bf16(torch, rng.normal(size=(M, N)))
+    st = torch.cuda.current_stream()
+    a, b, r = _np(A), _np(Bt), _np(res)
+    lin = a @ b.T
+    for epi, want in ((U.SUR_EPI_RELU, np.maximum(lin + bias.cpu().numpy(), 0)),
+                      (U.SUR_EPI_RESIDUAL, r + lin + bias.cpu().numpy()),
+                      (U.SUR_EPI_RELU_MASK, np.where(r > 0, lin, 0.0))):
+        out = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+        use_bias = None if epi == U.SUR_EPI_RELU_MASK else bias
+        U.sur_linear(A, Bt, use_bias, M, K, N, epi, res, out, None, st.cuda_stream)
+        st.synchronize()
+        got = _np(out)
+        assert np.allclose(got, want, rtol=1e-2, atol=2e-2), (epi, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("N", [128, 16])
+@pytest.mark.parametrize("M", [100, 5000, 100003])
+def test_wgrad_matches_numpy(torch, N, M):
+    rng = np.random.default_rng(N + M)
+    P = _bf16(torch, rng.normal(size=(M, 128)))
+    Q = _bf16(torch, rng.normal(size=(M, N)))
+    dW = torch.empty((128, N), dtype=torch.float32, device="cuda")
+    nb = U.sur_wgrad_scratch_bytes(N)
+    scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    U.sur_wgrad(P, Q, M, N, 0.5, dW, scratch, nb, st.cuda_stream)
+    st.synchronize()
+    p, q = _np(P), _np(Q)
+    ref = 0.5 * (p.T @ q)
+    scale = 0.5 * (np.abs(p).T @ np.abs(q)) + 1.0
+    err = np.abs(dW.cpu().numpy() - ref) / scale
+    assert err.max() < 1e-5, err.max()
+    # deterministic: a second call gives the same bits
+    dW2 = torch.empty_like(dW)
+    U.sur_wgrad(P, Q, M, N, 0.5, dW2, scratch, nb, st.cuda_stream)
+    st.synchronize()
+    assert torch.equal(dW, dW2)
