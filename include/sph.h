@@ -161,7 +161,8 @@ int sph_init_batch(const sph_params *params, const sph_instance *inst,
 int sph_instance_state(sph_ctx *ctx, double *t, double *dt, uint32_t *done,
                        uint64_t *steps);
 
-/* Copy a particle state from host memory (any order): pos[3n] float64
+/* Copy a particle state from host or device memory (any order; the arrays
+ * may live on either side, unified addressing decides): pos[3n] float64
  * (x,y,z interleaved), vel[3n] float32, rho[n] float32, ids[n] uint32 (a
  * permutation of 0..n-1 is not required, but ids must be distinct).  Sync.
  * The state needs sph_build_cells before sph_interact. */
@@ -211,8 +212,8 @@ typedef int (*sph_snapshot_fn)(void *user, uint64_t step, double t);
 int sph_rollout(sph_ctx *ctx, uint32_t nsteps, uint32_t save_every,
                 sph_snapshot_fn cb, void *user);
 
-/* Copy the current state (sorted order) to host arrays laid out as in
- * sph_upload.  Any pointer may be NULL to skip it.  Sync. */
+/* Copy the current state (sorted order) to host or device arrays laid out
+ * as in sph_upload.  Any pointer may be NULL to skip it.  Sync. */
 int sph_download(sph_ctx *ctx, double *pos, float *vel, float *rho,
                  uint32_t *ids);
 

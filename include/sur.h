@@ -45,6 +45,68 @@ int sur_wgrad(const void *d_P, const void *d_Q, uint32_t M, uint32_t N,
               float scale, float *d_dW, void *d_scratch,
               uint64_t scratch_bytes, void *stream);
 
+/* ---- the network -------------------------------------------------------
+ * Nodes: the particles of an SPH context (sph.h) in its current sorted order,
+ * with cells built.  Edges: every ordered pair within 2h (the FP64 predicate
+ * of the cell list).  Node input: the particle's last five velocities (a
+ * history array indexed by particle id: hist[id][15], oldest first) / v_scale
+ * and its boundary flag; edge input: (r_i - r_j)/2h and |r_i - r_j|/2h.
+ * Latent width 128; `layers` message-passing layers of
+ *   e' = e + W2 relu(W1a h_i + W1b h_j + W1c e + b1) + b2
+ *   h' = h + W4 relu(W3 [h, sum_j e'_ij] + b3) + b4,
+ * decoder W6 relu(W5 h + b5) + b6 -> normalised acceleration (3 of 16
+ * outputs); a = out * a_std + a_mean.  Parameters are one flat float array
+ * (per layer W[kin][kout] then b[kout]; layer order: node encoder 2, edge
+ * encoder 2, per message-passing layer W1a, W1b, W1c+b1, W2+b2, W3+b3,
+ * W4+b4, then decoder 2).  Every dense layer runs on the tensor cores
+ * (bf16 inputs, fp32 accumulation), forward and backward. */
+typedef struct sur_config {
+    uint32_t layers;           /* message-passing layers                     */
+    uint32_t max_nodes;        /* particles of the largest graph             */
+    uint32_t max_edges;        /* edges of the largest graph                 */
+    uint32_t train;            /* keep activations for sur_backward          */
+    float v_scale;             /* velocity normalisation [m/s]               */
+    float a_mean[3], a_std[3]; /* acceleration normalisation [m/s^2]         */
+    float dt_s;                /* time advanced per sur_advance call [s]     */
+} sur_config;
+
+typedef struct sur_ctx sur_ctx;
+struct sph_ctx;
+
+uint64_t sur_param_count(const sur_config *cfg);
+uint64_t sur_query_bytes(const sur_config *cfg);   /* device workspace size */
+int sur_init(const sur_config *cfg, void *d_workspace, uint64_t bytes,
+             void *stream, sur_ctx **out);          /* sync; params zero      */
+int sur_set_params(sur_ctx *ctx, const float *host, uint64_t count); /* sync; resets Adam */
+int sur_get_params(sur_ctx *ctx, float *host, uint64_t count);       /* sync */
+int sur_get_grads(sur_ctx *ctx, float *host, uint64_t count);        /* sync */
+
+/* Forward pass on the SPH context's particles; d_hist as above (device, n x
+ * 15 floats by id).  d_acc (device, n x 3 by id, may be NULL) receives the
+ * predicted acceleration.  Sync (reads the edge count). */
+int sur_forward(sur_ctx *ctx, struct sph_ctx *sph, const float *d_hist,
+                float *d_acc);
+
+/* Gradients of loss = mean over fluid particles of |out - target|^2 (out
+ * and target normalised accelerations; d_target device, n x 3 by id) with
+ * respect to all parameters, from the last sur_forward (train contexts).
+ * Writes the loss to *loss (host).  Sync. */
+int sur_backward(sur_ctx *ctx, struct sph_ctx *sph, const float *d_target,
+                 float *loss);
+
+/* One Adam step on the parameters with the gradients of sur_backward. */
+int sur_adam(sur_ctx *ctx, float lr, float beta1, float beta2, float eps);
+
+/* One surrogate call: forward, then semi-implicit Euler over dt_s of the
+ * SPH context's fluid particles (v += a dt_s, r += v dt_s; boundary and
+ * excluded particles stay) and a shift of the velocity history.  The SPH
+ * context's cells are stale afterwards (call sph_build_cells).  Sync. */
+int sur_advance(sur_ctx *ctx, struct sph_ctx *sph, float *d_hist);
+
+uint32_t sur_num_edges(const sur_ctx *ctx);
+const char *sur_last_error(const sur_ctx *ctx);
+void sur_destroy(sur_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

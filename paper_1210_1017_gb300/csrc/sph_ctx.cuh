@@ -1,0 +1,73 @@
+// The SPH context (private to libsph.so; shared by the SPH and surrogate
+// translation units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// Host view of the ensemble: the device table plus its search arrays.
+struct Table {
+    std::vector<Inst> inst;
+    std::vector<uint32_t> cell_base, row_base, id_base;   // n_inst + 1 each
+    uint64_t ncells = 0, nrows = 0, n = 0;
+    int max_ncx = 1;
+};
+
+}  // namespace sph
+
+struct sph_ctx {
+    sph_params p;
+    sph::Dev d;
+    sph::Table tab;
+    uint32_t n = 0, n_inst = 1;
+    cudaStream_t st = nullptr;
+    int bits = 0, passes = 0;
+    uint32_t tiles = 0, nparts = 0;
+    uint64_t ncells = 0;
+    // state, double-buffered for the reorder gather
+    double *x[2], *y[2], *z[2];
+    float4* vr[2];
+    uint32_t* id[2];
+    // start-of-step state: [0] written by the predictor, [1] after the
+    // mid-step reorder (read by the corrector)
+    double *px[2], *py[2], *pz[2];
+    float4* pvr[2];
+    float4 *posc, *ace;
+    double* stage_pos;       // host transfer staging: 3n doubles
+    float* stage_vr;         // 4n floats (velocity, then density)
+    uint32_t *key[2], *val[2];
+    uint32_t *cnt, *off, *bsum, *hist, *tilectr, *os_status, *nnb, *nnb64;
+    uint32_t *ucnt, *uoff, *ubsum;   // work units of the interaction
+    uint2* units;
+    uint4* part_u;
+    unsigned long long* lvl2_q;
+    uint32_t *done, *status;
+    double *diag_out, *diag_part;
+    unsigned long long* counters;
+    // ensemble table and per-member state (device)
+    sph::Inst* d_inst;
+    uint32_t *d_cell_base, *d_row_base, *d_id_base;
+    double *i_dt, *i_t;
+    uint32_t *i_done, *i_terms;
+    unsigned long long* i_steps;
+    float* i_last;
+    size_t os_bytes = 0;
+    // bookkeeping
+    int variant = 0;         // interaction block shape (see sph_autotune)
+    int cur = 0;             // state buffer index
+    int skey = 0;            // key/val buffer holding the last sort result
+    bool have_state = false;
+    bool cells_valid = false;
+    bool keys_ready = false; // labels + histograms already computed
+    int pre_state = 0;       // 0 none, 1 in px[0] (unsorted), 2 in px[1] (sorted)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+

@@ -12,15 +12,18 @@ enum Epilogue : int {
     kEpiResidual = 2,   // res + acc + bias
     kEpiEdge1 = 3,      // relu(acc + P[src] + Q[dst] + bias): factorised edge-MLP input
     kEpiReluMask = 4,   // acc where res > 0, else 0 (backward through a ReLU)
+    kEpiAccum = 5,      // out_f32 += acc (+ bias): gradient accumulation
 };
 
 struct LinearArgs {
-    const __nv_bfloat16* A;     // M x K, row-major
+    const __nv_bfloat16* A;     // M x K, row-major (row stride lda; 0 = K)
+    uint32_t lda;
     const __nv_bfloat16* Bt;    // N x K, row-major (the layer's weights transposed)
     const float* bias;          // N or null
     uint32_t M;
     int epi;
-    const __nv_bfloat16* res;   // M x N (residual / ReLU mask source)
+    const __nv_bfloat16* res;   // M x N (residual / ReLU mask source), row stride ldr (0 = N)
+    uint32_t ldr;
     const __nv_bfloat16* gp;    // node x N gathered at src (kEpiEdge1)
     const __nv_bfloat16* gq;    // node x N gathered at dst (kEpiEdge1)
     const uint32_t* src;
@@ -34,8 +37,9 @@ struct LinearArgs {
 // D[128 x N] = P^T Q summed over rows [0, M): P is M x 128, Q is M x N (bf16,
 // row-major with the given leading dimensions); dW = scale * D.
 struct WgradArgs {
-    const __nv_bfloat16* X;     // P
-    const __nv_bfloat16* dY;    // Q
+    const __nv_bfloat16* X;     // P (row stride ldp; 0 = 128)
+    const __nv_bfloat16* dY;    // Q (row stride ldq; 0 = N)
+    uint32_t ldp, ldq;
     uint32_t M;
     float* partial;             // nparts x 128 x N scratch
     uint32_t nparts;

@@ -19,13 +19,13 @@ namespace {
 // (rows past nrows read as zero).  Each thread moves 16-byte pieces.
 template <int K>
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src,
-                                           uint32_t row0, uint32_t nrows, int rows) {
+                                           uint32_t row0, uint32_t nrows, int rows, uint32_t ld) {
     const int pieces = rows * (K / 8);
     for (int c = threadIdx.x; c < pieces; c += blockDim.x) {
         const int r = c % rows, g = c / rows;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (row0 + r < nrows)
-            v = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * K + g * 8);
+            v = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * ld + g * 8);
         *reinterpret_cast<uint4*>(dst + kmajor_offset(r, g * 8, K)) = v;
     }
 }
@@ -34,7 +34,7 @@ __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat
 // TRANSPOSED operand: element (c, m - row0) of a (C x 128) K-major tile.
 template <int C>
 __device__ __forceinline__ void stage_transposed(unsigned char* dst, const __nv_bfloat16* src,
-                                                 uint32_t row0, uint32_t nrows) {
+                                                 uint32_t row0, uint32_t nrows, uint32_t ld) {
     // each thread takes 8 consecutive rows of one column block of 8: reads
     // eight 16-byte pieces and writes eight 16-byte core-matrix rows
     const int jobs = (C / 8) * 16;   // (column block, 8-row group)
@@ -45,7 +45,7 @@ __device__ __forceinline__ void stage_transposed(unsigned char* dst, const __nv_
         for (int rr = 0; rr < 8; ++rr) {
             const uint32_t m = row0 + rg * 8 + rr;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < nrows) v = *reinterpret_cast<const uint4*>(src + (size_t)m * C + cb * 8);
+            if (m < nrows) v = *reinterpret_cast<const uint4*>(src + (size_t)m * ld + cb * 8);
             const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
             for (int cc = 0; cc < 8; ++cc) t[cc][rr] = e[cc];
@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     if (w == 0) tmem_alloc(&s_tmem, tmem_cols<N>());
     if (tid == 0) mbar_init1(&s_bar);
-    stage_rows<K>(sb, g.Bt, 0, N, N);
+    stage_rows<K>(sb, g.Bt, 0, N, N, K);
+    const uint32_t lda = g.lda ? g.lda : (uint32_t)K;
+    const uint32_t ldr = g.ldr ? g.ldr : (uint32_t)N;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const uint32_t m0 = tile * 128;
-        stage_rows<K>(sa, g.A, m0, g.M, 128);
+        stage_rows<K>(sa, g.A, m0, g.M, 128, lda);
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
@@ -124,10 +126,11 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
                         x = fmaxf(x, 0.f);
                         break;
                     case kEpiRelu: x = fmaxf(x, 0.f); break;
-                    case kEpiResidual: x += bf(g.res, (size_t)m * N + n); break;
+                    case kEpiResidual: x += bf(g.res, (size_t)m * ldr + n); break;
                     case kEpiReluMask:   // backward through a ReLU: keep where act > 0
-                        x = bf(g.res, (size_t)m * N + n) > 0.f ? x : 0.f;
+                        x = bf(g.res, (size_t)m * ldr + n) > 0.f ? x : 0.f;
                         break;
+                    case kEpiAccum: x += g.out_f32[(size_t)m * g.ldo + n]; break;
                     default: break;
                 }
                 v[i] = x;
@@ -175,8 +178,8 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
     uint32_t phase = 0, first = 1;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_transposed<128>(sa, g.X, tile * 128, g.M);
-        stage_transposed<N>(sb, g.dY, tile * 128, g.M);
+        stage_transposed<128>(sa, g.X, tile * 128, g.M, g.ldp ? g.ldp : 128u);
+        stage_transposed<N>(sb, g.dY, tile * 128, g.M, g.ldq ? g.ldq : (uint32_t)N);
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {

@@ -1,0 +1,856 @@
+// The learned surrogate: a message-passing network on the radius-2h
+// neighbour graph of the SPH cell list (encoder, `layers` message-passing
+// layers, decoder), forward, backward and Adam, with every dense layer on the
+// tcgen05 tensor cores (sur_linear.cu) and the graph work in the kernels here.
+//
+// Nodes are the particles of an SPH context in its (cell, id)-sorted order;
+// inputs and outputs are indexed by particle id.  Node input: the last five
+// velocities / v_scale and the boundary flag (16 features).  Edge input:
+// (r_i - r_j) / 2h and |r_i - r_j| / 2h (padded to 16).  Latent width 128.
+//   edge update: e' = e + W2 relu(W1a h_i + W1b h_j + W1c e + b1) + b2
+//   node update: h' = h + W4 relu(W3 [h, sum_j e'_ij] + b3) + b4
+//   decoder:     out = W6 relu(W5 h + b5) + b6   (first 3 of 16 outputs: the
+//                normalised acceleration)
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "../../include/sur.h"
+#include "sph_ctx.cuh"
+#include "sur_internal.cuh"
+
+using namespace sur;
+
+namespace {
+
+constexpr int L = 128;       // latent width
+constexpr int KIN = 16;      // padded input width of the encoders
+constexpr int KOUT = 16;     // padded decoder output width
+constexpr uint32_t kWgradParts = 152;
+
+struct Layer {
+    int kin, kout;
+    bool bias;
+    size_t w_off, b_off;     // offsets in the flat parameter array
+    __nv_bfloat16* Wt;       // kout x kin (forward operand)
+    __nv_bfloat16* W;        // kin x kout (backward operand)
+};
+
+__global__ void k_cast_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                            size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// W (kin x kout, fp32 row-major) -> bf16 W and bf16 W^T.
+__global__ void k_refresh(const float* __restrict__ w, int kin, int kout, __nv_bfloat16* W,
+                          __nv_bfloat16* Wt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kin * kout) return;
+    const int r = i / kout, c = i % kout;
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+    W[i] = v;
+    Wt[(size_t)c * kin + r] = v;
+}
+
+// ----------------------------------------------------------------- graph --
+
+// Neighbours j != i with |r_ij|^2 < (2h)^2 (FP64 predicate, as the SPH
+// cell list defines them), visited in ascending sorted index: the 9 rows of
+// cells around i's cell in (z, y) order, cells in x order.
+template <int MODE>
+__global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const double* __restrict__ y,
+                        const double* __restrict__ z, const uint32_t* __restrict__ key,
+                        const uint32_t* __restrict__ off, uint32_t* __restrict__ cnt,
+                        const uint32_t* __restrict__ rowptr, uint32_t* __restrict__ col,
+                        uint32_t* __restrict__ src, __nv_bfloat16* __restrict__ xe, double inv2h) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const uint32_t n_in = off[d.ncells];
+    if (i >= n_in) {
+        if (MODE == 0) cnt[i] = 0;
+        return;
+    }
+    const uint32_t k = key[i];
+    uint32_t lo = 0, hi = d.n_inst;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d.cell_base[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    const sph::Inst& I = d.inst[lo];
+    const uint32_t lk = k - I.cell_base;
+    const int cx = (int)(lk % (uint32_t)I.ncx);
+    const uint32_t t = lk / (uint32_t)I.ncx;
+    const int cy = (int)(t % (uint32_t)I.ncy), cz = (int)(t / (uint32_t)I.ncy);
+    const double xi = x[i], yi = y[i], zi = z[i];
+    const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < I.ncx ? cx + 1 : I.ncx - 1;
+    uint32_t c = 0, e = MODE ? rowptr[i] : 0u;
+    for (int zz = cz - 1; zz <= cz + 1; ++zz) {
+        if (zz < 0 || zz >= I.ncz) continue;
+        for (int yy = cy - 1; yy <= cy + 1; ++yy) {
+            if (yy < 0 || yy >= I.ncy) continue;
+            const uint32_t rb = I.cell_base + (uint32_t)I.ncx * ((uint32_t)yy + (uint32_t)I.ncy * zz);
+            const uint32_t s = off[rb + xlo], en = off[rb + xhi + 1];
+            for (uint32_t j = s; j < en; ++j) {
+                if (j == i) continue;
+                const double dx = __dsub_rn(xi, x[j]);
+                const double dy = __dsub_rn(yi, y[j]);
+                const double dz = __dsub_rn(zi, z[j]);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                            __dmul_rn(dz, dz));
+                if (d2 < d.r2max_d) {
+                    if (MODE) {
+                        col[e] = j;
+                        src[e] = i;
+                        __nv_bfloat16* f = xe + (size_t)e * KIN;
+                        f[0] = __double2bfloat16(dx * inv2h);
+                        f[1] = __double2bfloat16(dy * inv2h);
+                        f[2] = __double2bfloat16(dz * inv2h);
+                        f[3] = __double2bfloat16(sqrt(d2) * inv2h);
+#pragma unroll
+                        for (int q = 4; q < KIN; ++q) f[q] = __float2bfloat16_rn(0.f);
+                        ++e;
+                    }
+                    ++c;
+                }
+            }
+        }
+    }
+    if (MODE == 0) cnt[i] = c;
+}
+
+// rev[e] = index of the edge (j, i) in row j (rows are sorted ascending).
+__global__ void k_graph_rev(uint32_t E, const uint32_t* __restrict__ rowptr,
+                            const uint32_t* __restrict__ col, const uint32_t* __restrict__ src,
+                            uint32_t* __restrict__ rev) {
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const uint32_t i = src[e], j = col[e];
+    uint32_t lo = rowptr[j], hi = rowptr[j + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (col[mid] < i) lo = mid + 1;
+        else hi = mid;
+    }
+    rev[e] = lo;
+}
+
+// Node inputs: five velocities (history indexed by particle id, oldest
+// first) / v_scale, boundary flag.
+__global__ void k_node_features(const sph::Dev d, const uint32_t* __restrict__ id,
+                                const float* __restrict__ hist, double inv_v,
+                                __nv_bfloat16* __restrict__ xn) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const uint32_t pid = id[i];
+    uint32_t lo = 0, hi = d.n_inst;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d.id_base[mid] <= pid) lo = mid;
+        else hi = mid;
+    }
+    const bool bound = pid < d.inst[lo].id_fluid;
+    __nv_bfloat16* f = xn + (size_t)i * KIN;
+#pragma unroll
+    for (int q = 0; q < 15; ++q) f[q] = __double2bfloat16((double)hist[(size_t)pid * 15 + q] * inv_v);
+    f[15] = __float2bfloat16_rn(bound ? 1.f : 0.f);
+}
+
+// out[i, 0:128] = sum over the edges of row i of e[edge, 0:128] (fp32 sum in
+// edge order, one warp per node, 4 features per lane).
+template <typename T>
+__global__ void k_rowsum(uint32_t n, const uint32_t* __restrict__ rowptr, const T* __restrict__ e,
+                         const uint32_t* __restrict__ perm, __nv_bfloat16* out_bf, float* out_f,
+                         uint32_t ldo) {
+    const uint32_t node = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (node >= n) return;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (uint32_t k = rowptr[node]; k < rowptr[node + 1]; ++k) {
+        const uint32_t ed = perm ? perm[k] : k;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (sizeof(T) == 2) s[q] += __bfloat162float(e[(size_t)ed * L + lane * 4 + q]);
+            else s[q] += e[(size_t)ed * L + lane * 4 + q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (out_bf) out_bf[(size_t)node * ldo + lane * 4 + q] = __float2bfloat16_rn(s[q]);
+        if (out_f) out_f[(size_t)node * ldo + lane * 4 + q] = s[q];
+    }
+}
+
+// out[i] += in[i] (fp32), and a bf16 copy of the sum.
+__global__ void k_add_gather(size_t count, float* __restrict__ acc, const float* __restrict__ node,
+                             const uint32_t* __restrict__ src, uint32_t ldn,
+                             __nv_bfloat16* __restrict__ out_bf) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = t / L, c = t % L;
+        float v = acc[t];
+        if (node) v += node[(size_t)src[e] * ldn + c];
+        acc[t] = v;
+        out_bf[t] = __float2bfloat16_rn(v);
+    }
+}
+
+// Column sums of an (M x C) matrix into grad[0:C] (block partials in a fixed
+// order, then one block adds them).
+template <typename T>
+__global__ void k_colsum_part(uint32_t M, int C, const T* __restrict__ in, uint32_t ld,
+                              float* __restrict__ part) {
+    const int c = threadIdx.x;   // blockDim = C
+    float s = 0.f;
+    for (uint32_t m = blockIdx.x; m < M; m += gridDim.x) {
+        if constexpr (sizeof(T) == 2) s += __bfloat162float(in[(size_t)m * ld + c]);
+        else s += in[(size_t)m * ld + c];
+    }
+    part[(size_t)blockIdx.x * C + c] = s;
+}
+
+__global__ void k_colsum_final(int nparts, int C, const float* __restrict__ part,
+                               float* __restrict__ out, float scale) {
+    const int c = threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int b = 0; b < nparts; ++b) s += part[(size_t)b * C + c];
+    out[c] = s * scale;
+}
+
+// Loss over fluid nodes and its gradient: out (n x 16 fp32, sorted order),
+// target (by id, n x 3).  dOUT (bf16, n x 16) = 2 (out - target) / n_fluid.
+__global__ void k_loss(const sph::Dev d, const uint32_t* __restrict__ id,
+                       const float* __restrict__ out, const float* __restrict__ target,
+                       const uint32_t* __restrict__ off, float inv_nf,
+                       __nv_bfloat16* __restrict__ dout, float* __restrict__ part) {
+    __shared__ float s_sum[256];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < d.n) {
+        const uint32_t n_in = off[d.ncells];
+        const uint32_t pid = id[i];
+        uint32_t lo = 0, hi = d.n_inst;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (d.id_base[mid] <= pid) lo = mid;
+            else hi = mid;
+        }
+        const bool fluid = i < n_in && pid >= d.inst[lo].id_fluid;
+#pragma unroll
+        for (int c = 0; c < KOUT; ++c) {
+            float g = 0.f;
+            if (fluid && c < 3) {
+                const float r = out[(size_t)i * KOUT + c] - target[(size_t)pid * 3 + c];
+                l += r * r;
+                g = 2.f * r * inv_nf;
+            }
+            dout[(size_t)i * KOUT + c] = __float2bfloat16_rn(g);
+        }
+    }
+    s_sum[threadIdx.x] = l;
+    __syncthreads();
+    for (int st = 128; st; st >>= 1) {
+        if (threadIdx.x < st) s_sum[threadIdx.x] += s_sum[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s_sum[0];
+}
+
+__global__ void k_loss_final(int nparts, const float* __restrict__ part, float inv_nf,
+                             float* __restrict__ loss) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[b];
+    *loss = (float)(s * inv_nf);
+}
+
+__global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Output (sorted order, normalised) -> by id, denormalised acceleration.
+__global__ void k_write_out(const sph::Dev d, const uint32_t* __restrict__ id,
+                            const float* __restrict__ out, float3 am, float3 as,
+                            float* __restrict__ acc_by_id) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const uint32_t pid = id[i];
+    acc_by_id[(size_t)pid * 3 + 0] = out[(size_t)i * KOUT + 0] * as.x + am.x;
+    acc_by_id[(size_t)pid * 3 + 1] = out[(size_t)i * KOUT + 1] * as.y + am.y;
+    acc_by_id[(size_t)pid * 3 + 2] = out[(size_t)i * KOUT + 2] * as.z + am.z;
+}
+
+// Semi-implicit Euler over dt_s for fluid particles of the SPH state (sorted
+// order): v += a dt, r += v dt (FP64 positions); boundary and excluded
+// particles stay.  The velocity history (by id) shifts by one.
+__global__ void k_advance(const sph::Dev d, const uint32_t* __restrict__ id, double* x, double* y,
+                          double* z, float4* vr, const uint32_t* __restrict__ off,
+                          const float* __restrict__ acc_by_id, float* hist, float dt) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const uint32_t pid = id[i];
+    uint32_t lo = 0, hi = d.n_inst;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d.id_base[mid] <= pid) lo = mid;
+        else hi = mid;
+    }
+    const bool fluid = i < off[d.ncells] && pid >= d.inst[lo].id_fluid;
+    float4 v = vr[i];
+    if (fluid) {
+        v.x += acc_by_id[(size_t)pid * 3 + 0] * dt;
+        v.y += acc_by_id[(size_t)pid * 3 + 1] * dt;
+        v.z += acc_by_id[(size_t)pid * 3 + 2] * dt;
+        x[i] += (double)(v.x * dt);
+        y[i] += (double)(v.y * dt);
+        z[i] += (double)(v.z * dt);
+        vr[i] = v;
+    }
+    float* h = hist + (size_t)pid * 15;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) h[q] = h[q + 3];
+    h[12] = fluid ? v.x : 0.f;
+    h[13] = fluid ? v.y : 0.f;
+    h[14] = fluid ? v.z : 0.f;
+}
+
+inline uint32_t nblk(size_t n, uint32_t t) { return (uint32_t)((n + t - 1) / t); }
+
+// out (cols x rows) = in (rows x cols)^T
+__global__ void k_transpose(const float* __restrict__ in, int rows, int cols, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int r = i / cols, c = i % cols;
+    out[(size_t)c * rows + r] = in[i];
+}
+inline uint32_t gridcap(size_t n, uint32_t t) {
+    const size_t b = (n + t - 1) / t;
+    return (uint32_t)(b > 4096 ? 4096 : (b ? b : 1));
+}
+
+struct Carve {
+    char* base;
+    size_t used = 0;
+    template <typename T>
+    T* take(size_t count) {
+        used = (used + 255) / 256 * 256;
+        T* p = base ? (T*)(base + used) : nullptr;
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct sur_ctx {
+    sur_config cfg;
+    cudaStream_t st = nullptr;
+    std::vector<Layer> layers;
+    size_t nparams = 0;
+    int NL = 0;
+    // parameters
+    float *w, *g, *m, *v;
+    unsigned long long adam_t = 0;
+    // graph
+    uint32_t *cnt, *rowptr, *bsum, *col, *src, *rev;
+    uint32_t n = 0, E = 0;
+    // activations (train: one per layer; inference: ping-pong)
+    __nv_bfloat16 *xn, *xe, *en1, *ee1;
+    std::vector<__nv_bfloat16*> XN, Ebuf, Z1, Y1;
+    __nv_bfloat16 *P, *Q, *D1;
+    float* out;
+    // backward
+    float *dH, *dXN, *dE, *partial, *colpart, *losspart, *loss;
+    __nv_bfloat16 *dHb, *dY1, *dEb, *dpre, *dPb, *dQb, *dD1, *dout, *dEe1, *dEn1;
+    float *acc;   // predicted acceleration by id (n x 3)
+    float* wg_tmp;   // 128 x 128 scratch for transposed weight gradients
+    bool have_forward = false;
+    std::string err;
+};
+
+namespace {
+
+void build_layers(sur_ctx* c) {
+    c->layers.clear();
+    size_t off = 0;
+    auto add = [&](int kin, int kout, bool bias) {
+        Layer l{};
+        l.kin = kin;
+        l.kout = kout;
+        l.bias = bias;
+        l.w_off = off;
+        off += (size_t)kin * kout;
+        l.b_off = off;
+        if (bias) off += kout;
+        c->layers.push_back(l);
+    };
+    add(KIN, L, true);  // 0 encoder node 1
+    add(L, L, true);    // 1 encoder node 2
+    add(KIN, L, true);  // 2 encoder edge 1
+    add(L, L, true);    // 3 encoder edge 2
+    for (int l = 0; l < c->NL; ++l) {
+        add(L, L, false);     // W1a (h_i)
+        add(L, L, false);     // W1b (h_j)
+        add(L, L, true);      // W1c (e), b1
+        add(L, L, true);      // W2, b2
+        add(2 * L, L, true);  // W3, b3
+        add(L, L, true);      // W4, b4
+    }
+    add(L, L, true);     // decoder 1
+    add(L, KOUT, true);  // decoder 2
+    c->nparams = off;
+}
+
+size_t carve(sur_ctx* c, void* base) {
+    Carve cv{(char*)base};
+    const size_t N = c->cfg.max_nodes, E = c->cfg.max_edges;
+    const bool train = c->cfg.train != 0;
+    const int NL = c->NL;
+    c->w = cv.take<float>(c->nparams);
+    c->g = cv.take<float>(c->nparams);
+    c->m = cv.take<float>(c->nparams);
+    c->v = cv.take<float>(c->nparams);
+    for (Layer& l : c->layers) {
+        l.Wt = cv.take<__nv_bfloat16>((size_t)l.kin * l.kout);
+        l.W = cv.take<__nv_bfloat16>((size_t)l.kin * l.kout);
+    }
+    c->cnt = cv.take<uint32_t>(N + 1);
+    c->rowptr = cv.take<uint32_t>(N + 2);
+    c->bsum = cv.take<uint32_t>(sph::scan_bsum_count(N + 1));
+    c->col = cv.take<uint32_t>(E);
+    c->src = cv.take<uint32_t>(E);
+    c->rev = cv.take<uint32_t>(E);
+    c->xn = cv.take<__nv_bfloat16>(N * KIN);
+    c->xe = cv.take<__nv_bfloat16>(E * KIN);
+    c->en1 = cv.take<__nv_bfloat16>(N * L);
+    c->ee1 = cv.take<__nv_bfloat16>(E * L);
+    const int nx = train ? NL + 1 : 2, ne = train ? NL + 1 : 2, nz = train ? NL : 1;
+    c->XN.assign(nx, nullptr);
+    c->Ebuf.assign(ne, nullptr);
+    c->Z1.assign(nz, nullptr);
+    c->Y1.assign(nz, nullptr);
+    for (auto& p : c->XN) p = cv.take<__nv_bfloat16>(N * 2 * L);
+    for (auto& p : c->Ebuf) p = cv.take<__nv_bfloat16>(E * L);
+    for (auto& p : c->Z1) p = cv.take<__nv_bfloat16>(E * L);
+    for (auto& p : c->Y1) p = cv.take<__nv_bfloat16>(N * L);
+    c->P = cv.take<__nv_bfloat16>(N * L);
+    c->Q = cv.take<__nv_bfloat16>(N * L);
+    c->D1 = cv.take<__nv_bfloat16>(N * L);
+    c->out = cv.take<float>(N * KOUT);
+    c->acc = cv.take<float>(N * 3);
+    c->partial = cv.take<float>((size_t)kWgradParts * L * L);
+    c->colpart = cv.take<float>((size_t)1024 * 2 * L);
+    c->losspart = cv.take<float>(nblk(N, 256) + 1);
+    c->loss = cv.take<float>(1);
+    c->wg_tmp = cv.take<float>((size_t)L * L);
+    if (train) {
+        c->dH = cv.take<float>(N * L);
+        c->dXN = cv.take<float>(N * 2 * L);
+        c->dE = cv.take<float>(E * L);
+        c->dHb = cv.take<__nv_bfloat16>(N * L);
+        c->dY1 = cv.take<__nv_bfloat16>(N * L);
+        c->dEb = cv.take<__nv_bfloat16>(E * L);
+        c->dpre = cv.take<__nv_bfloat16>(E * L);
+        c->dPb = cv.take<__nv_bfloat16>(N * L);
+        c->dQb = cv.take<__nv_bfloat16>(N * L);
+        c->dD1 = cv.take<__nv_bfloat16>(N * L);
+        c->dout = cv.take<__nv_bfloat16>(N * KOUT);
+        c->dEe1 = cv.take<__nv_bfloat16>(E * L);
+        c->dEn1 = cv.take<__nv_bfloat16>(N * L);
+    }
+    return (cv.used + 255) / 256 * 256;
+}
+
+int fail(sur_ctx* c, int code, const char* msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int linear(sur_ctx* c, const __nv_bfloat16* A, uint32_t lda, const Layer& l, bool use_W,
+           uint32_t M, int epi, const __nv_bfloat16* res, uint32_t ldr, __nv_bfloat16* out_bf,
+           float* out_f, uint32_t ldo, bool with_bias = true) {
+    LinearArgs g = {};
+    g.A = A;
+    g.lda = lda;
+    // forward: out = A W (+ b) uses W^T as the K-major operand; backward:
+    // dX = dY W^T uses W itself
+    g.Bt = use_W ? l.W : l.Wt;
+    g.bias = (!use_W && with_bias && l.bias) ? c->w + l.b_off : nullptr;
+    g.M = M;
+    g.epi = epi;
+    g.res = res;
+    g.ldr = ldr;
+    g.out_bf16 = out_bf;
+    g.out_f32 = out_f;
+    g.ldo = ldo;
+    const int K = use_W ? l.kout : l.kin, N = use_W ? l.kin : l.kout;
+    if (!launch_linear(K, N, g, c->st)) return fail(c, SPH_ERR_INVALID_ARG, "unsupported layer shape");
+    return SPH_OK;
+}
+
+int edge1(sur_ctx* c, const Layer& l, const __nv_bfloat16* e, __nv_bfloat16* out) {
+    LinearArgs g = {};
+    g.A = e;
+    g.Bt = l.Wt;
+    g.bias = c->w + l.b_off;
+    g.M = c->E;
+    g.epi = kEpiEdge1;
+    g.gp = c->P;
+    g.gq = c->Q;
+    g.src = c->src;
+    g.dst = c->col;
+    g.out_bf16 = out;
+    g.ldo = L;
+    if (!launch_linear(L, L, g, c->st)) return fail(c, SPH_ERR_INVALID_ARG, "edge layer");
+    return SPH_OK;
+}
+
+// grad of W (kin x kout) += X^T dY over M rows (X: M x kin with stride ldx,
+// dY: M x kout with stride ldy); kin = 16 layers are computed as (dY^T X)^T.
+void wgrad(sur_ctx* c, const Layer& l, const __nv_bfloat16* X, uint32_t ldx,
+           const __nv_bfloat16* dY, uint32_t ldy, uint32_t M, int kin_half = -1) {
+    WgradArgs g = {};
+    g.M = M;
+    g.partial = c->partial;
+    g.nparts = kWgradParts;
+    g.scale = 1.f;
+    float* dst = c->g + l.w_off;
+    if (l.kin == KIN) {
+        // D[128 x 16] = dY^T X = (dW)^T, then transposed into dW (16 x 128)
+        g.X = dY;
+        g.ldp = ldy;
+        g.dY = X;
+        g.ldq = ldx;
+        g.dW = c->wg_tmp;
+        launch_wgrad(KIN, g, c->st);
+        k_transpose<<<nblk((size_t)KIN * L, 256), 256, 0, c->st>>>(c->wg_tmp, L, KIN, dst);
+        return;
+    }
+    g.X = X;
+    g.ldp = ldx;
+    g.dY = dY;
+    g.ldq = ldy;
+    g.dW = dst + (kin_half > 0 ? (size_t)kin_half * L * l.kout : 0);
+    launch_wgrad(l.kout, g, c->st);
+}
+
+}  // namespace
+
+namespace {
+
+void colsum(sur_ctx* c, const void* in, bool bf16, uint32_t M, int C, uint32_t ld, float* out) {
+    const uint32_t parts = M == 0 ? 1u : (M < 1024u ? M : 1024u);
+    if (bf16)
+        k_colsum_part<__nv_bfloat16><<<parts, C, 0, c->st>>>(M, C, (const __nv_bfloat16*)in, ld, c->colpart);
+    else
+        k_colsum_part<float><<<parts, C, 0, c->st>>>(M, C, (const float*)in, ld, c->colpart);
+    k_colsum_final<<<1, C, 0, c->st>>>((int)parts, C, c->colpart, out, 1.f);
+}
+
+void cast(sur_ctx* c, const float* in, __nv_bfloat16* out, size_t n) {
+    k_cast_bf16<<<gridcap(n, 256), 256, 0, c->st>>>(in, out, n);
+}
+
+void refresh_all(sur_ctx* c) {
+    for (Layer& l : c->layers)
+        k_refresh<<<nblk((size_t)l.kin * l.kout, 256), 256, 0, c->st>>>(c->w + l.w_off, l.kin, l.kout,
+                                                                        l.W, l.Wt);
+}
+
+// dst (n x 128, stride 128) += src (n x 128, stride lds)
+__global__ void k_add_strided(uint32_t n, float* __restrict__ dst, const float* __restrict__ src,
+                              uint32_t lds) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= (size_t)n * L) return;
+    const size_t i = t / L, c = t % L;
+    dst[t] += src[i * lds + c];
+}
+
+int check(sur_ctx* c, const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return SPH_ERR_CUDA;
+    }
+    return SPH_OK;
+}
+
+int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
+    if (!s->cells_valid) return fail(c, SPH_ERR_STATE, "SPH cells not built");
+    if (s->n > c->cfg.max_nodes) return fail(c, SPH_ERR_INVALID_ARG, "more particles than max_nodes");
+    const uint32_t n = s->n;
+    c->n = n;
+    cudaStream_t st = c->st;
+    const sph::Dev& d = s->d;
+    const int cur = s->cur;
+    const double inv2h = 1.0 / (2.0 * s->p.h);
+    const uint32_t* key = s->key[s->skey];
+    k_graph<0><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
+                                             c->cnt, nullptr, nullptr, nullptr, nullptr, inv2h);
+    sph::launch_scan(c->cnt, n, c->bsum, c->rowptr, st);
+    uint32_t E = 0;
+    cudaMemcpyAsync(&E, c->rowptr + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check(c, "graph count");
+    if (E > c->cfg.max_edges) return fail(c, SPH_ERR_CAPACITY, "more edges than max_edges");
+    c->E = E;
+    k_graph<1><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
+                                             nullptr, c->rowptr, c->col, c->src, c->xe, inv2h);
+    if (c->cfg.train && E) k_graph_rev<<<nblk(E, 256), 256, 0, st>>>(E, c->rowptr, c->col, c->src, c->rev);
+    k_node_features<<<nblk(n, 256), 256, 0, st>>>(d, s->id[cur], hist, 1.0 / (double)c->cfg.v_scale, c->xn);
+    const std::vector<Layer>& Ls = c->layers;
+    const bool train = c->cfg.train != 0;
+    int rc;
+    // encoders
+    if ((rc = linear(c, c->xn, 0, Ls[0], false, n, kEpiRelu, nullptr, 0, c->en1, nullptr, L))) return rc;
+    if ((rc = linear(c, c->en1, 0, Ls[1], false, n, kEpiNone, nullptr, 0, c->XN[0], nullptr, 2 * L))) return rc;
+    if ((rc = linear(c, c->xe, 0, Ls[2], false, E, kEpiRelu, nullptr, 0, c->ee1, nullptr, L))) return rc;
+    if ((rc = linear(c, c->ee1, 0, Ls[3], false, E, kEpiNone, nullptr, 0, c->Ebuf[0], nullptr, L))) return rc;
+    // message passing
+    for (int l = 0; l < c->NL; ++l) {
+        __nv_bfloat16* xn_cur = c->XN[train ? l : l % 2];
+        __nv_bfloat16* xn_next = c->XN[train ? l + 1 : (l + 1) % 2];
+        __nv_bfloat16* e_in = c->Ebuf[train ? l : l % 2];
+        __nv_bfloat16* e_out = c->Ebuf[train ? l + 1 : (l + 1) % 2];
+        __nv_bfloat16* z1 = c->Z1[train ? l : 0];
+        __nv_bfloat16* y1 = c->Y1[train ? l : 0];
+        const Layer* w = &Ls[4 + 6 * l];
+        if ((rc = linear(c, xn_cur, 2 * L, w[0], false, n, kEpiNone, nullptr, 0, c->P, nullptr, L))) return rc;
+        if ((rc = linear(c, xn_cur, 2 * L, w[1], false, n, kEpiNone, nullptr, 0, c->Q, nullptr, L))) return rc;
+        if ((rc = edge1(c, w[2], e_in, z1))) return rc;
+        if ((rc = linear(c, z1, 0, w[3], false, E, kEpiResidual, e_in, L, e_out, nullptr, L))) return rc;
+        k_rowsum<__nv_bfloat16><<<nblk((size_t)n * 32, 256), 256, 0, st>>>(n, c->rowptr, e_out, nullptr,
+                                                                           xn_cur + L, nullptr, 2 * L);
+        if ((rc = linear(c, xn_cur, 0, w[4], false, n, kEpiRelu, nullptr, 0, y1, nullptr, L))) return rc;
+        if ((rc = linear(c, y1, 0, w[5], false, n, kEpiResidual, xn_cur, 2 * L, xn_next, nullptr, 2 * L)))
+            return rc;
+    }
+    __nv_bfloat16* h_last = c->XN[train ? c->NL : c->NL % 2];
+    const Layer* dec = &Ls[4 + 6 * c->NL];
+    if ((rc = linear(c, h_last, 2 * L, dec[0], false, n, kEpiRelu, nullptr, 0, c->D1, nullptr, L))) return rc;
+    if ((rc = linear(c, c->D1, 0, dec[1], false, n, kEpiNone, nullptr, 0, nullptr, c->out, KOUT))) return rc;
+    c->have_forward = true;
+    return check(c, "sur_forward");
+}
+
+int backward(sur_ctx* c, sph_ctx* s, const float* target, float* loss_host) {
+    if (!c->cfg.train) return fail(c, SPH_ERR_STATE, "context not created for training");
+    if (!c->have_forward) return fail(c, SPH_ERR_STATE, "no forward pass to differentiate");
+    cudaStream_t st = c->st;
+    const uint32_t n = c->n, E = c->E;
+    const std::vector<Layer>& Ls = c->layers;
+    const sph::Dev& d = s->d;
+    const int cur = s->cur;
+    // fluid count for the mean
+    uint32_t nf = 0;
+    {
+        // count fluid in-domain particles on the host side from the tables
+        uint32_t n_in = 0;
+        cudaMemcpyAsync(&n_in, s->off + s->tab.ncells, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        uint64_t nb = 0;
+        for (size_t q = 0; q < s->tab.inst.size(); ++q) nb += s->tab.inst[q].id_fluid - s->tab.inst[q].id_base;
+        nf = n_in > nb ? (uint32_t)(n_in - nb) : 1u;
+    }
+    const float inv_nf = 1.f / (float)nf;
+    cudaMemsetAsync(c->g, 0, c->nparams * sizeof(float), st);
+    const uint32_t lb = nblk(n, 256);
+    k_loss<<<lb, 256, 0, st>>>(d, s->id[cur], c->out, target, s->off, inv_nf, c->dout, c->losspart);
+    k_loss_final<<<1, 32, 0, st>>>((int)lb, c->losspart, inv_nf, c->loss);
+    int rc;
+    // decoder
+    const Layer* dec = &Ls[4 + 6 * c->NL];
+    __nv_bfloat16* h_last = c->XN[c->NL];
+    colsum(c, c->dout, true, n, KOUT, KOUT, c->g + dec[1].b_off);
+    wgrad(c, dec[1], c->D1, L, c->dout, KOUT, n);
+    if ((rc = linear(c, c->dout, 0, dec[1], true, n, kEpiReluMask, c->D1, L, c->dD1, nullptr, L))) return rc;
+    colsum(c, c->dD1, true, n, L, L, c->g + dec[0].b_off);
+    wgrad(c, dec[0], h_last, 2 * L, c->dD1, L, n);
+    if ((rc = linear(c, c->dD1, 0, dec[0], true, n, kEpiNone, nullptr, 0, nullptr, c->dH, L))) return rc;
+    cudaMemsetAsync(c->dE, 0, (size_t)E * L * sizeof(float), st);
+    for (int l = c->NL - 1; l >= 0; --l) {
+        const Layer* w = &Ls[4 + 6 * l];
+        __nv_bfloat16* xn_cur = c->XN[l];
+        __nv_bfloat16* e_in = c->Ebuf[l];
+        __nv_bfloat16* z1 = c->Z1[l];
+        __nv_bfloat16* y1 = c->Y1[l];
+        // node update h' = h + W4 relu(W3 [h, agg] + b3) + b4
+        cast(c, c->dH, c->dHb, (size_t)n * L);
+        colsum(c, c->dH, false, n, L, L, c->g + w[5].b_off);
+        wgrad(c, w[5], y1, L, c->dHb, L, n);
+        if ((rc = linear(c, c->dHb, 0, w[5], true, n, kEpiReluMask, y1, L, c->dY1, nullptr, L))) return rc;
+        colsum(c, c->dY1, true, n, L, L, c->g + w[4].b_off);
+        wgrad(c, w[4], xn_cur, 2 * L, c->dY1, L, n, 0);
+        wgrad(c, w[4], xn_cur + L, 2 * L, c->dY1, L, n, 1);
+        if ((rc = linear(c, c->dY1, 0, w[4], true, n, kEpiNone, nullptr, 0, nullptr, c->dXN, 2 * L))) return rc;
+        k_add_strided<<<nblk((size_t)n * L, 256), 256, 0, st>>>(n, c->dH, c->dXN, 2 * L);
+        // aggregation and edge update e' = e + W2 relu(pre) + b2
+        k_add_gather<<<gridcap((size_t)E * L, 256), 256, 0, st>>>((size_t)E * L, c->dE, c->dXN + L,
+                                                                  c->src, 2 * L, c->dEb);
+        colsum(c, c->dE, false, E, L, L, c->g + w[3].b_off);
+        wgrad(c, w[3], z1, L, c->dEb, L, E);
+        if ((rc = linear(c, c->dEb, 0, w[3], true, E, kEpiReluMask, z1, L, c->dpre, nullptr, L))) return rc;
+        colsum(c, c->dpre, true, E, L, L, c->g + w[2].b_off);
+        wgrad(c, w[2], e_in, L, c->dpre, L, E);
+        if ((rc = linear(c, c->dpre, 0, w[2], true, E, kEpiAccum, nullptr, 0, nullptr, c->dE, L))) return rc;
+        // pre = W1a h_i + W1b h_j + ...: sums over the edges of i and of j
+        k_rowsum<__nv_bfloat16><<<nblk((size_t)n * 32, 256), 256, 0, st>>>(n, c->rowptr, c->dpre, nullptr,
+                                                                           c->dPb, nullptr, L);
+        k_rowsum<__nv_bfloat16><<<nblk((size_t)n * 32, 256), 256, 0, st>>>(n, c->rowptr, c->dpre, c->rev,
+                                                                           c->dQb, nullptr, L);
+        wgrad(c, w[0], xn_cur, 2 * L, c->dPb, L, n);
+        wgrad(c, w[1], xn_cur, 2 * L, c->dQb, L, n);
+        if ((rc = linear(c, c->dPb, 0, w[0], true, n, kEpiAccum, nullptr, 0, nullptr, c->dH, L))) return rc;
+        if ((rc = linear(c, c->dQb, 0, w[1], true, n, kEpiAccum, nullptr, 0, nullptr, c->dH, L))) return rc;
+    }
+    // encoders
+    cast(c, c->dE, c->dEb, (size_t)E * L);
+    colsum(c, c->dE, false, E, L, L, c->g + Ls[3].b_off);
+    wgrad(c, Ls[3], c->ee1, L, c->dEb, L, E);
+    if ((rc = linear(c, c->dEb, 0, Ls[3], true, E, kEpiReluMask, c->ee1, L, c->dEe1, nullptr, L))) return rc;
+    colsum(c, c->dEe1, true, E, L, L, c->g + Ls[2].b_off);
+    wgrad(c, Ls[2], c->xe, KIN, c->dEe1, L, E);
+    cast(c, c->dH, c->dHb, (size_t)n * L);
+    colsum(c, c->dH, false, n, L, L, c->g + Ls[1].b_off);
+    wgrad(c, Ls[1], c->en1, L, c->dHb, L, n);
+    if ((rc = linear(c, c->dHb, 0, Ls[1], true, n, kEpiReluMask, c->en1, L, c->dEn1, nullptr, L))) return rc;
+    colsum(c, c->dEn1, true, n, L, L, c->g + Ls[0].b_off);
+    wgrad(c, Ls[0], c->xn, KIN, c->dEn1, L, n);
+    if (loss_host) {
+        cudaMemcpyAsync(loss_host, c->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check(c, "sur_backward");
+    }
+    return check(c, "sur_backward");
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t sur_param_count(const sur_config* cfg) {
+    if (!cfg) return 0;
+    sur_ctx tmp;
+    tmp.NL = (int)cfg->layers;
+    build_layers(&tmp);
+    return tmp.nparams;
+}
+
+uint64_t sur_query_bytes(const sur_config* cfg) {
+    if (!cfg || cfg->layers == 0 || cfg->max_nodes == 0) return 0;
+    sur_ctx tmp;
+    tmp.cfg = *cfg;
+    tmp.NL = (int)cfg->layers;
+    build_layers(&tmp);
+    return carve(&tmp, nullptr);
+}
+
+int sur_init(const sur_config* cfg, void* ws, uint64_t bytes, void* stream, sur_ctx** out) {
+    if (!cfg || !out || !ws || cfg->layers == 0 || cfg->layers > 64 || cfg->max_nodes == 0 ||
+        !(cfg->v_scale > 0.f) || ((uintptr_t)ws % 256) != 0)
+        return SPH_ERR_INVALID_ARG;
+    sur_ctx* c = new sur_ctx();
+    c->cfg = *cfg;
+    c->NL = (int)cfg->layers;
+    c->st = (cudaStream_t)stream;
+    build_layers(c);
+    if (carve(c, ws) > bytes) {
+        delete c;
+        return SPH_ERR_WORKSPACE;
+    }
+    cudaMemsetAsync(c->w, 0, 4 * c->nparams * sizeof(float), c->st);
+    refresh_all(c);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) {
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+int sur_set_params(sur_ctx* c, const float* host, uint64_t count) {
+    if (!c || !host || count != c->nparams) return SPH_ERR_INVALID_ARG;
+    cudaMemcpyAsync(c->w, host, count * sizeof(float), cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(c->m, 0, count * sizeof(float), c->st);
+    cudaMemsetAsync(c->v, 0, count * sizeof(float), c->st);
+    c->adam_t = 0;
+    refresh_all(c);
+    return cudaStreamSynchronize(c->st) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+int sur_get_params(sur_ctx* c, float* host, uint64_t count) {
+    if (!c || !host || count != c->nparams) return SPH_ERR_INVALID_ARG;
+    cudaMemcpyAsync(host, c->w, count * sizeof(float), cudaMemcpyDeviceToHost, c->st);
+    return cudaStreamSynchronize(c->st) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+int sur_get_grads(sur_ctx* c, float* host, uint64_t count) {
+    if (!c || !host || count != c->nparams) return SPH_ERR_INVALID_ARG;
+    cudaMemcpyAsync(host, c->g, count * sizeof(float), cudaMemcpyDeviceToHost, c->st);
+    return cudaStreamSynchronize(c->st) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+int sur_forward(sur_ctx* c, sph_ctx* s, const float* d_hist, float* d_acc) {
+    if (!c || !s || !d_hist) return SPH_ERR_INVALID_ARG;
+    int rc = forward(c, s, d_hist);
+    if (rc) return rc;
+    const float3 am = make_float3(c->cfg.a_mean[0], c->cfg.a_mean[1], c->cfg.a_mean[2]);
+    const float3 as = make_float3(c->cfg.a_std[0], c->cfg.a_std[1], c->cfg.a_std[2]);
+    if (d_acc)
+        k_write_out<<<nblk(s->n, 256), 256, 0, c->st>>>(s->d, s->id[s->cur], c->out, am, as, d_acc);
+    return check(c, "sur_forward");
+}
+
+int sur_backward(sur_ctx* c, sph_ctx* s, const float* d_target, float* loss) {
+    if (!c || !s || !d_target) return SPH_ERR_INVALID_ARG;
+    return backward(c, s, d_target, loss);
+}
+
+int sur_adam(sur_ctx* c, float lr, float beta1, float beta2, float eps) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    c->adam_t += 1;
+    const float c1 = 1.f - powf(beta1, (float)c->adam_t);
+    const float c2 = 1.f - powf(beta2, (float)c->adam_t);
+    k_adam<<<gridcap(c->nparams, 256), 256, 0, c->st>>>(c->nparams, c->w, c->g, c->m, c->v, lr, beta1,
+                                                        beta2, eps, c1, c2);
+    refresh_all(c);
+    return check(c, "sur_adam");
+}
+
+int sur_advance(sur_ctx* c, sph_ctx* s, float* d_hist) {
+    if (!c || !s || !d_hist) return SPH_ERR_INVALID_ARG;
+    int rc = forward(c, s, d_hist);
+    if (rc) return rc;
+    const float3 am = make_float3(c->cfg.a_mean[0], c->cfg.a_mean[1], c->cfg.a_mean[2]);
+    const float3 as = make_float3(c->cfg.a_std[0], c->cfg.a_std[1], c->cfg.a_std[2]);
+    const int cur = s->cur;
+    k_write_out<<<nblk(s->n, 256), 256, 0, c->st>>>(s->d, s->id[cur], c->out, am, as, c->acc);
+    k_advance<<<nblk(s->n, 256), 256, 0, c->st>>>(s->d, s->id[cur], s->x[cur], s->y[cur], s->z[cur],
+                                                  s->vr[cur], s->off, c->acc, d_hist, c->cfg.dt_s);
+    s->cells_valid = false;
+    s->keys_ready = false;
+    s->pre_state = 0;
+    return check(c, "sur_advance");
+}
+
+uint32_t sur_num_edges(const sur_ctx* c) { return c ? c->E : 0; }
+
+const char* sur_last_error(const sur_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+void sur_destroy(sur_ctx* c) { delete c; }
+
+}  // extern "C"

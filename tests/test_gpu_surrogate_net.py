@@ -1,0 +1,206 @@
+"""The surrogate network through the C ABI (graph, forward, backward, Adam,
+integration step) against the FP64 reference of oracle/sur_oracle.py on the
+same seeded particles and weights, with the reference rounding to bfloat16
+wherever the GPU stores bfloat16."""
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+from oracle import sur_oracle as so
+from paper_1210_1017_gb300 import cases
+from paper_1210_1017_gb300 import sph as S
+from paper_1210_1017_gb300 import surrogate as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    return t
+
+
+class Setup:
+    """A jittered particle block on the GPU with a random velocity history,
+    and the same data by particle id for the reference."""
+
+    def __init__(self, torch, n, layers, seed=0, train=True, v_scale=0.5):
+        self.case = c = cases.random_block(n, seed=seed + 21, jitter=0.3)
+        self.layers = layers
+        self.sim = S.Simulation.from_case(c)
+        self.sim.build_cells()
+        rng = np.random.default_rng(seed)
+        self.n = c.n
+        order = np.argsort(c.ids)
+        self.pos = c.pos[order]                       # by id
+        self.bnd = np.arange(c.n) < c.n_bound
+        self.hist = rng.normal(0, 0.4, (c.n, 15)).astype(np.float32)
+        self.hist[self.bnd] = 0
+        self.target = rng.normal(0, 1.0, (c.n, 3)).astype(np.float32)
+        self.d_hist = torch.tensor(self.hist, device="cuda")
+        self.d_target = torch.tensor(self.target, device="cuda")
+        self.v_scale = v_scale
+        self.sur = U.Surrogate(self.sim, layers=layers, train=train, v_scale=v_scale)
+        self.w = so.init_params(layers, seed=seed + 5)
+        self.sur.set_params(self.w)
+        self.src, self.dst = so.graph(self.pos, c.h)
+        self.xn = so.node_features(self.hist, self.bnd, np.float32(v_scale))
+        self.xe = so.edge_features(self.pos, c.h, self.src, self.dst)
+
+    def gpu_forward(self, torch):
+        acc = torch.zeros((self.n, 3), dtype=torch.float32, device="cuda")
+        self.sur.forward(self.d_hist, acc)
+        self.sim.synchronize()
+        return acc.cpu().numpy().astype(np.float64)
+
+    def ref(self, bf16=True):
+        return so.forward_backward(self.w, self.layers, self.xn, self.xe, self.src, self.dst,
+                                   self.target, ~self.bnd, bf16=bf16)
+
+
+def _cos(a, b):
+    a, b = a.ravel(), b.ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,layers", [(700, 1), (2000, 2), (2000, 10)])
+def test_graph_and_forward_match_reference(torch, n, layers):
+    s = Setup(torch, n, layers, seed=n + layers)
+    got = s.gpu_forward(torch)
+    # the graph: the same FP64 predicate, so the same number of edges
+    assert s.sur.num_edges == len(s.src)
+    out, _, _ = s.ref(bf16=True)
+    ref = out[:, :3]
+    assert _cos(got, ref) >= 0.9999, _cos(got, ref)
+    assert _rel(got, ref) <= 1e-2, _rel(got, ref)
+    # element-wise against the output scale
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 5e-2 * scale
+    # the bf16 storage error itself, for the record (FP64 without rounding)
+    out64, _, _ = s.ref(bf16=False)
+    assert _rel(got, out64[:, :3]) <= 5e-2
+
+
+@pytest.mark.parametrize("n,layers", [(1500, 1), (2000, 3), (2000, 10)])
+def test_backward_matches_reference_gradients(torch, n, layers):
+    s = Setup(torch, n, layers, seed=3 * n + layers)
+    s.gpu_forward(torch)
+    loss = s.sur.backward(s.d_target)
+    g = s.sur.grads().astype(np.float64)
+    _, lref, gref = s.ref(bf16=True)
+    assert abs(loss - lref) <= 1e-2 * lref, (loss, lref)
+    assert _cos(g, gref) >= 0.9999, _cos(g, gref)
+    o = 0
+    for name, ki, ko, has_b in so.layer_shapes(layers):
+        for part, size in (("W", ki * ko), ("b", ko if has_b else 0)):
+            if size == 0:
+                continue
+            a, b = g[o:o + size], gref[o:o + size]
+            o += size
+            if np.linalg.norm(b) < 1e-6 * np.linalg.norm(gref):
+                continue
+            assert _rel(a, b) <= 3e-2, (name, part, _rel(a, b))
+    assert o == len(g)
+
+
+def test_inference_context_gives_the_training_forward(torch):
+    s = Setup(torch, 1800, 4, seed=9)
+    a = s.gpu_forward(torch)
+    inf = U.Surrogate(s.sim, layers=4, train=False, v_scale=s.v_scale)
+    inf.set_params(s.w)
+    acc = torch.zeros((s.n, 3), dtype=torch.float32, device="cuda")
+    inf.forward(s.d_hist, acc)
+    s.sim.synchronize()
+    assert np.array_equal(acc.cpu().numpy().astype(np.float64), a)
+    # and repeated calls are deterministic
+    assert np.array_equal(s.gpu_forward(torch), a)
+
+
+def test_adam_step_matches_reference(torch):
+    s = Setup(torch, 900, 1, seed=4)
+    s.gpu_forward(torch)
+    s.sur.backward(s.d_target)
+    g = s.sur.grads().astype(np.float64)
+    w0 = s.sur.params().astype(np.float64)
+    lr = 1e-3
+    s.sur.adam(lr)
+    w1 = s.sur.params().astype(np.float64)
+    ref, m, v = so.adam(w0, g, np.zeros_like(g), np.zeros_like(g), 1, lr)
+    assert np.abs(w1 - ref).max() <= 1e-5 * lr + 2e-7 * np.abs(w0).max()
+    # second step with fresh gradients
+    s.gpu_forward(torch)
+    s.sur.backward(s.d_target)
+    g2 = s.sur.grads().astype(np.float64)
+    s.sur.adam(lr)
+    w2 = s.sur.params().astype(np.float64)
+    ref2, _, _ = so.adam(w1, g2, m, v, 2, lr)
+    assert np.abs(w2 - ref2).max() <= 1e-5 * lr + 2e-7 * np.abs(w1).max()
+
+
+def test_advance_is_semi_implicit_euler_and_shifts_history(torch):
+    dt = 2e-3
+    s = Setup(torch, 1200, 2, seed=6)
+    sur = U.Surrogate(s.sim, layers=2, train=False, v_scale=s.v_scale,
+                      a_mean=(0.1, -0.2, -9.81), a_std=(2.0, 3.0, 4.0), dt_s=dt)
+    sur.set_params(s.w)
+    acc = torch.zeros((s.n, 3), dtype=torch.float32, device="cuda")
+    sur.forward(s.d_hist, acc)
+    s.sim.synchronize()
+    acc = acc.cpu().numpy()
+    before = s.sim.download()
+    hist = s.d_hist.clone()
+    sur.advance(hist)
+    after = s.sim.download()
+    ob, oa = np.argsort(before["ids"]), np.argsort(after["ids"])
+    pb, vb = before["pos"][ob], before["vel"][ob].astype(np.float64)
+    pa, va = after["pos"][oa], after["vel"][oa].astype(np.float64)
+    fluid = ~s.bnd
+    # the denormalised output is out * a_std + a_mean of the plain forward
+    out, _, _ = s.ref(bf16=True)
+    want_acc = out[:, :3] * np.array([2.0, 3.0, 4.0]) + np.array([0.1, -0.2, -9.81])
+    assert _rel(acc, want_acc) <= 1e-2
+    pw, vw = so.euler_step(pb, vb, acc.astype(np.float64), fluid, dt)
+    np.testing.assert_allclose(va, vw, rtol=0, atol=1e-5 * (np.abs(vw).max() + 1))
+    np.testing.assert_allclose(pa, pw, rtol=0, atol=1e-9)
+    assert np.array_equal(pa[s.bnd], pb[s.bnd]) and np.array_equal(va[s.bnd], vb[s.bnd])
+    h = hist.cpu().numpy()
+    assert np.array_equal(h[:, :12], s.hist[:, 3:])
+    assert np.array_equal(h[fluid, 12:], after["vel"][oa][fluid])
+    assert np.all(h[s.bnd, 12:] == 0)
+    # the cells are stale until rebuilt; the next call needs them
+    with pytest.raises(S.SphError):
+        sur.forward(hist, None)
+    s.sim.build_cells()
+    sur.forward(hist, None)
+
+
+def test_training_reduces_the_loss_on_a_learnable_target(torch):
+    s = Setup(torch, 1500, 2, seed=8)
+    # a smooth function of the inputs: the newest velocity, scaled
+    tgt = (0.5 * s.hist[:, 12:15] / s.v_scale).astype(np.float32)
+    d_t = torch.tensor(tgt, device="cuda")
+    losses = []
+    for _ in range(150):
+        s.sur.forward(s.d_hist, None)
+        losses.append(s.sur.backward(d_t))
+        s.sur.adam(1e-3)
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def test_errors_are_reported_not_faulted(torch):
+    s = Setup(torch, 600, 1, seed=2, train=False)
+    with pytest.raises(S.SphError, match="STATE"):
+        s.sur.backward(s.d_target)          # inference context
+    small = U.Surrogate(s.sim, layers=1, max_edges=100, v_scale=1.0)
+    with pytest.raises(S.SphError, match="CAPACITY"):
+        small.forward(s.d_hist, None)
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        U.sur_set_params(s.sur.ctx, np.zeros(5, np.float32))
