@@ -217,6 +217,11 @@ int sph_rollout(sph_ctx *ctx, uint32_t nsteps, uint32_t save_every,
 int sph_download(sph_ctx *ctx, double *pos, float *vel, float *rho,
                  uint32_t *ids);
 
+/* As sph_download, with each array indexed by particle id instead of the
+ * sorted order (row id holds particle id).  Needs every uploaded id below
+ * n (SPH_ERR_STATE otherwise).  Sync. */
+int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
+
 /* Copy an internal device array to host memory for inspection.  bytes must
  * equal the array's size (see sph_array_bytes).  Sync.
  *   SPH_ARRAY_KEY      uint32[n]  cell label of each particle, sorted order

@@ -103,6 +103,20 @@ int sur_adam(sur_ctx *ctx, float lr, float beta1, float beta2, float eps);
  * context's cells are stale afterwards (call sph_build_cells).  Sync. */
 int sur_advance(sur_ctx *ctx, struct sph_ctx *sph, float *d_hist);
 
+/* A training sample from seven saved frames of the SPH context's particles
+ * (d_frames: device, 7 x n x 3 float64 by id, frame f = x at time
+ * t_k + (f - 5) dt_s).  Input frames 1..5 get random-walk noise (per frame
+ * increments N(0, sigma^2/5) from a counter-based SplitMix64/Box-Muller
+ * stream of `seed`, so x^k has std sigma; boundary particles none).
+ * Writes (device, by id): d_pos n x 3 float64 = noisy x^k; d_vel n x 3 =
+ * (x~^k - x~^{k-1}) / dt_s; d_hist n x 15 = the five finite-difference
+ * velocities, oldest first; d_target n x 3 = ((x^{k+1} - 2 x~^k +
+ * x~^{k-1}) / dt_s^2 - a_mean) / a_std, the normalised acceleration that
+ * sur_advance needs to land on the clean x^{k+1}.  Async. */
+int sur_make_sample(sur_ctx *ctx, struct sph_ctx *sph, const double *d_frames,
+                    double sigma, uint64_t seed, double *d_pos, float *d_vel,
+                    float *d_hist, float *d_target);
+
 uint32_t sur_num_edges(const sur_ctx *ctx);
 const char *sur_last_error(const sur_ctx *ctx);
 void sur_destroy(sur_ctx *ctx);

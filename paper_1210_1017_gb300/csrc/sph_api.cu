@@ -46,13 +46,32 @@ int bit_length(uint64_t v) {
 
 __global__ void k_unpack(uint32_t n, const double* __restrict__ pos, const float* __restrict__ vel,
                          const float* __restrict__ rho, double* x, double* y, double* z,
-                         float4* vr) {
+                         float4* vr, const uint32_t* __restrict__ id, uint32_t* id_flag) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (id[i] >= n) atomicOr(id_flag, 1u);
     x[i] = pos[3 * (size_t)i];
     y[i] = pos[3 * (size_t)i + 1];
     z[i] = pos[3 * (size_t)i + 2];
     vr[i] = make_float4(vel[3 * (size_t)i], vel[3 * (size_t)i + 1], vel[3 * (size_t)i + 2], rho[i]);
+}
+
+// Scatter by id (every id < n, distinct).
+__global__ void k_pack_by_id(uint32_t n, const double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ z, const float4* __restrict__ vr,
+                             const uint32_t* __restrict__ id, double* pos, float* vel, float* rho) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = id[i];
+    if (k >= n) return;
+    pos[3 * (size_t)k] = x[i];
+    pos[3 * (size_t)k + 1] = y[i];
+    pos[3 * (size_t)k + 2] = z[i];
+    const float4 v = vr[i];
+    vel[3 * (size_t)k] = v.x;
+    vel[3 * (size_t)k + 1] = v.y;
+    vel[3 * (size_t)k + 2] = v.z;
+    rho[k] = v.w;
 }
 
 __global__ void k_pack(uint32_t n, const double* __restrict__ x, const double* __restrict__ y,
@@ -203,6 +222,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->lvl2_q = cv.take<unsigned long long>(4 * kReduceBlocks);
     c->done = cv.take<uint32_t>(1);
     c->status = cv.take<uint32_t>(1);
+    c->id_flag = cv.take<uint32_t>(1);
     c->diag_out = cv.take<double>(8);
     c->diag_part = cv.take<double>(8 * kDiagBlocks);
     c->counters = cv.take<unsigned long long>(8);
@@ -525,15 +545,21 @@ int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho
     cudaMemcpyAsync(dvel, vel, 3 * n * sizeof(float), cudaMemcpyDefault, st);
     cudaMemcpyAsync(drho, rho, n * sizeof(float), cudaMemcpyDefault, st);
     cudaMemcpyAsync(c->id[c->cur], ids, n * sizeof(uint32_t), cudaMemcpyDefault, st);
+    cudaMemsetAsync(c->id_flag, 0, sizeof(uint32_t), st);
     k_unpack<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(c->n, dpos, dvel, drho, c->x[c->cur],
-                                                         c->y[c->cur], c->z[c->cur], c->vr[c->cur]);
+                                                         c->y[c->cur], c->z[c->cur], c->vr[c->cur],
+                                                         c->id[c->cur], c->id_flag);
     rc = post_launch(c, "upload");
     if (rc) return rc;
+    uint32_t flag = 1;
+    cudaMemcpyAsync(&flag, c->id_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     c->have_state = true;
     c->cells_valid = false;
     c->keys_ready = false;
     c->pre_state = 0;
-    return cuda_check(c, cudaStreamSynchronize(st), "upload sync");
+    rc = cuda_check(c, cudaStreamSynchronize(st), "upload sync");
+    c->ids_dense = rc == SPH_OK && flag == 0;
+    return rc;
 }
 
 int sph_build_cells(sph_ctx* c) {
@@ -649,6 +675,25 @@ int sph_download(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids)
     if (rho) cudaMemcpyAsync(rho, dr, n * sizeof(float), cudaMemcpyDefault, st);
     if (ids) cudaMemcpyAsync(ids, c->id[c->cur], n * sizeof(uint32_t), cudaMemcpyDefault, st);
     return cuda_check(c, cudaStreamSynchronize(st), "download");
+}
+
+int sph_download_by_id(sph_ctx* c, double* pos, float* vel, float* rho) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
+    if (!c->ids_dense) return fail(c, SPH_ERR_STATE, "ids are not all below n");
+    const size_t n = c->n;
+    cudaStream_t st = c->st;
+    double* dpos = c->stage_pos;
+    float* dv = c->stage_vr;
+    float* dr = dv + 3 * n;
+    k_pack_by_id<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(
+        c->n, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->vr[c->cur], c->id[c->cur], dpos, dv, dr);
+    int rc = post_launch(c, "download_by_id pack");
+    if (rc) return rc;
+    if (pos) cudaMemcpyAsync(pos, dpos, 3 * n * sizeof(double), cudaMemcpyDefault, st);
+    if (vel) cudaMemcpyAsync(vel, dv, 3 * n * sizeof(float), cudaMemcpyDefault, st);
+    if (rho) cudaMemcpyAsync(rho, dr, n * sizeof(float), cudaMemcpyDefault, st);
+    return cuda_check(c, cudaStreamSynchronize(st), "download_by_id");
 }
 
 uint64_t sph_array_bytes(const sph_ctx* c, int which) {

@@ -49,6 +49,7 @@ struct sph_ctx {
     uint4* part_u;
     unsigned long long* lvl2_q;
     uint32_t *done, *status;
+    uint32_t* id_flag;       // set by the upload when some id >= n
     double *diag_out, *diag_part;
     unsigned long long* counters;
     // ensemble table and per-member state (device)
@@ -64,6 +65,7 @@ struct sph_ctx {
     int cur = 0;             // state buffer index
     int skey = 0;            // key/val buffer holding the last sort result
     bool have_state = false;
+    bool ids_dense = false;  // every id < n (ids then index by-id arrays)
     bool cells_valid = false;
     bool keys_ready = false; // labels + histograms already computed
     int pre_state = 0;       // 0 none, 1 in px[0] (unsorted), 2 in px[1] (sorted)

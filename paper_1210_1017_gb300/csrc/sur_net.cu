@@ -332,6 +332,65 @@ __global__ void k_advance(const sph::Dev d, const uint32_t* __restrict__ id, dou
 
 inline uint32_t nblk(size_t n, uint32_t t) { return (uint32_t)((n + t - 1) / t); }
 
+// ---------------------------------------------------------- training data --
+
+// SplitMix64 finaliser (Steele, Lea & Flood, 2014) as a counter-based
+// generator: the 64-bit output for counter k under a seed.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One standard normal per counter (Box-Muller on two 32-bit uniforms).
+__device__ __forceinline__ double normal01(uint64_t seed, uint64_t k) {
+    const uint64_t r = splitmix64(seed ^ splitmix64(k));
+    const double u1 = ((double)(uint32_t)(r >> 32) + 1.0) * (1.0 / 4294967296.0);   // (0, 1]
+    const double u2 = (double)(uint32_t)r * (1.0 / 4294967296.0);                    // [0, 1)
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// A training sample from seven saved frames by id (f = 0..6 hold
+// x^{k-5} .. x^{k+1}, spaced dt): random-walk noise on the input frames
+// (increments of std sigma / sqrt(5) from frame 1 on, so x^k carries std
+// sigma; boundary particles none), finite-difference velocities of the
+// noisy frames, and the acceleration that brings the noisy x^k to the clean
+// x^{k+1} under semi-implicit Euler, normalised.
+__global__ void k_make_sample(const sph::Dev d, const double* __restrict__ frames, uint32_t n,
+                              double sigma, uint64_t seed, double dt, float3 am, float3 as,
+                              double* __restrict__ pos, float* __restrict__ vel,
+                              float* __restrict__ hist, float* __restrict__ target) {
+    const uint32_t pid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pid >= n) return;
+    uint32_t lo = 0, hi = d.n_inst;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (d.id_base[mid] <= pid) lo = mid;
+        else hi = mid;
+    }
+    const bool bound = pid < d.inst[lo].id_fluid;
+    const double step_sd = bound ? 0.0 : sigma / sqrt(5.0);
+    const double inv_dt = 1.0 / dt;
+    const float amv[3] = {am.x, am.y, am.z}, asv[3] = {as.x, as.y, as.z};
+    for (int a = 0; a < 3; ++a) {
+        double xt[6];
+        double walk = 0.0;
+        for (int f = 0; f < 6; ++f) {
+            if (f > 0 && step_sd > 0.0)
+                walk += step_sd * normal01(seed, ((uint64_t)pid * 8u + (uint64_t)f) * 4u + (uint64_t)a);
+            xt[f] = frames[((size_t)f * n + pid) * 3 + a] + walk;
+        }
+        for (int f = 1; f < 6; ++f)
+            hist[(size_t)pid * 15 + (f - 1) * 3 + a] = (float)((xt[f] - xt[f - 1]) * inv_dt);
+        const double x6 = frames[((size_t)6 * n + pid) * 3 + a];
+        const double acc = (x6 - 2.0 * xt[5] + xt[4]) * inv_dt * inv_dt;
+        pos[(size_t)pid * 3 + a] = xt[5];
+        vel[(size_t)pid * 3 + a] = (float)((xt[5] - xt[4]) * inv_dt);
+        target[(size_t)pid * 3 + a] = (float)((acc - (double)amv[a]) / (double)asv[a]);
+    }
+}
+
 // out (cols x rows) = in (rows x cols)^T
 __global__ void k_transpose(const float* __restrict__ in, int rows, int cols, float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -593,6 +652,7 @@ int check(sur_ctx* c, const char* what) {
 
 int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
     if (!s->cells_valid) return fail(c, SPH_ERR_STATE, "SPH cells not built");
+    if (!s->ids_dense) return fail(c, SPH_ERR_STATE, "by-id arrays need every id below n");
     if (s->n > c->cfg.max_nodes) return fail(c, SPH_ERR_INVALID_ARG, "more particles than max_nodes");
     const uint32_t n = s->n;
     c->n = n;
@@ -845,6 +905,20 @@ int sur_advance(sur_ctx* c, sph_ctx* s, float* d_hist) {
     s->keys_ready = false;
     s->pre_state = 0;
     return check(c, "sur_advance");
+}
+
+int sur_make_sample(sur_ctx* c, sph_ctx* s, const double* d_frames, double sigma,
+                    uint64_t seed, double* d_pos, float* d_vel, float* d_hist, float* d_target) {
+    if (!c || !s || !d_frames || !d_pos || !d_vel || !d_hist || !d_target || !(sigma >= 0.0) ||
+        !(c->cfg.dt_s > 0.f))
+        return SPH_ERR_INVALID_ARG;
+    if (s->n > c->cfg.max_nodes) return fail(c, SPH_ERR_INVALID_ARG, "more particles than max_nodes");
+    const float3 am = make_float3(c->cfg.a_mean[0], c->cfg.a_mean[1], c->cfg.a_mean[2]);
+    const float3 as = make_float3(c->cfg.a_std[0], c->cfg.a_std[1], c->cfg.a_std[2]);
+    k_make_sample<<<nblk(s->n, 256), 256, 0, c->st>>>(s->d, d_frames, s->n, sigma, seed,
+                                                      (double)c->cfg.dt_s, am, as, d_pos, d_vel,
+                                                      d_hist, d_target);
+    return check(c, "sur_make_sample");
 }
 
 uint32_t sur_num_edges(const sur_ctx* c) { return c ? c->E : 0; }

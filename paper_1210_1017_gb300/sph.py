@@ -28,7 +28,7 @@ ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE"
           -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE"}
 SPH_RADIX_SORT_STATIC_MAX_N = 1 << 20
 
-EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells",
+EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph_download_by_id",
             "sph_interact", "sph_predict", "sph_correct", "sph_step",
             "sph_rollout", "sph_download", "sph_array_bytes", "sph_read_array",
             "sph_neighbour_counts_fp64", "sph_diagnostics", "sph_check",
@@ -117,6 +117,7 @@ def lib(build: bool = False):
     L.sph_step.argtypes = [vp, u32]
     L.sph_rollout.argtypes = [vp, u32, u32, SNAPSHOT_FN, vp]
     L.sph_download.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_download_by_id.argtypes = [vp, vp, vp, vp]
     L.sph_array_bytes.argtypes = [vp, i32]
     L.sph_array_bytes.restype = u64
     L.sph_read_array.argtypes = [vp, i32, vp, u64]
@@ -287,6 +288,11 @@ def sph_download(ctx, pos=None, vel=None, rho=None, ids=None):
            "sph_download")
 
 
+def sph_download_by_id(ctx, pos=None, vel=None, rho=None):
+    _check(lib().sph_download_by_id(ctx, _ptr(pos), _ptr(vel), _ptr(rho)), ctx,
+           "sph_download_by_id")
+
+
 def sph_read_array(ctx, which: int, out: np.ndarray):
     nbytes = lib().sph_array_bytes(ctx, which)
     assert out.nbytes == nbytes, (out.nbytes, nbytes)
@@ -431,6 +437,8 @@ class Simulation:
         vel = np.ascontiguousarray(vel, dtype=np.float32) if isinstance(vel, np.ndarray) else vel
         rho = np.ascontiguousarray(rho, dtype=np.float32) if isinstance(rho, np.ndarray) else rho
         ids = np.ascontiguousarray(ids, dtype=np.uint32) if isinstance(ids, np.ndarray) else ids
+        # device tensors come from torch's current stream
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
         sph_upload(self.ctx, pos, vel, rho, ids)
 
     def build_cells(self):
@@ -466,6 +474,20 @@ class Simulation:
         ids = np.empty(n, np.uint32)
         sph_download(self.ctx, pos, vel, rho, ids)
         return dict(pos=pos, vel=vel, rho=rho, ids=ids)
+
+    def download_to(self, pos=None, vel=None, rho=None, ids=None):
+        """Copy the state into caller-owned arrays or device tensors (sorted
+        order; any may be None)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        sph_download(self.ctx, pos, vel, rho, ids)
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def download_by_id(self, pos=None, vel=None, rho=None):
+        """State indexed by particle id into caller-owned arrays or device
+        tensors (any may be None)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        sph_download_by_id(self.ctx, pos, vel, rho)
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
     def read(self, which):
         n = self.n

@@ -16,7 +16,8 @@ class SurConfig(C.Structure):
 
 EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_param_count",
             "sur_query_bytes", "sur_init", "sur_set_params", "sur_get_params", "sur_get_grads",
-            "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_num_edges",
+            "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_make_sample",
+            "sur_num_edges",
             "sur_last_error", "sur_destroy"]
 SUR_EPI_NONE, SUR_EPI_RELU, SUR_EPI_RESIDUAL, SUR_EPI_RELU_MASK = 0, 1, 2, 4
 
@@ -45,6 +46,7 @@ def lib():
         L.sur_backward.argtypes = [vp, vp, vp, vp]
         L.sur_adam.argtypes = [vp, f, f, f, f]
         L.sur_advance.argtypes = [vp, vp, vp]
+        L.sur_make_sample.argtypes = [vp, vp, vp, C.c_double, u64, vp, vp, vp, vp]
         L.sur_num_edges.argtypes = [vp]
         L.sur_num_edges.restype = u32
         L.sur_last_error.argtypes = [vp]
@@ -138,6 +140,11 @@ def sur_advance(ctx, sph_ctx, d_hist):
     _chk(lib().sur_advance(ctx, sph_ctx, _p(d_hist)), ctx, "sur_advance")
 
 
+def sur_make_sample(ctx, sph_ctx, d_frames, sigma, seed, d_pos, d_vel, d_hist, d_target):
+    _chk(lib().sur_make_sample(ctx, sph_ctx, _p(d_frames), sigma, seed, _p(d_pos), _p(d_vel),
+                               _p(d_hist), _p(d_target)), ctx, "sur_make_sample")
+
+
 def sur_num_edges(ctx) -> int:
     return int(lib().sur_num_edges(ctx))
 
@@ -157,17 +164,26 @@ class Surrogate:
     tensor (n, 15) by particle id: the last five velocities, oldest first."""
 
     def __init__(self, sim, layers=10, max_edges=None, train=False, v_scale=1.0,
-                 a_mean=(0.0, 0.0, 0.0), a_std=(1.0, 1.0, 1.0), dt_s=0.0, edges_per_node=90):
+                 a_mean=(0.0, 0.0, 0.0), a_std=(1.0, 1.0, 1.0), dt_s=0.0, edges_per_node=90,
+                 max_nodes=None):
         import torch
         self.sim = sim
         self.torch = torch
+        max_nodes = int(max_nodes or sim.n)
         if max_edges is None:
-            max_edges = sim.n * edges_per_node
-        self.cfg = make_config(layers, sim.n, int(max_edges), train, v_scale, a_mean, a_std, dt_s)
+            max_edges = max_nodes * edges_per_node
+        self.cfg = make_config(layers, max_nodes, int(max_edges), train, v_scale, a_mean, a_std,
+                               dt_s)
         self.nparams = sur_param_count(self.cfg)
         nbytes = sur_query_bytes(self.cfg)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=sim.device)
         self.ctx = sur_init(self.cfg, self.workspace.data_ptr(), nbytes, sim.stream.cuda_stream)
+
+    def bind(self, sim):
+        """Work on the particles of another simulation on the same stream
+        (at most max_nodes particles)."""
+        assert sim.stream == self.sim.stream and sim.n <= self.cfg.max_nodes
+        self.sim = sim
 
     def set_params(self, w):
         sur_set_params(self.ctx, w)
@@ -178,17 +194,37 @@ class Surrogate:
     def grads(self):
         return sur_get_grads(self.ctx, self.nparams)
 
+    # Tensors come from torch's current stream and the library works on the
+    # simulation's stream: each call orders the two both ways.
+    def _enter(self):
+        self.sim.stream.wait_stream(self.torch.cuda.current_stream(self.sim.device))
+
+    def _leave(self):
+        self.torch.cuda.current_stream(self.sim.device).wait_stream(self.sim.stream)
+
     def forward(self, hist, acc=None):
+        self._enter()
         sur_forward(self.ctx, self.sim.ctx, hist, acc)
+        self._leave()
 
     def backward(self, target):
-        return sur_backward(self.ctx, self.sim.ctx, target)
+        self._enter()
+        loss = sur_backward(self.ctx, self.sim.ctx, target)
+        self._leave()
+        return loss
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         sur_adam(self.ctx, lr, beta1, beta2, eps)
 
     def advance(self, hist):
+        self._enter()
         sur_advance(self.ctx, self.sim.ctx, hist)
+        self._leave()
+
+    def make_sample(self, frames, sigma, seed, pos, vel, hist, target):
+        self._enter()
+        sur_make_sample(self.ctx, self.sim.ctx, frames, sigma, seed, pos, vel, hist, target)
+        self._leave()
 
     @property
     def num_edges(self):

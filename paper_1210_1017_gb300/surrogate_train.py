@@ -1,0 +1,354 @@
+"""Training data, training loop and rollout evaluation of the learned
+surrogate, all on one GPU through the C ABI (include/sph.h, include/sur.h).
+
+* Data: groups of dam-break ensemble members run by the GPU SPH with a fixed
+  step (the smallest adaptive step of a pilot run), positions saved by id
+  every ``steps_per_frame`` steps into device memory (frames spaced dt_s).
+* Samples: seven consecutive frames of a group -> noisy input state,
+  velocity history and normalised target acceleration (sur_make_sample).
+* Training: forward, backward and Adam on the tensor-core kernels of the
+  library; a sample is one whole group (all its members at one time).
+* Evaluation: surrogate rollouts against the SPH frames (position RMSE / dp,
+  front position, kinetic + potential energy) and against constant-velocity
+  extrapolation (the update without a learned acceleration).
+
+PyTorch only holds device memory and streams here; the statistics of the
+data (means, standard deviations) and the error metrics are plain tensor
+reductions outside the hot path.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import cases
+from . import sph as S
+from . import surrogate as U
+
+
+# ------------------------------------------------------------------- data --
+
+@dataclass
+class Group:
+    """Ensemble members simulated together, with their saved frames."""
+    ens: "cases.Ensemble"
+    sim: "S.Simulation"
+    frames: object = None           # torch float64 (F, n, 3) by id
+    dt: float = 0.0                 # SPH step
+    steps_per_frame: int = 4
+    fluid: object = None            # torch bool (n,) by id
+
+    @property
+    def n(self):
+        return self.ens.n
+
+    @property
+    def dt_s(self):
+        return self.dt * self.steps_per_frame
+
+
+def make_group(specs, dp=0.02, t_end=1.0, stream=None, dt_fixed=0.0):
+    ens = cases.ensemble([cases.ensemble_instance(sp, dp=dp) for sp in specs], t_end=t_end)
+    sim = S.Simulation(ens.params, ens.n, members=ens.members, stream=stream, dt_fixed=dt_fixed)
+    sim.upload(ens.pos, ens.vel, ens.rho, ens.ids)
+    return Group(ens=ens, sim=sim)
+
+
+def pilot_dt(group: Group, t_end: float, chunk: int = 100) -> float:
+    """Smallest adaptive CFL step over all members until t_end (the fixed
+    step of the data runs)."""
+    sim = group.sim
+    sim.upload(group.ens.pos, group.ens.vel, group.ens.rho, group.ens.ids)
+    dt_min = math.inf
+    while True:
+        sim.step(chunk)
+        t, dt, done, _ = sim.instance_state()
+        live = dt > 0
+        if live.any():
+            dt_min = min(dt_min, float(dt[live].min()))
+        if done.all() or float(t.min()) >= t_end:
+            break
+    return dt_min
+
+
+def record(group: Group, dt: float, n_frames: int, steps_per_frame: int = 4):
+    """Run the group with the fixed step dt from its initial state and keep
+    n_frames position frames by id (device, float64), steps_per_frame steps
+    apart."""
+    import torch
+    ens = group.ens
+    sim = S.Simulation(ens.params, ens.n, members=ens.members, stream=group.sim.stream,
+                       dt_fixed=dt)
+    sim.upload(ens.pos, ens.vel, ens.rho, ens.ids)
+    frames = torch.empty((n_frames, ens.n, 3), dtype=torch.float64, device=sim.device)
+    for f in range(n_frames):
+        if f:
+            sim.step(steps_per_frame)
+        sim.download_by_id(pos=frames[f])
+    sim.check()
+    group.sim.close()
+    group.sim = sim
+    group.frames = frames
+    group.dt = dt
+    group.steps_per_frame = steps_per_frame
+    fluid = np.ones(ens.n, bool)
+    for q, m in enumerate(ens.members):
+        b = int(ens.id_base[q])
+        fluid[b:b + int(m["n_bound"])] = False
+    group.fluid = torch.tensor(fluid, device=sim.device)
+    return group
+
+
+def data_stats(groups):
+    """Velocity scale and per-axis mean / std of the (clean) finite-difference
+    accelerations over the fluid particles of all frames."""
+    import torch
+    vs, acc = [], []
+    for g in groups:
+        fr = g.frames[:, g.fluid]
+        v = (fr[1:] - fr[:-1]) / g.dt_s
+        a = (fr[2:] - 2 * fr[1:-1] + fr[:-2]) / g.dt_s ** 2
+        vs.append(v.reshape(-1, 3))
+        acc.append(a.reshape(-1, 3))
+    v = torch.cat(vs)
+    a = torch.cat(acc)
+    v_scale = float(v.pow(2).mean().sqrt())
+    a_mean = tuple(float(x) for x in a.mean(0))
+    a_std = tuple(max(float(x), 1e-3) for x in a.std(0))
+    return v_scale, a_mean, a_std
+
+
+# ----------------------------------------------------------- parameters --
+
+def layer_list(layers: int):
+    """(name, kin, kout, has_bias) in the order of the flat parameter array
+    of include/sur.h."""
+    L, K = 128, 16
+    out = [("enc_n0", K, L, True), ("enc_n1", L, L, True),
+           ("enc_e0", K, L, True), ("enc_e1", L, L, True)]
+    for l in range(layers):
+        out += [(f"mp{l}_w1a", L, L, False), (f"mp{l}_w1b", L, L, False),
+                (f"mp{l}_w1c", L, L, True), (f"mp{l}_w2", L, L, True),
+                (f"mp{l}_w3", 2 * L, L, True), (f"mp{l}_w4", L, L, True)]
+    out += [("dec0", L, L, True), ("dec1", L, K, True)]
+    return out
+
+
+def init_params(layers: int, seed: int = 0, mean_degree: float = 50.0,
+                residual_gain: float = 0.1) -> np.ndarray:
+    """Initial weights: He-normal for layers feeding a ReLU, 1/sqrt(kin)
+    times ``residual_gain`` for the residual branches, the aggregate half of
+    W3 scaled by 1/mean_degree (the sum runs over that many edges), a small
+    last decoder layer and zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, ki, ko, has_b in layer_list(layers):
+        if name.endswith(("w2", "w4")):
+            W = rng.normal(0, residual_gain / math.sqrt(ki), (ki, ko))
+        elif name in ("enc_n1", "enc_e1"):
+            W = rng.normal(0, 1.0 / math.sqrt(ki), (ki, ko))
+        elif name == "dec1":
+            W = rng.normal(0, 0.01 / math.sqrt(ki), (ki, ko))
+        else:
+            W = rng.normal(0, math.sqrt(2.0 / ki), (ki, ko))
+        if name.endswith("w3"):
+            W[ki // 2:] /= mean_degree
+        if name.endswith(("w1a", "w1b", "w1c")):
+            W /= math.sqrt(3.0)          # three terms enter the same ReLU
+        parts.append(W.ravel())
+        if has_b:
+            parts.append(np.zeros(ko))
+    return np.concatenate(parts).astype(np.float32)
+
+
+# --------------------------------------------------------------- training --
+
+@dataclass
+class TrainLog:
+    step: list = field(default_factory=list)
+    loss: list = field(default_factory=list)
+    seconds: float = 0.0
+    samples: int = 0
+    nodes: int = 0
+    edges: int = 0
+
+
+class Trainer:
+    """One surrogate context serving several groups (same stream)."""
+
+    def __init__(self, groups, layers=10, sigma=3e-4, seed=0, edges_per_node=80, stats=None,
+                 train=True):
+        import torch
+        self.torch = torch
+        self.groups = groups
+        self.layers = layers
+        self.sigma = sigma
+        self.rng = np.random.default_rng(seed)
+        self.seed = seed
+        self.dt_s = groups[0].dt_s
+        for g in groups:
+            assert abs(g.dt_s - self.dt_s) < 1e-15 * max(1.0, self.dt_s) + 1e-18
+        self.v_scale, self.a_mean, self.a_std = stats or data_stats(groups)
+        nmax = max(g.n for g in groups)
+        dev = groups[0].sim.device
+        self.sur = U.Surrogate(groups[0].sim, layers=layers, train=train, v_scale=self.v_scale,
+                               a_mean=self.a_mean, a_std=self.a_std, dt_s=self.dt_s,
+                               max_nodes=nmax, max_edges=nmax * edges_per_node)
+        self.sur.set_params(init_params(layers, seed))
+        f64, f32 = torch.float64, torch.float32
+        self.pos = torch.empty((nmax, 3), dtype=f64, device=dev)
+        self.vel = torch.empty((nmax, 3), dtype=f32, device=dev)
+        self.hist = torch.empty((nmax, 15), dtype=f32, device=dev)
+        self.tgt = torch.empty((nmax, 3), dtype=f32, device=dev)
+        self.rho = torch.full((nmax,), float(groups[0].ens.params["rho0"]), dtype=f32,
+                              device=dev)
+        self.ids = torch.arange(nmax, dtype=torch.int32, device=dev)
+        self.log = TrainLog()
+
+    def load_sample(self, g: Group, k: int, sigma: float, seed: int):
+        """Frames k-5 .. k+1 of group g -> the group's SPH state (noisy x^k,
+        v^k, cells built), velocity history and target."""
+        n = g.n
+        self.sur.bind(g.sim)
+        self.sur.make_sample(g.frames[k - 5], sigma, seed, self.pos, self.vel, self.hist,
+                             self.tgt)
+        g.sim.upload(self.pos[:n], self.vel[:n], self.rho[:n], self.ids[:n])
+        g.sim.build_cells()
+
+    def step(self, lr: float):
+        g = self.groups[int(self.rng.integers(len(self.groups)))]
+        k = int(self.rng.integers(5, g.frames.shape[0] - 1))
+        self.load_sample(g, k, self.sigma, self.seed * 1000003 + self.log.samples)
+        self.sur.forward(self.hist, None)
+        loss = self.sur.backward(self.tgt)
+        self.sur.adam(lr)
+        self.log.samples += 1
+        self.log.nodes += g.n
+        self.log.edges += self.sur.num_edges
+        return loss
+
+    def train(self, steps: int, lr0=1e-4, lr1=1e-6, log_every=50, verbose=False):
+        """Adam with the learning rate decaying exponentially from lr0 to lr1."""
+        t0 = time.perf_counter()
+        for i in range(steps):
+            lr = lr0 * (lr1 / lr0) ** (i / max(steps - 1, 1))
+            loss = self.step(lr)
+            if not math.isfinite(loss):
+                raise FloatingPointError(f"loss {loss} at step {i}")
+            if i % log_every == 0 or i == steps - 1:
+                self.log.step.append(i)
+                self.log.loss.append(loss)
+                if verbose:
+                    print(f"step {i:6d}  loss {loss:.5f}  lr {lr:.2e}", flush=True)
+        self.groups[0].sim.synchronize()
+        self.log.seconds += time.perf_counter() - t0
+        return self.log
+
+    def one_step_loss(self, g: Group, ks, sigma=0.0):
+        """Mean loss (normalised acceleration MSE) of the current weights on
+        frames ks of group g, without training, and the same for a zero
+        prediction (the constant-velocity update) for comparison."""
+        torch = self.torch
+        net, zero = [], []
+        for k in ks:
+            self.load_sample(g, int(k), sigma, 0)
+            self.sur.forward(self.hist, None)
+            net.append(self.sur.backward(self.tgt))      # loss only; no Adam step
+            a = self.tgt[:g.n][g.fluid]
+            # zero predicted acceleration: out = -a_mean / a_std
+            am = torch.tensor(self.a_mean, device=a.device, dtype=a.dtype)
+            sd = torch.tensor(self.a_std, device=a.device, dtype=a.dtype)
+            zero.append(float(((-am / sd - a) ** 2).sum(1).mean()))
+        return float(np.mean(net)), float(np.mean(zero))
+
+
+# ------------------------------------------------------------- evaluation --
+
+def member_of(ens):
+    """Member index of every particle id (numpy)."""
+    q = np.zeros(ens.n, np.int64)
+    for m in range(len(ens.members)):
+        q[int(ens.id_base[m]):int(ens.id_base[m + 1])] = m
+    return q
+
+
+def metrics(ens, pos, ref, fluid, dp, g=9.81, vel=None, mass=None):
+    """Position RMSE / dp over fluid particles, mean |front difference| over
+    members (front: largest x of fluid particles within 2 dp of the floor,
+    the floor being each member's lowest fluid z at t = 0 minus dp / 2) and
+    the per-member fronts.  pos, ref: (n, 3) by id (torch or numpy)."""
+    pos = np.asarray(pos.cpu() if hasattr(pos, "cpu") else pos)
+    ref = np.asarray(ref.cpu() if hasattr(ref, "cpu") else ref)
+    fluid = np.asarray(fluid.cpu() if hasattr(fluid, "cpu") else fluid)
+    d = pos[fluid] - ref[fluid]
+    rmse = float(np.sqrt((d * d).sum(1).mean())) / dp
+    q = member_of(ens)
+    fronts = []
+    for m in range(len(ens.members)):
+        sel = fluid & (q == m)
+        z0 = float(ens.pos[np.argsort(ens.ids)][sel][:, 2].min()) - 0.5 * dp
+        lo = lambda p: p[sel][p[sel][:, 2] < z0 + 2 * dp]
+        fa, fb = lo(pos), lo(ref)
+        fronts.append((float(fa[:, 0].max()) if len(fa) else float("nan"),
+                       float(fb[:, 0].max()) if len(fb) else float("nan")))
+    fr = np.array(fronts)
+    return dict(rmse_dp=rmse, front_err=float(np.nanmean(np.abs(fr[:, 0] - fr[:, 1]))),
+                fronts=fronts)
+
+
+def mechanical_energy(pos_prev, pos, dt_s, fluid, mass, g=9.81):
+    """Kinetic (finite-difference velocity) plus potential energy of the
+    fluid particles, in joules (float64 numpy)."""
+    p0 = np.asarray(pos_prev.cpu() if hasattr(pos_prev, "cpu") else pos_prev)[fluid]
+    p1 = np.asarray(pos.cpu() if hasattr(pos, "cpu") else pos)[fluid]
+    v = (p1 - p0) / dt_s
+    return float(mass * (0.5 * (v * v).sum() + g * p1[:, 2].sum()))
+
+
+def rollout(trainer: Trainer, g: Group, k0: int, n_calls: int, every: int = 1):
+    """Surrogate rollout of group g from frame k0 (history from frames
+    k0-5..k0, no noise) for n_calls calls; returns [(call, pos by id)] every
+    ``every`` calls and the seconds per call (advance + cell rebuild, timed
+    on the stream)."""
+    torch = trainer.torch
+    sur = trainer.sur
+    trainer.load_sample(g, k0, 0.0, 0)
+    hist = trainer.hist[:g.n].clone()
+    out = []
+    st = g.sim.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    secs = 0.0
+    for c in range(1, n_calls + 1):
+        ev0.record(st)
+        sur.advance(hist)
+        g.sim.build_cells()
+        ev1.record(st)
+        ev1.synchronize()
+        secs += ev0.elapsed_time(ev1) / 1e3
+        if c % every == 0 or c == n_calls:
+            p = torch.empty((g.n, 3), dtype=torch.float64, device=g.sim.device)
+            g.sim.download_by_id(pos=p)
+            out.append((c, p))
+    return out, secs / n_calls
+
+
+def evaluate_group(trainer: Trainer, g: Group, k0: int, n_calls: int, every: int = 10):
+    """Surrogate and constant-velocity rollouts against the group's SPH
+    frames: per saved call, RMSE / dp and front error of both."""
+    dp = float(g.ens.params["dp"])
+    fluid = g.fluid.cpu().numpy()
+    n_calls = min(n_calls, g.frames.shape[0] - 1 - k0)
+    traj, spc = rollout(trainer, g, k0, n_calls, every)
+    x0, xm = g.frames[k0], g.frames[k0 - 1]
+    rows = []
+    for c, p in traj:
+        ref = g.frames[k0 + c]
+        cv = x0 + c * (x0 - xm)             # constant-velocity extrapolation
+        ms = metrics(g.ens, p, ref, fluid, dp)
+        mc = metrics(g.ens, cv, ref, fluid, dp)
+        rows.append(dict(call=c, t=c * g.dt_s, rmse_dp=ms["rmse_dp"], front_err=ms["front_err"],
+                         cv_rmse_dp=mc["rmse_dp"], cv_front_err=mc["front_err"]))
+    return rows, spc

@@ -167,8 +167,12 @@ def test_advance_is_semi_implicit_euler_and_shifts_history(torch):
     want_acc = out[:, :3] * np.array([2.0, 3.0, 4.0]) + np.array([0.1, -0.2, -9.81])
     assert _rel(acc, want_acc) <= 1e-2
     pw, vw = so.euler_step(pb, vb, acc.astype(np.float64), fluid, dt)
-    np.testing.assert_allclose(va, vw, rtol=0, atol=1e-5 * (np.abs(vw).max() + 1))
-    np.testing.assert_allclose(pa, pw, rtol=0, atol=1e-9)
+    # the GPU keeps velocities in FP32 and positions in FP64: v is off by its
+    # rounding, r by that rounding times dt
+    ulp = 2.0 ** -23 * (np.abs(vw).max() + 1)
+    np.testing.assert_allclose(va, vw, rtol=0, atol=2 * ulp)
+    np.testing.assert_allclose(pa, pw, rtol=0, atol=2 * ulp * dt + 1e-12)
+    assert np.all(np.abs((pa - pb)[fluid] - va[fluid] * dt) <= ulp * dt + 1e-12)
     assert np.array_equal(pa[s.bnd], pb[s.bnd]) and np.array_equal(va[s.bnd], vb[s.bnd])
     h = hist.cpu().numpy()
     assert np.array_equal(h[:, :12], s.hist[:, 3:])
@@ -204,3 +208,86 @@ def test_errors_are_reported_not_faulted(torch):
         small.forward(s.d_hist, None)
     with pytest.raises(S.SphError, match="INVALID_ARG"):
         U.sur_set_params(s.sur.ctx, np.zeros(5, np.float32))
+
+
+def _frames(s, rng, dt):
+    """Seven frames by id: ballistic motion with a per-particle acceleration
+    (boundary particles fixed)."""
+    v0 = rng.normal(0, 0.3, (s.n, 3))
+    a0 = rng.normal(0, 5.0, (s.n, 3))
+    v0[s.bnd] = 0
+    a0[s.bnd] = 0
+    t = (np.arange(7) - 5) * dt
+    return s.pos[None] + v0[None] * t[:, None, None] + 0.5 * a0[None] * t[:, None, None] ** 2
+
+
+def test_make_sample_without_noise_is_the_finite_difference_definition(torch):
+    dt = 1e-3
+    s = Setup(torch, 1500, 1, seed=12)
+    sur = U.Surrogate(s.sim, layers=1, train=False, v_scale=1.0, a_mean=(0.5, -1.0, 2.0),
+                      a_std=(3.0, 2.0, 4.0), dt_s=dt, max_edges=1)
+    fr = _frames(s, np.random.default_rng(1), dt)
+    d_fr = torch.tensor(fr, device="cuda")
+    pos = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    vel = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    hist = torch.empty((s.n, 15), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    sur.make_sample(d_fr, 0.0, 7, pos, vel, hist, tgt)
+    torch.cuda.synchronize()
+    v = (fr[1:6] - fr[0:5]) / dt                       # v^{k-4} .. v^k
+    a = (fr[6] - 2 * fr[5] + fr[4]) / dt ** 2
+    want_t = (a - np.array([0.5, -1.0, 2.0])) / np.array([3.0, 2.0, 4.0])
+    assert np.array_equal(pos.cpu().numpy(), fr[5])
+    np.testing.assert_allclose(vel.cpu().numpy(), v[4], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(hist.cpu().numpy(), v.transpose(1, 0, 2).reshape(s.n, 15),
+                               rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(tgt.cpu().numpy(), want_t, rtol=1e-5, atol=1e-4)
+
+
+def test_make_sample_noise_is_a_random_walk_of_the_stated_size(torch):
+    dt, sigma = 1e-3, 3e-4
+    s = Setup(torch, 6000, 1, seed=13)
+    sur = U.Surrogate(s.sim, layers=1, train=False, v_scale=1.0, dt_s=dt, max_edges=1)
+    fr = _frames(s, np.random.default_rng(2), dt)
+    d_fr = torch.tensor(fr, device="cuda")
+    outs = []
+    for seed in (11, 11, 12):
+        pos = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+        vel = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        hist = torch.empty((s.n, 15), dtype=torch.float32, device="cuda")
+        tgt = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+        sur.make_sample(d_fr, sigma, seed, pos, vel, hist, tgt)
+        torch.cuda.synchronize()
+        outs.append((pos.cpu().numpy(), hist.cpu().numpy().astype(np.float64),
+                     tgt.cpu().numpy().astype(np.float64)))
+    assert all(np.array_equal(a, b) for a, b in zip(outs[0], outs[1]))     # same seed
+    assert not np.array_equal(outs[0][0], outs[2][0])                       # other seed
+    pos, hist, tgt = outs[0]
+    f = ~s.bnd
+    nu = pos - fr[5]
+    assert np.all(nu[s.bnd] == 0)
+    assert abs(nu[f].std() / sigma - 1) < 0.05 and abs(nu[f].mean()) < 0.05 * sigma
+    # velocity noise: increments of std sigma / sqrt(5) per frame, independent
+    v_clean = ((fr[1:6] - fr[0:5]) / dt).transpose(1, 0, 2).reshape(s.n, 15)
+    inc = (hist - v_clean)[f] * dt
+    sd = inc.std(axis=0)
+    assert np.all(np.abs(sd / (sigma / np.sqrt(5)) - 1) < 0.06), sd
+    c = np.corrcoef(inc[:, 0], inc[:, 3])[0, 1]
+    assert abs(c) < 0.05
+    # the target lands the noisy x^k on the clean x^{k+1}: a dt^2 = x6 - 2 x~5 + x~4
+    x4 = pos - hist[:, 12:15] * dt
+    a = tgt                                       # a_mean 0, a_std 1
+    np.testing.assert_allclose((a * dt * dt)[f], (fr[6] - 2 * pos + x4)[f], rtol=0, atol=1e-9)
+
+
+def test_download_by_id_is_the_sorted_download_reordered(torch):
+    s = Setup(torch, 900, 1, seed=14)
+    d = s.sim.download()
+    pos = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    vel = torch.empty((s.n, 3), dtype=torch.float32, device="cuda")
+    rho = np.empty(s.n, np.float32)
+    s.sim.download_by_id(pos, vel, rho)
+    o = np.argsort(d["ids"])
+    assert np.array_equal(pos.cpu().numpy(), d["pos"][o])
+    assert np.array_equal(vel.cpu().numpy(), d["vel"][o])
+    assert np.array_equal(rho, d["rho"][o])
