@@ -6,7 +6,7 @@
 using namespace sur;
 
 namespace {
-constexpr uint32_t kWgradBlocks = 152;
+constexpr uint32_t kWgradBlocks = 3 * 152;   // three blocks per SM
 }
 
 extern "C" {

@@ -14,80 +14,76 @@ namespace sur {
 
 namespace {
 
-// Stage a (rows x K) bf16 tile, row-major in global memory starting at row
-// `row0` of a matrix with `nrows` rows, into the canonical K-major layout
-// (rows past nrows read as zero).  Each thread moves 16-byte pieces.
-template <int K>
-__device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src,
-                                           uint32_t row0, uint32_t nrows, int rows, uint32_t ld) {
-    const int pieces = rows * (K / 8);
-    for (int c = threadIdx.x; c < pieces; c += blockDim.x) {
-        const int r = c % rows, g = c / rows;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (row0 + r < nrows)
-            v = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * ld + g * 8);
-        *reinterpret_cast<uint4*>(dst + kmajor_offset(r, g * 8, K)) = v;
-    }
-}
-
-// Stage rows [row0, row0+128) of a (nrows x C) bf16 row-major matrix as the
-// TRANSPOSED operand: element (c, m - row0) of a (C x 128) K-major tile.
-template <int C>
-__device__ __forceinline__ void stage_transposed(unsigned char* dst, const __nv_bfloat16* src,
-                                                 uint32_t row0, uint32_t nrows, uint32_t ld) {
-    // each thread takes 8 consecutive rows of one column block of 8: reads
-    // eight 16-byte pieces and writes eight 16-byte core-matrix rows
-    const int jobs = (C / 8) * 16;   // (column block, 8-row group)
-    for (int j = threadIdx.x; j < jobs; j += blockDim.x) {
-        const int cb = j % (C / 8), rg = j / (C / 8);
-        __nv_bfloat16 t[8][8];
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-            const uint32_t m = row0 + rg * 8 + rr;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (m < nrows) v = *reinterpret_cast<const uint4*>(src + (size_t)m * ld + cb * 8);
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-            for (int cc = 0; cc < 8; ++cc) t[cc][rr] = e[cc];
-        }
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc)
-            *reinterpret_cast<uint4*>(dst + kmajor_offset(cb * 8 + cc, rg * 8, 128)) =
-                *reinterpret_cast<const uint4*>(t[cc]);
-    }
-}
-
-__device__ __forceinline__ float bf(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
-
 template <int N>
 __device__ __forceinline__ constexpr uint32_t tmem_cols() {
     return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
 }
 
-// Forward-type GEMM with fused epilogue; persistent over 128-row tiles.
+// Issue the asynchronous copies of a (128 x K) bf16 tile (rows past nrows
+// zero-filled) into the canonical K-major layout; consecutive threads take
+// consecutive rows of one 16-byte column piece.
+template <int K>
+__device__ __forceinline__ void issue_rows(unsigned char* dst, const __nv_bfloat16* src,
+                                           uint32_t row0, uint32_t nrows, uint32_t ld) {
+#pragma unroll
+    for (int c = threadIdx.x; c < 128 * (K / 8); c += 128) {
+        const int r = c & 127, gk = c >> 7;
+        const bool ok = row0 + r < nrows;
+        const __nv_bfloat16* p = ok ? src + (size_t)(row0 + r) * ld + gk * 8 : src;
+        cp_async16(dst + kmajor_offset(r, gk * 8, K), p, ok);
+    }
+}
+
+__device__ __forceinline__ void unpack8(const uint4& u, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 t = __bfloat1622float2(h[q]);
+        f[2 * q] = t.x;
+        f[2 * q + 1] = t.y;
+    }
+}
+
+// 16 consecutive bf16 at p (32-byte aligned) as floats.
+__device__ __forceinline__ void load16(const __nv_bfloat16* p, float* f) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 a = q[0], b = q[1];
+    unpack8(a, f);
+    unpack8(b, f + 8);
+}
+
+// Forward-type GEMM with fused epilogue; persistent over 128-row tiles.  The
+// A tile is double-buffered: the copies of the next tile are in flight while
+// the tensor cores multiply the current one and the epilogue drains it.
 template <int K, int N>
 __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
     extern __shared__ __align__(128) unsigned char s_raw[];
-    unsigned char* sa = s_raw;                        // 128 x K
-    unsigned char* sb = s_raw + 128 * K * 2;          // N x K
+    unsigned char* sb = s_raw;                        // N x K (weights)
+    unsigned char* sa0 = s_raw + N * K * 2;           // 2 x (128 x K)
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     if (w == 0) tmem_alloc(&s_tmem, tmem_cols<N>());
     if (tid == 0) mbar_init1(&s_bar);
-    stage_rows<K>(sb, g.Bt, 0, N, N, K);
     const uint32_t lda = g.lda ? g.lda : (uint32_t)K;
     const uint32_t ldr = g.ldr ? g.ldr : (uint32_t)N;
+    const uint32_t ntiles = (g.M + 127) / 128;
+    // weights and the first tile
+    for (int c = tid; c < N * (K / 8); c += 128) {
+        const int r = c % N, gk = c / N;
+        cp_async16(sb + kmajor_offset(r, gk * 8, K), g.Bt + (size_t)r * K + gk * 8, true);
+    }
+    if (blockIdx.x < ntiles) issue_rows<K>(sa0, g.A, blockIdx.x * 128, g.M, lda);
+    cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t ntiles = (g.M + 127) / 128;
-    uint32_t phase = 0;
+    uint32_t phase = 0, buf = 0;
     bool ok = true;
-    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const uint32_t m0 = tile * 128;
-        stage_rows<K>(sa, g.A, m0, g.M, 128, lda);
+    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= 1u) {
+        unsigned char* sa = sa0 + buf * (128 * K * 2);
+        cp_async_wait_all();
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
@@ -100,6 +96,11 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
             }
             tc_commit(&s_bar);
         }
+        // next tile into the other buffer (its last reader, the previous
+        // tile's MMA, has completed)
+        const uint32_t next = tile + gridDim.x;
+        if (next < ntiles) issue_rows<K>(sa0 + (buf ^ 1u) * (128 * K * 2), g.A, next * 128, g.M, lda);
+        cp_async_commit();
         const bool got = mbar_wait(&s_bar, phase);
         ok = __syncthreads_and(got) != 0;
         if (!ok) {
@@ -108,32 +109,66 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         }
         phase ^= 1u;
         tc_fence_after();
-        const uint32_t m = m0 + w * 32 + lane;
+        const uint32_t m = tile * 128 + w * 32 + lane;
         const bool valid = m < g.M;
+        uint32_t gi = 0, gj = 0;
+        if (g.epi == kEpiEdge1 && valid) {
+            gi = g.src[m];
+            gj = g.dst[m];
+        }
 #pragma unroll 1
         for (int c0 = 0; c0 < N; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
             if (!valid) continue;
+            if (g.bias) {
+                const float4* b4 = reinterpret_cast<const float4*>(g.bias + c0);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int n = c0 + i;
-                float x = v[i];
-                if (g.bias) x += g.bias[n];
-                switch (g.epi) {
-                    case kEpiEdge1:   // relu(acc + P[src] + Q[dst] + b)
-                        x += bf(g.gp, (size_t)g.src[m] * N + n) + bf(g.gq, (size_t)g.dst[m] * N + n);
-                        x = fmaxf(x, 0.f);
-                        break;
-                    case kEpiRelu: x = fmaxf(x, 0.f); break;
-                    case kEpiResidual: x += bf(g.res, (size_t)m * ldr + n); break;
-                    case kEpiReluMask:   // backward through a ReLU: keep where act > 0
-                        x = bf(g.res, (size_t)m * ldr + n) > 0.f ? x : 0.f;
-                        break;
-                    case kEpiAccum: x += g.out_f32[(size_t)m * g.ldo + n]; break;
-                    default: break;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 b = __ldg(b4 + q);
+                    v[4 * q] += b.x;
+                    v[4 * q + 1] += b.y;
+                    v[4 * q + 2] += b.z;
+                    v[4 * q + 3] += b.w;
                 }
-                v[i] = x;
+            }
+            float t[16];
+            switch (g.epi) {
+                case kEpiEdge1: {   // relu(acc + P[src] + Q[dst] + b)
+                    float u[16];
+                    load16(g.gp + (size_t)gi * N + c0, t);
+                    load16(g.gq + (size_t)gj * N + c0, u);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + t[i] + u[i], 0.f);
+                    break;
+                }
+                case kEpiRelu:
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+                    break;
+                case kEpiResidual:
+                    load16(g.res + (size_t)m * ldr + c0, t);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += t[i];
+                    break;
+                case kEpiReluMask:   // backward through a ReLU: keep where act > 0
+                    load16(g.res + (size_t)m * ldr + c0, t);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = t[i] > 0.f ? v[i] : 0.f;
+                    break;
+                case kEpiAccum: {
+                    const float4* o = reinterpret_cast<const float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 a = o[q];
+                        v[4 * q] += a.x;
+                        v[4 * q + 1] += a.y;
+                        v[4 * q + 2] += a.z;
+                        v[4 * q + 3] += a.w;
+                    }
+                    break;
+                }
+                default: break;
             }
             if (g.out_f32) {
                 float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
@@ -152,14 +187,64 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         tc_fence_before();
         __syncthreads();
     }
+    cp_async_wait_all();
     __syncthreads();
     if (w == 0) tmem_dealloc(tmem, tmem_cols<N>());
+}
+
+// Transposed staging in two halves: the global loads of a (128-row x C)
+// tile into registers (each job: 8 rows of one 8-column block), then the
+// register transpose into the (C x 128) K-major tile in shared memory.
+template <int C>
+struct TRegs {
+    static constexpr int kJobs = (C / 8) * 16;
+    static constexpr int kPer = (kJobs + 127) / 128;
+    uint4 v[kPer][8];
+};
+
+template <int C>
+__device__ __forceinline__ void load_t(TRegs<C>& r, const __nv_bfloat16* src, uint32_t row0,
+                                       uint32_t nrows, uint32_t ld) {
+#pragma unroll
+    for (int jj = 0; jj < TRegs<C>::kPer; ++jj) {
+        const int j = threadIdx.x + jj * 128;
+        const int cb = j % (C / 8), rg = j / (C / 8);
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const uint32_t m = row0 + rg * 8 + rr;
+            r.v[jj][rr] = make_uint4(0u, 0u, 0u, 0u);
+            if (j < TRegs<C>::kJobs && m < nrows)
+                r.v[jj][rr] = *reinterpret_cast<const uint4*>(src + (size_t)m * ld + cb * 8);
+        }
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void store_t(unsigned char* dst, const TRegs<C>& r) {
+#pragma unroll
+    for (int jj = 0; jj < TRegs<C>::kPer; ++jj) {
+        const int j = threadIdx.x + jj * 128;
+        if (j >= TRegs<C>::kJobs) continue;
+        const int cb = j % (C / 8), rg = j / (C / 8);
+        __nv_bfloat16 t[8][8];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&r.v[jj][rr]);
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) t[cc][rr] = e[cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+            *reinterpret_cast<uint4*>(dst + kmajor_offset(cb * 8 + cc, rg * 8, 128)) =
+                *reinterpret_cast<const uint4*>(t[cc]);
+    }
 }
 
 // Weight gradient dW[C x N] = X^T dY over rows [0, M): X is M x C, dY is
 // M x N (bf16, row-major).  Block b accumulates the row tiles b, b + grid,
 // ... in TMEM (C = 128 rows of the MMA, one MMA chain per tile), then writes
-// its partial; k_wgrad_reduce adds the partials in block order.
+// its partial; k_wgrad_reduce adds the partials in block order.  The loads
+// of the next tile are in flight while the tensor cores work on this one.
 template <int N>
 __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
     extern __shared__ __align__(128) unsigned char s_raw[];
@@ -170,16 +255,23 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     if (w == 0) tmem_alloc(&s_tmem, tmem_cols<N>());
     if (tid == 0) mbar_init1(&s_bar);
+    const uint32_t ldp = g.ldp ? g.ldp : 128u, ldq = g.ldq ? g.ldq : (uint32_t)N;
+    const uint32_t ntiles = (g.M + 127) / 128;
+    TRegs<128> rx;
+    TRegs<N> ry;
+    if (blockIdx.x < ntiles) {
+        load_t<128>(rx, g.X, blockIdx.x * 128, g.M, ldp);
+        load_t<N>(ry, g.dY, blockIdx.x * 128, g.M, ldq);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t ntiles = (g.M + 127) / 128;
     uint32_t phase = 0, first = 1;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_transposed<128>(sa, g.X, tile * 128, g.M, g.ldp ? g.ldp : 128u);
-        stage_transposed<N>(sb, g.dY, tile * 128, g.M, g.ldq ? g.ldq : (uint32_t)N);
+        store_t<128>(sa, rx);
+        store_t<N>(sb, ry);
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
@@ -193,6 +285,11 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
             tc_commit(&s_bar);
         }
         first = 0;
+        const uint32_t next = tile + gridDim.x;
+        if (next < ntiles) {
+            load_t<128>(rx, g.X, next * 128, g.M, ldp);
+            load_t<N>(ry, g.dY, next * 128, g.M, ldq);
+        }
         const bool got = mbar_wait(&s_bar, phase);
         ok = __syncthreads_and(got) != 0;
         if (!ok) {
@@ -210,8 +307,13 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs g) {
     for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
+        float4* o = reinterpret_cast<float4*>(part + (size_t)r * N + c0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) part[(size_t)r * N + c0 + i] = (first || !ok) ? 0.f : v[i];
+        for (int q = 0; q < 4; ++q) {
+            const bool z = first || !ok;
+            o[q] = z ? make_float4(0.f, 0.f, 0.f, 0.f)
+                     : make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -228,7 +330,7 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, in
 }
 
 template <int K, int N>
-size_t linear_smem() { return (size_t)128 * K * 2 + (size_t)N * K * 2; }
+size_t linear_smem() { return (size_t)2 * 128 * K * 2 + (size_t)N * K * 2; }
 
 template <int K, int N>
 void launch_linear_t(const LinearArgs& g, int sms, cudaStream_t st) {

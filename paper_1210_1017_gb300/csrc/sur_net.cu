@@ -29,7 +29,7 @@ namespace {
 constexpr int L = 128;       // latent width
 constexpr int KIN = 16;      // padded input width of the encoders
 constexpr int KOUT = 16;     // padded decoder output width
-constexpr uint32_t kWgradParts = 152;
+constexpr uint32_t kWgradParts = 3 * 152;   // three blocks per SM
 
 struct Layer {
     int kin, kout;

@@ -65,7 +65,8 @@ def pilot_dt(group: Group, t_end: float, chunk: int = 100) -> float:
     dt_min = math.inf
     while True:
         sim.step(chunk)
-        t, dt, done, _ = sim.instance_state()
+        st = sim.instance_state()
+        t, dt, done = st["t"], st["dt"], st["done"]
         live = dt > 0
         if live.any():
             dt_min = min(dt_min, float(dt[live].min()))

@@ -1,7 +1,8 @@
 """Training the surrogate on GPU SPH rollouts: the data pipeline runs, the
 loss falls, and the trained network predicts the next-frame acceleration of
-members it never saw better than the update without it (zero learned
-acceleration, i.e. constant-velocity extrapolation)."""
+a member it never saw better than the update without it (zero learned
+acceleration, i.e. constant-velocity extrapolation), and its rollout stays
+closer to the SPH frames."""
 import numpy as np
 import pytest
 
@@ -49,7 +50,9 @@ def test_recorded_frames_are_the_fixed_step_sph_run(torch, data):
 
 def test_training_lowers_the_loss_and_beats_zero_acceleration_on_held_out(torch, data):
     train, held, dt = data
-    tr = T.Trainer([train], layers=2, sigma=3e-4, seed=1)
+    # noise-free samples: at a 4-step call (under a millisecond) a position
+    # noise of 3e-4 m would put ~1e3 m/s^2 of noise into the targets
+    tr = T.Trainer([train], layers=2, sigma=0.0, seed=1)
     before, zero = tr.one_step_loss(held, range(10, 60, 10))
     log = tr.train(400, lr0=1e-3, lr1=1e-4, log_every=20)
     assert np.isfinite(log.loss).all()
@@ -63,3 +66,5 @@ def test_training_lowers_the_loss_and_beats_zero_acceleration_on_held_out(torch,
     rows, spc = T.evaluate_group(tr, held, 10, 20, every=10)
     assert len(rows) == 2 and spc > 0
     assert all(np.isfinite(r["rmse_dp"]) for r in rows)
+    # the learned rollout stays closer to SPH than constant velocity
+    assert rows[-1]["rmse_dp"] < rows[-1]["cv_rmse_dp"], rows
