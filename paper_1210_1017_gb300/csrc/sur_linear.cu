@@ -52,6 +52,49 @@ __device__ __forceinline__ void load16(const __nv_bfloat16* p, float* f) {
     unpack8(b, f + 8);
 }
 
+// Epilogue operands of one row and NP columns, in registers: bf16 rows in
+// a (residual, ReLU mask, P[src]) and b (Q[dst]); an fp32 row (gradient
+// accumulation) spans a then b.
+template <int NP>
+struct EpiOps {
+    uint4 a[NP / 8];
+    uint4 b[NP / 8];
+};
+
+template <int N, int NP>
+__device__ __forceinline__ void epi_load(EpiOps<NP>& o, const LinearArgs& g, uint32_t m,
+                                         uint32_t gi, uint32_t gj, uint32_t ldr, int col0) {
+    switch (g.epi) {
+        case kEpiEdge1: {
+            const uint4* p = reinterpret_cast<const uint4*>(g.gp + (size_t)gi * N + col0);
+            const uint4* q = reinterpret_cast<const uint4*>(g.gq + (size_t)gj * N + col0);
+#pragma unroll
+            for (int i = 0; i < NP / 8; ++i) {
+                o.a[i] = p[i];
+                o.b[i] = q[i];
+            }
+            break;
+        }
+        case kEpiResidual:
+        case kEpiReluMask: {
+            const uint4* p = reinterpret_cast<const uint4*>(g.res + (size_t)m * ldr + col0);
+#pragma unroll
+            for (int i = 0; i < NP / 8; ++i) o.a[i] = p[i];
+            break;
+        }
+        case kEpiAccum: {
+            const uint4* p = reinterpret_cast<const uint4*>(g.out_f32 + (size_t)m * g.ldo + col0);
+#pragma unroll
+            for (int i = 0; i < NP / 8; ++i) {
+                o.a[i] = p[i];
+                o.b[i] = p[NP / 8 + i];
+            }
+            break;
+        }
+        default: break;
+    }
+}
+
 // Forward-type GEMM with fused epilogue; persistent over 128-row tiles.  The
 // A tile is double-buffered: the copies of the next tile are in flight while
 // the tensor cores multiply the current one and the epilogue drains it.
@@ -101,6 +144,17 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         const uint32_t next = tile + gridDim.x;
         if (next < ntiles) issue_rows<K>(sa0 + (buf ^ 1u) * (128 * K * 2), g.A, next * 128, g.M, lda);
         cp_async_commit();
+        // this thread's row: its epilogue operands load while the MMA runs
+        const uint32_t m = tile * 128 + w * 32 + lane;
+        const bool valid = m < g.M;
+        uint32_t gi = 0, gj = 0;
+        if (g.epi == kEpiEdge1 && valid) {
+            gi = g.src[m];
+            gj = g.dst[m];
+        }
+        constexpr int NP = N < 128 ? N : 128;   // columns per epilogue pass
+        EpiOps<NP> op;
+        if (valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, 0);
         const bool got = mbar_wait(&s_bar, phase);
         ok = __syncthreads_and(got) != 0;
         if (!ok) {
@@ -109,79 +163,79 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         }
         phase ^= 1u;
         tc_fence_after();
-        const uint32_t m = tile * 128 + w * 32 + lane;
-        const bool valid = m < g.M;
-        uint32_t gi = 0, gj = 0;
-        if (g.epi == kEpiEdge1 && valid) {
-            gi = g.src[m];
-            gj = g.dst[m];
-        }
-#pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
-            if (!valid) continue;
-            if (g.bias) {
-                const float4* b4 = reinterpret_cast<const float4*>(g.bias + c0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 b = __ldg(b4 + q);
-                    v[4 * q] += b.x;
-                    v[4 * q + 1] += b.y;
-                    v[4 * q + 2] += b.z;
-                    v[4 * q + 3] += b.w;
-                }
-            }
-            float t[16];
-            switch (g.epi) {
-                case kEpiEdge1: {   // relu(acc + P[src] + Q[dst] + b)
-                    float u[16];
-                    load16(g.gp + (size_t)gi * N + c0, t);
-                    load16(g.gq + (size_t)gj * N + c0, u);
+        for (int h = 0; h < N / NP; ++h) {
+            if (h > 0 && valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, h * NP);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + t[i] + u[i], 0.f);
-                    break;
-                }
-                case kEpiRelu:
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-                    break;
-                case kEpiResidual:
-                    load16(g.res + (size_t)m * ldr + c0, t);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += t[i];
-                    break;
-                case kEpiReluMask:   // backward through a ReLU: keep where act > 0
-                    load16(g.res + (size_t)m * ldr + c0, t);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = t[i] > 0.f ? v[i] : 0.f;
-                    break;
-                case kEpiAccum: {
-                    const float4* o = reinterpret_cast<const float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
+            for (int cl = 0; cl < NP; cl += 16) {
+                const int c0 = h * NP + cl;
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
+                if (!valid) continue;
+                if (g.bias) {
+                    const float4* b4 = reinterpret_cast<const float4*>(g.bias + c0);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 a = o[q];
-                        v[4 * q] += a.x;
-                        v[4 * q + 1] += a.y;
-                        v[4 * q + 2] += a.z;
-                        v[4 * q + 3] += a.w;
+                        const float4 b = __ldg(b4 + q);
+                        v[4 * q] += b.x;
+                        v[4 * q + 1] += b.y;
+                        v[4 * q + 2] += b.z;
+                        v[4 * q + 3] += b.w;
                     }
-                    break;
                 }
-                default: break;
-            }
-            if (g.out_f32) {
-                float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
+                float t[16], u[16];
+                switch (g.epi) {
+                    case kEpiEdge1:   // relu(acc + P[src] + Q[dst] + b)
+                        unpack8(op.a[cl / 8], t);
+                        unpack8(op.a[cl / 8 + 1], t + 8);
+                        unpack8(op.b[cl / 8], u);
+                        unpack8(op.b[cl / 8 + 1], u + 8);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
-            if (g.out_bf16) {
-                __nv_bfloat162 h[8];
+                        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + t[i] + u[i], 0.f);
+                        break;
+                    case kEpiRelu:
 #pragma unroll
-                for (int q = 0; q < 8; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                uint4* o = reinterpret_cast<uint4*>(g.out_bf16 + (size_t)m * g.ldo + c0);
-                o[0] = *reinterpret_cast<uint4*>(&h[0]);
-                o[1] = *reinterpret_cast<uint4*>(&h[4]);
+                        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+                        break;
+                    case kEpiResidual:
+                        unpack8(op.a[cl / 8], t);
+                        unpack8(op.a[cl / 8 + 1], t + 8);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] += t[i];
+                        break;
+                    case kEpiReluMask:   // backward through a ReLU: keep where act > 0
+                        unpack8(op.a[cl / 8], t);
+                        unpack8(op.a[cl / 8 + 1], t + 8);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = t[i] > 0.f ? v[i] : 0.f;
+                        break;
+                    case kEpiAccum:
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int k = cl / 4 + q;
+                            const uint4 x = k < NP / 8 ? op.a[k % (NP / 8)] : op.b[k % (NP / 8)];
+                            v[4 * q] += __uint_as_float(x.x);
+                            v[4 * q + 1] += __uint_as_float(x.y);
+                            v[4 * q + 2] += __uint_as_float(x.z);
+                            v[4 * q + 3] += __uint_as_float(x.w);
+                        }
+                        break;
+                    default: break;
+                }
+                if (g.out_f32) {
+                    float4* o = reinterpret_cast<float4*>(g.out_f32 + (size_t)m * g.ldo + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (g.out_bf16) {
+                    __nv_bfloat162 hh[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) hh[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                    uint4* o = reinterpret_cast<uint4*>(g.out_bf16 + (size_t)m * g.ldo + c0);
+                    o[0] = *reinterpret_cast<uint4*>(&hh[0]);
+                    o[1] = *reinterpret_cast<uint4*>(&hh[4]);
+                }
             }
         }
         tc_fence_before();
@@ -340,12 +394,19 @@ void launch_linear_t(const LinearArgs& g, int sms, cudaStream_t st) {
         cudaFuncSetAttribute(k_linear<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         init = true;
     }
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_linear<K, N>, 128, smem);
-    // keep every resident block's TMEM inside the SM's 512 columns
-    const int cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-    if (per_sm * cols > 512) per_sm = 512 / cols;
-    if (per_sm < 1) per_sm = 1;
+    // resident blocks per SM: shared memory, registers and the SM's 512
+    // TMEM columns
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_linear<K, N>);
+        const int cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+        const int by_smem = (int)((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
+        const int by_regs = fa.numRegs > 0 ? 65536 / (128 * fa.numRegs) : 1;
+        per_sm = by_smem < by_regs ? by_smem : by_regs;
+        if (per_sm > 512 / cols) per_sm = 512 / cols;
+        if (per_sm < 1) per_sm = 1;
+    }
     const uint32_t tiles = (g.M + 127) / 128;
     uint32_t grid = (uint32_t)(sms * per_sm);
     if (grid > tiles) grid = tiles ? tiles : 1;

@@ -207,6 +207,7 @@ __global__ void k_colsum_part(uint32_t M, int C, const T* __restrict__ in, uint3
                               float* __restrict__ part) {
     const int c = threadIdx.x;   // blockDim = C
     float s = 0.f;
+#pragma unroll 8
     for (uint32_t m = blockIdx.x; m < M; m += gridDim.x) {
         if constexpr (sizeof(T) == 2) s += __bfloat162float(in[(size_t)m * ld + c]);
         else s += in[(size_t)m * ld + c];

@@ -353,3 +353,141 @@ def evaluate_group(trainer: Trainer, g: Group, k0: int, n_calls: int, every: int
         rows.append(dict(call=c, t=c * g.dt_s, rmse_dp=ms["rmse_dp"], front_err=ms["front_err"],
                          cv_rmse_dp=mc["rmse_dp"], cv_front_err=mc["front_err"]))
     return rows, spc
+
+
+def evaluate_case(trainer: Trainer, case, t_sim: float, every: int = 10, pilot_t: float = None,
+                  edges_per_node: int = 80, sph_steps_timed: int = 200):
+    """The trained network on a standalone case (its own resolution and
+    step) against the GPU SPH on the same case: both start from rest, the
+    SPH runs with the fixed step dt (smallest adaptive step of a pilot run)
+    and the surrogate advances 4 dt per call.  Returns per saved call the
+    position RMSE / dp and front error, and the simulated seconds per wall
+    second of both."""
+    import torch
+    st = trainer.groups[0].sim.stream
+    g = Group(ens=cases.ensemble([case]), sim=None)
+    g.sim = S.Simulation(case.params(), case.n, stream=st)
+    dt = pilot_dt(g, pilot_t if pilot_t is not None else min(t_sim, 0.2))
+    n_calls = int(round(t_sim / (4 * dt)))
+    # SPH frames: 6 initial frames 4 steps apart, then every `every` calls
+    sim = S.Simulation(case.params(), case.n, stream=st, dt_fixed=dt)
+    sim.upload(case.pos, case.vel, case.rho, case.ids)
+    dev = sim.device
+    first = torch.empty((7, case.n, 3), dtype=torch.float64, device=dev)
+    for f in range(7):
+        if f:
+            sim.step(4)
+        sim.download_by_id(pos=first[f])
+    ref = {}
+    c = 1                      # frame 6 = call 1 after frame 5
+    ref[1] = first[6].clone()
+    while c < n_calls:
+        k = min(every - (c % every) if c % every else every, n_calls - c)
+        sim.step(4 * k)
+        c += k
+        p = torch.empty((case.n, 3), dtype=torch.float64, device=dev)
+        sim.download_by_id(pos=p)
+        ref[c] = p
+    # SPH speed: fixed-step steps timed on the stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.step(20)
+    e0.record(st)
+    sim.step(sph_steps_timed)
+    e1.record(st)
+    e1.synchronize()
+    sph_sps = dt * sph_steps_timed / (e0.elapsed_time(e1) / 1e3)
+    sim.close()
+    # surrogate on the case, same weights and normalisation, this case's step
+    g.frames, g.dt, g.steps_per_frame = first, dt, 4
+    g.fluid = torch.tensor(np.arange(case.n) >= case.n_bound, device=dev)   # by id
+    sur = U.Surrogate(g.sim, layers=trainer.layers, train=False, v_scale=trainer.v_scale,
+                      a_mean=trainer.a_mean, a_std=trainer.a_std, dt_s=4 * dt,
+                      max_nodes=case.n, max_edges=case.n * edges_per_node)
+    sur.set_params(trainer.sur.params())
+    ev = Trainer.__new__(Trainer)
+    ev.torch, ev.sur = torch, sur
+    f64, f32 = torch.float64, torch.float32
+    ev.pos = torch.empty((case.n, 3), dtype=f64, device=dev)
+    ev.vel = torch.empty((case.n, 3), dtype=f32, device=dev)
+    ev.hist = torch.empty((case.n, 15), dtype=f32, device=dev)
+    ev.tgt = torch.empty((case.n, 3), dtype=f32, device=dev)
+    ev.rho = torch.full((case.n,), float(case.rho0), dtype=f32, device=dev)
+    ev.ids = torch.arange(case.n, dtype=torch.int32, device=dev)
+    traj, spc = rollout(ev, g, 5, n_calls, every)
+    dp = float(case.dp)
+    fluid = g.fluid.cpu().numpy()
+    rows = []
+    for c, p in traj:
+        if c not in ref:
+            continue
+        m = metrics(g.ens, p, ref[c], fluid, dp)
+        rows.append(dict(call=c, t=c * 4 * dt, rmse_dp=m["rmse_dp"], front_err=m["front_err"]))
+    sur_sps = 4 * dt / spc
+    sur.close()
+    g.sim.close()
+    return dict(dt=dt, calls=n_calls, rows=rows, sur_seconds_per_call=spc, sur_sim_per_s=sur_sps,
+                sph_sim_per_s=sph_sps, speedup=sur_sps / sph_sps, n=case.n)
+
+
+def main(argv=None):
+    """Train on dam-break ensemble members and evaluate (JSON report)."""
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--group-size", type=int, default=8)
+    ap.add_argument("--train-groups", type=int, default=3)
+    ap.add_argument("--t-end", type=float, default=1.0)
+    ap.add_argument("--layers", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--lr0", type=float, default=3e-4)
+    ap.add_argument("--lr1", type=float, default=1e-5)
+    ap.add_argument("--sigma", type=float, default=0.0)
+    ap.add_argument("--eval-calls", type=int, default=1000)
+    ap.add_argument("--case-seconds", type=float, default=0.1)
+    ap.add_argument("--case", default="c2", choices=["c2", "none"])
+    ap.add_argument("--save-params", default=None)
+    a = ap.parse_args(argv)
+    report = dict(args=vars(a))
+    t0 = time.perf_counter()
+    st = torch.cuda.Stream()
+    specs = cases.ensemble_specs(256, seed=1017)
+    gs = a.group_size
+    groups = [make_group(specs[i * gs:(i + 1) * gs], t_end=a.t_end, stream=st)
+              for i in range(a.train_groups + 1)]
+    dt = min(pilot_dt(g, a.t_end) for g in groups)
+    n_frames = int(a.t_end / (4 * dt)) + 1
+    for g in groups:
+        record(g, dt, n_frames)
+    train, held = groups[:-1], groups[-1]
+    report["data"] = dict(dt=dt, dt_s=4 * dt, frames=n_frames,
+                          train_particles=[g.n for g in train], held_particles=held.n,
+                          seconds=time.perf_counter() - t0)
+    print(json.dumps(report["data"]), flush=True)
+    tr = Trainer(train, layers=a.layers, sigma=a.sigma, seed=0)
+    report["stats"] = dict(v_scale=tr.v_scale, a_mean=tr.a_mean, a_std=tr.a_std)
+    ks = range(10, n_frames - 2, max(1, (n_frames - 12) // 8))
+    report["untrained_held_one_step"], report["zero_held_one_step"] = tr.one_step_loss(held, ks)
+    tr.sur.bind(train[0].sim)
+    log = tr.train(a.steps, lr0=a.lr0, lr1=a.lr1, log_every=50, verbose=True)
+    report["train"] = dict(steps=log.step, loss=log.loss, seconds=log.seconds,
+                           samples=log.samples, nodes=log.nodes, edges=log.edges,
+                           edges_per_s=log.edges / log.seconds)
+    report["trained_held_one_step"], _ = tr.one_step_loss(held, ks)
+    if a.save_params:
+        np.save(a.save_params, tr.sur.params())
+    tr.sur.bind(held.sim)
+    rows, spc = evaluate_group(tr, held, 5, a.eval_calls, every=25)
+    report["held_rollout"] = dict(rows=rows, seconds_per_call=spc)
+    print(json.dumps(report["held_rollout"]["rows"][-1]), flush=True)
+    if a.case == "c2":
+        report["c2"] = evaluate_case(tr, cases.c2_dam_break_obstacles(), a.case_seconds)
+        print(json.dumps({k: v for k, v in report["c2"].items() if k != "rows"}), flush=True)
+    report["seconds"] = time.perf_counter() - t0
+    with open(a.out, "w") as f:
+        json.dump(report, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
