@@ -181,7 +181,7 @@ class Trainer:
     """One surrogate context serving several groups (same stream)."""
 
     def __init__(self, groups, layers=10, sigma=3e-4, seed=0, edges_per_node=80, stats=None,
-                 train=True):
+                 train=True, max_nodes=0):
         import torch
         self.torch = torch
         self.groups = groups
@@ -193,7 +193,7 @@ class Trainer:
         for g in groups:
             assert abs(g.dt_s - self.dt_s) < 1e-15 * max(1.0, self.dt_s) + 1e-18
         self.v_scale, self.a_mean, self.a_std = stats or data_stats(groups)
-        nmax = max(g.n for g in groups)
+        nmax = max(max(g.n for g in groups), int(max_nodes))
         dev = groups[0].sim.device
         self.sur = U.Surrogate(groups[0].sim, layers=layers, train=train, v_scale=self.v_scale,
                                a_mean=self.a_mean, a_std=self.a_std, dt_s=self.dt_s,
@@ -465,7 +465,7 @@ def main(argv=None):
                           train_particles=[g.n for g in train], held_particles=held.n,
                           seconds=time.perf_counter() - t0)
     print(json.dumps(report["data"]), flush=True)
-    tr = Trainer(train, layers=a.layers, sigma=a.sigma, seed=0)
+    tr = Trainer(train, layers=a.layers, sigma=a.sigma, seed=0, max_nodes=held.n)
     report["stats"] = dict(v_scale=tr.v_scale, a_mean=tr.a_mean, a_std=tr.a_std)
     ks = range(10, n_frames - 2, max(1, (n_frames - 12) // 8))
     report["untrained_held_one_step"], report["zero_held_one_step"] = tr.one_step_loss(held, ks)

@@ -52,7 +52,7 @@ def test_training_lowers_the_loss_and_beats_zero_acceleration_on_held_out(torch,
     train, held, dt = data
     # noise-free samples: at a 4-step call (under a millisecond) a position
     # noise of 3e-4 m would put ~1e3 m/s^2 of noise into the targets
-    tr = T.Trainer([train], layers=2, sigma=0.0, seed=1)
+    tr = T.Trainer([train], layers=2, sigma=0.0, seed=1, max_nodes=held.n)
     before, zero = tr.one_step_loss(held, range(10, 60, 10))
     log = tr.train(400, lr0=1e-3, lr1=1e-4, log_every=20)
     assert np.isfinite(log.loss).all()
