@@ -39,7 +39,8 @@ FLOP_CANDIDATE, FLOP_FLUID_PAIR, FLOP_BOUNDARY_PAIR = 8, 50, 12
 SMS, FP32_LANES, MAX_CLOCK_GHZ = 152, 128, 2.07
 
 
-WORKLOADS = ("dam_break_32m", "dam_break_obstacles_1m", "dam_break_6k", "dam_break_ensemble_256")
+WORKLOADS = ("dam_break_32m", "dam_break_obstacles_1m", "dam_break_6k", "dam_break_ensemble_256",
+             "surrogate_obstacles_1m")
 
 
 def workload(name):
@@ -355,6 +356,99 @@ def run_ours(args):
     return 0
 
 
+def run_surrogate(args):
+    """The learned surrogate on the 1.39M-particle dam break with obstacles:
+    simulated seconds per wall second of surrogate calls (each advances 4 SPH
+    steps: graph, 10 message-passing layers on the tensor cores, Euler step,
+    cell rebuild) next to the plain GPU SPH on the same case.  Weights are
+    the random initialisation: the speed does not depend on them."""
+    import torch
+
+    from paper_1210_1017_gb300 import cases
+    from paper_1210_1017_gb300 import sph as S
+    from paper_1210_1017_gb300 import surrogate as U
+    from paper_1210_1017_gb300 import surrogate_train as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    S.lib(build=True)
+    case = cases.c2_dam_break_obstacles()
+    st = torch.cuda.Stream()
+    sim = S.Simulation.from_case(case, device=local, stream=st)
+    sim.build_cells()
+    sim.autotune(reps=3)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0 = sim.diagnostics()
+    e0.record(st)
+    sim.step(4 * args.steps)
+    e1.record(st)
+    e1.synchronize()
+    d1 = sim.diagnostics()
+    sph_s = e0.elapsed_time(e1) / 1e3
+    sph_sim = d1["t"] - d0["t"]
+    dt = sph_sim / (4 * args.steps)
+    sur = U.Surrogate(sim, layers=10, train=False, v_scale=1.0, dt_s=4 * dt, edges_per_node=80)
+    sur.set_params(T.init_params(10, 0))
+    hist = torch.zeros((case.n, 15), dtype=torch.float32, device=sim.device)
+    sim.build_cells()
+    for _ in range(args.warmup):
+        sur.advance(hist)
+        sim.build_cells()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        sur.advance(hist)
+        sim.build_cells()
+    e1.record(st)
+    e1.synchronize()
+    clocks = sampler.stop()
+    sur_s = e0.elapsed_time(e1) / 1e3
+    E = sur.num_edges
+    value = args.steps * 4 * dt / sur_s
+    # dominant kernel: the edge GEMM (K = N = 128, residual epilogue), run on
+    # its own over 16M rows (inputs larger than L2); algorithmic bytes per
+    # row: A 256 + residual 256 + output 256
+    M = 1 << 24
+    A = torch.randn((M, 128), device=sim.device).to(torch.bfloat16)
+    R = torch.randn((M, 128), device=sim.device).to(torch.bfloat16)
+    O = torch.empty((M, 128), dtype=torch.bfloat16, device=sim.device)
+    Bt = (torch.randn((128, 128), device=sim.device) / 11.3).to(torch.bfloat16)
+    bias = torch.zeros(128, device=sim.device)
+    cs = torch.cuda.current_stream()
+    for _ in range(3):
+        U.sur_linear(A, Bt, bias, M, 128, 128, U.SUR_EPI_RESIDUAL, R, O, None, cs.cuda_stream)
+    e0.record(cs)
+    for _ in range(10):
+        U.sur_linear(A, Bt, bias, M, 128, 128, U.SUR_EPI_RESIDUAL, R, O, None, cs.cuda_stream)
+    e1.record(cs)
+    e1.synchronize()
+    t_gemm = e0.elapsed_time(e1) / 10 / 1e3
+    pk, src = peaks()
+    gbs = 3 * 256 * M / t_gemm / 1e9
+    line = {"metric": "surrogate simulated s per wall s", "value": value, "unit": "sim-s/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sur_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate_obstacles_1m", "n_particles": case.n, "edges": E,
+                       "layers": 10, "latent": 128, "sph_steps_per_call": 4, "dt": dt,
+                       "weights": "random initialisation"},
+            "sph_sim_per_s": sph_sim / sph_s, "speedup_vs_sph": value / (sph_sim / sph_s),
+            "edges_per_s": E * args.steps / sur_s,
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None,
+                         "kernel": "k_linear<128,128> residual epilogue, 16M rows",
+                         "ms_per_launch": round(t_gemm * 1e3, 4)},
+            "gpu_launches": None, "clocks": clocks, "peaks_source": src}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +462,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "surrogate_obstacles_1m":
+        return run_surrogate(args)
     return run_ours(args)
 
 

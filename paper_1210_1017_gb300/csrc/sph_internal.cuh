@@ -122,7 +122,7 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 // size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
 constexpr int kMinUnit = 64;
-constexpr int kNumVariants = 4;
+constexpr int kNumVariants = 5;
 
 struct InteractArgs {
     const uint2* units;

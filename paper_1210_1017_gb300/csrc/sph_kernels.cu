@@ -5,6 +5,7 @@
 // neighbour counts and FP64 conservation sums.  Every kernel serves an
 // ensemble of independent instances (see sph_internal.cuh); a single
 // simulation is the ensemble of one.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "sph_internal.cuh"
@@ -196,17 +197,24 @@ constexpr uint32_t kIdxMask = (1u << 26) - 1;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Shape of one interaction variant: W warps per block (units of W*32
-// particles), STAGE staged candidates, CAP list slots per lane.  Dynamic
-// shared memory: staged posc and velrhop (STAGE float4 each), then the 16-bit
-// per-lane lists; the global-memory fallback reuses the staging area for
-// 32-bit list entries.
-template <int W, int STAGE, int CAP>
+// particles), STAGE staged candidates, WCAP hit-mask words per lane.  Dynamic
+// shared memory: staged posc and velrhop (STAGE float4 each), the staged
+// positions in half precision (one uint4 of three half2 per candidate pair),
+// then per warp WCAP x 32 hit-mask words and WCAP word descriptors.  The
+// global-memory fallback keeps 32-bit lists of kFallbackCap entries per lane
+// in the staging area.
+constexpr int kFallbackCap = 64;
+
+template <int W, int STAGE, int WCAP>
 struct Shape {
-    static constexpr size_t smem =
-        (size_t)STAGE * 2 * sizeof(float4) + (size_t)W * CAP * 32 * sizeof(uint16_t);
-    static_assert((size_t)W * CAP * 32 * sizeof(uint32_t) <= (size_t)STAGE * 2 * sizeof(float4),
+    static constexpr size_t stage_bytes = (size_t)STAGE * 2 * sizeof(float4);
+    static constexpr size_t half_bytes = (size_t)STAGE / 2 * sizeof(uint4);
+    static constexpr size_t word_bytes = (size_t)W * WCAP * 32 * sizeof(uint32_t);
+    static constexpr size_t smem = stage_bytes + half_bytes + word_bytes +
+                                   (size_t)W * WCAP * sizeof(uint32_t);
+    static_assert((size_t)W * kFallbackCap * 32 * sizeof(uint32_t) <= stage_bytes,
                   "fallback lists must fit in the staging area");
-    static_assert(STAGE <= (1 << 14), "staged index must fit 14 bits");
+    static_assert(STAGE <= (1 << 16) && STAGE % 2 == 0, "staged index must fit 16 bits");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -260,15 +268,21 @@ struct PairAcc {
 // choice); only fluid particles keep them, since boundary particles never
 // move (Sec. 2.3).  The pair j = i (all offsets zero) contributes exactly
 // nothing, which lets lists be padded with it.
-template <bool MOM>
+template <bool MOM, bool CHECK = false>
 __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, const float4& pi,
                                            const float4& vi, float ci, float dx, float dy, float dz,
-                                           const float4& pj, const float4& vj, PairAcc& s) {
+                                           const float4& pj, const float4& vj, PairAcc& s,
+                                           bool real = true) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // CHECK: the entry came from the conservative half-precision pre-filter;
+    // the FP32 neighbour test (the same expression as the candidate test of
+    // the global-memory path) decides, and counts the pair
+    const bool use = CHECK ? (real && d2 < d.r2max) : true;
+    if (CHECK) s.np += use ? 1u : 0u;
     // Wendland C2: grad_i W = F r_ij, F = -5 aD/h^2 (1 - q/2)^3
     const float q = sqrt_approx(d2) * d.inv_h;
     const float wq = fmaf(-0.5f, q, 1.0f);
-    const float F = d.fc * (wq * wq * wq);
+    const float F = use ? d.fc * (wq * wq * wq) : 0.f;
     const float dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = vi.z - vj.z;
     const float vr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
     s.dr = fmaf(vr, F, s.dr);                                      // Eq. 7
@@ -281,7 +295,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
         s.ax = fmaf(-f, dx, s.ax);
         s.ay = fmaf(-f, dy, s.ay);
         s.az = fmaf(-f, dz, s.az);
-        s.mu = fmaxf(s.mu, fluid ? fabsf(nu) : 0.f);
+        s.mu = fmaxf(s.mu, (fluid && use) ? fabsf(nu) : 0.f);
     }
 }
 
@@ -299,11 +313,14 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
 // the particles' own cell origins (FP32), plus whole-cell offsets.  A unit
 // whose runs do not fit the staging area reads its candidates from global
 // memory instead.  Units of instances that are done are skipped.
-template <int W, int STAGE, int CAP, int MINB, bool COUNTS>
+template <int W, int STAGE, int WCAP, int MINB, bool COUNTS>
 __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     extern __shared__ __align__(128) unsigned char s_raw[];
     float4* s_p = reinterpret_cast<float4*>(s_raw);
     float4* s_v = s_p + STAGE;
+    uint4* s_h = reinterpret_cast<uint4*>(s_v + STAGE);            // STAGE / 2 candidate pairs
+    uint32_t* s_words = reinterpret_cast<uint32_t*>(s_h + STAGE / 2);
+    uint32_t* s_desc = s_words + W * WCAP * 32;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_rs[9], s_rb[9], s_len[9], s_base[10];
     __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
@@ -404,6 +421,21 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
             }
         }
         __syncthreads();
+        // half-precision copies in cell units (cell = 2h = 1), two
+        // candidates per uint4: (x0, x1), (y0, y1), (z0, z1) as half2
+        const float inv_cs = 1.0f / d.csf;
+        const uint32_t nst = s_base[9];
+        for (uint32_t k = tid; 2 * k < nst; k += W * 32) {
+            const float4 p0 = s_p[2 * k];
+            const float4 p1 = 2 * k + 1 < nst ? s_p[2 * k + 1] : p0;
+            const __half2 hx = __floats2half2_rn(p0.x * inv_cs, p1.x * inv_cs);
+            const __half2 hy = __floats2half2_rn(p0.y * inv_cs, p1.y * inv_cs);
+            const __half2 hz = __floats2half2_rn(p0.z * inv_cs, p1.z * inv_cs);
+            s_h[k] = make_uint4(*reinterpret_cast<const uint32_t*>(&hx),
+                                *reinterpret_cast<const uint32_t*>(&hy),
+                                *reinterpret_cast<const uint32_t*>(&hz), 0u);
+        }
+        __syncthreads();
     }
 
     const uint32_t act = __ballot_sync(kFull, valid);
@@ -414,40 +446,70 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         const int xhi = wxmax + 1 < ncx ? wxmax + 1 : ncx - 1;
         uint32_t cnt = 0;
         if (staged) {
-            uint16_t* lst = reinterpret_cast<uint16_t*>(s_v + STAGE) + w * (CAP * 32) + lane;
+            // candidate test in half precision, two candidates per
+            // instruction, against a conservative threshold (cell units:
+            // |r_ij|^2 < 1 + 2^-6); each lane keeps one 32-bit hit mask per
+            // word of 32 staged candidates (bit p: candidate base + 2p, bit
+            // 16 + p: candidate base + 2p + 1).  The pair phase applies the
+            // exact FP32 test.
+            uint32_t* wl = s_words + w * (WCAP * 32) + lane;
+            uint32_t* wd = s_desc + w * WCAP;
             const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
-            const uint32_t selfe = self | (1u << 14);      // the pair (i, i), x offset 0
             const bool anyfluid = __any_sync(kFull, fluid);
-            // pair phase: two list entries per iteration, short lists padded
-            // with the zero-contribution pair (i, i)
+            const float inv_cs = 1.0f / d.csf;
+            const __half2 thr = __float2half2_rn(1.0f + 1.0f / 64.0f);
+            const __half2 hqy = __float2half2_rn(pi.y * inv_cs);
+            const __half2 hqz = __float2half2_rn(pi.z * inv_cs);
+            uint32_t nw = 0, lane_hits = 0;
+            // pair phase over the stored words: each lane pops its own hits,
+            // two per iteration; lanes that run out use the pair (i, i)
             auto flush = [&]() {
-                const uint32_t mx = __reduce_max_sync(kFull, cnt);
+                __syncwarp();   // the words and lane 0's descriptors are written
+                const uint32_t mx = __reduce_max_sync(kFull, lane_hits);
+                uint32_t wi = 0, cm = 0, jb = 0;
+                float oxf = 0.f;
                 for (uint32_t t = 0; t < mx; t += 2) {
-                    const uint32_t e0 = t < cnt ? lst[t * 32] : selfe;
-                    const uint32_t e1 = t + 1 < cnt ? lst[(t + 1) * 32] : selfe;
-                    const uint32_t j0 = e0 & 0x3fffu, j1 = e1 & 0x3fffu;
-                    const float ox0 = (float)((int)(e0 >> 14) - 1);
-                    const float ox1 = (float)((int)(e1 >> 14) - 1);
-                    const float4 p0 = s_p[j0], v0 = s_v[j0];
-                    const float4 p1 = s_p[j1], v1 = s_v[j1];
+                    uint32_t j2[2];
+                    float ox2[2];
+                    bool re[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        while (cm == 0 && wi < nw) {
+                            cm = wl[wi * 32];
+                            const uint32_t dsc = wd[wi];
+                            jb = dsc & 0xffffu;
+                            oxf = (float)(cx - (ulo + (int)(dsc >> 16)));
+                            ++wi;
+                        }
+                        re[k] = cm != 0;
+                        if (cm) {
+                            const uint32_t b = 31u - __clz(cm);
+                            cm ^= 1u << b;
+                            j2[k] = jb + ((b & 15u) << 1) + (b >> 4);
+                            ox2[k] = oxf;
+                        } else {
+                            j2[k] = self;
+                            ox2[k] = 0.f;
+                        }
+                    }
+                    const float4 p0 = s_p[j2[0]], v0 = s_v[j2[0]];
+                    const float4 p1 = s_p[j2[1]], v1 = s_v[j2[1]];
                     if (anyfluid) {
-                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
-                                         pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
-                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
-                                         pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
+                        pair_terms<true, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[0], d.csf, pi.x) - p0.x,
+                                               pi.y - p0.y, pi.z - p0.z, p0, v0, acc, re[0]);
+                        pair_terms<true, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[1], d.csf, pi.x) - p1.x,
+                                               pi.y - p1.y, pi.z - p1.z, p1, v1, acc, re[1]);
                     } else {
-                        pair_terms<false>(d, c0, fluid, pi, vi, ci, fmaf(ox0, d.csf, pi.x) - p0.x,
-                                          pi.y - p0.y, pi.z - p0.z, p0, v0, acc);
-                        pair_terms<false>(d, c0, fluid, pi, vi, ci, fmaf(ox1, d.csf, pi.x) - p1.x,
-                                          pi.y - p1.y, pi.z - p1.z, p1, v1, acc);
+                        pair_terms<false, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[0], d.csf, pi.x) - p0.x,
+                                                pi.y - p0.y, pi.z - p0.z, p0, v0, acc, re[0]);
+                        pair_terms<false, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[1], d.csf, pi.x) - p1.x,
+                                                pi.y - p1.y, pi.z - p1.z, p1, v1, acc, re[1]);
                     }
                 }
-                acc.np += cnt;
-                cnt = 0;
+                __syncwarp();   // every lane is done reading before the words are reused
+                nw = 0;
+                lane_hits = 0;
             };
-            // candidate test: every candidate of the warp's cells against
-            // every lane (broadcast loads); the pair (i, i) is kept and its
-            // count removed at the end
             for (int r = 0; r < 9; ++r) {
                 if (!s_ok[r]) continue;
                 const uint32_t rs = s_rs[r], sb = s_base[r];
@@ -457,42 +519,34 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                     const bool adj = valid && ox >= -1 && ox <= 1;
                     if (adj) ncand += ge - gs;
                     if (gs == ge) continue;
-                    const float qx = fmaf((float)ox, d.csf, pi.x);
-                    const uint32_t code = (uint32_t)(ox + 1) << 14;
-                    const uint32_t e = sb + (ge - rs);
-                    for (uint32_t c0i = sb + (gs - rs); c0i < e; c0i += CAP) {
-                        const uint32_t c1 = (e - c0i) > (uint32_t)CAP ? c0i + CAP : e;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)CAP) flush();
-                        uint16_t* lp = lst + cnt * 32;
-                        uint32_t j = c0i;
-                        for (; j + 4 <= c1; j += 4) {
-                            const float4 a0 = s_p[j], a1 = s_p[j + 1], a2 = s_p[j + 2],
-                                         a3 = s_p[j + 3];
-                            const float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
-                            const float x1 = qx - a1.x, y1 = pi.y - a1.y, z1 = pi.z - a1.z;
-                            const float x2 = qx - a2.x, y2 = pi.y - a2.y, z2 = pi.z - a2.z;
-                            const float x3 = qx - a3.x, y3 = pi.y - a3.y, z3 = pi.z - a3.z;
-                            const uint32_t h0 = adj && fmaf(x0, x0, fmaf(y0, y0, z0 * z0)) < d.r2max;
-                            const uint32_t h1 = adj && fmaf(x1, x1, fmaf(y1, y1, z1 * z1)) < d.r2max;
-                            const uint32_t h2 = adj && fmaf(x2, x2, fmaf(y2, y2, z2 * z2)) < d.r2max;
-                            const uint32_t h3 = adj && fmaf(x3, x3, fmaf(y3, y3, z3 * z3)) < d.r2max;
-                            const uint32_t o1 = h0, o2 = o1 + h1, o3 = o2 + h2;
-                            if (h0) lp[0] = (uint16_t)(code | j);
-                            if (h1) lp[o1 * 32] = (uint16_t)(code | (j + 1));
-                            if (h2) lp[o2 * 32] = (uint16_t)(code | (j + 2));
-                            if (h3) lp[o3 * 32] = (uint16_t)(code | (j + 3));
-                            const uint32_t nh = o3 + h3;
-                            lp += nh * 32;
-                            cnt += nh;
+                    const __half2 hqx = __float2half2_rn(fmaf((float)ox, d.csf, pi.x) * inv_cs);
+                    const uint32_t s0 = sb + (gs - rs), e0 = sb + (ge - rs);
+                    for (uint32_t base = s0 & ~1u; base < e0; base += 32) {
+                        if (nw == (uint32_t)WCAP) flush();
+                        const uint32_t lim = e0 - base < 32u ? e0 - base : 32u;   // slots in use
+                        const uint32_t npair = (lim + 1) >> 1;
+                        const uint4* hp = s_h + (base >> 1);
+                        uint32_t m = 0;
+#pragma unroll 4
+                        for (uint32_t q2 = 0; q2 < npair; ++q2) {
+                            const uint4 hv = hp[q2];
+                            const __half2 dx = __hsub2(hqx, *reinterpret_cast<const __half2*>(&hv.x));
+                            const __half2 dy = __hsub2(hqy, *reinterpret_cast<const __half2*>(&hv.y));
+                            const __half2 dz = __hsub2(hqz, *reinterpret_cast<const __half2*>(&hv.z));
+                            const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+                            m |= (__hlt2_mask(r2, thr) & 0x00010001u) << q2;
                         }
-                        for (; j < c1; ++j) {
-                            const float4 a0 = s_p[j];
-                            const float x0 = qx - a0.x, y0 = pi.y - a0.y, z0 = pi.z - a0.z;
-                            if (adj && fmaf(x0, x0, fmaf(y0, y0, z0 * z0)) < d.r2max) {
-                                lp[0] = (uint16_t)(code | j);
-                                lp += 32;
-                                ++cnt;
-                            }
+                        // slots outside [s0, e0) and lanes not adjacent to the cell
+                        const uint32_t ev = lim >= 32u ? 0xffffu : ((1u << ((lim + 1) >> 1)) - 1u);
+                        const uint32_t od = (lim >> 1) >= 16u ? 0xffffu : ((1u << (lim >> 1)) - 1u);
+                        uint32_t keep = ev | (od << 16);
+                        if (base < s0) keep &= ~1u;
+                        m = adj ? (m & keep) : 0u;
+                        if (__any_sync(kFull, m != 0u)) {
+                            wl[nw * 32] = m;
+                            if (lane == 0) wd[nw] = base | ((uint32_t)(xx - ulo) << 16);
+                            lane_hits += __popc(m);
+                            ++nw;
                         }
                     }
                 }
@@ -500,7 +554,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
             flush();
         } else {
             // candidates straight from global memory (unit too large to stage)
-            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (CAP * 32);
+            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (kFallbackCap * 32);
             auto flush = [&]() {
                 const uint32_t mx = __reduce_max_sync(kFull, cnt);
                 for (uint32_t t = 0; t < mx; ++t) {
@@ -534,9 +588,9 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                     if (gs == ge) continue;
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = code_yz | ((uint32_t)(ox + 1) << 26);
-                    for (uint32_t c0i = gs; c0i < ge; c0i += CAP) {
-                        const uint32_t c1 = (ge - c0i) > (uint32_t)CAP ? c0i + CAP : ge;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)CAP) flush();
+                    for (uint32_t c0i = gs; c0i < ge; c0i += kFallbackCap) {
+                        const uint32_t c1 = (ge - c0i) > (uint32_t)kFallbackCap ? c0i + kFallbackCap : ge;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kFallbackCap) flush();
 #pragma unroll 4
                         for (uint32_t j = c0i; j < c1; ++j) {
                             const float4 pj = __ldg(a.posc + j);
@@ -996,8 +1050,8 @@ struct Variant {
     int grid;   // persistent grid on this GPU (set by prepare_interact)
 };
 
-// (warps, staged candidates, list slots, resident blocks per SM that the
-// shared memory allows -- also the register budget hint)
+// (warps, staged candidates, hit-mask words per lane, resident blocks per SM
+// that the shared memory allows -- also the register budget hint)
 #define SPH_VARIANT(Wv, Sv, Cv, Bv)                                                    \
     Variant {                                                                         \
         Wv, k_interact<Wv, Sv, Cv, Bv, false>, k_interact<Wv, Sv, Cv, Bv, true>,      \
@@ -1005,10 +1059,11 @@ struct Variant {
     }
 
 Variant g_variants[kNumVariants] = {
-    SPH_VARIANT(4, 2048, 96, 2),   // 128-particle units
-    SPH_VARIANT(2, 1280, 96, 4),   // 64-particle units
-    SPH_VARIANT(3, 1536, 64, 3),   // 96-particle units
-    SPH_VARIANT(8, 3072, 80, 1),   // 256-particle units
+    SPH_VARIANT(4, 2048, 48, 2),   // 128-particle units
+    SPH_VARIANT(2, 1024, 40, 4),   // 64-particle units
+    SPH_VARIANT(3, 1536, 40, 2),   // 96-particle units
+    SPH_VARIANT(8, 3072, 40, 1),   // 256-particle units
+    SPH_VARIANT(2, 1280, 48, 3),   // 64-particle units, deeper staging
 };
 
 }  // namespace
