@@ -121,8 +121,8 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 // cells spanning at most kSpan cells (uint2: first particle, end).  The unit
 // size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
-constexpr int kMinUnit = 64;
-constexpr int kNumVariants = 5;
+constexpr int kMinUnit = 32;
+constexpr int kNumVariants = 7;
 
 struct InteractArgs {
     const uint2* units;

@@ -468,12 +468,13 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                 const uint32_t mx = __reduce_max_sync(kFull, lane_hits);
                 uint32_t wi = 0, cm = 0, jb = 0;
                 float oxf = 0.f;
-                for (uint32_t t = 0; t < mx; t += 2) {
-                    uint32_t j2[2];
-                    float ox2[2];
-                    bool re[2];
+                constexpr int kPop = 2;   // pairs per iteration (independent chains)
+                for (uint32_t t = 0; t < mx; t += kPop) {
+                    uint32_t j2[kPop];
+                    float ox2[kPop];
+                    bool re[kPop];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
+                    for (int k = 0; k < kPop; ++k) {
                         while (cm == 0 && wi < nw) {
                             cm = wl[wi * 32];
                             const uint32_t dsc = wd[wi];
@@ -492,18 +493,26 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                             ox2[k] = 0.f;
                         }
                     }
-                    const float4 p0 = s_p[j2[0]], v0 = s_v[j2[0]];
-                    const float4 p1 = s_p[j2[1]], v1 = s_v[j2[1]];
+                    float4 pp[kPop], vv[kPop];
+#pragma unroll
+                    for (int k = 0; k < kPop; ++k) {
+                        pp[k] = s_p[j2[k]];
+                        vv[k] = s_v[j2[k]];
+                    }
                     if (anyfluid) {
-                        pair_terms<true, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[0], d.csf, pi.x) - p0.x,
-                                               pi.y - p0.y, pi.z - p0.z, p0, v0, acc, re[0]);
-                        pair_terms<true, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[1], d.csf, pi.x) - p1.x,
-                                               pi.y - p1.y, pi.z - p1.z, p1, v1, acc, re[1]);
+#pragma unroll
+                        for (int k = 0; k < kPop; ++k)
+                            pair_terms<true, true>(d, c0, fluid, pi, vi, ci,
+                                                   fmaf(ox2[k], d.csf, pi.x) - pp[k].x,
+                                                   pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
+                                                   re[k]);
                     } else {
-                        pair_terms<false, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[0], d.csf, pi.x) - p0.x,
-                                                pi.y - p0.y, pi.z - p0.z, p0, v0, acc, re[0]);
-                        pair_terms<false, true>(d, c0, fluid, pi, vi, ci, fmaf(ox2[1], d.csf, pi.x) - p1.x,
-                                                pi.y - p1.y, pi.z - p1.z, p1, v1, acc, re[1]);
+#pragma unroll
+                        for (int k = 0; k < kPop; ++k)
+                            pair_terms<false, true>(d, c0, fluid, pi, vi, ci,
+                                                    fmaf(ox2[k], d.csf, pi.x) - pp[k].x,
+                                                    pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
+                                                    re[k]);
                     }
                 }
                 __syncwarp();   // every lane is done reading before the words are reused
@@ -1060,10 +1069,12 @@ struct Variant {
 
 Variant g_variants[kNumVariants] = {
     SPH_VARIANT(4, 2048, 48, 2),   // 128-particle units
-    SPH_VARIANT(2, 1024, 40, 4),   // 64-particle units
-    SPH_VARIANT(3, 1536, 40, 2),   // 96-particle units
+    SPH_VARIANT(4, 1536, 24, 3),   // 128-particle units, three blocks per SM
+    SPH_VARIANT(3, 1280, 24, 3),   // 96-particle units
     SPH_VARIANT(8, 3072, 40, 1),   // 256-particle units
-    SPH_VARIANT(2, 1280, 48, 3),   // 64-particle units, deeper staging
+    SPH_VARIANT(2, 896, 24, 5),    // 64-particle units, five blocks per SM
+    SPH_VARIANT(3, 1152, 24, 4),   // 96-particle units, four blocks per SM
+    SPH_VARIANT(2, 1024, 24, 4),   // 64-particle units
 };
 
 }  // namespace
