@@ -48,8 +48,29 @@ struct WgradArgs {
     uint32_t* status;
 };
 
+// Fused edge update of one message-passing layer over M edges (latent 128):
+//   z  = relu(e W1c + b1 + P[src] + Q[dst])      (stored to Z when Z != null)
+//   e' = e + z W2 + b2                           (stored to Eout)
+// W1t, W2t: the weights transposed (N x K, K-major), bf16.
+struct EdgeArgs {
+    const __nv_bfloat16* E;
+    const __nv_bfloat16* W1t;
+    const __nv_bfloat16* W2t;
+    const float* b1;
+    const float* b2;
+    const __nv_bfloat16* P;
+    const __nv_bfloat16* Q;
+    const uint32_t* src;
+    const uint32_t* dst;
+    uint32_t M;
+    __nv_bfloat16* Z;
+    __nv_bfloat16* Eout;
+    uint32_t* status;
+};
+
 int num_sms();
 bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st);
+void launch_edge_layer(const EdgeArgs& g, cudaStream_t st);
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st);
 
 }  // namespace sur

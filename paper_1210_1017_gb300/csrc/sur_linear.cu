@@ -383,6 +383,179 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, in
     out[i] = s * scale;
 }
 
+
+// Fused edge update (see EdgeArgs): per 128-edge tile, tcgen05 MMA 1 (e W1c)
+// into TMEM columns [0, 128), the first epilogue writes z = relu(...) as the
+// K-major A operand of MMA 2 in shared memory (and to global memory for the
+// backward pass), MMA 2 (z W2) into columns [128, 256), and the second
+// epilogue adds the bias and the residual e, read back from the staged e
+// tile, so z is never re-read from HBM.  The e tile is double-buffered and
+// the gathered rows P[src], Q[dst] of the next tile are copied in with
+// cp.async while MMA 2 and the second epilogue run.
+constexpr size_t kEdgeSmem = (size_t)7 * 128 * 128 * 2;   // W1c, W2, z, 2 x e, P, Q
+
+__device__ __forceinline__ void issue_gather(unsigned char* dst, const __nv_bfloat16* table,
+                                             const uint32_t* idx, uint32_t row0, uint32_t nrows) {
+    // thread t copies row t of the tile: 16 pieces of 16 bytes
+    const int r = threadIdx.x;
+    const bool ok = row0 + r < nrows;
+    const __nv_bfloat16* p = ok ? table + (size_t)idx[row0 + r] * 128 : table;
+#pragma unroll
+    for (int gk = 0; gk < 16; ++gk) cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
+}
+
+__device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, float* f) {
+    unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0, 128)), f);
+    unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0 + 8, 128)), f + 8);
+}
+
+__global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
+    constexpr int K = 128, N = 128;
+    constexpr uint32_t T = 128 * 128 * 2;          // bytes of one 128 x 128 bf16 tile
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    unsigned char* sw1 = s_raw;                    // W1c^T, N x K
+    unsigned char* sw2 = sw1 + T;                  // W2^T
+    unsigned char* sz = sw2 + T;                   // z tile
+    unsigned char* sp = sz + T;                    // P[src] rows
+    unsigned char* sq = sp + T;                    // Q[dst] rows
+    unsigned char* sa0 = sq + T;                   // 2 x e tile
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    if (w == 0) tmem_alloc(&s_tmem, 256);
+    if (tid == 0) mbar_init1(&s_bar);
+    const uint32_t ntiles = (g.M + 127) / 128;
+    for (int c = tid; c < N * (K / 8); c += 128) {
+        const int r = c % N, gk = c / N;
+        cp_async16(sw1 + kmajor_offset(r, gk * 8, K), g.W1t + (size_t)r * K + gk * 8, true);
+        cp_async16(sw2 + kmajor_offset(r, gk * 8, K), g.W2t + (size_t)r * K + gk * 8, true);
+    }
+    if (blockIdx.x < ntiles) {
+        issue_rows<K>(sa0, g.E, blockIdx.x * 128, g.M, K);
+        issue_gather(sp, g.P, g.src, blockIdx.x * 128, g.M);
+        issue_gather(sq, g.Q, g.dst, blockIdx.x * 128, g.M);
+    }
+    cp_async_commit();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = tmem + ((uint32_t)(w * 32) << 16);
+    uint32_t phase = 0, buf = 0;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= 1u) {
+        unsigned char* sa = sa0 + buf * T;
+        cp_async_wait_all();                       // e, P, Q of this tile
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < K / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sa) + s * 256, kLBO, (K / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw1) + s * 256, kLBO, (K / 8) * 128);
+                tc_mma(tmem, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
+            }
+            tc_commit(&s_bar);
+        }
+        const uint32_t next = tile + gridDim.x;
+        if (next < ntiles) issue_rows<K>(sa0 + (buf ^ 1u) * T, g.E, next * 128, g.M, K);
+        cp_async_commit();
+        const int r = w * 32 + lane;               // this thread's row of the tile
+        const uint32_t m = tile * 128 + r;
+        const bool valid = m < g.M;
+        bool got = mbar_wait(&s_bar, phase);
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 1: z = relu(acc + b1 + P[src] + Q[dst]) -> shared (MMA 2) and global
+#pragma unroll 2
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16], t[16], u[16];
+            tmem_ld16(lane_base + c0, v);
+            const float4* b4 = reinterpret_cast<const float4*>(g.b1 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 b = __ldg(b4 + q);
+                v[4 * q] += b.x;
+                v[4 * q + 1] += b.y;
+                v[4 * q + 2] += b.z;
+                v[4 * q + 3] += b.w;
+            }
+            lds16(sp, r, c0, t);
+            lds16(sq, r, c0, u);
+            __nv_bfloat162 hh[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                hh[q] = __floats2bfloat162_rn(fmaxf(v[2 * q] + t[2 * q] + u[2 * q], 0.f),
+                                              fmaxf(v[2 * q + 1] + t[2 * q + 1] + u[2 * q + 1], 0.f));
+            const uint4 z0 = *reinterpret_cast<uint4*>(&hh[0]);
+            const uint4 z1 = *reinterpret_cast<uint4*>(&hh[4]);
+            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0, K)) = z0;
+            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0 + 8, K)) = z1;
+            if (g.Z && valid) {
+                uint4* o = reinterpret_cast<uint4*>(g.Z + (size_t)m * N + c0);
+                o[0] = z0;
+                o[1] = z1;
+            }
+        }
+        fence_async_shared();
+        tc_fence_before();
+        __syncthreads();                           // z complete; P, Q tiles free
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < K / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sz) + s * 256, kLBO, (K / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw2) + s * 256, kLBO, (K / 8) * 128);
+                tc_mma(tmem + 128, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
+            }
+            tc_commit(&s_bar);
+        }
+        if (next < ntiles) {
+            issue_gather(sp, g.P, g.src, next * 128, g.M);
+            issue_gather(sq, g.Q, g.dst, next * 128, g.M);
+        }
+        cp_async_commit();
+        got = mbar_wait(&s_bar, phase);
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 2: e' = e + acc + b2 (e from the staged tile)
+#pragma unroll 2
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16], t[16];
+            tmem_ld16(lane_base + 128 + c0, v);
+            if (!valid) continue;
+            const float4* b4 = reinterpret_cast<const float4*>(g.b2 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 b = __ldg(b4 + q);
+                v[4 * q] += b.x;
+                v[4 * q + 1] += b.y;
+                v[4 * q + 2] += b.z;
+                v[4 * q + 3] += b.w;
+            }
+            lds16(sa, r, c0, t);
+            __nv_bfloat162 hh[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                hh[q] = __floats2bfloat162_rn(v[2 * q] + t[2 * q], v[2 * q + 1] + t[2 * q + 1]);
+            uint4* o = reinterpret_cast<uint4*>(g.Eout + (size_t)m * N + c0);
+            o[0] = *reinterpret_cast<uint4*>(&hh[0]);
+            o[1] = *reinterpret_cast<uint4*>(&hh[4]);
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0 && g.status) atomicOr(g.status, 1u);
+    cp_async_wait_all();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, 256);
+}
+
 template <int K, int N>
 size_t linear_smem() { return (size_t)2 * 128 * K * 2 + (size_t)N * K * 2; }
 
@@ -454,6 +627,20 @@ bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st) {
     else if (K == 128 && N == 256) launch_linear_t<128, 256>(g, sms, st);
     else return false;
     return true;
+}
+
+void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) {
+    static bool init = false;
+    const size_t smem = kEdgeSmem;
+    if (!init) {
+        cudaFuncSetAttribute(k_edge_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init = true;
+    }
+    if (g.M == 0) return;
+    const uint32_t tiles = (g.M + 127) / 128;
+    uint32_t grid = (uint32_t)num_sms();   // one block per SM (224 KB of shared memory)
+    if (grid > tiles) grid = tiles;
+    k_edge_layer<<<grid, 128, smem, st>>>(g);
 }
 
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st) {

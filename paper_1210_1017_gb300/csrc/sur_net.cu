@@ -500,11 +500,11 @@ size_t carve(sur_ctx* c, void* base) {
     c->xe = cv.take<__nv_bfloat16>(E * KIN);
     c->en1 = cv.take<__nv_bfloat16>(N * L);
     c->ee1 = cv.take<__nv_bfloat16>(E * L);
-    const int nx = train ? NL + 1 : 2, ne = train ? NL + 1 : 2, nz = train ? NL : 1;
+    const int nx = train ? NL + 1 : 2, ne = train ? NL + 1 : 2, nz = train ? NL : 0;
     c->XN.assign(nx, nullptr);
     c->Ebuf.assign(ne, nullptr);
     c->Z1.assign(nz, nullptr);
-    c->Y1.assign(nz, nullptr);
+    c->Y1.assign(train ? NL : 1, nullptr);
     for (auto& p : c->XN) p = cv.take<__nv_bfloat16>(N * 2 * L);
     for (auto& p : c->Ebuf) p = cv.take<__nv_bfloat16>(E * L);
     for (auto& p : c->Z1) p = cv.take<__nv_bfloat16>(E * L);
@@ -564,21 +564,24 @@ int linear(sur_ctx* c, const __nv_bfloat16* A, uint32_t lda, const Layer& l, boo
     return SPH_OK;
 }
 
-int edge1(sur_ctx* c, const Layer& l, const __nv_bfloat16* e, __nv_bfloat16* out) {
-    LinearArgs g = {};
-    g.A = e;
-    g.Bt = l.Wt;
-    g.bias = c->w + l.b_off;
-    g.M = c->E;
-    g.epi = kEpiEdge1;
-    g.gp = c->P;
-    g.gq = c->Q;
+// The fused edge update of one layer: z = relu(e W1c + b1 + P[src] + Q[dst])
+// (kept for the backward pass when z != null), e' = e + z W2 + b2.
+void edge_layer(sur_ctx* c, const Layer& l1, const Layer& l2, const __nv_bfloat16* e,
+                __nv_bfloat16* z, __nv_bfloat16* e_out) {
+    EdgeArgs g = {};
+    g.E = e;
+    g.W1t = l1.Wt;
+    g.W2t = l2.Wt;
+    g.b1 = c->w + l1.b_off;
+    g.b2 = c->w + l2.b_off;
+    g.P = c->P;
+    g.Q = c->Q;
     g.src = c->src;
     g.dst = c->col;
-    g.out_bf16 = out;
-    g.ldo = L;
-    if (!launch_linear(L, L, g, c->st)) return fail(c, SPH_ERR_INVALID_ARG, "edge layer");
-    return SPH_OK;
+    g.M = c->E;
+    g.Z = z;
+    g.Eout = e_out;
+    launch_edge_layer(g, c->st);
 }
 
 // grad of W (kin x kout) += X^T dY over M rows (X: M x kin with stride ldx,
@@ -688,13 +691,12 @@ int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
         __nv_bfloat16* xn_next = c->XN[train ? l + 1 : (l + 1) % 2];
         __nv_bfloat16* e_in = c->Ebuf[train ? l : l % 2];
         __nv_bfloat16* e_out = c->Ebuf[train ? l + 1 : (l + 1) % 2];
-        __nv_bfloat16* z1 = c->Z1[train ? l : 0];
+        __nv_bfloat16* z1 = train ? c->Z1[l] : nullptr;
         __nv_bfloat16* y1 = c->Y1[train ? l : 0];
         const Layer* w = &Ls[4 + 6 * l];
         if ((rc = linear(c, xn_cur, 2 * L, w[0], false, n, kEpiNone, nullptr, 0, c->P, nullptr, L))) return rc;
         if ((rc = linear(c, xn_cur, 2 * L, w[1], false, n, kEpiNone, nullptr, 0, c->Q, nullptr, L))) return rc;
-        if ((rc = edge1(c, w[2], e_in, z1))) return rc;
-        if ((rc = linear(c, z1, 0, w[3], false, E, kEpiResidual, e_in, L, e_out, nullptr, L))) return rc;
+        edge_layer(c, w[2], w[3], e_in, train ? z1 : nullptr, e_out);
         k_rowsum<__nv_bfloat16><<<nblk((size_t)n * 32, 256), 256, 0, st>>>(n, c->rowptr, e_out, nullptr,
                                                                            xn_cur + L, nullptr, 2 * L);
         if ((rc = linear(c, xn_cur, 0, w[4], false, n, kEpiRelu, nullptr, 0, y1, nullptr, L))) return rc;

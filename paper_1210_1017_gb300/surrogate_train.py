@@ -443,7 +443,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--lr0", type=float, default=3e-4)
     ap.add_argument("--lr1", type=float, default=1e-5)
-    ap.add_argument("--sigma", type=float, default=0.0)
+    ap.add_argument("--sigma", type=float, default=3e-6)
     ap.add_argument("--eval-calls", type=int, default=1000)
     ap.add_argument("--case-seconds", type=float, default=0.1)
     ap.add_argument("--case", default="c2", choices=["c2", "none"])
