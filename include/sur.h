@@ -45,6 +45,21 @@ int sur_wgrad(const void *d_P, const void *d_Q, uint32_t M, uint32_t N,
               float scale, float *d_dW, void *d_scratch,
               uint64_t scratch_bytes, void *stream);
 
+/* The fused edge update of one message-passing layer (the network's hot
+ * kernel) on its own, over M edges of latent width 128 (all arrays device,
+ * bf16 row-major unless noted, 16-byte aligned):
+ *   z  = relu(E W1 + b1 + P[src] + Q[dst])   -> Z (M x 128; may be NULL)
+ *   E' = E + z W2 + b2                        -> Eout (M x 128)
+ * W1t, W2t: the 128 x 128 weights transposed (row n holds output n); b1, b2:
+ * float[128]; P, Q: node tables (rows indexed by src[m], dst[m], uint32).
+ * bf16 inputs, fp32 accumulation on the tensor cores, results rounded to
+ * bf16.  Async on `stream`.  SPH_ERR_INVALID_ARG for NULL or unaligned
+ * pointers. */
+int sur_edge_layer(const void *d_E, const void *d_W1t, const void *d_W2t,
+                   const float *d_b1, const float *d_b2, const void *d_P,
+                   const void *d_Q, const uint32_t *d_src, const uint32_t *d_dst,
+                   uint32_t M, void *d_Z, void *d_Eout, void *stream);
+
 /* ---- the network -------------------------------------------------------
  * Nodes: the particles of an SPH context (sph.h) in its current sorted order,
  * with cells built.  Edges: every ordered pair within 2h (the FP64 predicate

@@ -54,4 +54,30 @@ int sur_wgrad(const void* P, const void* Q, uint32_t M, uint32_t N, float scale,
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }
 
+int sur_edge_layer(const void* E, const void* W1t, const void* W2t, const float* b1,
+                   const float* b2, const void* P, const void* Q, const uint32_t* src,
+                   const uint32_t* dst, uint32_t M, void* Z, void* Eout, void* stream) {
+    if (!E || !W1t || !W2t || !b1 || !b2 || !P || !Q || !src || !dst || !Eout)
+        return SPH_ERR_INVALID_ARG;
+    const void* ptrs[] = {E, W1t, W2t, P, Q, Eout, b1, b2};
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16u) return SPH_ERR_INVALID_ARG;
+    if (Z && reinterpret_cast<uintptr_t>(Z) % 16u) return SPH_ERR_INVALID_ARG;
+    EdgeArgs g = {};
+    g.E = static_cast<const __nv_bfloat16*>(E);
+    g.W1t = static_cast<const __nv_bfloat16*>(W1t);
+    g.W2t = static_cast<const __nv_bfloat16*>(W2t);
+    g.b1 = b1;
+    g.b2 = b2;
+    g.P = static_cast<const __nv_bfloat16*>(P);
+    g.Q = static_cast<const __nv_bfloat16*>(Q);
+    g.src = src;
+    g.dst = dst;
+    g.M = M;
+    g.Z = static_cast<__nv_bfloat16*>(Z);
+    g.Eout = static_cast<__nv_bfloat16*>(Eout);
+    launch_edge_layer(g, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
 }  // extern "C"

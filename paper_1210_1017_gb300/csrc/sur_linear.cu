@@ -396,12 +396,26 @@ constexpr size_t kEdgeSmem = (size_t)7 * 128 * 128 * 2;   // W1c, W2, z, 2 x e, 
 
 __device__ __forceinline__ void issue_gather(unsigned char* dst, const __nv_bfloat16* table,
                                              const uint32_t* idx, uint32_t row0, uint32_t nrows) {
-    // thread t copies row t of the tile: 16 pieces of 16 bytes
-    const int r = threadIdx.x;
+    // threads t and t + 128 copy row t of the tile: 8 pieces of 16 bytes each
+    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
     const bool ok = row0 + r < nrows;
     const __nv_bfloat16* p = ok ? table + (size_t)idx[row0 + r] * 128 : table;
 #pragma unroll
-    for (int gk = 0; gk < 16; ++gk) cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
+    for (int gk = 8 * h; gk < 8 * h + 8; ++gk)
+        cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
+}
+
+// issue_rows for a 256-thread block
+template <int K>
+__device__ __forceinline__ void issue_rows256(unsigned char* dst, const __nv_bfloat16* src,
+                                              uint32_t row0, uint32_t nrows, uint32_t ld) {
+#pragma unroll
+    for (int c = threadIdx.x; c < 128 * (K / 8); c += 256) {
+        const int r = c & 127, gk = c >> 7;
+        const bool ok = row0 + r < nrows;
+        const __nv_bfloat16* p = ok ? src + (size_t)(row0 + r) * ld + gk * 8 : src;
+        cp_async16(dst + kmajor_offset(r, gk * 8, K), p, ok);
+    }
 }
 
 __device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, float* f) {
@@ -409,7 +423,9 @@ __device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, 
     unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0 + 8, 128)), f + 8);
 }
 
-__global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
+// 256 threads: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (the
+// tile's rows) and split the 128 columns of each epilogue between them.
+__global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
     constexpr int K = 128, N = 128;
     constexpr uint32_t T = 128 * 128 * 2;          // bytes of one 128 x 128 bf16 tile
     extern __shared__ __align__(128) unsigned char s_raw[];
@@ -425,13 +441,13 @@ __global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
     if (w == 0) tmem_alloc(&s_tmem, 256);
     if (tid == 0) mbar_init1(&s_bar);
     const uint32_t ntiles = (g.M + 127) / 128;
-    for (int c = tid; c < N * (K / 8); c += 128) {
+    for (int c = tid; c < N * (K / 8); c += 256) {
         const int r = c % N, gk = c / N;
         cp_async16(sw1 + kmajor_offset(r, gk * 8, K), g.W1t + (size_t)r * K + gk * 8, true);
         cp_async16(sw2 + kmajor_offset(r, gk * 8, K), g.W2t + (size_t)r * K + gk * 8, true);
     }
     if (blockIdx.x < ntiles) {
-        issue_rows<K>(sa0, g.E, blockIdx.x * 128, g.M, K);
+        issue_rows256<K>(sa0, g.E, blockIdx.x * 128, g.M, K);
         issue_gather(sp, g.P, g.src, blockIdx.x * 128, g.M);
         issue_gather(sq, g.Q, g.dst, blockIdx.x * 128, g.M);
     }
@@ -440,7 +456,8 @@ __global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t lane_base = tmem + ((uint32_t)(w * 32) << 16);
+    const int wq = w & 3, half = w >> 2;                 // lane quarter, column half
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
     uint32_t phase = 0, buf = 0;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= 1u) {
@@ -459,9 +476,9 @@ __global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
             tc_commit(&s_bar);
         }
         const uint32_t next = tile + gridDim.x;
-        if (next < ntiles) issue_rows<K>(sa0 + (buf ^ 1u) * T, g.E, next * 128, g.M, K);
+        if (next < ntiles) issue_rows256<K>(sa0 + (buf ^ 1u) * T, g.E, next * 128, g.M, K);
         cp_async_commit();
-        const int r = w * 32 + lane;               // this thread's row of the tile
+        const int r = wq * 32 + lane;              // this thread's row of the tile
         const uint32_t m = tile * 128 + r;
         const bool valid = m < g.M;
         bool got = mbar_wait(&s_bar, phase);
@@ -471,7 +488,7 @@ __global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
         tc_fence_after();
         // epilogue 1: z = relu(acc + b1 + P[src] + Q[dst]) -> shared (MMA 2) and global
 #pragma unroll 2
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
             float v[16], t[16], u[16];
             tmem_ld16(lane_base + c0, v);
             const float4* b4 = reinterpret_cast<const float4*>(g.b1 + c0);
@@ -525,7 +542,7 @@ __global__ void __launch_bounds__(128) k_edge_layer(const EdgeArgs g) {
         tc_fence_after();
         // epilogue 2: e' = e + acc + b2 (e from the staged tile)
 #pragma unroll 2
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
             float v[16], t[16];
             tmem_ld16(lane_base + 128 + c0, v);
             if (!valid) continue;
@@ -640,7 +657,7 @@ void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) {
     const uint32_t tiles = (g.M + 127) / 128;
     uint32_t grid = (uint32_t)num_sms();   // one block per SM (224 KB of shared memory)
     if (grid > tiles) grid = tiles;
-    k_edge_layer<<<grid, 128, smem, st>>>(g);
+    k_edge_layer<<<grid, 256, smem, st>>>(g);
 }
 
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st) {

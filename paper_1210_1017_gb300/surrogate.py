@@ -14,7 +14,8 @@ class SurConfig(C.Structure):
                 ("train", C.c_uint32), ("v_scale", C.c_float), ("a_mean", C.c_float * 3),
                 ("a_std", C.c_float * 3), ("dt_s", C.c_float)]
 
-EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_param_count",
+EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_edge_layer",
+            "sur_param_count",
             "sur_query_bytes", "sur_init", "sur_set_params", "sur_get_params", "sur_get_grads",
             "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_make_sample",
             "sur_num_edges",
@@ -33,6 +34,7 @@ def lib():
         L.sur_wgrad_scratch_bytes.argtypes = [u32]
         L.sur_wgrad_scratch_bytes.restype = u64
         L.sur_wgrad.argtypes = [vp, vp, u32, u32, C.c_float, vp, vp, u64, vp]
+        L.sur_edge_layer.argtypes = [vp] * 9 + [u32, vp, vp, vp]
         PC = C.POINTER(SurConfig)
         f = C.c_float
         L.sur_param_count.argtypes = [PC]
@@ -73,6 +75,12 @@ def sur_wgrad_scratch_bytes(N):
 def sur_wgrad(P, Q, M, N, scale, dW, scratch, scratch_bytes, stream):
     _sph._check(lib().sur_wgrad(_p(P), _p(Q), M, N, scale, _p(dW), _p(scratch), scratch_bytes,
                                 stream), what="sur_wgrad")
+
+
+def sur_edge_layer(E, W1t, W2t, b1, b2, P, Q, src, dst, M, Z, Eout, stream):
+    _sph._check(lib().sur_edge_layer(_p(E), _p(W1t), _p(W2t), _p(b1), _p(b2), _p(P), _p(Q),
+                                     _p(src), _p(dst), M, _p(Z), _p(Eout), stream),
+                what="sur_edge_layer")
 
 
 def _chk(rc, ctx, what):

@@ -19,7 +19,8 @@ def torch():
 
 
 def _bf16(torch, a):
-    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
+    # row-major device memory: the C ABI takes raw pointers
+    return torch.tensor(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).contiguous().cuda()
 
 
 def _np(t):
@@ -88,3 +89,44 @@ def test_wgrad_matches_numpy(torch, N, M):
     U.sur_wgrad(P, Q, M, N, 0.5, dW2, scratch, nb, st.cuda_stream)
     st.synchronize()
     assert torch.equal(dW, dW2)
+
+
+@pytest.mark.parametrize("M", [1, 300, 5000, 70001])
+def test_fused_edge_layer_matches_numpy(torch, M):
+    """z = relu(E W1 + b1 + P[src] + Q[dst]) (bf16), E' = E + z W2 + b2 (bf16),
+    against numpy in float64 on the same bf16 inputs; z within one bf16
+    rounding of the reference, E' within its rounding plus the effect of z's."""
+    rng = np.random.default_rng(M)
+    nodes = max(2, M // 7)
+    E = _bf16(torch, rng.normal(size=(M, 128)))
+    W1 = rng.normal(size=(128, 128)) / 11.3
+    W2 = rng.normal(size=(128, 128)) / 11.3
+    W1t, W2t = _bf16(torch, W1.T), _bf16(torch, W2.T)
+    b1 = torch.tensor(rng.normal(size=128).astype(np.float32)).cuda()
+    b2 = torch.tensor(rng.normal(size=128).astype(np.float32)).cuda()
+    P = _bf16(torch, rng.normal(size=(nodes, 128)))
+    Q = _bf16(torch, rng.normal(size=(nodes, 128)))
+    src = np.sort(rng.integers(0, nodes, M)).astype(np.uint32)
+    dst = rng.integers(0, nodes, M).astype(np.uint32)
+    d_src = torch.tensor(src.view(np.int32)).cuda()
+    d_dst = torch.tensor(dst.view(np.int32)).cuda()
+    Z = torch.empty((M, 128), dtype=torch.bfloat16, device="cuda")
+    Eo = torch.empty((M, 128), dtype=torch.bfloat16, device="cuda")
+    st = torch.cuda.current_stream()
+    U.sur_edge_layer(E, W1t, W2t, b1, b2, P, Q, d_src, d_dst, M, Z, Eo, st.cuda_stream)
+    st.synchronize()
+    e, w1, w2 = _np(E), _np(W1t).T, _np(W2t).T
+    pre = e @ w1 + b1.cpu().numpy() + _np(P)[src] + _np(Q)[dst]
+    z_ref = np.maximum(pre, 0)
+    z = _np(Z)
+    scale1 = np.abs(e) @ np.abs(w1) + np.abs(b1.cpu().numpy()) + np.abs(_np(P)[src]) + np.abs(_np(Q)[dst])
+    assert np.all(np.abs(z - z_ref) <= 2.0 ** -8 * np.abs(z_ref) + 1e-5 * scale1)
+    # the second GEMM on the GPU's own z
+    eo_ref = e + z @ w2 + b2.cpu().numpy()
+    scale2 = np.abs(e) + np.abs(z) @ np.abs(w2) + np.abs(b2.cpu().numpy())
+    assert np.all(np.abs(_np(Eo) - eo_ref) <= 2.0 ** -8 * np.abs(eo_ref) + 1e-5 * scale2)
+    # without Z the update is the same
+    Eo2 = torch.empty_like(Eo)
+    U.sur_edge_layer(E, W1t, W2t, b1, b2, P, Q, d_src, d_dst, M, None, Eo2, st.cuda_stream)
+    st.synchronize()
+    assert torch.equal(Eo, Eo2)
