@@ -14,6 +14,8 @@
 
 #include <stdint.h>
 
+#include "sph.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -131,6 +133,16 @@ int sur_advance(sur_ctx *ctx, struct sph_ctx *sph, float *d_hist);
 int sur_make_sample(sur_ctx *ctx, struct sph_ctx *sph, const double *d_frames,
                     double sigma, uint64_t seed, double *d_pos, float *d_vel,
                     float *d_hist, float *d_target);
+
+/* ncalls surrogate calls (each: cell rebuild if needed, then sur_advance);
+ * after every save_every calls (and the last) the stream is synchronised
+ * and cb(user, call, t) runs, t = call * dt_s, from which the caller may
+ * read the state (sph_download, sph_download_by_id); a non-zero return
+ * stops early (still SPH_OK).  The cells are rebuilt at the end.  cb may
+ * be NULL.  Sync. */
+int sur_rollout(sur_ctx *ctx, struct sph_ctx *sph, float *d_hist,
+                uint32_t ncalls, uint32_t save_every, sph_snapshot_fn cb,
+                void *user);
 
 uint32_t sur_num_edges(const sur_ctx *ctx);
 const char *sur_last_error(const sur_ctx *ctx);

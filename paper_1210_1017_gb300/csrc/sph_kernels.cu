@@ -313,20 +313,27 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
 // the particles' own cell origins (FP32), plus whole-cell offsets.  A unit
 // whose runs do not fit the staging area reads its candidates from global
 // memory instead.  Units of instances that are done are skipped.
-template <int W, int STAGE, int WCAP, int MINB, bool COUNTS>
-__global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
+// SPLIT warps share each group of 32 particles: warp w takes particles
+// (w % W) * 32 + lane of the unit and every SPLIT-th candidate cell of each
+// neighbour row (cells xlo + w / W, xlo + w / W + SPLIT, ...); the parts'
+// sums are added in a fixed order at the end.  More warps per block at the
+// same staging footprint.
+template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT>
+__global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
+    constexpr int NT = W * SPLIT * 32;
     extern __shared__ __align__(128) unsigned char s_raw[];
     float4* s_p = reinterpret_cast<float4*>(s_raw);
     float4* s_v = s_p + STAGE;
     uint4* s_h = reinterpret_cast<uint4*>(s_v + STAGE);            // STAGE / 2 candidate pairs
     uint32_t* s_words = reinterpret_cast<uint32_t*>(s_h + STAGE / 2);
-    uint32_t* s_desc = s_words + W * WCAP * 32;
+    uint32_t* s_desc = s_words + W * SPLIT * WCAP * 32;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_rs[9], s_rb[9], s_len[9], s_base[10];
     __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
     __shared__ int s_ok[9];
     __shared__ int s_mode;
-    __shared__ uint32_t s_ru[W][4];
+    __shared__ uint32_t s_ru[W * SPLIT][4];
+    __shared__ float s_comb[SPLIT > 1 ? W * 32 : 1][8];   // the second part's sums
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) mbar_init(&s_bar, 1);
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                        : 0u;
     }
     __syncthreads();
-    for (int r9 = tid; r9 < 9 * nce; r9 += W * 32) {
+    for (int r9 = tid; r9 < 9 * nce; r9 += NT) {
         const int r = r9 / nce, c = r9 - r * nce;
         s_off[r][c] = s_ok[r] ? __ldg(a.off + s_rb[r] + ulo + c) : 0u;
     }
@@ -387,7 +394,8 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         }
     }
     // own particle, while the copies are in flight
-    const uint32_t i = i0 + tid;
+    const int part = w / W;
+    const uint32_t i = i0 + (uint32_t)((w % W) * 32 + lane);
     const bool valid = i < i1;
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = make_float4(0.f, 0.f, 0.f, 1.f);
     int cx = 0;
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         // shift the staged y, z into the frame of this unit's row
         for (int r = 0; r < 9; ++r) {
             const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
-            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += W * 32) {
+            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += NT) {
                 s_p[k].y += oy;
                 s_p[k].z += oz;
             }
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         // candidates per uint4: (x0, x1), (y0, y1), (z0, z1) as half2
         const float inv_cs = 1.0f / d.csf;
         const uint32_t nst = s_base[9];
-        for (uint32_t k = tid; 2 * k < nst; k += W * 32) {
+        for (uint32_t k = tid; 2 * k < nst; k += NT) {
             const float4 p0 = s_p[2 * k];
             const float4 p1 = 2 * k + 1 < nst ? s_p[2 * k + 1] : p0;
             const __half2 hx = __floats2half2_rn(p0.x * inv_cs, p1.x * inv_cs);
@@ -522,7 +530,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
             for (int r = 0; r < 9; ++r) {
                 if (!s_ok[r]) continue;
                 const uint32_t rs = s_rs[r], sb = s_base[r];
-                for (int xx = xlo; xx <= xhi; ++xx) {
+                for (int xx = xlo + part; xx <= xhi; xx += SPLIT) {
                     const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
                     const int ox = cx - xx;
                     const bool adj = valid && ox >= -1 && ox <= 1;
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
                 const float qy = fmaf((float)(-dy), d.csf, pi.y);
                 const float qz = fmaf((float)(-dz), d.csf, pi.z);
                 const uint32_t code_yz = ((uint32_t)(1 - dy) << 28) | ((uint32_t)(1 - dz) << 30);
-                for (int xx = xlo; xx <= xhi; ++xx) {
+                for (int xx = xlo + part; xx <= xhi; xx += SPLIT) {
                     const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
                     const int ox = cx - xx;
                     const bool adj = valid && ox >= -1 && ox <= 1;
@@ -617,11 +625,35 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         }
     }
 
+    if (SPLIT > 1) {
+        // part 1 hands its sums to part 0 (fixed order: part 0 + part 1)
+        const int slot = (w % W) * 32 + lane;
+        if (part == 1) {
+            s_comb[slot][0] = acc.ax;
+            s_comb[slot][1] = acc.ay;
+            s_comb[slot][2] = acc.az;
+            s_comb[slot][3] = acc.dr;
+            s_comb[slot][4] = acc.mu;
+            s_comb[slot][5] = __uint_as_float(acc.np);
+            s_comb[slot][6] = __uint_as_float(ncand);
+        }
+        __syncthreads();
+        if (part == 0) {
+            acc.ax += s_comb[slot][0];
+            acc.ay += s_comb[slot][1];
+            acc.az += s_comb[slot][2];
+            acc.dr += s_comb[slot][3];
+            acc.mu = fmaxf(acc.mu, s_comb[slot][4]);
+            acc.np += __float_as_uint(s_comb[slot][5]);
+            ncand += __float_as_uint(s_comb[slot][6]);
+        }
+    }
+    const bool owner = part == 0;                   // writes this particle's results
     const float m = d.mass;
     const float4 out =
         make_float4(fmaf(m, acc.ax, d.gx), fmaf(m, acc.ay, d.gy), fmaf(m, acc.az, d.gz), m * acc.dr);
-    const uint32_t npairs = valid ? acc.np - 1u : 0u;   // without the pair (i, i)
-    if (valid) {
+    const uint32_t npairs = (valid && owner) ? acc.np - 1u : 0u;   // without the pair (i, i)
+    if (valid && owner) {
         a.ace[i] = out;
         if (COUNTS) a.nnb[i] = npairs;
     }
@@ -635,18 +667,18 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
         cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
         mm = fmaxf(mm, __shfl_xor_sync(kFull, mm, o));
     }
-    if (lane == 0 && act) {
+    if (lane == 0 && act && owner) {
         atomicMax(d.is.terms + 3 * q + 0, __float_as_uint(am));
         atomicMax(d.is.terms + 3 * q + 1, __float_as_uint(cm));
         atomicMax(d.is.terms + 3 * q + 2, __float_as_uint(mm));
     }
-    t_bad |= (valid && !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) &&
-                         isfinite(out.w)))
+    t_bad |= (valid && owner && !(isfinite(out.x) && isfinite(out.y) && isfinite(out.z) &&
+                                  isfinite(out.w)))
                  ? kStatusNonFinite
                  : 0u;
     t_np += fluid ? npairs : 0u;
     t_nb += fluid ? 0u : npairs;
-    t_nc += ncand;
+    t_nc += owner ? ncand : 0u;
     __syncthreads();   // the next unit overwrites the shared staging
     }
 
@@ -666,7 +698,7 @@ __global__ void __launch_bounds__(W * 32, MINB) k_interact(const Dev d, const In
     __syncthreads();
     if (tid == 0) {
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
-        for (int k = 0; k < W; ++k) {
+        for (int k = 0; k < W * SPLIT; ++k) {
             u.x += s_ru[k][0];
             u.y += s_ru[k][1];
             u.z |= s_ru[k][2];
@@ -1053,7 +1085,8 @@ namespace {
 using KernelPtr = void (*)(const Dev, const InteractArgs);
 
 struct Variant {
-    int warps;
+    int warps;              // warps of particles (the unit is warps x 32 particles)
+    int split;              // warps per group of 32 particles
     KernelPtr plain, counted;
     size_t smem;
     int grid;   // persistent grid on this GPU (set by prepare_interact)
@@ -1061,20 +1094,20 @@ struct Variant {
 
 // (warps, staged candidates, hit-mask words per lane, resident blocks per SM
 // that the shared memory allows -- also the register budget hint)
-#define SPH_VARIANT(Wv, Sv, Cv, Bv)                                                    \
+#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv)                                                \
     Variant {                                                                         \
-        Wv, k_interact<Wv, Sv, Cv, Bv, false>, k_interact<Wv, Sv, Cv, Bv, true>,      \
-            Shape<Wv, Sv, Cv>::smem, 0                                                \
+        Wv, Pv, k_interact<Wv, Sv, Cv, Bv, false, Pv>, k_interact<Wv, Sv, Cv, Bv, true, Pv>, \
+            Shape<Wv * Pv, Sv, Cv>::smem, 0                                           \
     }
 
 Variant g_variants[kNumVariants] = {
-    SPH_VARIANT(4, 2048, 48, 2),   // 128-particle units
-    SPH_VARIANT(4, 1536, 24, 3),   // 128-particle units, three blocks per SM
-    SPH_VARIANT(3, 1280, 24, 3),   // 96-particle units
-    SPH_VARIANT(8, 3072, 40, 1),   // 256-particle units
-    SPH_VARIANT(2, 896, 24, 5),    // 64-particle units, five blocks per SM
-    SPH_VARIANT(3, 1152, 24, 4),   // 96-particle units, four blocks per SM
-    SPH_VARIANT(2, 1024, 24, 4),   // 64-particle units
+    SPH_VARIANT(4, 2048, 48, 2, 1),   // 128-particle units
+    SPH_VARIANT(4, 1536, 24, 3, 1),   // 128-particle units, three blocks per SM
+    SPH_VARIANT(3, 1152, 24, 4, 1),   // 96-particle units, four blocks per SM
+    SPH_VARIANT(4, 2048, 24, 2, 2),   // 128-particle units, two warps per 32 particles
+    SPH_VARIANT(2, 1280, 24, 3, 2),   // 64-particle units, two warps per 32 particles
+    SPH_VARIANT(3, 1536, 24, 2, 2),   // 96-particle units, two warps per 32 particles
+    SPH_VARIANT(8, 3072, 40, 1, 1),   // 256-particle units
 };
 
 }  // namespace
@@ -1092,14 +1125,14 @@ void prepare_interact() {
         cudaFuncSetAttribute(v.plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         cudaFuncSetAttribute(v.counted, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.plain, v.warps * 32, v.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.plain, v.warps * v.split * 32, v.smem);
         v.grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
 }
 
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st) {
     const Variant& v = g_variants[d.variant];
-    (counts ? v.counted : v.plain)<<<v.grid, v.warps * 32, v.smem, st>>>(d, a);
+    (counts ? v.counted : v.plain)<<<v.grid, v.warps * v.split * 32, v.smem, st>>>(d, a);
 }
 
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,

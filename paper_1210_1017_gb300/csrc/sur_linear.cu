@@ -22,11 +22,11 @@ __device__ __forceinline__ constexpr uint32_t tmem_cols() {
 // Issue the asynchronous copies of a (128 x K) bf16 tile (rows past nrows
 // zero-filled) into the canonical K-major layout; consecutive threads take
 // consecutive rows of one 16-byte column piece.
-template <int K>
+template <int K, int THR = 128>
 __device__ __forceinline__ void issue_rows(unsigned char* dst, const __nv_bfloat16* src,
                                            uint32_t row0, uint32_t nrows, uint32_t ld) {
 #pragma unroll
-    for (int c = threadIdx.x; c < 128 * (K / 8); c += 128) {
+    for (int c = threadIdx.x; c < 128 * (K / 8); c += THR) {
         const int r = c & 127, gk = c >> 7;
         const bool ok = row0 + r < nrows;
         const __nv_bfloat16* p = ok ? src + (size_t)(row0 + r) * ld + gk * 8 : src;
@@ -98,8 +98,15 @@ __device__ __forceinline__ void epi_load(EpiOps<NP>& o, const LinearArgs& g, uin
 // Forward-type GEMM with fused epilogue; persistent over 128-row tiles.  The
 // A tile is double-buffered: the copies of the next tile are in flight while
 // the tensor cores multiply the current one and the epilogue drains it.
+// Block size of k_linear: 256 threads (the two warps sharing a TMEM lane
+// quarter split the output columns) when N >= 32, else 128.
+template <int N>
+__host__ __device__ constexpr int linear_threads() { return N >= 32 ? 256 : 128; }
+
 template <int K, int N>
-__global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
+__global__ void __launch_bounds__(linear_threads<N>(), 1) k_linear(const LinearArgs g) {
+    constexpr int THR = linear_threads<N>();
+    constexpr int NCOL = N / (THR / 128);             // output columns per thread
     extern __shared__ __align__(128) unsigned char s_raw[];
     unsigned char* sb = s_raw;                        // N x K (weights)
     unsigned char* sa0 = s_raw + N * K * 2;           // 2 x (128 x K)
@@ -112,11 +119,11 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
     const uint32_t ldr = g.ldr ? g.ldr : (uint32_t)N;
     const uint32_t ntiles = (g.M + 127) / 128;
     // weights and the first tile
-    for (int c = tid; c < N * (K / 8); c += 128) {
+    for (int c = tid; c < N * (K / 8); c += THR) {
         const int r = c % N, gk = c / N;
         cp_async16(sb + kmajor_offset(r, gk * 8, K), g.Bt + (size_t)r * K + gk * 8, true);
     }
-    if (blockIdx.x < ntiles) issue_rows<K>(sa0, g.A, blockIdx.x * 128, g.M, lda);
+    if (blockIdx.x < ntiles) issue_rows<K, THR>(sa0, g.A, blockIdx.x * 128, g.M, lda);
     cp_async_commit();
     tc_fence_before();
     __syncthreads();
@@ -142,19 +149,20 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         // next tile into the other buffer (its last reader, the previous
         // tile's MMA, has completed)
         const uint32_t next = tile + gridDim.x;
-        if (next < ntiles) issue_rows<K>(sa0 + (buf ^ 1u) * (128 * K * 2), g.A, next * 128, g.M, lda);
+        if (next < ntiles) issue_rows<K, THR>(sa0 + (buf ^ 1u) * (128 * K * 2), g.A, next * 128, g.M, lda);
         cp_async_commit();
-        // this thread's row: its epilogue operands load while the MMA runs
-        const uint32_t m = tile * 128 + w * 32 + lane;
+        // this thread's row and columns: its epilogue operands load while the MMA runs
+        const int wq = w & 3, col0 = (w >> 2) * NCOL;
+        const uint32_t m = tile * 128 + wq * 32 + lane;
         const bool valid = m < g.M;
         uint32_t gi = 0, gj = 0;
         if (g.epi == kEpiEdge1 && valid) {
             gi = g.src[m];
             gj = g.dst[m];
         }
-        constexpr int NP = N < 128 ? N : 128;   // columns per epilogue pass
+        constexpr int NP = NCOL < 128 ? NCOL : 128;   // columns per epilogue pass
         EpiOps<NP> op;
-        if (valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, 0);
+        if (valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, col0);
         const bool got = mbar_wait(&s_bar, phase);
         ok = __syncthreads_and(got) != 0;
         if (!ok) {
@@ -164,13 +172,13 @@ __global__ void __launch_bounds__(128) k_linear(const LinearArgs g) {
         phase ^= 1u;
         tc_fence_after();
 #pragma unroll
-        for (int h = 0; h < N / NP; ++h) {
-            if (h > 0 && valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, h * NP);
+        for (int h = 0; h < NCOL / NP; ++h) {
+            if (h > 0 && valid) epi_load<N, NP>(op, g, m, gi, gj, ldr, col0 + h * NP);
 #pragma unroll
             for (int cl = 0; cl < NP; cl += 16) {
-                const int c0 = h * NP + cl;
+                const int c0 = col0 + h * NP + cl;
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + c0, v);
+                tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + c0, v);
                 if (!valid) continue;
                 if (g.bias) {
                     const float4* b4 = reinterpret_cast<const float4*>(g.bias + c0);
@@ -592,7 +600,7 @@ void launch_linear_t(const LinearArgs& g, int sms, cudaStream_t st) {
         cudaFuncGetAttributes(&fa, k_linear<K, N>);
         const int cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
         const int by_smem = (int)((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
-        const int by_regs = fa.numRegs > 0 ? 65536 / (128 * fa.numRegs) : 1;
+        const int by_regs = fa.numRegs > 0 ? 65536 / (linear_threads<N>() * fa.numRegs) : 1;
         per_sm = by_smem < by_regs ? by_smem : by_regs;
         if (per_sm > 512 / cols) per_sm = 512 / cols;
         if (per_sm < 1) per_sm = 1;
@@ -600,7 +608,7 @@ void launch_linear_t(const LinearArgs& g, int sms, cudaStream_t st) {
     const uint32_t tiles = (g.M + 127) / 128;
     uint32_t grid = (uint32_t)(sms * per_sm);
     if (grid > tiles) grid = tiles ? tiles : 1;
-    k_linear<K, N><<<grid, 128, smem, st>>>(g);
+    k_linear<K, N><<<grid, linear_threads<N>(), smem, st>>>(g);
 }
 
 template <int N>

@@ -924,6 +924,30 @@ int sur_make_sample(sur_ctx* c, sph_ctx* s, const double* d_frames, double sigma
     return check(c, "sur_make_sample");
 }
 
+int sur_rollout(sur_ctx* c, sph_ctx* s, float* d_hist, uint32_t ncalls, uint32_t save_every,
+                sph_snapshot_fn cb, void* user) {
+    if (!c || !s || !d_hist) return SPH_ERR_INVALID_ARG;
+    if (!(c->cfg.dt_s > 0.f)) return fail(c, SPH_ERR_INVALID_ARG, "dt_s must be positive");
+    if (save_every == 0) save_every = ncalls ? ncalls : 1;
+    double t = 0.0;
+    for (uint32_t k = 1; k <= ncalls; ++k) {
+        if (!s->cells_valid) {
+            const int rc = sph_build_cells(s);
+            if (rc) return fail(c, rc, "cell rebuild failed");
+        }
+        const int rc = sur_advance(c, s, d_hist);
+        if (rc) return rc;
+        t += (double)c->cfg.dt_s;
+        if (cb && (k % save_every == 0 || k == ncalls)) {
+            if (cudaStreamSynchronize(c->st) != cudaSuccess) return check(c, "sur_rollout");
+            if (cb(user, k, t)) break;
+        }
+    }
+    const int rc = sph_build_cells(s);
+    if (rc) return fail(c, rc, "cell rebuild failed");
+    return check(c, "sur_rollout");
+}
+
 uint32_t sur_num_edges(const sur_ctx* c) { return c ? c->E : 0; }
 
 const char* sur_last_error(const sur_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

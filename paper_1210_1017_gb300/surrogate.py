@@ -17,7 +17,7 @@ class SurConfig(C.Structure):
 EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_edge_layer",
             "sur_param_count",
             "sur_query_bytes", "sur_init", "sur_set_params", "sur_get_params", "sur_get_grads",
-            "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_make_sample",
+            "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_rollout", "sur_make_sample",
             "sur_num_edges",
             "sur_last_error", "sur_destroy"]
 SUR_EPI_NONE, SUR_EPI_RELU, SUR_EPI_RESIDUAL, SUR_EPI_RELU_MASK = 0, 1, 2, 4
@@ -49,6 +49,7 @@ def lib():
         L.sur_adam.argtypes = [vp, f, f, f, f]
         L.sur_advance.argtypes = [vp, vp, vp]
         L.sur_make_sample.argtypes = [vp, vp, vp, C.c_double, u64, vp, vp, vp, vp]
+        L.sur_rollout.argtypes = [vp, vp, vp, u32, u32, _sph.SNAPSHOT_FN, vp]
         L.sur_num_edges.argtypes = [vp]
         L.sur_num_edges.restype = u32
         L.sur_last_error.argtypes = [vp]
@@ -148,6 +149,14 @@ def sur_advance(ctx, sph_ctx, d_hist):
     _chk(lib().sur_advance(ctx, sph_ctx, _p(d_hist)), ctx, "sur_advance")
 
 
+def sur_rollout(ctx, sph_ctx, d_hist, ncalls, save_every=0, cb=None):
+    """cb(call, t) -> truthy to stop; called every save_every calls."""
+    fn = _sph.SNAPSHOT_FN(lambda user, k, t: int(bool(cb(int(k), float(t))))) if cb else \
+        _sph.SNAPSHOT_FN(0)
+    _chk(lib().sur_rollout(ctx, sph_ctx, _p(d_hist), ncalls, save_every, fn, None), ctx,
+         "sur_rollout")
+
+
 def sur_make_sample(ctx, sph_ctx, d_frames, sigma, seed, d_pos, d_vel, d_hist, d_target):
     _chk(lib().sur_make_sample(ctx, sph_ctx, _p(d_frames), sigma, seed, _p(d_pos), _p(d_vel),
                                _p(d_hist), _p(d_target)), ctx, "sur_make_sample")
@@ -227,6 +236,11 @@ class Surrogate:
     def advance(self, hist):
         self._enter()
         sur_advance(self.ctx, self.sim.ctx, hist)
+        self._leave()
+
+    def rollout(self, hist, ncalls, save_every=0, cb=None):
+        self._enter()
+        sur_rollout(self.ctx, self.sim.ctx, hist, ncalls, save_every, cb)
         self._leave()
 
     def make_sample(self, frames, sigma, seed, pos, vel, hist, target):
