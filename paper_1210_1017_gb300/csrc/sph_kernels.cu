@@ -203,16 +203,20 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // then per warp WCAP x 32 hit-mask words and WCAP word descriptors.  The
 // global-memory fallback keeps 32-bit lists of kFallbackCap entries per lane
 // in the staging area.
-constexpr int kFallbackCap = 64;
+constexpr int kFallbackCap = 64;   // at most; fewer when the staging area is small
 
 template <int W, int STAGE, int WCAP>
 struct Shape {
     static constexpr size_t stage_bytes = (size_t)STAGE * 2 * sizeof(float4);
+    static constexpr int fb_cap =
+        stage_bytes / ((size_t)W * 32 * sizeof(uint32_t)) < (size_t)kFallbackCap
+            ? (int)(stage_bytes / ((size_t)W * 32 * sizeof(uint32_t)))
+            : kFallbackCap;
     static constexpr size_t half_bytes = (size_t)STAGE / 2 * sizeof(uint4);
     static constexpr size_t word_bytes = (size_t)W * WCAP * 32 * sizeof(uint32_t);
     static constexpr size_t smem = stage_bytes + half_bytes + word_bytes +
                                    (size_t)W * WCAP * sizeof(uint32_t);
-    static_assert((size_t)W * kFallbackCap * 32 * sizeof(uint32_t) <= stage_bytes,
+    static_assert(fb_cap >= 16 && (size_t)W * fb_cap * 32 * sizeof(uint32_t) <= stage_bytes,
                   "fallback lists must fit in the staging area");
     static_assert(STAGE <= (1 << 16) && STAGE % 2 == 0, "staged index must fit 16 bits");
 };
@@ -321,6 +325,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
 template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     constexpr int NT = W * SPLIT * 32;
+    constexpr int FBCAP = Shape<W * SPLIT, STAGE, WCAP>::fb_cap;   // fallback list slots
     extern __shared__ __align__(128) unsigned char s_raw[];
     float4* s_p = reinterpret_cast<float4*>(s_raw);
     float4* s_v = s_p + STAGE;
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     __shared__ int s_ok[9];
     __shared__ int s_mode;
     __shared__ uint32_t s_ru[W * SPLIT][4];
-    __shared__ float s_comb[SPLIT > 1 ? W * 32 : 1][8];   // the second part's sums
+    __shared__ float s_comb[SPLIT > 1 ? (SPLIT - 1) * W * 32 : 1][8];   // parts 1.. sums
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) mbar_init(&s_bar, 1);
@@ -571,7 +576,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             flush();
         } else {
             // candidates straight from global memory (unit too large to stage)
-            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (kFallbackCap * 32);
+            uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (FBCAP * 32);
             auto flush = [&]() {
                 const uint32_t mx = __reduce_max_sync(kFull, cnt);
                 for (uint32_t t = 0; t < mx; ++t) {
@@ -605,9 +610,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     if (gs == ge) continue;
                     const float qx = fmaf((float)ox, d.csf, pi.x);
                     const uint32_t code = code_yz | ((uint32_t)(ox + 1) << 26);
-                    for (uint32_t c0i = gs; c0i < ge; c0i += kFallbackCap) {
-                        const uint32_t c1 = (ge - c0i) > (uint32_t)kFallbackCap ? c0i + kFallbackCap : ge;
-                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)kFallbackCap) flush();
+                    for (uint32_t c0i = gs; c0i < ge; c0i += FBCAP) {
+                        const uint32_t c1 = (ge - c0i) > (uint32_t)FBCAP ? c0i + FBCAP : ge;
+                        if (__reduce_max_sync(kFull, cnt) + (c1 - c0i) > (uint32_t)FBCAP) flush();
 #pragma unroll 4
                         for (uint32_t j = c0i; j < c1; ++j) {
                             const float4 pj = __ldg(a.posc + j);
@@ -626,26 +631,32 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     }
 
     if (SPLIT > 1) {
-        // part 1 hands its sums to part 0 (fixed order: part 0 + part 1)
+        // parts 1 .. SPLIT-1 hand their sums to part 0, which adds them in
+        // part order (a fixed order: the result does not depend on timing)
         const int slot = (w % W) * 32 + lane;
-        if (part == 1) {
-            s_comb[slot][0] = acc.ax;
-            s_comb[slot][1] = acc.ay;
-            s_comb[slot][2] = acc.az;
-            s_comb[slot][3] = acc.dr;
-            s_comb[slot][4] = acc.mu;
-            s_comb[slot][5] = __uint_as_float(acc.np);
-            s_comb[slot][6] = __uint_as_float(ncand);
+        if (part > 0) {
+            float* c = s_comb[(part - 1) * W * 32 + slot];
+            c[0] = acc.ax;
+            c[1] = acc.ay;
+            c[2] = acc.az;
+            c[3] = acc.dr;
+            c[4] = acc.mu;
+            c[5] = __uint_as_float(acc.np);
+            c[6] = __uint_as_float(ncand);
         }
         __syncthreads();
         if (part == 0) {
-            acc.ax += s_comb[slot][0];
-            acc.ay += s_comb[slot][1];
-            acc.az += s_comb[slot][2];
-            acc.dr += s_comb[slot][3];
-            acc.mu = fmaxf(acc.mu, s_comb[slot][4]);
-            acc.np += __float_as_uint(s_comb[slot][5]);
-            ncand += __float_as_uint(s_comb[slot][6]);
+#pragma unroll
+            for (int pp = 1; pp < SPLIT; ++pp) {
+                const float* c = s_comb[(pp - 1) * W * 32 + slot];
+                acc.ax += c[0];
+                acc.ay += c[1];
+                acc.az += c[2];
+                acc.dr += c[3];
+                acc.mu = fmaxf(acc.mu, c[4]);
+                acc.np += __float_as_uint(c[5]);
+                ncand += __float_as_uint(c[6]);
+            }
         }
     }
     const bool owner = part == 0;                   // writes this particle's results
@@ -1101,13 +1112,13 @@ struct Variant {
     }
 
 Variant g_variants[kNumVariants] = {
-    SPH_VARIANT(4, 2048, 48, 2, 1),   // 128-particle units
-    SPH_VARIANT(4, 1536, 24, 3, 1),   // 128-particle units, three blocks per SM
-    SPH_VARIANT(3, 1152, 24, 4, 1),   // 96-particle units, four blocks per SM
     SPH_VARIANT(4, 2048, 24, 2, 2),   // 128-particle units, two warps per 32 particles
+    SPH_VARIANT(4, 2048, 48, 2, 1),   // 128-particle units
+    SPH_VARIANT(3, 1280, 16, 3, 2),   // 96-particle units, two warps per 32, three blocks per SM
+    SPH_VARIANT(3, 1408, 16, 3, 2),
     SPH_VARIANT(2, 1280, 24, 3, 2),   // 64-particle units, two warps per 32 particles
-    SPH_VARIANT(3, 1536, 24, 2, 2),   // 96-particle units, two warps per 32 particles
-    SPH_VARIANT(8, 3072, 40, 1, 1),   // 256-particle units
+    SPH_VARIANT(4, 1792, 20, 2, 2),
+    SPH_VARIANT(3, 1152, 24, 4, 1),   // 96-particle units, four blocks per SM
 };
 
 }  // namespace
