@@ -425,25 +425,33 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             break;
         }
         phase ^= 1u;
-        // shift the staged y, z into the frame of this unit's row
-        for (int r = 0; r < 9; ++r) {
-            const float oy = (float)(r % 3 - 1) * d.csf, oz = (float)(r / 3 - 1) * d.csf;
-            for (uint32_t k = s_base[r] + tid; k < s_base[r + 1]; k += NT) {
-                s_p[k].y += oy;
-                s_p[k].z += oz;
-            }
-        }
-        __syncthreads();
-        // half-precision copies in cell units (cell = 2h = 1), two
-        // candidates per uint4: (x0, x1), (y0, y1), (z0, z1) as half2
+        // one pass over candidate pairs: shift the staged y, z into the
+        // frame of this unit's row (the run r of a candidate gives the
+        // offsets), then keep half-precision copies in cell units (cell =
+        // 2h = 1), two candidates per uint4: (x0, x1), (y0, y1), (z0, z1)
         const float inv_cs = 1.0f / d.csf;
         const uint32_t nst = s_base[9];
         for (uint32_t k = tid; 2 * k < nst; k += NT) {
-            const float4 p0 = s_p[2 * k];
-            const float4 p1 = 2 * k + 1 < nst ? s_p[2 * k + 1] : p0;
-            const __half2 hx = __floats2half2_rn(p0.x * inv_cs, p1.x * inv_cs);
-            const __half2 hy = __floats2half2_rn(p0.y * inv_cs, p1.y * inv_cs);
-            const __half2 hz = __floats2half2_rn(p0.z * inv_cs, p1.z * inv_cs);
+            float4 pp[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t j = 2 * k + (uint32_t)e;
+                if (j >= nst) {
+                    pp[e] = pp[0];
+                    continue;
+                }
+                int r = 0;
+#pragma unroll
+                for (int q2 = 1; q2 < 9; ++q2) r += s_base[q2] <= j ? 1 : 0;
+                float4 v = s_p[j];
+                v.y += (float)(r % 3 - 1) * d.csf;
+                v.z += (float)(r / 3 - 1) * d.csf;
+                s_p[j] = v;
+                pp[e] = v;
+            }
+            const __half2 hx = __floats2half2_rn(pp[0].x * inv_cs, pp[1].x * inv_cs);
+            const __half2 hy = __floats2half2_rn(pp[0].y * inv_cs, pp[1].y * inv_cs);
+            const __half2 hz = __floats2half2_rn(pp[0].z * inv_cs, pp[1].z * inv_cs);
             s_h[k] = make_uint4(*reinterpret_cast<const uint32_t*>(&hx),
                                 *reinterpret_cast<const uint32_t*>(&hy),
                                 *reinterpret_cast<const uint32_t*>(&hz), 0u);
