@@ -1,0 +1,75 @@
+"""Parity at the full sizes the benchmark runs (1.39M-particle dam break with
+obstacles, 35.4M-particle dam break), in the launch configuration bench.py
+times (the autotuned interaction shape): cell labels, (label, id) order and
+cell offsets bit for bit over all particles, FP64-predicate neighbour counts
+bit for bit over all particles, and density rates and accelerations of
+sampled blocks of particles (which the oracle can evaluate on their own)
+within the 2e-5 scaled bar."""
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import oracle
+from paper_1210_1017_gb300 import cases
+from paper_1210_1017_gb300 import sph as S
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    yield
+
+
+@pytest.mark.parametrize("name", ["dam_break_obstacles_1m", "dam_break_32m"])
+def test_full_size_parity(name):
+    case = cases.c2_dam_break_obstacles() if name == "dam_break_obstacles_1m" else \
+        cases.c3_dam_break_32m()
+    sim = S.Simulation.from_case(case)
+    sim.build_cells()
+    sim.autotune(reps=1)
+    sim.build_cells()
+    keys = sim.read(S.SPH_ARRAY_KEY)
+    off = sim.read(S.SPH_ARRAY_CELL_OFF)
+    st = sim.download()
+    O = oracle.Oracle(case.params())
+    ref = O.build_cells(case.pos, case.ids)
+    assert np.array_equal(st["ids"], ref["sorted_ids"])
+    assert np.array_equal(keys, ref["sorted_key"])
+    assert np.array_equal(off, ref["cell_off"])
+    del ref
+    # FP64-predicate neighbour counts, every particle
+    got = sim.neighbour_counts_fp64()
+    assert np.array_equal(got, O.neighbour_counts(st["pos"]))
+    # rates of sampled blocks of sorted particles (bulk, near the floor,
+    # near the free surface), the interaction launched as bench.py does
+    sim.interact(counts=True)
+    ace = sim.read(S.SPH_ARRAY_ACE)
+    ost = oracle.State(st["pos"], st["vel"], st["rho"], st["ids"])
+    fluid = st["ids"] >= case.n_bound
+    n = case.n
+    worst = 0.0
+    for frac in (0.1, 0.5, 0.9):
+        i0 = int(frac * n)
+        i1 = min(n, i0 + 3000)
+        r = O.interact(ost, i0=i0, i1=i1)
+        sl = slice(i0, i1)
+        f = fluid[sl]
+        ea = np.linalg.norm(ace[sl][f, :3] - r["a"][sl][f], axis=1) / np.maximum(r["sa"][sl][f], 1e-300)
+        sd = r["sd"][sl]
+        ed = np.abs(ace[sl][:, 3] - r["drho"][sl]) / np.where(sd > 0, sd, 1.0)
+        if f.any():
+            worst = max(worst, float(ea.max()))
+        worst = max(worst, float(ed.max()))
+        # boundary particles carry gravity only
+        assert np.array_equal(ace[sl][~f, :3], np.tile(np.float32(case.gravity), ((~f).sum(), 1)))
+    print(f"{name}: max scaled error over sampled blocks {worst:.2e}")
+    assert worst <= REL_TOL
+    sim.check()
+    sim.close()
