@@ -55,13 +55,13 @@ def _run(case, steps=0):
 
 def test_single_particle_falls_freely():
     case = _case([[0.5, 0.5, 2.0]], 0, 0.02, 0.026, below=2.0)
-    r = _run(case, steps=20)
+    r = _run(case, steps=200)
     assert r["nnb"][0] == 0 and r["nnb64"][0] == 0
     assert np.array_equal(r["ace"][0], np.float32([0.0, 0.0, -9.81, 0.0]))
     # symplectic midpoint under constant gravity: z = z0 - g t^2 / 2, up to
     # the FP32 rounding of the velocity (FP64 positions)
     t = r["diag"]["t"]
-    assert r["diag"]["n_out"] == 0 and t > 0.05
+    assert r["diag"]["n_out"] == 0 and t > 0.04
     z = r["after"]["pos"][0, 2]
     assert abs(z - (2.0 - 0.5 * 9.81 * t * t)) < 1e-6
     assert r["after"]["pos"][0, 0] == 0.5 and r["after"]["pos"][0, 1] == 0.5
