@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     uint32_t* s_words = reinterpret_cast<uint32_t*>(s_h + STAGE / 2);
     uint32_t* s_desc = s_words + W * SPLIT * WCAP * 32;
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ uint32_t s_rs[9], s_rb[9], s_len[9], s_base[10];
+    __shared__ uint32_t s_rs[9], s_len[9], s_base[10];
     __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
     __shared__ int s_ok[9];
     __shared__ int s_mode;
@@ -364,37 +364,52 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     const int ulo = xb > 0 ? xb - 1 : 0;
     const int uhi = xe + 1 < ncx ? xe + 1 : ncx - 1;
     const int nce = uhi - ulo + 2;                 // offsets per neighbour row
-    if (tid < 9) {
-        const int yy = cy + tid % 3 - 1, zz = cz + tid / 3 - 1;
-        const bool ok = yy >= 0 && yy < ncy && zz >= 0 && zz < ncz;
-        s_ok[tid] = ok;
-        s_rb[tid] = ok ? I.cell_base + (uint32_t)ncx * ((uint32_t)yy + (uint32_t)ncy * (uint32_t)zz)
-                       : 0u;
-    }
-    __syncthreads();
+    // cell offsets of the 9 neighbour rows (each thread derives its row's
+    // base label itself: no barrier before the loads)
     for (int r9 = tid; r9 < 9 * nce; r9 += NT) {
         const int r = r9 / nce, c = r9 - r * nce;
-        s_off[r][c] = s_ok[r] ? __ldg(a.off + s_rb[r] + ulo + c) : 0u;
+        const int yy = cy + r % 3 - 1, zz = cz + r / 3 - 1;
+        const bool ok = yy >= 0 && yy < ncy && zz >= 0 && zz < ncz;
+        const uint32_t rb =
+            I.cell_base + (uint32_t)ncx * ((uint32_t)yy + (uint32_t)ncy * (uint32_t)zz);
+        s_off[r][c] = ok ? __ldg(a.off + rb + ulo + c) : 0u;
+        if (c == 0) s_ok[r] = ok;
     }
     __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (int r = 0; r < 9; ++r) {
-            s_base[r] = acc;
-            s_rs[r] = s_off[r][0];
-            s_len[r] = s_off[r][nce - 1] - s_off[r][0];
-            acc += s_len[r];
+    // staging plan and copies by the first warp: lane r < 9 owns run r
+    if (w == 0) {
+        const uint32_t len = lane < 9 ? s_off[lane][nce - 1] - s_off[lane][0] : 0u;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
         }
-        s_base[9] = acc;
-        const int mode = acc <= (uint32_t)STAGE;
-        s_mode = mode;
-        if (mode) {
-            mbar_expect_tx(&s_bar, acc * 2u * (uint32_t)sizeof(float4));
-            for (int r = 0; r < 9; ++r) {
-                if (s_len[r] == 0) continue;
-                const uint32_t bytes = s_len[r] * (uint32_t)sizeof(float4);
-                bulk_g2s(s_p + s_base[r], a.posc + s_rs[r], bytes, &s_bar);
-                bulk_g2s(s_v + s_base[r], a.velrhop + s_rs[r], bytes, &s_bar);
+        const uint32_t base = incl - len;
+        const uint32_t total = __shfl_sync(kFull, incl, 8);
+        if (lane < 9) {
+            s_base[lane] = base;
+            s_rs[lane] = s_off[lane][0];
+            s_len[lane] = len;
+        }
+        if (lane == 0) {
+            s_base[9] = total;
+            s_mode = total <= (uint32_t)STAGE;
+            if (total <= (uint32_t)STAGE)
+                mbar_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4));
+        }
+        __syncwarp();
+        // the expected byte count is registered before any copy is issued
+        if (total <= (uint32_t)STAGE && lane < 18) {
+            const int r = lane >> 1;
+            const uint32_t rl = __shfl_sync(0x3ffffu, len, r);
+            const uint32_t rbase = __shfl_sync(0x3ffffu, base, r);
+            const uint32_t rs = s_off[r][0];
+            if (rl) {
+                if (lane & 1)
+                    bulk_g2s(s_v + rbase, a.velrhop + rs, rl * (uint32_t)sizeof(float4), &s_bar);
+                else
+                    bulk_g2s(s_p + rbase, a.posc + rs, rl * (uint32_t)sizeof(float4), &s_bar);
             }
         }
     }
