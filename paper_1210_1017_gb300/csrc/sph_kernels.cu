@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
         if (staged) {
             // candidate test in half precision, two candidates per
             // instruction, against a conservative threshold (cell units:
-            // |r_ij|^2 < 1 + 2^-6); each lane keeps one 32-bit hit mask per
+            // |r_ij|^2 - (1 + 2^-6) < 0); each lane keeps one 32-bit hit mask per
             // word of 32 staged candidates (bit p: candidate base + 2p, bit
             // 16 + p: candidate base + 2p + 1).  The pair phase applies the
             // exact FP32 test.
@@ -493,7 +493,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
             const bool anyfluid = __any_sync(kFull, fluid);
             const float inv_cs = 1.0f / d.csf;
-            const __half2 thr = __float2half2_rn(1.0f + 1.0f / 64.0f);
+            // minus the threshold, folded into the first fused multiply-add;
+            // a set sign bit of r^2 - thr marks a candidate
+            const __half2 nthr = __float2half2_rn(-(1.0f + 1.0f / 64.0f));
             const __half2 hqy = __float2half2_rn(pi.y * inv_cs);
             const __half2 hqz = __float2half2_rn(pi.z * inv_cs);
             uint32_t nw = 0, lane_hits = 0;
@@ -503,11 +505,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 __syncwarp();   // the words and lane 0's descriptors are written
                 const uint32_t mx = __reduce_max_sync(kFull, lane_hits);
                 uint32_t wi = 0, cm = 0, jb = 0;
-                float oxf = 0.f;
+                float qxw = 0.f;                         // i's x in the word's cell frame
                 constexpr int kPop = 2;   // pairs per iteration (independent chains)
                 for (uint32_t t = 0; t < mx; t += kPop) {
                     uint32_t j2[kPop];
-                    float ox2[kPop];
+                    float qx2[kPop];
                     bool re[kPop];
 #pragma unroll
                     for (int k = 0; k < kPop; ++k) {
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             cm = wl[wi * 32];
                             const uint32_t dsc = wd[wi];
                             jb = dsc & 0xffffu;
-                            oxf = (float)(cx - (ulo + (int)(dsc >> 16)));
+                            qxw = fmaf((float)(cx - (ulo + (int)(dsc >> 16))), d.csf, pi.x);
                             ++wi;
                         }
                         re[k] = cm != 0;
@@ -523,10 +525,10 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             const uint32_t b = 31u - __clz(cm);
                             cm ^= 1u << b;
                             j2[k] = jb + ((b & 15u) << 1) + (b >> 4);
-                            ox2[k] = oxf;
+                            qx2[k] = qxw;
                         } else {
                             j2[k] = self;
-                            ox2[k] = 0.f;
+                            qx2[k] = pi.x;
                         }
                     }
                     float4 pp[kPop], vv[kPop];
@@ -538,15 +540,13 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     if (anyfluid) {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<true, true>(d, c0, fluid, pi, vi, ci,
-                                                   fmaf(ox2[k], d.csf, pi.x) - pp[k].x,
+                            pair_terms<true, true>(d, c0, fluid, pi, vi, ci, qx2[k] - pp[k].x,
                                                    pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
                                                    re[k]);
                     } else {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<false, true>(d, c0, fluid, pi, vi, ci,
-                                                    fmaf(ox2[k], d.csf, pi.x) - pp[k].x,
+                            pair_terms<false, true>(d, c0, fluid, pi, vi, ci, qx2[k] - pp[k].x,
                                                     pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
                                                     re[k]);
                     }
@@ -578,8 +578,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             const __half2 dx = __hsub2(hqx, *reinterpret_cast<const __half2*>(&hv.x));
                             const __half2 dy = __hsub2(hqy, *reinterpret_cast<const __half2*>(&hv.y));
                             const __half2 dz = __hsub2(hqz, *reinterpret_cast<const __half2*>(&hv.z));
-                            const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
-                            m |= (__hlt2_mask(r2, thr) & 0x00010001u) << q2;
+                            const __half2 r2t = __hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, nthr)));
+                            const uint32_t sg = *reinterpret_cast<const uint32_t*>(&r2t);
+                            m |= (sg >> (15 - q2)) & (0x00010001u << q2);
                         }
                         // slots outside [s0, e0) and lanes not adjacent to the cell
                         const uint32_t ev = lim >= 32u ? 0xffffu : ((1u << ((lim + 1) >> 1)) - 1u);

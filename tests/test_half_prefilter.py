@@ -2,8 +2,9 @@
 FP32 neighbour test accepts.
 
 The kernel first tests candidates two at a time in half precision on
-positions scaled to cell units (cell size 2h = 1), against the threshold
-1 + 2^-6, then applies the exact FP32 test |r_ij|^2 < (2h)^2 to the survivors.
+positions scaled to cell units (cell size 2h = 1): the sign of
+|r_ij|^2 - (1 + 2^-6), accumulated by fused multiply-adds; then it applies the
+exact FP32 test |r_ij|^2 < (2h)^2 to the survivors.
 This emulates the half-precision arithmetic with numpy (every operation
 rounded once to the nearest float16; the fused multiply-adds exactly in
 float64, then rounded once) on pairs placed near the support radius, and
@@ -21,11 +22,14 @@ def hfma(a, b, c):
     return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float16)
 
 
-def half_d2(q, p):
+def half_hit(q, p):
+    """The kernel's test: the sign of dx dx + (dy dy + (dz dz - THR)), each
+    fused multiply-add rounded once to float16 (negative or -0: candidate)."""
     dx = (q[:, 0] - p[:, 0]).astype(np.float16)
     dy = (q[:, 1] - p[:, 1]).astype(np.float16)
     dz = (q[:, 2] - p[:, 2]).astype(np.float16)
-    return hfma(dx, dx, hfma(dy, dy, (dz * dz).astype(np.float16)))
+    v = hfma(dx, dx, hfma(dy, dy, hfma(dz, dz, np.full_like(dz, -THR))))
+    return np.signbit(v)
 
 
 def fp32_d2(q, p):
@@ -52,9 +56,9 @@ def test_half_prefilter_keeps_every_fp32_neighbour():
     assert inside.sum() > 0.9 * n
     hq, hp = h(q * inv), h(p * inv)
     assert np.all(np.abs(hq.astype(np.float64)) <= 3) and np.all(np.isfinite(hp.astype(np.float64)))
-    keep = half_d2(hq, hp) < THR
+    keep = half_hit(hq, hp)
     assert np.all(keep[inside]), int((~keep[inside]).sum())
     # and it rejects most pairs well outside the support
     p2 = (q - u * (cs * rng.uniform(1.05, 2.0, n))[:, None]).astype(np.float32)
-    far = half_d2(h(q * inv), h(p2 * inv)) < THR
+    far = half_hit(h(q * inv), h(p2 * inv))
     assert far.mean() < 1e-3
