@@ -48,10 +48,16 @@ __device__ __forceinline__ uint32_t cell_key(const Dev& d, const Inst& I, double
     const double tx = __dmul_rn(__dsub_rn(x, I.x0), d.inv_cs);
     const double ty = __dmul_rn(__dsub_rn(y, I.y0), d.inv_cs);
     const double tz = __dmul_rn(__dsub_rn(z, I.z0), d.inv_cs);
-    const bool in = (tx >= 0.0) && (tx < (double)I.ncx) && (ty >= 0.0) &&
-                    (ty < (double)I.ncy) && (tz >= 0.0) && (tz < (double)I.ncz);
-    if (!in) return d.ncells;
+    // t in [0, nc) <=> floor(t) in [0, nc) for finite t (the conversion
+    // saturates far outside); infinities and NaNs (exponent all ones) are
+    // out.  The range test thus runs on integers, not on the FP64 pipe.
+    const bool finite = ((uint32_t)__double2hiint(tx) & 0x7ff00000u) != 0x7ff00000u &&
+                        ((uint32_t)__double2hiint(ty) & 0x7ff00000u) != 0x7ff00000u &&
+                        ((uint32_t)__double2hiint(tz) & 0x7ff00000u) != 0x7ff00000u;
     const int cx = __double2int_rd(tx), cy = __double2int_rd(ty), cz = __double2int_rd(tz);
+    const bool in = finite && cx >= 0 && cx < I.ncx && cy >= 0 && cy < I.ncy && cz >= 0 &&
+                    cz < I.ncz;
+    if (!in) return d.ncells;
     return I.cell_base + (uint32_t)cx +
            (uint32_t)I.ncx * ((uint32_t)cy + (uint32_t)I.ncy * (uint32_t)cz);
 }
