@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(linear_threads<N>(), 1) k_linear(const LinearA
     constexpr int THR = linear_threads<N>();
     constexpr int NCOL = N / (THR / 128);             // output columns per thread
     extern __shared__ __align__(128) unsigned char s_raw[];
+    __shared__ __align__(16) float s_bias[N];          // read by every row: staged once
     unsigned char* sb = s_raw;                        // N x K (weights)
     unsigned char* sa0 = s_raw + N * K * 2;           // 2 x (128 x K)
     __shared__ __align__(8) uint64_t s_bar;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(linear_threads<N>(), 1) k_linear(const LinearA
         const int r = c % N, gk = c / N;
         cp_async16(sb + kmajor_offset(r, gk * 8, K), g.Bt + (size_t)r * K + gk * 8, true);
     }
+    for (int c = tid; c < N; c += THR) s_bias[c] = g.bias ? g.bias[c] : 0.f;
     if (blockIdx.x < ntiles) issue_rows<K, THR>(sa0, g.A, blockIdx.x * 128, g.M, lda);
     cp_async_commit();
     tc_fence_before();
@@ -181,10 +183,10 @@ __global__ void __launch_bounds__(linear_threads<N>(), 1) k_linear(const LinearA
                 tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + c0, v);
                 if (!valid) continue;
                 if (g.bias) {
-                    const float4* b4 = reinterpret_cast<const float4*>(g.bias + c0);
+                    const float4* b4 = reinterpret_cast<const float4*>(s_bias + c0);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 b = __ldg(b4 + q);
+                        const float4 b = b4[q];
                         v[4 * q] += b.x;
                         v[4 * q + 1] += b.y;
                         v[4 * q + 2] += b.z;
@@ -443,6 +445,7 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
     unsigned char* sp = sz + T;                    // P[src] rows
     unsigned char* sq = sp + T;                    // Q[dst] rows
     unsigned char* sa0 = sq + T;                   // 2 x e tile
+    __shared__ __align__(16) float s_b1[128], s_b2[128];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -453,6 +456,10 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
         const int r = c % N, gk = c / N;
         cp_async16(sw1 + kmajor_offset(r, gk * 8, K), g.W1t + (size_t)r * K + gk * 8, true);
         cp_async16(sw2 + kmajor_offset(r, gk * 8, K), g.W2t + (size_t)r * K + gk * 8, true);
+    }
+    if (tid < 128) {
+        s_b1[tid] = g.b1[tid];
+        s_b2[tid] = g.b2[tid];
     }
     if (blockIdx.x < ntiles) {
         issue_rows256<K>(sa0, g.E, blockIdx.x * 128, g.M, K);
@@ -499,10 +506,10 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
         for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
             float v[16], t[16], u[16];
             tmem_ld16(lane_base + c0, v);
-            const float4* b4 = reinterpret_cast<const float4*>(g.b1 + c0);
+            const float4* b4 = reinterpret_cast<const float4*>(s_b1 + c0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 b = __ldg(b4 + q);
+                const float4 b = b4[q];
                 v[4 * q] += b.x;
                 v[4 * q + 1] += b.y;
                 v[4 * q + 2] += b.z;
@@ -554,10 +561,10 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
             float v[16], t[16];
             tmem_ld16(lane_base + 128 + c0, v);
             if (!valid) continue;
-            const float4* b4 = reinterpret_cast<const float4*>(g.b2 + c0);
+            const float4* b4 = reinterpret_cast<const float4*>(s_b2 + c0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 b = __ldg(b4 + q);
+                const float4 b = b4[q];
                 v[4 * q] += b.x;
                 v[4 * q + 1] += b.y;
                 v[4 * q + 2] += b.z;
