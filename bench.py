@@ -125,6 +125,19 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(ms, count, dist=None, device="cpu"):
+    """Whole-job figures of a replicated run: the slowest rank's timed
+    milliseconds and the work summed over ranks (single process: as given)."""
+    if dist is None:
+        return float(ms), int(count)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(count)], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), int(c.item())
+
+
 def cpu_baseline(case, max_seconds=25.0):
     """The FP64 oracle as it stands, on this host's cores: one interaction
     evaluation (its own grid over all particles + the pair sums) for a
@@ -263,15 +276,7 @@ def run_ours(args):
     pf = d1["pairs_fluid_total"] - d0["pairs_fluid_total"]
     pb = d1["pairs_boundary_total"] - d0["pairs_boundary_total"]
     cand = d1["candidates_total"] - d0["candidates_total"]
-    t_max = ms
-    pairs_all = pairs
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        p = torch.tensor([pairs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p)
-        pairs_all = int(p.item())
+    t_max, pairs_all = reduce_over_ranks(ms, pairs, dist, device="cuda")
     value = pairs_all / (t_max * 1e-3)
     steps_per_s = args.steps / (t_max * 1e-3)
 
