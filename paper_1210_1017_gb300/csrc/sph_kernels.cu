@@ -505,12 +505,14 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             const __half2 hqy = __float2half2_rn(pi.y * inv_cs);
             const __half2 hqz = __float2half2_rn(pi.z * inv_cs);
             uint32_t nw = 0, lane_hits = 0;
+            uint32_t lane_nz = 0;   // bit w: stored word w holds hits of this lane
+            static_assert(WCAP <= 32, "one bit per stored word");
             // pair phase over the stored words: each lane pops its own hits,
             // two per iteration; lanes that run out use the pair (i, i)
             auto flush = [&]() {
                 __syncwarp();   // the words and lane 0's descriptors are written
                 const uint32_t mx = __reduce_max_sync(kFull, lane_hits);
-                uint32_t wi = 0, cm = 0, jb = 0;
+                uint32_t nz = lane_nz, cm = 0, jb = 0;
                 float qxw = 0.f;                         // i's x in the word's cell frame
                 constexpr int kPop = 2;   // pairs per iteration (independent chains)
                 for (uint32_t t = 0; t < mx; t += kPop) {
@@ -519,12 +521,14 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     bool re[kPop];
 #pragma unroll
                     for (int k = 0; k < kPop; ++k) {
-                        while (cm == 0 && wi < nw) {
+                        // at most one step: the lane visits only its non-empty words
+                        if (cm == 0 && nz != 0) {
+                            const uint32_t wi = __ffs(nz) - 1;
+                            nz &= nz - 1;
                             cm = wl[wi * 32];
                             const uint32_t dsc = wd[wi];
                             jb = dsc & 0xffffu;
                             qxw = fmaf((float)(cx - (ulo + (int)(dsc >> 16))), d.csf, pi.x);
-                            ++wi;
                         }
                         re[k] = cm != 0;
                         if (cm) {
@@ -560,6 +564,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 __syncwarp();   // every lane is done reading before the words are reused
                 nw = 0;
                 lane_hits = 0;
+                lane_nz = 0;
             };
             for (int r = 0; r < 9; ++r) {
                 if (!s_ok[r]) continue;
@@ -598,6 +603,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             wl[nw * 32] = m;
                             if (lane == 0) wd[nw] = base | ((uint32_t)(xx - ulo) << 16);
                             lane_hits += __popc(m);
+                            lane_nz |= (m != 0u ? 1u : 0u) << nw;
                             ++nw;
                         }
                     }
@@ -1143,7 +1149,7 @@ struct Variant {
 
 Variant g_variants[kNumVariants] = {
     SPH_VARIANT(4, 2048, 24, 2, 2),   // 128-particle units, two warps per 32 particles
-    SPH_VARIANT(4, 2048, 48, 2, 1),   // 128-particle units
+    SPH_VARIANT(4, 2048, 32, 2, 1),   // 128-particle units
     SPH_VARIANT(3, 1280, 16, 3, 2),   // 96-particle units, two warps per 32, three blocks per SM
     SPH_VARIANT(3, 1408, 16, 3, 2),
     SPH_VARIANT(2, 1280, 24, 3, 2),   // 64-particle units, two warps per 32 particles
