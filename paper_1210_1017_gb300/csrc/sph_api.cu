@@ -217,7 +217,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->ucnt = cv.take<uint32_t>(t.nrows + 1);
     c->uoff = cv.take<uint32_t>(t.nrows + 2);
     c->ubsum = cv.take<uint32_t>(scan_bsum_count(t.nrows + 1));
-    c->units = cv.take<uint2>(max_units(n, (uint32_t)t.nrows, (uint32_t)t.max_ncx));
+    c->units = cv.take<uint2>(max_units(n, (uint32_t)t.nrows, t.ncells));
     c->part_u = cv.take<uint4>(kMaxGridBlocks);
     c->lvl2_q = cv.take<unsigned long long>(4 * kReduceBlocks);
     c->done = cv.take<uint32_t>(1);
@@ -270,6 +270,7 @@ Dev make_dev(const sph_ctx* c) {
     d.max_ncx = c->tab.max_ncx;
     d.variant = c->variant;
     d.unit = variant_unit(c->variant);
+    d.stage = variant_stage(c->variant);
     d.csf = (float)cs;
     d.h = (float)p->h;
     d.inv_h = (float)(1.0 / p->h);

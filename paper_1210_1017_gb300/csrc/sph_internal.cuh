@@ -66,6 +66,7 @@ struct Dev {
     int max_ncx;
     int variant;           // interaction variant (block shape) in use
     int unit;              // its unit size in particles
+    int stage;             // its staging capacity in candidates
     float csf;             // 2h
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
@@ -138,8 +139,9 @@ struct InteractArgs {
     uint4* part_u;        // per block (persistent grid): fluid-i pairs, candidates,
                           // status bits, boundary-i pairs
 };
-uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx);   // bound on units
+uint32_t max_units(uint32_t n, uint32_t nrows, uint64_t ncells);   // bound on units
 int variant_unit(int variant);               // particles per unit of a variant
+int variant_stage(int variant);              // staged candidates of a variant
 uint32_t interact_grid(int variant);         // blocks of its persistent launch
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
                   uint32_t* uoff, uint2* units, cudaStream_t st);

@@ -771,7 +771,27 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
     if (r >= d.nrows) return;
     const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
     const int ncx = I.ncx;
-    const uint32_t* o = off + I.cell_base + (size_t)(r - I.row_base) * (uint32_t)ncx;
+    const uint32_t lr = r - I.row_base;
+    const int cy = (int)(lr % (uint32_t)I.ncy), cz = (int)(lr / (uint32_t)I.ncy);
+    const uint32_t* o = off + I.cell_base + (size_t)lr * (uint32_t)ncx;
+    // the 9 neighbour rows (null outside the instance): a unit's staged
+    // candidates are their particles in cells [first - 1, last + 1]
+    const uint32_t* nb[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int yy = cy + k % 3 - 1, zz = cz + k / 3 - 1;
+        nb[k] = (yy >= 0 && yy < I.ncy && zz >= 0 && zz < I.ncz)
+                    ? off + I.cell_base + ((size_t)zz * (uint32_t)I.ncy + (uint32_t)yy) * (uint32_t)ncx
+                    : nullptr;
+    }
+    auto staged = [&](int xf, int xl) {
+        const int a0 = xf > 0 ? xf - 1 : 0, a1 = xl + 2 < ncx ? xl + 2 : ncx;
+        uint32_t t = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (nb[k]) t += nb[k][a1] - nb[k][a0];
+        return t;
+    };
     uint32_t n = 0, out = MODE ? uoff[r] : 0u;
     uint32_t start = 0xffffffffu;
     int lo = 0, last = 0;
@@ -779,7 +799,10 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
     for (int x = 0; x < ncx; ++x) {
         const uint32_t b = o[x + 1];
         if (a != b) {
-            if (start != 0xffffffffu && (x - last > 3 || x - lo >= kSpan)) {
+            // a unit also closes before a cell that would make its staged
+            // candidates exceed the staging area of the variant in use
+            if (start != 0xffffffffu &&
+                (x - last > 3 || x - lo >= kSpan || staged(lo, x) > (uint32_t)d.stage)) {
                 if (MODE) units[out + n] = make_uint2(start, a);
                 ++n;
                 start = 0xffffffffu;
@@ -1120,11 +1143,12 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
 }
 
 // Upper bound on the number of units: every unit but the last of its row
-// either holds the unit size (at least kMinUnit) or ends at a gap or at kSpan
-// cells; a row of ncx cells has at most ncx / 4 + 1 gap-separated stretches,
-// each cut at most ncx / kSpan + 1 more times.
-uint32_t max_units(uint32_t n, uint32_t nrows, uint32_t max_ncx) {
-    return (n + kMinUnit - 1) / kMinUnit + nrows * (max_ncx / 4 + max_ncx / kSpan + 2);
+// either holds the unit size (at least kMinUnit particles) or closes before a
+// non-empty cell (a gap, the span limit or the staging limit), and a row has
+// no more such closures than non-empty cells (at most min(n, ncells) in all).
+uint32_t max_units(uint32_t n, uint32_t nrows, uint64_t ncells) {
+    const uint64_t cells = ncells < n ? ncells : n;
+    return (uint32_t)((n + kMinUnit - 1) / kMinUnit + cells + nrows);
 }
 
 namespace {
@@ -1134,6 +1158,7 @@ using KernelPtr = void (*)(const Dev, const InteractArgs);
 struct Variant {
     int warps;              // warps of particles (the unit is warps x 32 particles)
     int split;              // warps per group of 32 particles
+    int stage;              // staged candidates
     KernelPtr plain, counted;
     size_t smem;
     int grid;   // persistent grid on this GPU (set by prepare_interact)
@@ -1143,7 +1168,7 @@ struct Variant {
 // that the shared memory allows -- also the register budget hint)
 #define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv)                                                \
     Variant {                                                                         \
-        Wv, Pv, k_interact<Wv, Sv, Cv, Bv, false, Pv>, k_interact<Wv, Sv, Cv, Bv, true, Pv>, \
+        Wv, Pv, Sv, k_interact<Wv, Sv, Cv, Bv, false, Pv>, k_interact<Wv, Sv, Cv, Bv, true, Pv>, \
             Shape<Wv * Pv, Sv, Cv>::smem, 0                                           \
     }
 
@@ -1160,6 +1185,8 @@ Variant g_variants[kNumVariants] = {
 }  // namespace
 
 int variant_unit(int v) { return g_variants[v].warps * 32; }
+
+int variant_stage(int v) { return g_variants[v].stage; }
 
 // Persistent grid: every resident block of the variant on this GPU.
 uint32_t interact_grid(int v) { return (uint32_t)g_variants[v].grid; }
