@@ -784,13 +784,22 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
                     ? off + I.cell_base + ((size_t)zz * (uint32_t)I.ncy + (uint32_t)yy) * (uint32_t)ncx
                     : nullptr;
     }
-    auto staged = [&](int xf, int xl) {
-        const int a0 = xf > 0 ? xf - 1 : 0, a1 = xl + 2 < ncx ? xl + 2 : ncx;
+    // the unit's lower run bounds are fixed while it grows: kept in base
+    uint32_t base = 0;
+    auto set_base = [&](int xf) {
+        const int a0 = xf > 0 ? xf - 1 : 0;
+        base = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (nb[k]) base += __ldg(nb[k] + a0);
+    };
+    auto staged = [&](int xl) {
+        const int a1 = xl + 2 < ncx ? xl + 2 : ncx;
         uint32_t t = 0;
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-            if (nb[k]) t += nb[k][a1] - nb[k][a0];
-        return t;
+            if (nb[k]) t += __ldg(nb[k] + a1);
+        return t - base;
     };
     uint32_t n = 0, out = MODE ? uoff[r] : 0u;
     uint32_t start = 0xffffffffu;
@@ -801,8 +810,15 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
         if (a != b) {
             // a unit also closes before a cell that would make its staged
             // candidates exceed the staging area of the variant in use
-            if (start != 0xffffffffu &&
-                (x - last > 3 || x - lo >= kSpan || staged(lo, x) > (uint32_t)d.stage)) {
+            // the exact 9-row count is only needed near the capacity: the own
+            // row's share times 9 at half the capacity gates it (a missed cut
+            // only sends a unit down the slower global-memory path)
+            bool full = false;
+            if (start != 0xffffffffu) {
+                const uint32_t own = o[x + 2 < ncx ? x + 2 : ncx] - o[lo > 0 ? lo - 1 : 0];
+                full = 18u * own > (uint32_t)d.stage && staged(x) > (uint32_t)d.stage;
+            }
+            if (start != 0xffffffffu && (x - last > 3 || x - lo >= kSpan || full)) {
                 if (MODE) units[out + n] = make_uint2(start, a);
                 ++n;
                 start = 0xffffffffu;
@@ -810,13 +826,17 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
             if (start == 0xffffffffu) {
                 start = a;
                 lo = x;
+                set_base(lo);
             }
             last = x;
             while (b - start > (uint32_t)d.unit) {
                 if (MODE) units[out + n] = make_uint2(start, start + d.unit);
                 ++n;
                 start += d.unit;
-                lo = x;
+                if (lo != x) {
+                    lo = x;
+                    set_base(lo);
+                }
             }
         }
         a = b;
