@@ -214,6 +214,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->os_bytes = 4 * sizeof(uint32_t) + (size_t)passes * tiles * 256 * sizeof(uint32_t);
     c->tilectr = cv.take<uint32_t>(c->os_bytes / sizeof(uint32_t));
     c->os_status = c->tilectr ? c->tilectr + 4 : nullptr;
+    c->csum = cv.take<uint32_t>(t.ncells + t.nrows + 1);
     c->ucnt = cv.take<uint32_t>(t.nrows + 1);
     c->uoff = cv.take<uint32_t>(t.nrows + 2);
     c->ubsum = cv.take<uint32_t>(scan_bsum_count(t.nrows + 1));
@@ -303,7 +304,7 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
         src = 1 - src;
     }
     c->skey = src;
-    launch_units(c->d, c->off, c->ucnt, c->ubsum, c->uoff, c->units, st);
+    launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, st);
     ReorderArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.skey = c->key[src];
@@ -815,7 +816,7 @@ int sph_set_variant(sph_ctx* c, uint32_t v) {
         c->graph[g] = nullptr;
     }
     // the work units depend on the block shape: recut them for the current cells
-    if (c->cells_valid) launch_units(c->d, c->off, c->ucnt, c->ubsum, c->uoff, c->units, c->st);
+    if (c->cells_valid) launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->st);
     return post_launch(c, "set variant");
 }
 

@@ -45,6 +45,7 @@ struct sph_ctx {
     uint32_t *key[2], *val[2];
     uint32_t *cnt, *off, *bsum, *hist, *tilectr, *os_status, *nnb, *nnb64;
     uint32_t *ucnt, *uoff, *ubsum;   // work units of the interaction
+    uint32_t* csum;                  // staged-candidate prefix sums per row
     uint2* units;
     uint4* part_u;
     unsigned long long* lvl2_q;

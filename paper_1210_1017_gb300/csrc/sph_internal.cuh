@@ -143,8 +143,8 @@ uint32_t max_units(uint32_t n, uint32_t nrows, uint64_t ncells);   // bound on u
 int variant_unit(int variant);               // particles per unit of a variant
 int variant_stage(int variant);              // staged candidates of a variant
 uint32_t interact_grid(int variant);         // blocks of its persistent launch
-void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
-                  uint32_t* uoff, uint2* units, cudaStream_t st);
+void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
+                  uint32_t* ubsum, uint32_t* uoff, uint2* units, cudaStream_t st);
 // Once per context (current device): opt in to the shared memory and size
 // the persistent grid from the device's SM count and occupancy.
 void prepare_interact();

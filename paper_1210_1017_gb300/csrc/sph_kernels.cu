@@ -325,9 +325,11 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
 // memory instead.  Units of instances that are done are skipped.
 // SPLIT warps share each group of 32 particles: warp w takes particles
 // (w % W) * 32 + lane of the unit and every SPLIT-th candidate cell of each
-// neighbour row (cells xlo + w / W, xlo + w / W + SPLIT, ...); the parts'
-// sums are added in a fixed order at the end.  More warps per block at the
-// same staging footprint.
+// neighbour row r, starting at cell xlo + (w / W + r) % SPLIT (the rotation
+// evens out the parts' shares when a warp's cell range is odd; every lane
+// keeps a similar share of its own neighbours in each part); the parts' sums
+// are added in a fixed order at the end.  More warps per block at the same
+// staging footprint.
 template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     constexpr int NT = W * SPLIT * 32;
@@ -569,7 +571,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             for (int r = 0; r < 9; ++r) {
                 if (!s_ok[r]) continue;
                 const uint32_t rs = s_rs[r], sb = s_base[r];
-                for (int xx = xlo + part; xx <= xhi; xx += SPLIT) {
+                for (int xx = xlo + (part + r) % SPLIT; xx <= xhi; xx += SPLIT) {
                     const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
                     const int ox = cx - xx;
                     const bool adj = valid && ox >= -1 && ox <= 1;
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 const float qy = fmaf((float)(-dy), d.csf, pi.y);
                 const float qz = fmaf((float)(-dz), d.csf, pi.z);
                 const uint32_t code_yz = ((uint32_t)(1 - dy) << 28) | ((uint32_t)(1 - dz) << 30);
-                for (int xx = xlo + part; xx <= xhi; xx += SPLIT) {
+                for (int xx = xlo + (part + r) % SPLIT; xx <= xhi; xx += SPLIT) {
                     const uint32_t gs = s_off[r][xx - ulo], ge = s_off[r][xx - ulo + 1];
                     const int ox = cx - xx;
                     const bool adj = valid && ox >= -1 && ox <= 1;
@@ -755,15 +757,47 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     }
 }
 
+// Staged-candidate prefix sums of each row: for row r and x in [0, ncx],
+// csum[I.cell_base + lr ncx + r + x] = sum over the 9 neighbour rows (dy, dz
+// in {-1, 0, 1}, inside the instance) of off[row + x].  The particles of the
+// 9 runs of cells [x0, x1) then number csum[x1] - csum[x0].  One block per
+// row, threads along x (coalesced).
+__global__ void __launch_bounds__(128) k_row_csum(const Dev d, const uint32_t* __restrict__ off,
+                                                  uint32_t* __restrict__ csum) {
+    const uint32_t r = blockIdx.x;
+    const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
+    const int ncx = I.ncx;
+    const uint32_t lr = r - I.row_base;
+    const int cy = (int)(lr % (uint32_t)I.ncy), cz = (int)(lr / (uint32_t)I.ncy);
+    uint32_t* out = csum + I.cell_base + (size_t)lr * (uint32_t)ncx + r;
+    for (int x = threadIdx.x; x <= ncx; x += blockDim.x) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int yy = cy + k % 3 - 1, zz = cz + k / 3 - 1;
+            if (yy >= 0 && yy < I.ncy && zz >= 0 && zz < I.ncz)
+                t += __ldg(off + I.cell_base +
+                           ((size_t)zz * (uint32_t)I.ncy + (uint32_t)yy) * (uint32_t)ncx + x);
+        }
+        out[x] = t;
+    }
+}
+
 // Work units.  A row of cells is cut into units of consecutive particles:
 // a unit closes before a cell that lies more than 3 cells past the unit's
 // last non-empty cell (so no unit spans an empty stretch), when it would
-// reach kSpan cells, or when it holds d.unit particles (the block size of the
-// interaction variant in use).  One thread walks one
-// (global) row; mode 0 counts the units of each row, mode 1 writes them at
-// the row's offset (uint2: first particle, end).
+// reach kSpan cells, when its staged candidates (the 9 neighbour rows over
+// cells [first - 1, last + 1]) would exceed the staging area of the
+// interaction variant in use (d.stage), or when it holds d.unit particles
+// (the variant's block size).  One thread walks one (global) row, reading
+// the offsets and staged-candidate sums in chunks of kUnitChunk cells (all
+// loads of a chunk in flight together); mode 0 counts the units of each
+// row, mode 1 writes them at the row's offset (uint2: first particle, end).
+constexpr int kUnitChunk = 16;
+
 template <int MODE>
 __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __restrict__ off,
+                                               const uint32_t* __restrict__ csum,
                                                uint32_t* __restrict__ ucnt,
                                                const uint32_t* __restrict__ uoff,
                                                uint2* __restrict__ units) {
@@ -772,74 +806,54 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
     const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
     const int ncx = I.ncx;
     const uint32_t lr = r - I.row_base;
-    const int cy = (int)(lr % (uint32_t)I.ncy), cz = (int)(lr / (uint32_t)I.ncy);
     const uint32_t* o = off + I.cell_base + (size_t)lr * (uint32_t)ncx;
-    // the 9 neighbour rows (null outside the instance): a unit's staged
-    // candidates are their particles in cells [first - 1, last + 1]
-    const uint32_t* nb[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int yy = cy + k % 3 - 1, zz = cz + k / 3 - 1;
-        nb[k] = (yy >= 0 && yy < I.ncy && zz >= 0 && zz < I.ncz)
-                    ? off + I.cell_base + ((size_t)zz * (uint32_t)I.ncy + (uint32_t)yy) * (uint32_t)ncx
-                    : nullptr;
-    }
-    // the unit's lower run bounds are fixed while it grows: kept in base
-    uint32_t base = 0;
-    auto set_base = [&](int xf) {
-        const int a0 = xf > 0 ? xf - 1 : 0;
-        base = 0;
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            if (nb[k]) base += __ldg(nb[k] + a0);
-    };
-    auto staged = [&](int xl) {
-        const int a1 = xl + 2 < ncx ? xl + 2 : ncx;
-        uint32_t t = 0;
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            if (nb[k]) t += __ldg(nb[k] + a1);
-        return t - base;
-    };
+    const uint32_t* cs = csum + I.cell_base + (size_t)lr * (uint32_t)ncx + r;
     uint32_t n = 0, out = MODE ? uoff[r] : 0u;
     uint32_t start = 0xffffffffu;
+    uint32_t base = 0;   // cs[first - 1] of the open unit (clamped at 0)
     int lo = 0, last = 0;
-    uint32_t a = o[0];
-    for (int x = 0; x < ncx; ++x) {
-        const uint32_t b = o[x + 1];
-        if (a != b) {
-            // a unit also closes before a cell that would make its staged
-            // candidates exceed the staging area of the variant in use
-            // the exact 9-row count is only needed near the capacity: the own
-            // row's share times 9 at half the capacity gates it (a missed cut
-            // only sends a unit down the slower global-memory path)
-            bool full = false;
-            if (start != 0xffffffffu) {
-                const uint32_t own = o[x + 2 < ncx ? x + 2 : ncx] - o[lo > 0 ? lo - 1 : 0];
-                full = 18u * own > (uint32_t)d.stage && staged(x) > (uint32_t)d.stage;
-            }
-            if (start != 0xffffffffu && (x - last > 3 || x - lo >= kSpan || full)) {
-                if (MODE) units[out + n] = make_uint2(start, a);
-                ++n;
-                start = 0xffffffffu;
-            }
-            if (start == 0xffffffffu) {
-                start = a;
-                lo = x;
-                set_base(lo);
-            }
-            last = x;
-            while (b - start > (uint32_t)d.unit) {
-                if (MODE) units[out + n] = make_uint2(start, start + d.unit);
-                ++n;
-                start += d.unit;
-                if (lo != x) {
+    uint32_t a = __ldg(o);
+    for (int x0 = 0; x0 < ncx; x0 += kUnitChunk) {
+        // ob[k] = o[x + 1], cc[k] = cs[x - 1], cc[k + 3] = cs[x + 2] for
+        // x = x0 + k (indexes clamped to [0, ncx])
+        uint32_t ob[kUnitChunk], cc[kUnitChunk + 3];
+#pragma unroll
+        for (int k = 0; k < kUnitChunk; ++k) {
+            const int xi = x0 + 1 + k;
+            ob[k] = __ldg(o + (xi < ncx ? xi : ncx));
+        }
+#pragma unroll
+        for (int k = 0; k < kUnitChunk + 3; ++k) {
+            const int xi = x0 - 1 + k;
+            cc[k] = __ldg(cs + (xi < 0 ? 0 : (xi < ncx ? xi : ncx)));
+        }
+#pragma unroll
+        for (int k = 0; k < kUnitChunk; ++k) {
+            const int x = x0 + k;
+            const uint32_t b = ob[k];
+            if (x < ncx && a != b) {
+                if (start != 0xffffffffu &&
+                    (x - last > 3 || x - lo >= kSpan || cc[k + 3] - base > (uint32_t)d.stage)) {
+                    if (MODE) units[out + n] = make_uint2(start, a);
+                    ++n;
+                    start = 0xffffffffu;
+                }
+                if (start == 0xffffffffu) {
+                    start = a;
                     lo = x;
-                    set_base(lo);
+                    base = cc[k];
+                }
+                last = x;
+                while (b - start > (uint32_t)d.unit) {
+                    if (MODE) units[out + n] = make_uint2(start, start + d.unit);
+                    ++n;
+                    start += d.unit;
+                    lo = x;
+                    base = cc[k];
                 }
             }
+            if (x < ncx) a = b;
         }
-        a = b;
     }
     if (start != 0xffffffffu) {
         if (MODE) units[out + n] = make_uint2(start, a);
@@ -1229,11 +1243,12 @@ void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStrea
     (counts ? v.counted : v.plain)<<<v.grid, v.warps * v.split * 32, v.smem, st>>>(d, a);
 }
 
-void launch_units(const Dev& d, const uint32_t* off, uint32_t* ucnt, uint32_t* ubsum,
-                  uint32_t* uoff, uint2* units, cudaStream_t st) {
-    k_units<0><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, ucnt, uoff, units);
+void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
+                  uint32_t* ubsum, uint32_t* uoff, uint2* units, cudaStream_t st) {
+    k_row_csum<<<d.nrows, 128, 0, st>>>(d, off, csum);
+    k_units<0><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
     launch_scan(ucnt, d.nrows, ubsum, uoff, st);
-    k_units<1><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, ucnt, uoff, units);
+    k_units<1><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
 }
 
 void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st) {

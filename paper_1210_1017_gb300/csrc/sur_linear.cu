@@ -44,14 +44,6 @@ __device__ __forceinline__ void unpack8(const uint4& u, float* f) {
     }
 }
 
-// 16 consecutive bf16 at p (32-byte aligned) as floats.
-__device__ __forceinline__ void load16(const __nv_bfloat16* p, float* f) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 a = q[0], b = q[1];
-    unpack8(a, f);
-    unpack8(b, f + 8);
-}
-
 // Epilogue operands of one row and NP columns, in registers: bf16 rows in
 // a (residual, ReLU mask, P[src]) and b (Q[dst]); an fp32 row (gradient
 // accumulation) spans a then b.
