@@ -451,7 +451,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
         // one pass over candidate pairs: shift the staged y, z into the
         // frame of this unit's row (the run r of a candidate gives the
         // offsets), then keep half-precision copies in cell units (cell =
-        // 2h = 1), two candidates per uint4: (x0, x1), (y0, y1), (z0, z1)
+        // 2h = 1) centred on the cell (minus 1/2), two candidates per uint4:
+        // (x0, x1), (y0, y1), (z0, z1) and their squared norms (k0, k1),
+        // computed from the rounded coordinates
         const float inv_cs = 1.0f / d.csf;
         const uint32_t nst = s_base[9];
         for (uint32_t k = tid; 2 * k < nst; k += NT) {
@@ -472,12 +474,19 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 s_p[j] = v;
                 pp[e] = v;
             }
-            const __half2 hx = __floats2half2_rn(pp[0].x * inv_cs, pp[1].x * inv_cs);
-            const __half2 hy = __floats2half2_rn(pp[0].y * inv_cs, pp[1].y * inv_cs);
-            const __half2 hz = __floats2half2_rn(pp[0].z * inv_cs, pp[1].z * inv_cs);
+            const __half2 hx = __floats2half2_rn(fmaf(pp[0].x, inv_cs, -0.5f),
+                                                 fmaf(pp[1].x, inv_cs, -0.5f));
+            const __half2 hy = __floats2half2_rn(fmaf(pp[0].y, inv_cs, -0.5f),
+                                                 fmaf(pp[1].y, inv_cs, -0.5f));
+            const __half2 hz = __floats2half2_rn(fmaf(pp[0].z, inv_cs, -0.5f),
+                                                 fmaf(pp[1].z, inv_cs, -0.5f));
+            const float2 fx = __half22float2(hx), fy = __half22float2(hy), fz = __half22float2(hz);
+            const __half2 hk = __floats2half2_rn(fmaf(fx.x, fx.x, fmaf(fy.x, fy.x, fz.x * fz.x)),
+                                                 fmaf(fx.y, fx.y, fmaf(fy.y, fy.y, fz.y * fz.y)));
             s_h[k] = make_uint4(*reinterpret_cast<const uint32_t*>(&hx),
                                 *reinterpret_cast<const uint32_t*>(&hy),
-                                *reinterpret_cast<const uint32_t*>(&hz), 0u);
+                                *reinterpret_cast<const uint32_t*>(&hz),
+                                *reinterpret_cast<const uint32_t*>(&hk));
         }
         __syncthreads();
     }
@@ -491,21 +500,30 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
         uint32_t cnt = 0;
         if (staged) {
             // candidate test in half precision, two candidates per
-            // instruction, against a conservative threshold (cell units:
-            // |r_ij|^2 - (1 + 2^-6) < 0); each lane keeps one 32-bit hit mask per
-            // word of 32 staged candidates (bit p: candidate base + 2p, bit
-            // 16 + p: candidate base + 2p + 1).  The pair phase applies the
-            // exact FP32 test.
+            // instruction, against a conservative threshold (cell units,
+            // centred coordinates q of particle i and p of the candidate:
+            // |q - p|^2 - thr = (|p|^2 + (|q|^2 - thr)) - 2 q.p < 0, thr =
+            // 1 + 2^-6, one add and three fused multiply-adds); each lane
+            // keeps one 32-bit hit mask per word of 32 staged candidates
+            // (bit p: candidate base + 2p, bit 16 + p: candidate base + 2p +
+            // 1).  The pair phase applies the exact FP32 test.  Rounding:
+            // for |q - p| <= 1 every intermediate stays below 8, so the
+            // computed value exceeds the exact one by at most 7.8e-3, and the
+            // rounded coordinates move |q - p|^2 by at most 2.6e-3: a pair
+            // within the support always tests negative.
             uint32_t* wl = s_words + w * (WCAP * 32) + lane;
             uint32_t* wd = s_desc + w * WCAP;
             const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
             const bool anyfluid = __any_sync(kFull, fluid);
             const float inv_cs = 1.0f / d.csf;
-            // minus the threshold, folded into the first fused multiply-add;
-            // a set sign bit of r^2 - thr marks a candidate
-            const __half2 nthr = __float2half2_rn(-(1.0f + 1.0f / 64.0f));
-            const __half2 hqy = __float2half2_rn(pi.y * inv_cs);
-            const __half2 hqz = __float2half2_rn(pi.z * inv_cs);
+            const float thr = 1.0f + 1.0f / 64.0f;
+            // y and z of i, centred and rounded; -2 q_y, -2 q_z (exact)
+            const __half2 hqy = __float2half2_rn(fmaf(pi.y, inv_cs, -0.5f));
+            const __half2 hqz = __float2half2_rn(fmaf(pi.z, inv_cs, -0.5f));
+            const float qy = __low2float(hqy), qz = __low2float(hqz);
+            const float qyz2 = fmaf(qy, qy, qz * qz) - thr;
+            const __half2 m2qy = __float2half2_rn(-2.0f * qy);
+            const __half2 m2qz = __float2half2_rn(-2.0f * qz);
             uint32_t nw = 0, lane_hits = 0;
             uint32_t lane_nz = 0;   // bit w: stored word w holds hits of this lane
             static_assert(WCAP <= 32, "one bit per stored word");
@@ -577,7 +595,13 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     const bool adj = valid && ox >= -1 && ox <= 1;
                     if (adj) ncand += ge - gs;
                     if (gs == ge) continue;
-                    const __half2 hqx = __float2half2_rn(fmaf((float)ox, d.csf, pi.x) * inv_cs);
+                    // x of i in the candidate cell's frame, centred and
+                    // rounded; |q|^2 - thr
+                    const __half2 hqx =
+                        __float2half2_rn(fmaf(fmaf((float)ox, d.csf, pi.x), inv_cs, -0.5f));
+                    const float qx = __low2float(hqx);
+                    const __half2 hc = __float2half2_rn(fmaf(qx, qx, qyz2));
+                    const __half2 m2qx = __float2half2_rn(-2.0f * qx);
                     const uint32_t s0 = sb + (gs - rs), e0 = sb + (ge - rs);
                     for (uint32_t base = s0 & ~1u; base < e0; base += 32) {
                         if (nw == (uint32_t)WCAP) flush();
@@ -588,10 +612,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
 #pragma unroll 4
                         for (uint32_t q2 = 0; q2 < npair; ++q2) {
                             const uint4 hv = hp[q2];
-                            const __half2 dx = __hsub2(hqx, *reinterpret_cast<const __half2*>(&hv.x));
-                            const __half2 dy = __hsub2(hqy, *reinterpret_cast<const __half2*>(&hv.y));
-                            const __half2 dz = __hsub2(hqz, *reinterpret_cast<const __half2*>(&hv.z));
-                            const __half2 r2t = __hfma2(dx, dx, __hfma2(dy, dy, __hfma2(dz, dz, nthr)));
+                            const __half2 s0 = __hadd2(*reinterpret_cast<const __half2*>(&hv.w), hc);
+                            const __half2 r2t = __hfma2(
+                                m2qx, *reinterpret_cast<const __half2*>(&hv.x),
+                                __hfma2(m2qy, *reinterpret_cast<const __half2*>(&hv.y),
+                                        __hfma2(m2qz, *reinterpret_cast<const __half2*>(&hv.z), s0)));
                             const uint32_t sg = *reinterpret_cast<const uint32_t*>(&r2t);
                             m |= (sg >> (15 - q2)) & (0x00010001u << q2);
                         }
