@@ -270,29 +270,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 struct PairAcc {
     float ax, ay, az, dr, mu;
+    float npf;       // pairs counted by the FP32 test (exact below 2^24)
     uint32_t np;
 };
 
 // Pair terms of Eqs. 7 and 9 for i (pi, vi) and j (pj, vj) at offset
 // (dx, dy, dz) = r_i - r_j.  MOM: evaluate the momentum terms (a warp-uniform
-// choice); only fluid particles keep them, since boundary particles never
-// move (Sec. 2.3).  The pair j = i (all offsets zero) contributes exactly
-// nothing, which lets lists be padded with it.
+// choice).  They are accumulated for every particle; the caller keeps them
+// only for fluid particles, since boundary particles never move (Sec. 2.3).
+// A pair with v_ij = 0 whose offset lies outside the support (the particle
+// itself, placed 4 cells away) contributes exactly nothing and is not
+// counted, which lets lane work be padded with it.  Masks are products with
+// 0 or 1 rather than selects, keeping the integer/logic pipe free.
 template <bool MOM, bool CHECK = false>
-__device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, const float4& pi,
+__device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4& pi,
                                            const float4& vi, float ci, float dx, float dy, float dz,
-                                           const float4& pj, const float4& vj, PairAcc& s,
-                                           bool real = true) {
+                                           const float4& pj, const float4& vj, PairAcc& s) {
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     // CHECK: the entry came from the conservative half-precision pre-filter;
-    // the FP32 neighbour test (the same expression as the candidate test of
-    // the global-memory path) decides, and counts the pair
-    const bool use = CHECK ? (real && d2 < d.r2max) : true;
-    if (CHECK) s.np += use ? 1u : 0u;
+    // the FP32 neighbour test (the same predicate as the candidate test of the
+    // global-memory path) decides and counts the pair: use = [d2 < (2h)^2],
+    // the saturated sign of 2^100 ((2h)^2 - d2), exact (power-of-two scaling)
+    const float use = CHECK ? __saturatef(fmaf(d2, -0x1p100f, d.r2max * 0x1p100f)) : 1.f;
+    if (CHECK) s.npf += use;
     // Wendland C2: grad_i W = F r_ij, F = -5 aD/h^2 (1 - q/2)^3
     const float q = sqrt_approx(d2) * d.inv_h;
     const float wq = fmaf(-0.5f, q, 1.0f);
-    const float F = use ? d.fc * (wq * wq * wq) : 0.f;
+    const float F = CHECK ? d.fc * (wq * wq * wq) * use : d.fc * (wq * wq * wq);
     const float dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = vi.z - vj.z;
     const float vr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
     s.dr = fmaf(vr, F, s.dr);                                      // Eq. 7
@@ -300,12 +304,13 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, bool fluid, c
         const float nu = d.h * vr * rcp_approx(d2 + d.eta2);       // Sec. 2.2
         const float rrj = vj.w * d.inv_rho0;
         const float cj = c0 * rrj * rrj * rrj;
-        const float visc = vr < 0.f ? -d.alpha * (ci + cj) * nu * rcp_approx(vi.w + vj.w) : 0.f;
-        const float f = fluid ? (pi.w + pj.w + visc) * F : 0.f;    // Eq. 9
+        // Pi_ij only for approaching pairs (v_ij . r_ij < 0, the sign of nu)
+        const float visc = -d.alpha * (ci + cj) * fminf(nu, 0.f) * rcp_approx(vi.w + vj.w);
+        const float f = (pi.w + pj.w + visc) * F;                  // Eq. 9
         s.ax = fmaf(-f, dx, s.ax);
         s.ay = fmaf(-f, dy, s.ay);
         s.az = fmaf(-f, dz, s.az);
-        s.mu = fmaxf(s.mu, (fluid && use) ? fabsf(nu) : 0.f);
+        s.mu = fmaxf(s.mu, CHECK ? fabsf(nu) * use : fabsf(nu));
     }
 }
 
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     }
     const float rri = vi.w * d.inv_rho0;
     const float ci = c0 * rri * rri * rri;
-    PairAcc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+    PairAcc acc = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
     uint32_t ncand = 0;
     __syncthreads();
     const bool staged = s_mode != 0;
@@ -528,17 +533,18 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             uint32_t lane_nz = 0;   // bit w: stored word w holds hits of this lane
             static_assert(WCAP <= 32, "one bit per stored word");
             // pair phase over the stored words: each lane pops its own hits,
-            // two per iteration; lanes that run out use the pair (i, i)
+            // two per iteration; lanes that run out are padded with i itself,
+            // placed 4 cells away (no contribution, not counted)
             auto flush = [&]() {
                 __syncwarp();   // the words and lane 0's descriptors are written
                 const uint32_t mx = __reduce_max_sync(kFull, lane_hits);
                 uint32_t nz = lane_nz, cm = 0, jb = 0;
                 float qxw = 0.f;                         // i's x in the word's cell frame
+                const float qpad = fmaf(4.0f, d.csf, pi.x);   // pads: i itself, out of range
                 constexpr int kPop = 2;   // pairs per iteration (independent chains)
                 for (uint32_t t = 0; t < mx; t += kPop) {
                     uint32_t j2[kPop];
                     float qx2[kPop];
-                    bool re[kPop];
 #pragma unroll
                     for (int k = 0; k < kPop; ++k) {
                         // at most one step: the lane visits only its non-empty words
@@ -550,15 +556,16 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             jb = dsc & 0xffffu;
                             qxw = fmaf((float)(cx - (ulo + (int)(dsc >> 16))), d.csf, pi.x);
                         }
-                        re[k] = cm != 0;
                         if (cm) {
                             const uint32_t b = 31u - __clz(cm);
                             cm ^= 1u << b;
-                            j2[k] = jb + ((b & 15u) << 1) + (b >> 4);
+                            // bit b: candidate jb + 2 (b mod 16) + b / 16
+                            const uint32_t hi = b >> 4;
+                            j2[k] = jb + 2u * b - 31u * hi;
                             qx2[k] = qxw;
                         } else {
                             j2[k] = self;
-                            qx2[k] = pi.x;
+                            qx2[k] = qpad;
                         }
                     }
                     float4 pp[kPop], vv[kPop];
@@ -570,18 +577,18 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     if (anyfluid) {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<true, true>(d, c0, fluid, pi, vi, ci, qx2[k] - pp[k].x,
-                                                   pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
-                                                   re[k]);
+                            pair_terms<true, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
+                                                   pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc);
                     } else {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<false, true>(d, c0, fluid, pi, vi, ci, qx2[k] - pp[k].x,
-                                                    pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc,
-                                                    re[k]);
+                            pair_terms<false, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
+                                                    pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc);
                     }
                 }
                 __syncwarp();   // every lane is done reading before the words are reused
+                acc.np += (uint32_t)acc.npf;
+                acc.npf = 0.f;
                 nw = 0;
                 lane_hits = 0;
                 lane_nz = 0;
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                         const float oz = (float)((int)(e >> 30) - 1);
                         const float4 pj = __ldg(a.posc + j);
                         const float4 vj = __ldg(a.velrhop + j);
-                        pair_terms<true>(d, c0, fluid, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
+                        pair_terms<true>(d, c0, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
                                          fmaf(oy, d.csf, pi.y) - pj.y, fmaf(oz, d.csf, pi.z) - pj.z,
                                          pj, vj, acc);
                     }
@@ -724,8 +731,10 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     }
     const bool owner = part == 0;                   // writes this particle's results
     const float m = d.mass;
-    const float4 out =
-        make_float4(fmaf(m, acc.ax, d.gx), fmaf(m, acc.ay, d.gy), fmaf(m, acc.az, d.gz), m * acc.dr);
+    // boundary particles keep gravity only (their momentum sums are dropped)
+    const float4 out = make_float4(fmaf(m, fluid ? acc.ax : 0.f, d.gx),
+                                   fmaf(m, fluid ? acc.ay : 0.f, d.gy),
+                                   fmaf(m, fluid ? acc.az : 0.f, d.gz), m * acc.dr);
     const uint32_t npairs = (valid && owner) ? acc.np - 1u : 0u;   // without the pair (i, i)
     if (valid && owner) {
         a.ace[i] = out;
