@@ -274,6 +274,22 @@ struct PairAcc {
     uint32_t np;
 };
 
+// Hit-mask bits of the slots [0, lim) of a 32-candidate word (slot s at
+// bit 8 (s mod 4) + s / 4), for lim = 0 .. 32.
+struct KeepTable {
+    uint32_t v[33];
+};
+constexpr KeepTable make_keep_table() {
+    KeepTable t{};
+    for (int lim = 0; lim <= 32; ++lim) {
+        uint32_t k = 0;
+        for (int sl = 0; sl < lim; ++sl) k |= 1u << (8 * (sl & 3) + (sl >> 2));
+        t.v[lim] = k;
+    }
+    return t;
+}
+__constant__ KeepTable c_keep = make_keep_table();
+
 // Pair terms of Eqs. 7 and 9 for i (pi, vi) and j (pj, vj) at offset
 // (dx, dy, dz) = r_i - r_j.  MOM: evaluate the momentum terms (a warp-uniform
 // choice).  They are accumulated for every particle; the caller keeps them
@@ -510,8 +526,8 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             // |q - p|^2 - thr = (|p|^2 + (|q|^2 - thr)) - 2 q.p < 0, thr =
             // 1 + 2^-6, one add and three fused multiply-adds); each lane
             // keeps one 32-bit hit mask per word of 32 staged candidates
-            // (bit p: candidate base + 2p, bit 16 + p: candidate base + 2p +
-            // 1).  The pair phase applies the exact FP32 test.  Rounding:
+            // (bit 8k + j: candidate base + 4j + k).  The pair phase applies
+            // the exact FP32 test.  Rounding:
             // for |q - p| <= 1 every intermediate stays below 8, so the
             // computed value exceeds the exact one by at most 7.8e-3, and the
             // rounded coordinates move |q - p|^2 by at most 2.6e-3: a pair
@@ -559,9 +575,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                         if (cm) {
                             const uint32_t b = 31u - __clz(cm);
                             cm ^= 1u << b;
-                            // bit b: candidate jb + 2 (b mod 16) + b / 16
-                            const uint32_t hi = b >> 4;
-                            j2[k] = jb + 2u * b - 31u * hi;
+                            // bit b = 8k + j: candidate jb + 4j + k
+                            const uint32_t hi = b >> 3;
+                            j2[k] = jb + 4u * b - 31u * hi;
                             qx2[k] = qxw;
                         } else {
                             j2[k] = self;
@@ -615,22 +631,29 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                         const uint32_t lim = e0 - base < 32u ? e0 - base : 32u;   // slots in use
                         const uint32_t npair = (lim + 1) >> 1;
                         const uint4* hp = s_h + (base >> 1);
-                        uint32_t m = 0;
-#pragma unroll 4
-                        for (uint32_t q2 = 0; q2 < npair; ++q2) {
-                            const uint4 hv = hp[q2];
-                            const __half2 s0 = __hadd2(*reinterpret_cast<const __half2*>(&hv.w), hc);
+                        // the sign bits of r^2 - thr for two candidate pairs
+                        // (four candidates) gathered into one byte each, then
+                        // placed: bit 8k + j <-> candidate base + 4j + k.  A
+                        // pair slot past the word's end is read (inside the
+                        // shared allocation) and masked below.
+                        auto test_pair = [&](const uint4 hv) {
+                            const __half2 kc = __hadd2(*reinterpret_cast<const __half2*>(&hv.w), hc);
                             const __half2 r2t = __hfma2(
                                 m2qx, *reinterpret_cast<const __half2*>(&hv.x),
                                 __hfma2(m2qy, *reinterpret_cast<const __half2*>(&hv.y),
-                                        __hfma2(m2qz, *reinterpret_cast<const __half2*>(&hv.z), s0)));
-                            const uint32_t sg = *reinterpret_cast<const uint32_t*>(&r2t);
-                            m |= (sg >> (15 - q2)) & (0x00010001u << q2);
+                                        __hfma2(m2qz, *reinterpret_cast<const __half2*>(&hv.z), kc)));
+                            return *reinterpret_cast<const uint32_t*>(&r2t);
+                        };
+                        uint32_t m = 0;
+#pragma unroll 4
+                        for (uint32_t q2 = 0; q2 < npair; q2 += 2) {
+                            const uint32_t sa = test_pair(hp[q2]), sb = test_pair(hp[q2 + 1]);
+                            const uint32_t t = __byte_perm(sa, sb, 0x7531);
+                            const uint32_t jj = q2 >> 1;
+                            m |= (t >> (7 - jj)) & (0x01010101u << jj);
                         }
                         // slots outside [s0, e0) and lanes not adjacent to the cell
-                        const uint32_t ev = lim >= 32u ? 0xffffu : ((1u << ((lim + 1) >> 1)) - 1u);
-                        const uint32_t od = (lim >> 1) >= 16u ? 0xffffu : ((1u << (lim >> 1)) - 1u);
-                        uint32_t keep = ev | (od << 16);
+                        uint32_t keep = c_keep.v[lim];
                         if (base < s0) keep &= ~1u;
                         m = adj ? (m & keep) : 0u;
                         if (__any_sync(kFull, m != 0u)) {
