@@ -274,6 +274,16 @@ struct PairAcc {
     uint32_t np;
 };
 
+// The sign bits (15 and 31) of a and of b, each spread over one byte of the
+// result (0xff if set): byte 0 <- a bit 15, 1 <- a bit 31, 2 <- b bit 15,
+// 3 <- b bit 31 (prmt selects a byte and, with the selector's high bit,
+// replicates that byte's sign bit).
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xFDB9;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
 // Hit-mask bits of the slots [0, lim) of a 32-candidate word (slot s at
 // bit 8 (s mod 4) + s / 4), for lim = 0 .. 32.
 struct KeepTable {
@@ -632,10 +642,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                         const uint32_t npair = (lim + 1) >> 1;
                         const uint4* hp = s_h + (base >> 1);
                         // the sign bits of r^2 - thr for two candidate pairs
-                        // (four candidates) gathered into one byte each, then
-                        // placed: bit 8k + j <-> candidate base + 4j + k.  A
-                        // pair slot past the word's end is read (inside the
-                        // shared allocation) and masked below.
+                        // (four candidates) spread into one byte each (all
+                        // ones or zero), then one bit of each byte kept: bit
+                        // 8k + j <-> candidate base + 4j + k.  A pair slot
+                        // past the word's end is read (inside the shared
+                        // allocation) and masked below.
                         auto test_pair = [&](const uint4 hv) {
                             const __half2 kc = __hadd2(*reinterpret_cast<const __half2*>(&hv.w), hc);
                             const __half2 r2t = __hfma2(
@@ -645,12 +656,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             return *reinterpret_cast<const uint32_t*>(&r2t);
                         };
                         uint32_t m = 0;
-#pragma unroll 4
-                        for (uint32_t q2 = 0; q2 < npair; q2 += 2) {
-                            const uint32_t sa = test_pair(hp[q2]), sb = test_pair(hp[q2 + 1]);
-                            const uint32_t t = __byte_perm(sa, sb, 0x7531);
-                            const uint32_t jj = q2 >> 1;
-                            m |= (t >> (7 - jj)) & (0x01010101u << jj);
+#pragma unroll
+                        for (uint32_t jj = 0; jj < 8; ++jj) {
+                            if (2 * jj >= npair) break;
+                            const uint32_t sa = test_pair(hp[2 * jj]), sb = test_pair(hp[2 * jj + 1]);
+                            m |= sign_bytes(sa, sb) & (0x01010101u << jj);
                         }
                         // slots outside [s0, e0) and lanes not adjacent to the cell
                         uint32_t keep = c_keep.v[lim];
