@@ -334,10 +334,16 @@ def run_ours(args):
     de0 = sim.diagnostics()
     barrier()
     t0 = time.perf_counter()
+    parts = np.zeros(3)
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         S.sph_upload(sim.ctx, pin["pos"], pin["vel"], pin["rho"], pin["ids"])
+        tb = time.perf_counter()
         S.sph_step(sim.ctx, 1)
+        sim.synchronize()
+        tc = time.perf_counter()
         S.sph_download(sim.ctx, out["pos"], out["vel"], out["rho"], out["ids"])
+        parts += (tb - ta, tc - tb, time.perf_counter() - tc)
     t_e2e = time.perf_counter() - t0
     de1 = sim.diagnostics()
     barrier()
@@ -346,6 +352,7 @@ def run_ours(args):
     e2e = {"value": e2e_pairs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_h2d,
            "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
            "ms_per_step": round(t_e2e / e2e_steps * 1e3, 3),
+           "ms_upload_step_download": [round(v / e2e_steps * 1e3, 3) for v in parts],
            "note": "per step: sph_upload (pinned host) + sph_step(1) + sph_download (pinned host)"}
 
     kps = sim.kernels_per_step()
