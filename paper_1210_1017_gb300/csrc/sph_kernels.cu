@@ -348,12 +348,14 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
 // runs are copied to shared memory with bulk asynchronous copies; their y, z
 // are then shifted into the frame of the unit's row, so a candidate's offset
 // from particle i only needs i's own cell offset in x.  Each warp then tests
-// every candidate of its lanes' cells (one broadcast shared-memory load, all
-// lanes), appends hits (|r_ij| < 2h) to per-lane lists, and evaluates the
-// pair terms from the lists with all lanes busy.  Positions are relative to
-// the particles' own cell origins (FP32), plus whole-cell offsets.  A unit
-// whose runs do not fit the staging area reads its candidates from global
-// memory instead.  Units of instances that are done are skipped.
+// every candidate of its lanes' cells in half precision (one broadcast
+// shared-memory load per two candidates, all lanes) against a conservative
+// threshold, keeps the hits as per-lane mask words, and evaluates the pair
+// terms from the masks with all lanes busy, applying the exact FP32 test
+// |r_ij| < 2h there.  Positions are relative to the particles' own cell
+// origins (FP32), plus whole-cell offsets.  A unit whose runs do not fit the
+// staging area reads its candidates from global memory instead (FP32 test,
+// 32-bit lists).  Units of instances that are done are skipped.
 // SPLIT warps share each group of 32 particles: warp w takes particles
 // (w % W) * 32 + lane of the unit and every SPLIT-th candidate cell of each
 // neighbour row r, starting at cell xlo + (w / W + r) % SPLIT (the rotation
