@@ -36,7 +36,11 @@ class _Params(C.Structure):
                 ("alpha", C.c_double), ("eta2_coef", C.c_double),
                 ("g", C.c_double * 3), ("cfl", C.c_double),
                 ("mass", C.c_double), ("dmin", C.c_double * 3),
-                ("dmax", C.c_double * 3), ("n_bound", C.c_int64)]
+                ("dmax", C.c_double * 3), ("n_bound", C.c_int64),
+                ("kernel", C.c_int64)]
+
+# Smoothing kernels the oracle knows (Sec. 2.1), by the name a case uses.
+KERNELS = {"wendland": 0, "cubic": 1}
 
 
 _lib = None
@@ -80,6 +84,11 @@ def lib():
         L.or_step.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, u32,
                               C.c_double, C.c_int, i64]
         L.or_step.restype = C.c_double
+        L.or_verlet_update.argtypes = [P, C.c_int64] + [dp] * 11 + [u32, dp, dp,
+                                                                    C.c_double, C.c_int]
+        L.or_verlet_step.argtypes = [P, C.c_int64] + [dp] * 11 + [u32, C.c_double,
+                                                                  C.c_int, C.c_int, i64]
+        L.or_verlet_step.restype = C.c_double
         L.or_diagnostics.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp,
                                      u32, dp]
         L.or_num_threads.restype = C.c_int
@@ -99,6 +108,7 @@ def params(p: dict) -> _Params:
         s.dmax[a] = p["dmax"][a]
     s.cfl, s.mass = p["cfl"], p["mass"]
     s.n_bound = int(p["n_bound"])
+    s.kernel = KERNELS[p.get("kernel", "wendland")]
     return s
 
 
@@ -265,6 +275,39 @@ class Oracle:
         dt = self.L.or_step(C.byref(self.P), st.n, *st.arrays(), _u(st.ids),
                             float(dt_fixed), int(brute), _i(pairs))
         return dt, int(pairs[0])
+
+    def verlet_update(self, st: State, prev: State, a, drho, dt, euler):
+        """Verlet update in place on ``st`` (S^n -> S^n+1) from the rates at
+        S^n; ``prev`` holds the velocities and densities one step earlier and
+        receives those of S^n."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        drho = np.ascontiguousarray(drho, dtype=np.float64)
+        self.L.or_verlet_update(C.byref(self.P), st.n, *st.arrays(),
+                                _d(prev.vx), _d(prev.vy), _d(prev.vz), _d(prev.rho),
+                                _u(st.ids), _d(a), _d(drho), float(dt), int(bool(euler)))
+        return st
+
+    def verlet_step(self, st: State, prev: State, euler, dt_fixed=0.0, brute=False):
+        """One Verlet step in place (``prev`` as in verlet_update); returns
+        (dt, pairs)."""
+        pairs = np.zeros(1, dtype=np.int64)
+        dt = self.L.or_verlet_step(C.byref(self.P), st.n, *st.arrays(),
+                                   _d(prev.vx), _d(prev.vy), _d(prev.vz), _d(prev.rho),
+                                   _u(st.ids), float(dt_fixed), int(bool(euler)),
+                                   int(brute), _i(pairs))
+        return dt, int(pairs[0])
+
+    def verlet_run(self, st: State, nsteps, every=40, dt_fixed=0.0, prev=None, first=0):
+        """``nsteps`` Verlet steps in place, counting steps from ``first``:
+        step k is an Euler step when k is a multiple of ``every`` (so the
+        first step of a run that starts at 0, which has no earlier state, is
+        one).  Returns (step sizes, the earlier state for a further run)."""
+        prev = st.copy() if prev is None else prev
+        dts = []
+        for k in range(first, first + nsteps):
+            dt, _ = self.verlet_step(st, prev, k % every == 0, dt_fixed=dt_fixed)
+            dts.append(dt)
+        return dts, prev
 
     def diagnostics(self, st: State):
         out = np.zeros(8, dtype=np.float64)

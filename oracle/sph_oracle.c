@@ -25,11 +25,15 @@
  *     form P = p/rho^2 is used.
  *   - rho_ij in Pi_ij is the pair mean (rho_i + rho_j)/2.
  *   - c_i = sqrt(dp/drho at rho_i) = c0 (rho_i/rho0)^((gamma-1)/2).
- *   - Kernel: Wendland C2 with h = 1.3 dp (the paper's cubic spline is a
- *     separate option not built here); support |r_ij| < 2h strictly.
+ *   - Kernel: Wendland C2 with h = 1.3 dp, or the paper's own cubic spline
+ *     (Sec. 2.1, or_params.kernel = 1); support |r_ij| < 2h strictly.
  *   - Integrator: the symplectic predictor-corrector (position-Verlet
  *     midpoint form) with two force evaluations per step; the step size is
- *     set from the first evaluation of each step.
+ *     set from the first evaluation of each step.  Or the paper's own
+ *     "second-order Verlet" (Sec. 3.3), one force evaluation per step, in
+ *     the form of the SPHysics formulation it cites: a leapfrog over two
+ *     steps, with an Euler step every N_s steps (the caller chooses which
+ *     steps; the first step, which has no earlier state, is one).
  *   - CFL step: dt = CFL * min( min_i sqrt(h/|a_i|),  h/(c_max + mu_max) ),
  *     mu_max = max over pairs of h |v_ij . r_ij| / (r_ij^2 + eta^2).
  *   - Particles outside the cell-grid domain are excluded (no interactions)
@@ -53,6 +57,7 @@ typedef struct {
     double cfl, mass;
     double dmin[3], dmax[3];
     int64_t n_bound;          /* ids below n_bound are boundary particles */
+    int64_t kernel;           /* 0: Wendland C2, 1: cubic spline (Sec. 2.1) */
 } or_params;
 
 /* ---------------------------------------------------------------- grid -- */
@@ -261,25 +266,43 @@ void or_neighbour_counts(const or_params *P, int64_t n, const double *x,
 
 /* ------------------------------------------------------------- physics -- */
 
-/* Wendland C2 kernel, W(q) = aD (1 - q/2)^4 (2q + 1), aD = 21/(16 pi h^3),
- * for q = r/h in [0, 2). */
+/* Smoothing kernels, q = r/h, compact support q < 2 (Sec. 2.1).
+ *
+ * Wendland C2:  W = aD (1 - q/2)^4 (2q + 1),  aD = 21/(16 pi h^3).
+ * Cubic spline (the kernel of the paper's results), aD = 1/(pi h^3):
+ *   W = aD (1 - 3/2 q^2 + 3/4 q^3)   for 0 <= q < 1,
+ *   W = aD/4 (2 - q)^3               for 1 <= q < 2. */
 double or_kernel_w(const or_params *P, double r)
 {
     const double h = P->h;
     const double q = r / h;
     if (q >= 2.0) return 0.0;
+    if (P->kernel == 1) {
+        const double aD = 1.0 / (M_PI * h * h * h);
+        if (q < 1.0) return aD * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+        const double w = 2.0 - q;
+        return 0.25 * aD * w * w * w;
+    }
     const double aD = 21.0 / (16.0 * M_PI * h * h * h);
     const double w = 1.0 - 0.5 * q;
     return aD * w * w * w * w * (2.0 * q + 1.0);
 }
 
-/* grad_i W_ij = F(r) r_ij with F = -5 aD / h^2 (1 - q/2)^3 (the derivative
- * of the Wendland kernel divided by r). */
+/* grad_i W_ij = F(r) r_ij, F = (dW/dr)/r:
+ *   Wendland C2:   F = -5 aD/h^2 (1 - q/2)^3
+ *   cubic spline:  F = aD/h^2 (9/4 q - 3)           for q < 1,
+ *                  F = -3/4 aD/h^2 (2 - q)^2 / q    for 1 <= q < 2. */
 double or_kernel_f(const or_params *P, double r)
 {
     const double h = P->h;
     const double q = r / h;
     if (q >= 2.0) return 0.0;
+    if (P->kernel == 1) {
+        const double aD = 1.0 / (M_PI * h * h * h);
+        if (q < 1.0) return aD / (h * h) * (2.25 * q - 3.0);
+        const double w = 2.0 - q;
+        return -0.75 * aD / (h * h) * w * w / q;
+    }
     const double aD = 21.0 / (16.0 * M_PI * h * h * h);
     const double w = 1.0 - 0.5 * q;
     return -5.0 * aD / (h * h) * w * w * w;
@@ -514,6 +537,69 @@ double or_step(const or_params *P, int64_t n, double *x, double *y, double *z,
                s0 + 6 * N, x, y, z, vx, vy, vz, rho, id, a, dr, dt);
     if (pairs_out) *pairs_out = pairs;
     free(a); free(dr); free(sa); free(sd); free(nn); free(s0);
+    return dt;
+}
+
+/* Verlet update (Sec. 3.3, in the SPHysics form): from the state S^n (x..rho,
+ * updated in place), the state one step earlier (vxm, vym, vzm, rhom) and
+ * the rates at S^n (a, drho):
+ *   fluid:          r1 = r + dt v + (dt^2/2) a
+ *                   v1 = vm + 2 dt a      (leapfrog step)
+ *                   v1 = v  + dt a        (Euler step, euler != 0)
+ *   all in-domain:  rho1 = rhom + 2 dt drho  (leapfrog)
+ *                   rho1 = rho  + dt drho    (Euler)
+ * Boundary particles keep r and v (Sec. 2.3).  On return (vxm.., rhom) holds
+ * the state on entry, i.e. S^n becomes the earlier state of the next step.
+ * Excluded particles are left unchanged (both states). */
+void or_verlet_update(const or_params *P, int64_t n, double *x, double *y,
+                      double *z, double *vx, double *vy, double *vz,
+                      double *rho, double *vxm, double *vym, double *vzm,
+                      double *rhom, const uint32_t *id, const double *a,
+                      const double *drho, double dt, int euler)
+{
+    int64_t nc[3];
+    or_grid_dims(P, nc);
+    const double dt2h = 0.5 * dt * dt;
+    const double dtv = euler ? dt : 2.0 * dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        if (!is_in(P, nc, x[i], y[i], z[i])) continue;
+        const double ux = vx[i], uy = vy[i], uz = vz[i], r = rho[i];
+        if ((int64_t)id[i] >= P->n_bound) {
+            x[i] = x[i] + (dt * ux + dt2h * a[3 * i]);
+            y[i] = y[i] + (dt * uy + dt2h * a[3 * i + 1]);
+            z[i] = z[i] + (dt * uz + dt2h * a[3 * i + 2]);
+            vx[i] = (euler ? ux : vxm[i]) + dtv * a[3 * i];
+            vy[i] = (euler ? uy : vym[i]) + dtv * a[3 * i + 1];
+            vz[i] = (euler ? uz : vzm[i]) + dtv * a[3 * i + 2];
+        }
+        rho[i] = (euler ? r : rhom[i]) + dtv * drho[i];
+        vxm[i] = ux; vym[i] = uy; vzm[i] = uz; rhom[i] = r;
+    }
+}
+
+/* One Verlet step: evaluate at S^n (cell list rebuilt), set dt from that
+ * evaluation (or use dt_fixed > 0), update.  Returns the dt used. */
+double or_verlet_step(const or_params *P, int64_t n, double *x, double *y,
+                      double *z, double *vx, double *vy, double *vz,
+                      double *rho, double *vxm, double *vym, double *vzm,
+                      double *rhom, const uint32_t *id, double dt_fixed,
+                      int euler, int brute, int64_t *pairs_out)
+{
+    const size_t N = (size_t)(n > 0 ? n : 1);
+    double *a = (double *)malloc(sizeof(double) * 3 * N);
+    double *dr = (double *)malloc(sizeof(double) * N);
+    double *sa = (double *)malloc(sizeof(double) * N);
+    double *sd = (double *)malloc(sizeof(double) * N);
+    uint32_t *nn = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    double terms[3];
+    const int64_t pairs = or_interact(P, n, x, y, z, vx, vy, vz, rho, id, brute,
+                                      0, n, a, dr, sa, sd, nn, terms);
+    const double dt = dt_fixed > 0.0 ? dt_fixed : or_dt(P, terms);
+    or_verlet_update(P, n, x, y, z, vx, vy, vz, rho, vxm, vym, vzm, rhom, id,
+                     a, dr, dt, euler);
+    if (pairs_out) *pairs_out = pairs;
+    free(a); free(dr); free(sa); free(sd); free(nn);
     return dt;
 }
 

@@ -87,6 +87,9 @@ class Case:
     fluid_height: float
     eta2_coef: float = 0.01
     gamma: float = 7.0
+    kernel: str = "wendland"          # or "cubic" (the paper's, Sec. 2.1)
+    integrator: str = "symplectic"    # or "verlet" (the paper's, Sec. 3.3)
+    verlet_every: int = 40            # Verlet: an Euler step every this many
     meta: dict = field(default_factory=dict)
 
     @property
@@ -107,7 +110,8 @@ class Case:
                     c0=self.c0, alpha=self.alpha, eta2_coef=self.eta2_coef,
                     gravity=tuple(self.gravity), cfl=self.cfl, mass=self.mass,
                     dmin=tuple(self.dmin), dmax=tuple(self.dmax),
-                    n_bound=int(self.n_bound))
+                    n_bound=int(self.n_bound), kernel=self.kernel,
+                    integrator=self.integrator, verlet_every=int(self.verlet_every))
 
 
 def _nsites(length: float, dp: float) -> int:
@@ -387,7 +391,8 @@ def ensemble(case_list, t_end=float("inf")) -> Ensemble:
     p = case_list[0].params()
     for c in case_list[1:]:
         q = c.params()
-        for k in ("dp", "h", "rho0", "alpha", "cfl", "mass", "gravity", "eta2_coef"):
+        for k in ("dp", "h", "rho0", "alpha", "cfl", "mass", "gravity", "eta2_coef",
+                  "kernel", "integrator", "verlet_every"):
             if q[k] != p[k]:
                 raise ValueError(f"ensemble members disagree on {k}")
     return Ensemble(cases=list(case_list), pos=pos, vel=vel, rho=rho, ids=ids,
