@@ -8,6 +8,11 @@ interaction kernel, both evaluations of each step counted.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                 [--workload dam_break_32m|dam_break_obstacles_1m|dam_break_6k]
+                [--formulation default|paper]
+
+--formulation paper runs the paper's own kernel and integrator instead (cubic
+spline of Sec. 2.1, second-order Verlet of Sec. 3.3: one force evaluation
+and one rebuild per step).
 
 Under torchrun (N > 1) every rank runs an independent replica (the path has
 no exchange step on one GPU); value = pairs of all ranks / max rank time.
@@ -58,6 +63,27 @@ def workload(name):
 
 def is_ensemble(w):
     return hasattr(w, "members")
+
+
+FORMULATIONS = {"default": ("wendland", "symplectic"), "paper": ("cubic", "verlet")}
+
+
+def with_formulation(w, name):
+    """The workload with the chosen kernel and integrator."""
+    import dataclasses
+    kernel, integrator = FORMULATIONS[name]
+    if is_ensemble(w):
+        w.params.update(kernel=kernel, integrator=integrator)
+        w.cases = [dataclasses.replace(c, kernel=kernel, integrator=integrator) for c in w.cases]
+        return w
+    return dataclasses.replace(w, kernel=kernel, integrator=integrator)
+
+
+def formulation_config(name):
+    if name == "paper":
+        return {"kernel": "cubic spline, h=1.3dp", "integrator":
+                "Verlet (Euler step every 40), 1 evaluation/step"}
+    return {"kernel": "Wendland C2, h=1.3dp", "integrator": "symplectic, 2 evaluations/step"}
 
 
 def peaks():
@@ -191,7 +217,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    case = workload(args.workload)
+    case = with_formulation(workload(args.workload), args.formulation)
     if is_ensemble(case):
         case = case.cases[0]
     import oracle
@@ -214,7 +240,8 @@ def run_reference(args):
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": case.name, "n_particles": case.n,
-                       "n_fluid": case.n_fluid, "dp": case.dp},
+                       "n_fluid": case.n_fluid, "dp": case.dp,
+                       "formulation": args.formulation},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": (f"each step: one oracle interaction evaluation (grid over "
                                         f"all {case.n} particles + pair sums of {count} fluid "
@@ -239,7 +266,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     S.lib(build=True)
-    case = workload(args.workload)
+    case = with_formulation(workload(args.workload), args.formulation)
+    evals_per_step = 1 if args.formulation == "paper" else 2
     if is_ensemble(case):
         sim = S.Simulation.from_ensemble(case, device=local)
     else:
@@ -281,7 +309,7 @@ def run_ours(args):
     steps_per_s = args.steps / (t_max * 1e-3)
 
     # --- dominant kernel: the interaction, timed per launch with events ------
-    nlaunch = 2 * args.steps
+    nlaunch = evals_per_step * args.steps
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nlaunch)]
     dsum = 0.0
     kflop = 0.0
@@ -367,8 +395,8 @@ def run_ours(args):
         cfg = {"workload": case.name, "n_particles": case.n, "n_fluid": case.n_fluid,
                "n_boundary": case.n_bound, "dp": case.dp}
         base_case = case
-    cfg.update({"kernel": "Wendland C2, h=1.3dp", "integrator": "symplectic, 2 evaluations/step",
-                "position_dtype": "f64", "l2": "inputs larger than L2",
+    cfg.update(formulation_config(args.formulation))
+    cfg.update({"formulation": args.formulation, "position_dtype": "f64", "l2": "inputs larger than L2",
                 "parallelism": f"replicas x{ws}", "interaction_variant": variant,
                 "variant_ms": [round(float(v), 3) for v in variant_ms]})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -503,6 +531,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dam_break_32m", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--formulation", default="default", choices=sorted(FORMULATIONS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

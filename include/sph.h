@@ -1,7 +1,7 @@
 /*
  * sph.h -- C ABI of libsph.so, the GB300 (sm_103a) weakly compressible SPH
- * hot path: cell list, pair interaction, CFL time step and symplectic update
- * of a set of particles (Valdez-Balderas, Dominguez, Rogers, Crespo,
+ * hot path: cell list, pair interaction, CFL time step and symplectic (or the
+ * paper's Verlet) update of a set of particles (Valdez-Balderas, Dominguez, Rogers, Crespo,
  * "Towards accelerating SPH simulations for free-surface flows on multi-GPU
  * clusters", single-GPU pipeline of Sec. 3).
  *
@@ -71,16 +71,33 @@ extern "C" {
  *             frozen (counted in sph_diag.n_out)
  *   n_bound   particles with id < n_bound are dynamic boundary particles
  *             (Sec. 2.3): density evolves, position and velocity never do
- *   dt_fixed  > 0: use this step size; otherwise the CFL step */
+ *   scheme    SPH_SCHEME_* bits; 0 = Wendland C2 kernel and the symplectic
+ *             predictor-corrector
+ *   dt_fixed  > 0: use this step size; otherwise the CFL step
+ *   verlet_every  with SPH_SCHEME_VERLET: an Euler step every this many
+ *             steps (0 = 40); see sph_verlet */
 typedef struct sph_params {
     double dp, h, rho0, gamma, c0, alpha, eta2_coef;
     double gravity[3];
     double cfl, mass;
     double dmin[3], dmax[3];
     uint32_t n_bound;
-    uint32_t reserved;
+    uint32_t scheme;
     double dt_fixed;
+    uint32_t verlet_every;
+    uint32_t reserved;     /* must be 0 */
 } sph_params;
+
+/* sph_params.scheme bits: the paper's own formulation.
+ *   SPH_SCHEME_CUBIC   the cubic spline kernel of Sec. 2.1 (the kernel of
+ *                      the paper's results) instead of Wendland C2:
+ *                      W = aD (1 - 3/2 q^2 + 3/4 q^3) for q < 1,
+ *                      aD/4 (2 - q)^3 for 1 <= q < 2, aD = 1/(pi h^3)
+ *   SPH_SCHEME_VERLET  the second-order Verlet integrator of Sec. 3.3 (one
+ *                      force evaluation per step) instead of the symplectic
+ *                      predictor-corrector; see sph_verlet */
+#define SPH_SCHEME_CUBIC   1u
+#define SPH_SCHEME_VERLET  2u
 
 typedef struct sph_sizes {
     uint64_t workspace_bytes;   /* device bytes sph_init needs            */
@@ -198,9 +215,26 @@ int sph_predict(sph_ctx *ctx);
  * e = -dt (drho/dt) / rho_half.  Advances t and the step count.  Async. */
 int sph_correct(sph_ctx *ctx);
 
-/* nsteps full steps: interact, CFL step, predict, rebuild, interact,
- * correct, rebuild (two force evaluations per step).  Builds the cells
- * first if needed.  Async. */
+/* Verlet step of Sec. 3.3 (contexts with SPH_SCHEME_VERLET; SPH_ERR_STATE
+ * otherwise), from the rates of the last sph_interact and the state one step
+ * earlier, in the SPHysics form the paper cites:
+ *   fluid:          r1 = r + dt v + dt^2/2 a
+ *                   v1 = v_prev + 2 dt a     (leapfrog step)
+ *                   v1 = v + dt a            (Euler step)
+ *   every in-domain particle: rho1 = rho_prev + 2 dt drho/dt (leapfrog),
+ *                   rho + dt drho/dt (Euler)
+ * Each member counts its steps from its last sph_upload (or sph_init); step
+ * k is an Euler step when k is a multiple of params.verlet_every, so the
+ * first step after an upload, which has no earlier state, is one.  Boundary
+ * particles keep r and v (Sec. 2.3).  Advances t and the step count and
+ * recomputes the cell labels.  Async.  sph_predict / sph_correct return
+ * SPH_ERR_STATE on these contexts. */
+int sph_verlet(sph_ctx *ctx);
+
+/* nsteps full steps.  Symplectic: interact, CFL step, predict, rebuild,
+ * interact, correct, rebuild (two force evaluations per step).  Verlet:
+ * interact, CFL step, sph_verlet, rebuild (one).  Builds the cells first if
+ * needed.  Async. */
 int sph_step(sph_ctx *ctx, uint32_t nsteps);
 
 /* Run nsteps steps; after every save_every steps (and at the end) wait for
@@ -232,7 +266,9 @@ int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
  *   SPH_ARRAY_NNB64    uint32[n]  neighbour counts with the FP64 predicate
  *                      (sph_neighbour_counts_fp64)
  *   SPH_ARRAY_POSC     float32[4n] cell-relative position and p/rho^2
- *   SPH_ARRAY_DT       float64[n_inst] current step size of each member */
+ *   SPH_ARRAY_DT       float64[n_inst] current step size of each member
+ *   SPH_ARRAY_PREV     float32[4n] (vx, vy, vz, rho) one step earlier, in the
+ *                      order of the state (Verlet contexts after a step) */
 #define SPH_ARRAY_KEY      0
 #define SPH_ARRAY_CELL_OFF 1
 #define SPH_ARRAY_ACE      2
@@ -240,6 +276,7 @@ int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
 #define SPH_ARRAY_NNB64    4
 #define SPH_ARRAY_POSC     5
 #define SPH_ARRAY_DT       6
+#define SPH_ARRAY_PREV     7
 uint64_t sph_array_bytes(const sph_ctx *ctx, int which);
 int sph_read_array(sph_ctx *ctx, int which, void *host, uint64_t bytes);
 

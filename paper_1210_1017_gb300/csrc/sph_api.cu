@@ -109,6 +109,8 @@ int validate_shared(const sph_params* p) {
         !(p->alpha >= 0.0) || !(p->eta2_coef > 0.0))
         return SPH_ERR_INVALID_ARG;
     if (p->gamma != 7.0) return SPH_ERR_INVALID_ARG;   // Tait law of Sec. 2.2
+    if ((p->scheme & ~(SPH_SCHEME_CUBIC | SPH_SCHEME_VERLET)) != 0u || p->reserved != 0u)
+        return SPH_ERR_INVALID_ARG;
     return SPH_OK;
 }
 
@@ -237,6 +239,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->i_steps = cv.take<unsigned long long>(n_inst);
     c->i_terms = cv.take<uint32_t>(3 * (size_t)n_inst);
     c->i_last = cv.take<float>(3 * (size_t)n_inst);
+    c->i_vphase = cv.take<uint32_t>(n_inst);
     return (cv.used + kAlign - 1) / kAlign * kAlign;
 }
 
@@ -256,6 +259,7 @@ Dev make_dev(const sph_ctx* c) {
     d.is.steps = c->i_steps;
     d.is.terms = c->i_terms;
     d.is.last = c->i_last;
+    d.is.vphase = c->i_vphase;
     d.inv_cs = 1.0 / cs;
     d.cs = cs;
     d.r2max_d = cs * cs;
@@ -277,8 +281,15 @@ Dev make_dev(const sph_ctx* c) {
     d.inv_h = (float)(1.0 / p->h);
     d.r2max = (float)(cs * cs);
     d.eta2 = (float)(p->eta2_coef * p->h * p->h);
-    const double aD = 21.0 / (16.0 * M_PI * p->h * p->h * p->h);
-    d.fc = (float)(-5.0 * aD / (p->h * p->h));
+    d.kern = (p->scheme & SPH_SCHEME_CUBIC) ? 1 : 0;
+    if (d.kern == 1) {
+        const double aD = 1.0 / (M_PI * p->h * p->h * p->h);   // cubic spline
+        d.fc = (float)(aD / (p->h * p->h));
+    } else {
+        const double aD = 21.0 / (16.0 * M_PI * p->h * p->h * p->h);   // Wendland C2
+        d.fc = (float)(-5.0 * aD / (p->h * p->h));
+    }
+    d.verlet_every = p->verlet_every ? p->verlet_every : 40u;
     d.alpha = (float)p->alpha;
     d.rho0 = (float)p->rho0;
     d.inv_rho0 = (float)(1.0 / p->rho0);
@@ -330,6 +341,9 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
         ra.dpy = c->py[1];
         ra.dpz = c->pz[1];
         ra.dpvr = c->pvr[1];
+    } else if (c->verlet) {
+        ra.spvr = c->pvr[0];   // (v, rho) one step earlier
+        ra.dpvr = c->pvr[1];
     }
     ra.posc = c->posc;
     ra.hist_to_zero = c->hist;
@@ -375,6 +389,7 @@ IntegrateArgs integrate_args(sph_ctx* c, int pre) {
     a.py = c->py[pre];
     a.pz = c->pz[pre];
     a.pvr = c->pvr[pre];
+    a.pvr_out = c->pvr[0];
     a.key = c->key[0];
     a.cnt = c->cnt;
     a.hist = c->hist;
@@ -396,6 +411,13 @@ void enqueue_build(sph_ctx* c) {
 
 // One full step on the current buffers (state starts and ends in c->cur).
 void enqueue_step(sph_ctx* c) {
+    if (c->verlet) {
+        enqueue_interact(c, false, true);
+        launch_verlet(c->d, integrate_args(c, 1), c->st);
+        c->keys_ready = true;
+        enqueue_build(c);
+        return;
+    }
     enqueue_interact(c, false, true);
     launch_predict(c->d, integrate_args(c, 0), c->st);
     c->keys_ready = true;
@@ -443,6 +465,7 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
         return SPH_ERR_WORKSPACE;
     }
     c->p = *params;
+    c->verlet = (params->scheme & SPH_SCHEME_VERLET) != 0u;
     c->n = (uint32_t)c->tab.n;
     c->n_inst = n_inst;
     c->st = (cudaStream_t)stream;
@@ -479,6 +502,7 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
     cudaMemsetAsync(c->i_steps, 0, n_inst * sizeof(unsigned long long), st);
     cudaMemsetAsync(c->i_terms, 0, 3 * (size_t)n_inst * sizeof(uint32_t), st);
     cudaMemsetAsync(c->i_last, 0, 3 * (size_t)n_inst * sizeof(float), st);
+    cudaMemsetAsync(c->i_vphase, 0, n_inst * sizeof(uint32_t), st);
     cudaMemsetAsync(c->cnt, 0, (c->ncells + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(c->hist, 0, 4 * 256 * sizeof(uint32_t), st);
     cudaMemsetAsync(c->done, 0, sizeof(uint32_t), st);
@@ -548,6 +572,8 @@ int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho
     cudaMemcpyAsync(drho, rho, n * sizeof(float), cudaMemcpyDefault, st);
     cudaMemcpyAsync(c->id[c->cur], ids, n * sizeof(uint32_t), cudaMemcpyDefault, st);
     cudaMemsetAsync(c->id_flag, 0, sizeof(uint32_t), st);
+    // Verlet: the first step after an upload has no earlier state (Euler)
+    cudaMemsetAsync(c->i_vphase, 0, c->n_inst * sizeof(uint32_t), st);
     k_unpack<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(c->n, dpos, dvel, drho, c->x[c->cur],
                                                          c->y[c->cur], c->z[c->cur], c->vr[c->cur],
                                                          c->id[c->cur], c->id_flag);
@@ -582,6 +608,7 @@ int sph_interact(sph_ctx* c, uint32_t flags) {
 
 int sph_predict(sph_ctx* c) {
     if (!c) return SPH_ERR_INVALID_ARG;
+    if (c->verlet) return fail(c, SPH_ERR_STATE, "predict on a Verlet context");
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
     launch_predict(c->d, integrate_args(c, 0), c->st);
     c->keys_ready = true;
@@ -592,6 +619,7 @@ int sph_predict(sph_ctx* c) {
 
 int sph_correct(sph_ctx* c) {
     if (!c) return SPH_ERR_INVALID_ARG;
+    if (c->verlet) return fail(c, SPH_ERR_STATE, "correct on a Verlet context");
     if (!c->cells_valid || c->pre_state != 2)
         return fail(c, SPH_ERR_STATE, "correct needs predict, build_cells and interact first");
     launch_correct(c->d, integrate_args(c, 1), c->st);
@@ -599,6 +627,16 @@ int sph_correct(sph_ctx* c) {
     c->pre_state = 0;
     c->cells_valid = false;
     return post_launch(c, "correct");
+}
+
+int sph_verlet(sph_ctx* c) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!c->verlet) return fail(c, SPH_ERR_STATE, "verlet on a symplectic context");
+    if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "verlet needs build_cells and interact first");
+    launch_verlet(c->d, integrate_args(c, 1), c->st);
+    c->keys_ready = true;
+    c->cells_valid = false;
+    return post_launch(c, "verlet");
 }
 
 int sph_step(sph_ctx* c, uint32_t nsteps) {
@@ -615,21 +653,27 @@ int sph_step(sph_ctx* c, uint32_t nsteps) {
         for (uint32_t s = 0; s < nsteps; ++s) enqueue_step(c);
         return post_launch(c, "step");
     }
-    const int g = c->cur;
-    if (!c->graph[g]) {
-        cudaGraph_t graph;
-        int rc = cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal),
-                            "begin capture");
-        if (rc) return rc;
-        enqueue_step(c);
-        rc = cuda_check(c, cudaStreamEndCapture(c->st, &graph), "end capture");
-        if (rc) return rc;
-        rc = cuda_check(c, cudaGraphInstantiate(&c->graph[g], graph, 0), "instantiate");
-        cudaGraphDestroy(graph);
-        if (rc) return rc;
-        if (c->cur != g) return fail(c, SPH_ERR_STATE, "step changed buffer parity");
-    }
+    // One graph per state-buffer parity the step starts from.  A symplectic
+    // step rebuilds twice and ends on the parity it started from; a Verlet
+    // step rebuilds once, so its steps alternate between the two graphs.
     for (uint32_t s = 0; s < nsteps; ++s) {
+        const int g = c->cur;
+        if (!c->graph[g]) {
+            cudaGraph_t graph;
+            int rc = cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal),
+                                "begin capture");
+            if (rc) return rc;
+            enqueue_step(c);   // host bookkeeping advances as the graph will
+            rc = cuda_check(c, cudaStreamEndCapture(c->st, &graph), "end capture");
+            if (rc) return rc;
+            rc = cuda_check(c, cudaGraphInstantiate(&c->graph[g], graph, 0), "instantiate");
+            cudaGraphDestroy(graph);
+            if (rc) return rc;
+            if ((c->cur != g) != c->verlet)
+                return fail(c, SPH_ERR_STATE, "step changed buffer parity");
+        } else if (c->verlet) {
+            c->cur = 1 - g;
+        }
         int rc = cuda_check(c, cudaGraphLaunch(c->graph[g], c->st), "graph launch");
         if (rc) return rc;
     }
@@ -707,6 +751,7 @@ uint64_t sph_array_bytes(const sph_ctx* c, int which) {
         case SPH_ARRAY_CELL_OFF: return (c->ncells + 2) * 4;
         case SPH_ARRAY_ACE:
         case SPH_ARRAY_POSC: return (uint64_t)c->n * 16;
+        case SPH_ARRAY_PREV: return c->verlet ? (uint64_t)c->n * 16 : 0;
         case SPH_ARRAY_DT: return 8ull * c->n_inst;
         default: return 0;
     }
@@ -725,6 +770,8 @@ int sph_read_array(sph_ctx* c, int which, void* host, uint64_t bytes) {
         case SPH_ARRAY_NNB64: src = c->nnb64; break;
         case SPH_ARRAY_POSC: src = c->posc; break;
         case SPH_ARRAY_DT: src = c->i_dt; break;
+        // in the state's order: after a rebuild the reordered copy
+        case SPH_ARRAY_PREV: src = c->cells_valid ? c->pvr[1] : c->pvr[0]; break;
     }
     int rc = cuda_check(c, cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, c->st), "read array");
     if (rc) return rc;
@@ -870,9 +917,13 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
-    // 2 x (interact + reduce) + predict + correct
-    // + 2 x (3 cell scan + passes + 5 unit list + reorder)
-    return 2u * 2u + 2u + 2u * (3u + (uint32_t)c->passes + 5u + 1u);
+    // one rebuild: 3 cell scan + passes + 6 unit list (row sums, count, 3 scan,
+    // fill) + reorder
+    const uint32_t rebuild = 3u + (uint32_t)c->passes + 6u + 1u;
+    // Verlet: interact + reduce + update + member advance + rebuild
+    if (c->verlet) return 2u + 2u + rebuild;
+    // symplectic: 2 x (interact + reduce) + predict + correct + 2 rebuilds
+    return 2u * 2u + 2u + 2u * rebuild;
 }
 
 const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

@@ -60,6 +60,7 @@ struct sph_ctx {
     uint32_t *i_done, *i_terms;
     unsigned long long* i_steps;
     float* i_last;
+    uint32_t* i_vphase;      // Verlet phase per member
     size_t os_bytes = 0;
     // bookkeeping
     int variant = 0;         // interaction block shape (see sph_autotune)
@@ -70,6 +71,8 @@ struct sph_ctx {
     bool cells_valid = false;
     bool keys_ready = false; // labels + histograms already computed
     int pre_state = 0;       // 0 none, 1 in px[0] (unsorted), 2 in px[1] (sorted)
+    bool verlet = false;     // Verlet integrator: pvr[0] / pvr[1] hold (v, rho) one
+                             // step earlier, before / after the reorder
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
 };

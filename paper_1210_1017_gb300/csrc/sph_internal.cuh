@@ -44,6 +44,8 @@ struct InstState {
     uint32_t* terms;        // 3 per instance, float bits of the running maxima of
                             // |a|^2, c and mu over the current evaluation
     float* last;            // 3 per instance: max |a|, max c, max mu of the last one
+    uint32_t* vphase;       // Verlet: steps since the last Euler step (0: the next
+                            // step is an Euler step); reset by an upload
 };
 
 // Per-context constants handed to kernels by value.
@@ -71,7 +73,10 @@ struct Dev {
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
     float eta2;            // eta^2
-    float fc;              // -5 aD / h^2 (Wendland C2 gradient factor)
+    float fc;              // gradient factor: -5 aD/h^2 (Wendland C2) or aD/h^2
+                           // (cubic spline, aD = 1/(pi h^3))
+    int kern;              // 0: Wendland C2, 1: cubic spline (Sec. 2.1)
+    uint32_t verlet_every; // Verlet: an Euler step every this many steps
     float alpha, rho0, inv_rho0, mass;
     float gx, gy, gz;
 };
@@ -172,6 +177,7 @@ struct IntegrateArgs {
     const float4* ace;
     double *px, *py, *pz;    // pre state: written by predict, read by correct
     float4* pvr;
+    float4* pvr_out;         // Verlet: receives (v, rho) on entry
     uint32_t* key;
     uint32_t* cnt;
     uint32_t* hist;
@@ -179,6 +185,10 @@ struct IntegrateArgs {
 };
 void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st);
 void launch_correct(const Dev& d, const IntegrateArgs& a, cudaStream_t st);
+// Verlet: pvr holds (v, rho) one step earlier (sorted like the state),
+// pvr_out receives the state's (v, rho) on entry; px.. are unused.  Then
+// each member's time, step count and Verlet phase advance.
+void launch_verlet(const Dev& d, const IntegrateArgs& a, cudaStream_t st);
 
 void launch_counts_fp64(const Dev& d, const double* x, const double* y, const double* z,
                         const uint32_t* key, const uint32_t* off, uint32_t* out,

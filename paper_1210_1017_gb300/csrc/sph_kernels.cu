@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
         a.dpx[dst] = a.spx[v];
         a.dpy[dst] = a.spy[v];
         a.dpz[dst] = a.spz[v];
-        a.dpvr[dst] = a.spvr[v];
     }
+    if (a.spvr) a.dpvr[dst] = a.spvr[v];
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < d.ncells) {
         const Inst& I = d.inst[find_instance(d.cell_base, d.n_inst, c)];
@@ -308,7 +308,8 @@ __constant__ KeepTable c_keep = make_keep_table();
 // itself, placed 4 cells away) contributes exactly nothing and is not
 // counted, which lets lane work be padded with it.  Masks are products with
 // 0 or 1 rather than selects, keeping the integer/logic pipe free.
-template <bool MOM, bool CHECK = false>
+// KERN: 0 Wendland C2, 1 cubic spline (Sec. 2.1).
+template <int KERN, bool MOM, bool CHECK = false>
 __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4& pi,
                                            const float4& vi, float ci, float dx, float dy, float dz,
                                            const float4& pj, const float4& vj, PairAcc& s) {
@@ -319,10 +320,21 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
     // the saturated sign of 2^100 ((2h)^2 - d2), exact (power-of-two scaling)
     const float use = CHECK ? __saturatef(fmaf(d2, -0x1p100f, d.r2max * 0x1p100f)) : 1.f;
     if (CHECK) s.npf += use;
-    // Wendland C2: grad_i W = F r_ij, F = -5 aD/h^2 (1 - q/2)^3
+    // grad_i W = F r_ij.  Wendland C2: F = -5 aD/h^2 (1 - q/2)^3.  Cubic
+    // spline: F = aD/h^2 (9/4 q - 3) for q < 1, -3/4 aD/h^2 (2 - q)^2 / q
+    // for 1 <= q < 2 (a select: the outer piece is infinite at q = 0).
     const float q = sqrt_approx(d2) * d.inv_h;
-    const float wq = fmaf(-0.5f, q, 1.0f);
-    const float F = CHECK ? d.fc * (wq * wq * wq) * use : d.fc * (wq * wq * wq);
+    float shape;
+    if (KERN == 1) {
+        const float wo = 2.0f - q;
+        const float outer = -0.75f * (wo * wo) * rcp_approx(q);
+        const float inner = fmaf(2.25f, q, -3.0f);
+        shape = q < 1.0f ? inner : outer;
+    } else {
+        const float wq = fmaf(-0.5f, q, 1.0f);
+        shape = wq * wq * wq;
+    }
+    const float F = CHECK ? d.fc * shape * use : d.fc * shape;
     const float dvx = vi.x - vj.x, dvy = vi.y - vj.y, dvz = vi.z - vj.z;
     const float vr = fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz));
     s.dr = fmaf(vr, F, s.dr);                                      // Eq. 7
@@ -363,7 +375,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
 // keeps a similar share of its own neighbours in each part); the parts' sums
 // are added in a fixed order at the end.  More warps per block at the same
 // staging footprint.
-template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT>
+template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     constexpr int NT = W * SPLIT * 32;
     constexpr int FBCAP = Shape<W * SPLIT, STAGE, WCAP>::fb_cap;   // fallback list slots
@@ -605,13 +617,15 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     if (anyfluid) {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<true, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
-                                                   pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc);
+                            pair_terms<KERN, true, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
+                                                         pi.y - pp[k].y, pi.z - pp[k].z, pp[k],
+                                                         vv[k], acc);
                     } else {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
-                            pair_terms<false, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
-                                                    pi.y - pp[k].y, pi.z - pp[k].z, pp[k], vv[k], acc);
+                            pair_terms<KERN, false, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
+                                                          pi.y - pp[k].y, pi.z - pp[k].z, pp[k],
+                                                          vv[k], acc);
                     }
                 }
                 __syncwarp();   // every lane is done reading before the words are reused
@@ -693,9 +707,9 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                         const float oz = (float)((int)(e >> 30) - 1);
                         const float4 pj = __ldg(a.posc + j);
                         const float4 vj = __ldg(a.velrhop + j);
-                        pair_terms<true>(d, c0, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
-                                         fmaf(oy, d.csf, pi.y) - pj.y, fmaf(oz, d.csf, pi.z) - pj.z,
-                                         pj, vj, acc);
+                        pair_terms<KERN, true>(d, c0, pi, vi, ci, fmaf(ox, d.csf, pi.x) - pj.x,
+                                               fmaf(oy, d.csf, pi.y) - pj.y,
+                                               fmaf(oz, d.csf, pi.z) - pj.z, pj, vj, acc);
                     }
                 }
                 acc.np += cnt;
@@ -1133,6 +1147,76 @@ __global__ void __launch_bounds__(256) k_correct(const Dev d, const IntegrateArg
     flush_hist(s_hist, a.hist, a.passes);
 }
 
+// Verlet step of Sec. 3.3 (the SPHysics form) for sorted particle k, from
+// the rates at S^n and (v, rho) one step earlier (a.pvr, sorted like the
+// state), then the new label:
+//   fluid:   r1 = r + dt v + dt^2/2 a (increment in FP32, r in FP64)
+//            v1 = v_prev + 2 dt a   (leapfrog) | v + dt a   (Euler step)
+//   all:     rho1 = rho_prev + 2 dt drho       | rho + dt drho
+// The member's Verlet phase picks the Euler step (phase 0).  a.pvr_out
+// receives the (v, rho) on entry.  Members that are done (dt = 0) and
+// excluded particles keep their state.
+__global__ void __launch_bounds__(256) k_verlet(const Dev d, const IntegrateArgs a) {
+    __shared__ uint32_t s_hist[4 * 256];
+    zero_hist(s_hist);
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < d.n;
+    uint32_t key = 0;
+    if (valid) {
+        const uint32_t n_in = a.off[d.ncells];
+        key = d.ncells;
+        if (k < n_in) {
+            const uint32_t id = a.id[k];
+            const uint32_t q = find_instance(d.id_base, d.n_inst, id);
+            const Inst& I = d.inst[q];
+            const double dt = d.is.dt[q];
+            double x = a.x[k], y = a.y[k], z = a.z[k];
+            const float4 vr = a.velrhop[k];
+            if (dt > 0.0) {
+                const bool euler = d.is.vphase[q] == 0u;
+                const float4 pv = euler ? vr : a.pvr[k];
+                const float dtf = (float)dt;
+                const float dtv = euler ? dtf : (float)(2.0 * dt);
+                const float hdt2 = (float)(0.5 * dt * dt);
+                const float4 ac = a.ace[k];
+                float4 nv = vr;
+                if (id >= I.id_fluid) {
+                    x += (double)fmaf(hdt2, ac.x, dtf * vr.x);
+                    y += (double)fmaf(hdt2, ac.y, dtf * vr.y);
+                    z += (double)fmaf(hdt2, ac.z, dtf * vr.z);
+                    a.x[k] = x;
+                    a.y[k] = y;
+                    a.z[k] = z;
+                    nv.x = fmaf(dtv, ac.x, pv.x);
+                    nv.y = fmaf(dtv, ac.y, pv.y);
+                    nv.z = fmaf(dtv, ac.z, pv.z);
+                }
+                nv.w = fmaf(dtv, ac.w, pv.w);
+                a.velrhop[k] = nv;
+                a.pvr_out[k] = vr;
+            }
+            key = cell_key(d, I, x, y, z);
+        }
+        a.key[k] = key;
+    }
+    count_key(valid, key, a.cnt, s_hist, a.passes, bits_for(d.ncells));
+    flush_hist(s_hist, a.hist, a.passes);
+}
+
+// After k_verlet: each running member's time, step count and Verlet phase
+// (0 again after verlet_every steps) advance.
+__global__ void __launch_bounds__(256) k_verlet_advance(const Dev d) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < d.n_inst && !d.is.done[q]) {
+        const double t = d.is.t[q] + d.is.dt[q];
+        d.is.t[q] = t;
+        d.is.steps[q] += 1ull;
+        const uint32_t ph = d.is.vphase[q] + 1u;
+        d.is.vphase[q] = ph >= d.verlet_every ? 0u : ph;
+        if (t >= d.inst[q].t_end) d.is.done[q] = 1u;
+    }
+}
+
 // Neighbour counts with the FP64 predicate (dx*dx + dy*dy) + dz*dz < (2h)^2,
 // every operation rounded as written.
 __global__ void __launch_bounds__(256) k_counts_fp64(const Dev d, const double* __restrict__ x,
@@ -1262,17 +1346,19 @@ struct Variant {
     int warps;              // warps of particles (the unit is warps x 32 particles)
     int split;              // warps per group of 32 particles
     int stage;              // staged candidates
-    KernelPtr plain, counted;
+    KernelPtr fn[2][2];     // [kernel: Wendland C2, cubic spline][with counts]
     size_t smem;
     int grid;   // persistent grid on this GPU (set by prepare_interact)
 };
 
 // (warps, staged candidates, hit-mask words per lane, resident blocks per SM
 // that the shared memory allows -- also the register budget hint)
-#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv)                                                \
-    Variant {                                                                         \
-        Wv, Pv, Sv, k_interact<Wv, Sv, Cv, Bv, false, Pv>, k_interact<Wv, Sv, Cv, Bv, true, Pv>, \
-            Shape<Wv * Pv, Sv, Cv>::smem, 0                                           \
+#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv)                                               \
+    Variant {                                                                        \
+        Wv, Pv, Sv,                                                                  \
+            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0>, k_interact<Wv, Sv, Cv, Bv, true, Pv, 0>}, \
+             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1>, k_interact<Wv, Sv, Cv, Bv, true, Pv, 1>}}, \
+            Shape<Wv * Pv, Sv, Cv>::smem, 0                                          \
     }
 
 Variant g_variants[kNumVariants] = {
@@ -1299,17 +1385,25 @@ void prepare_interact() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (Variant& v : g_variants) {
-        cudaFuncSetAttribute(v.plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
-        cudaFuncSetAttribute(v.counted, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        for (int k = 0; k < 2; ++k)
+            for (int c = 0; c < 2; ++c)
+                cudaFuncSetAttribute(v.fn[k][c], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)v.smem);
+        // one grid for both kernels of the shape: the smaller residency
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.plain, v.warps * v.split * 32, v.smem);
+        for (int k = 0; k < 2; ++k) {
+            int r = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, v.fn[k][0], v.warps * v.split * 32,
+                                                          v.smem);
+            per_sm = k == 0 || r < per_sm ? r : per_sm;
+        }
         v.grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
 }
 
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st) {
     const Variant& v = g_variants[d.variant];
-    (counts ? v.counted : v.plain)<<<v.grid, v.warps * v.split * 32, v.smem, st>>>(d, a);
+    v.fn[d.kern == 1 ? 1 : 0][counts ? 1 : 0]<<<v.grid, v.warps * v.split * 32, v.smem, st>>>(d, a);
 }
 
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
@@ -1331,6 +1425,11 @@ void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
 void launch_correct(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
     const uint32_t n = d.n > d.n_inst ? d.n : d.n_inst;
     k_correct<<<blocks_for(n, 256), 256, 0, st>>>(d, a);
+}
+
+void launch_verlet(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
+    k_verlet<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
+    k_verlet_advance<<<blocks_for(d.n_inst, 256), 256, 0, st>>>(d);
 }
 
 void launch_counts_fp64(const Dev& d, const double* x, const double* y, const double* z,

@@ -22,14 +22,15 @@ KERNEL_REV = "interact-v4.10"
 SPH_OK = 0
 SPH_INTERACT_COUNTS = 1
 SPH_ARRAY_KEY, SPH_ARRAY_CELL_OFF, SPH_ARRAY_ACE, SPH_ARRAY_NNB = 0, 1, 2, 3
-SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT = 4, 5, 6
+SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT, SPH_ARRAY_PREV = 4, 5, 6, 7
+SPH_SCHEME_CUBIC, SPH_SCHEME_VERLET = 1, 2
 ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
           -4: "SPH_ERR_TIMEOUT", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_CAPACITY",
           -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE"}
 SPH_RADIX_SORT_STATIC_MAX_N = 1 << 20
 
 EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph_download_by_id",
-            "sph_interact", "sph_predict", "sph_correct", "sph_step",
+            "sph_interact", "sph_predict", "sph_correct", "sph_verlet", "sph_step",
             "sph_rollout", "sph_download", "sph_array_bytes", "sph_read_array",
             "sph_neighbour_counts_fp64", "sph_diagnostics", "sph_check",
             "sph_kernels_per_step", "sph_last_error", "sph_destroy",
@@ -44,8 +45,9 @@ class SphParams(C.Structure):
                 ("eta2_coef", C.c_double), ("gravity", C.c_double * 3),
                 ("cfl", C.c_double), ("mass", C.c_double),
                 ("dmin", C.c_double * 3), ("dmax", C.c_double * 3),
-                ("n_bound", C.c_uint32), ("reserved", C.c_uint32),
-                ("dt_fixed", C.c_double)]
+                ("n_bound", C.c_uint32), ("scheme", C.c_uint32),
+                ("dt_fixed", C.c_double), ("verlet_every", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class SphInstance(C.Structure):
@@ -114,6 +116,7 @@ def lib(build: bool = False):
     L.sph_interact.argtypes = [vp, u32]
     L.sph_predict.argtypes = [vp]
     L.sph_correct.argtypes = [vp]
+    L.sph_verlet.argtypes = [vp]
     L.sph_step.argtypes = [vp, u32]
     L.sph_rollout.argtypes = [vp, u32, u32, SNAPSHOT_FN, vp]
     L.sph_download.argtypes = [vp, vp, vp, vp, vp]
@@ -170,6 +173,12 @@ def make_params(p: dict, dt_fixed: float = 0.0) -> SphParams:
     s.cfl, s.mass = p["cfl"], p["mass"]
     s.n_bound = int(p["n_bound"])
     s.dt_fixed = float(p.get("dt_fixed", dt_fixed))
+    kernel, integ = p.get("kernel", "wendland"), p.get("integrator", "symplectic")
+    if kernel not in ("wendland", "cubic") or integ not in ("symplectic", "verlet"):
+        raise ValueError(f"unknown formulation: kernel {kernel!r}, integrator {integ!r}")
+    s.scheme = (SPH_SCHEME_CUBIC if kernel == "cubic" else 0) | \
+        (SPH_SCHEME_VERLET if integ == "verlet" else 0)
+    s.verlet_every = int(p.get("verlet_every", 40))
     return s
 
 
@@ -271,6 +280,10 @@ def sph_predict(ctx):
 
 def sph_correct(ctx):
     _check(lib().sph_correct(ctx), ctx, "sph_correct")
+
+
+def sph_verlet(ctx):
+    _check(lib().sph_verlet(ctx), ctx, "sph_verlet")
 
 
 def sph_step(ctx, nsteps: int = 1):
@@ -453,6 +466,9 @@ class Simulation:
     def correct(self):
         sph_correct(self.ctx)
 
+    def verlet(self):
+        sph_verlet(self.ctx)
+
     def step(self, nsteps=1):
         sph_step(self.ctx, nsteps)
 
@@ -495,7 +511,8 @@ class Simulation:
                   SPH_ARRAY_CELL_OFF: ((int(self.sizes.ncells) + 2,), np.uint32),
                   SPH_ARRAY_ACE: ((n, 4), np.float32), SPH_ARRAY_NNB: ((n,), np.uint32),
                   SPH_ARRAY_NNB64: ((n,), np.uint32), SPH_ARRAY_POSC: ((n, 4), np.float32),
-                  SPH_ARRAY_DT: ((self.n_inst,), np.float64)}
+                  SPH_ARRAY_DT: ((self.n_inst,), np.float64),
+                  SPH_ARRAY_PREV: ((n, 4), np.float32)}
         shape, dt = shapes[which]
         return sph_read_array(self.ctx, which, np.empty(shape, dt))
 

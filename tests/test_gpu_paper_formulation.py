@@ -1,0 +1,254 @@
+"""The paper's own formulation on the GPU, through the C ABI, against the FP64
+oracle: the cubic spline kernel (Sec. 2.1) in the interaction and the
+second-order Verlet integrator (Sec. 3.3).
+
+Bars as for the default formulation: density rates and accelerations within
+2e-5 of the sum of the magnitudes of their pair terms; the Verlet update
+within FP32 rounding of its increments; the earlier state it keeps bit for
+bit; a free-running dam break within 1e-3 dp of the oracle's; ensemble
+members bit-identical to their stand-alone runs.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401
+import oracle
+from paper_1210_1017_gb300 import cases
+from paper_1210_1017_gb300 import sph as S
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    yield
+
+
+def _paper(case, kernel="cubic", integrator="verlet", every=40):
+    return dataclasses.replace(case, kernel=kernel, integrator=integrator, verlet_every=every)
+
+
+CASES = [
+    ("random_64", lambda: cases.random_block(64, seed=7)),
+    ("random_777", lambda: cases.random_block(777, seed=8, jitter=0.4)),
+    ("random_2000", lambda: cases.random_block(2000, seed=9, jitter=0.3)),
+    ("dam_break_6k", lambda: cases.c1_dam_break(shuffle_seed=3)),
+    # about 200 particles per cell: the global-memory path of the interaction
+    ("dense_h3dp", lambda: cases.random_block(3000, seed=5, h_over_dp=3.0, jitter=0.2)),
+]
+
+
+def _state(sim):
+    st = sim.download()
+    return st, oracle.State(st["pos"], st["vel"], st["rho"], st["ids"])
+
+
+def _rate_errors(ace, ref, fluid):
+    ea = np.linalg.norm(ace[fluid, :3] - ref["a"][fluid], axis=1) / ref["sa"][fluid]
+    ed = np.abs(ace[:, 3] - ref["drho"]) / np.where(ref["sd"] > 0, ref["sd"], 1.0)
+    gl = np.linalg.norm(ace[fluid, :3] - ref["a"][fluid]) / np.linalg.norm(ref["a"][fluid])
+    return ea, ed, gl
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_cubic_spline_interaction_within_2e5(name, make):
+    case = _paper(make(), integrator="symplectic")
+    sim = S.Simulation.from_case(case)
+    sim.build_cells()
+    sim.interact()
+    ace = sim.read(S.SPH_ARRAY_ACE)
+    st, ost = _state(sim)
+    ref = oracle.Oracle(case.params()).interact(ost, brute=case.n <= 2000)
+    fluid = st["ids"] >= case.n_bound
+    ea, ed, gl = _rate_errors(ace, ref, fluid)
+    print(f"{name} cubic: |a| {ea.max():.2e} drho {ed.max():.2e} global {gl:.2e}")
+    assert ea.max() <= REL_TOL and ed.max() <= REL_TOL and gl <= REL_TOL
+    # the kernel is really the cubic spline: the Wendland accelerations
+    # differ (density rates vanish for a state at rest)
+    wref = oracle.Oracle(dataclasses.replace(case, kernel="wendland").params()).interact(ost)
+    assert np.abs(wref["a"] - ref["a"]).max() > 1e-3 * np.abs(ref["a"]).max()
+    sim.close()
+
+
+def test_cubic_spline_every_variant_within_2e5():
+    case = _paper(cases.c1_dam_break(shuffle_seed=4))
+    sim = S.Simulation.from_case(case)
+    sim.step(10)
+    st, ost = _state(sim)
+    ref = oracle.Oracle(case.params()).interact(ost)
+    fluid = st["ids"] >= case.n_bound
+    for v in range(S.sph_num_variants()):
+        sim.set_variant(v)
+        sim.interact()
+        ea, ed, gl = _rate_errors(sim.read(S.SPH_ARRAY_ACE), ref, fluid)
+        print(f"variant {v}: {ea.max():.2e} {ed.max():.2e} {gl:.2e}")
+        assert ea.max() <= REL_TOL and ed.max() <= REL_TOL and gl <= REL_TOL
+    sim.close()
+
+
+def _update_ok(got, want, start, what):
+    """Positions within FP32 rounding of the increment, velocities and
+    densities within FP32 rounding of their values."""
+    disp = np.abs(want.pos() - start.pos()).max()
+    ep = np.abs(got["pos"] - want.pos()).max()
+    ev = np.abs(got["vel"] - want.vel()).max()
+    er = np.abs(got["rho"] - want.rho).max()
+    print(f"{what}: pos {ep / disp:.2e} of the step, vel {ev:.2e}, rho {er:.2e}")
+    assert ep <= 1e-6 * disp + 1e-15
+    assert ev <= 2e-7 * (np.abs(want.vel()).max() + 1)
+    assert er <= 2e-7 * want.rho.max()
+
+
+def test_verlet_euler_then_leapfrog_steps_match_the_oracle():
+    case = _paper(cases.random_block(1500, seed=21, jitter=0.3, vel_range=0.8),
+                  kernel="wendland")
+    O = oracle.Oracle(case.params())
+    sim = S.Simulation.from_case(case)
+    # step 0: an Euler step (no earlier state yet)
+    sim.build_cells()
+    sim.interact()
+    s0, o0 = _state(sim)
+    ace0 = sim.read(S.SPH_ARRAY_ACE).astype(np.float64)
+    dt0 = float(sim.read(S.SPH_ARRAY_DT)[0])
+    sim.verlet()
+    s1 = sim.download()                       # same order: no rebuild yet
+    prev = o0.copy()
+    o1 = O.verlet_update(o0.copy(), prev, ace0[:, :3], ace0[:, 3], dt0, euler=True)
+    _update_ok(s1, o1, o0, "Euler step")
+    # the earlier state kept for the next step is the state on entry
+    p1 = sim.read(S.SPH_ARRAY_PREV)
+    assert np.array_equal(p1[:, :3], s0["vel"]) and np.array_equal(p1[:, 3], s0["rho"])
+    # step 1: a leapfrog step, at the reordered state
+    sim.build_cells()
+    sim.interact()
+    s1b, o1b = _state(sim)
+    ace1 = sim.read(S.SPH_ARRAY_ACE).astype(np.float64)
+    dt1 = float(sim.read(S.SPH_ARRAY_DT)[0])
+    pr = sim.read(S.SPH_ARRAY_PREV)
+    k0 = {int(i): j for j, i in enumerate(s0["ids"])}
+    idx = np.array([k0[int(i)] for i in s1b["ids"]])
+    assert np.array_equal(pr[:, :3], s0["vel"][idx]) and np.array_equal(pr[:, 3], s0["rho"][idx])
+    prev = oracle.State(s1b["pos"], pr[:, :3], pr[:, 3], s1b["ids"])
+    sim.verlet()
+    s2 = sim.download()
+    o2 = O.verlet_update(o1b.copy(), prev, ace1[:, :3], ace1[:, 3], dt1, euler=False)
+    _update_ok(s2, o2, o1b, "leapfrog step")
+    b = s2["ids"] < case.n_bound
+    assert np.array_equal(s2["pos"][b], s1b["pos"][b]) and np.all(s2["vel"][b] == s1b["vel"][b])
+    d = sim.diagnostics()
+    assert d["step"] == 2 and d["t"] == pytest.approx(dt0 + dt1, rel=1e-15)
+    sim.close()
+
+
+def test_verlet_dam_break_200_steps_tracks_the_oracle():
+    """Cubic spline and Verlet (an Euler step every 40 steps), 200 steps of
+    the 6,000-fluid-particle dam break, free-running on both sides."""
+    case = _paper(cases.c1_dam_break())
+    O = oracle.Oracle(case.params())
+    ost = oracle.State.from_case(case)
+    dts, _ = O.verlet_run(ost, 200, every=40)
+    sim = S.Simulation.from_case(case)
+    sim.step(200)
+    st = sim.download()
+    d = sim.diagnostics()
+    k = np.argsort(st["ids"])
+    rms = np.sqrt(((st["pos"][k] - ost.pos()) ** 2).sum(1).mean())
+    print(f"Verlet 200 steps: t_gpu={d['t']:.6f} t_ref={sum(dts):.6f} rms/dp={rms / case.dp:.3e}")
+    assert d["t"] == pytest.approx(sum(dts), rel=1e-4)
+    assert rms < 1e-3 * case.dp
+    assert d["step"] == 200 and d["status"] == 0 and d["n_out"] == 0
+    assert d["mass"] == pytest.approx(case.n * case.mass, rel=1e-12)
+    b = st["ids"] < case.n_bound
+    assert np.array_equal(st["pos"][b], case.pos[st["ids"][b]])
+    sim.close()
+
+
+def test_verlet_free_fall_of_a_single_particle():
+    pos = np.array([[0.5, 0.5, 2.0]])
+    dp, h = 0.02, 0.026
+    dmin, dmax = (0.4, 0.4, 1.0), (0.6, 0.6, 2.2)
+    case = cases.Case(name="one", pos=pos, vel=np.zeros((1, 3), np.float32),
+                      rho=np.full(1, 1000.0, np.float32), ids=np.zeros(1, np.uint32),
+                      n_bound=0, dp=dp, h=h, rho0=1000.0, c0=20.0, alpha=0.01, cfl=0.2,
+                      gravity=(0.0, 0.0, -9.81), dmin=dmin, dmax=dmax, fluid_height=0.0,
+                      integrator="verlet", verlet_every=7)
+    sim = S.Simulation.from_case(case, dt_fixed=2e-4)
+    sim.step(200)
+    st = sim.download()
+    t = sim.diagnostics()["t"]
+    assert t == pytest.approx(0.04, rel=1e-12)
+    # exact for constant acceleration up to the FP32 rounding of v and of
+    # the FP32 position increments
+    assert abs(st["pos"][0, 2] - (2.0 - 0.5 * 9.81 * t * t)) < 1e-6
+    assert st["vel"][0, 2] == pytest.approx(-9.81 * t, rel=1e-5)
+    assert st["pos"][0, 0] == 0.5 and st["pos"][0, 1] == 0.5
+    sim.close()
+
+
+def test_ensemble_members_reproduce_standalone_verlet_runs():
+    """Each member keeps its own Verlet phase and step size."""
+    members = [_paper(cases.ensemble_instance(s), every=5)
+               for s in cases.ensemble_specs(3, seed=99)]
+    ens = cases.ensemble(members)
+    sim = S.Simulation.from_ensemble(ens)
+    sim.step(12)
+    st = sim.download()
+    k = np.argsort(st["ids"])
+    ist = sim.instance_state()
+    sim.close()
+    assert np.all(ist["steps"] == 12)
+    for q, case in enumerate(members):
+        alone = S.Simulation.from_case(case)
+        alone.step(12)
+        a = alone.download()
+        ka = np.argsort(a["ids"])
+        alone.close()
+        sl = ens.member_slice(q)
+        assert np.array_equal(st["pos"][k][sl], a["pos"][ka])
+        assert np.array_equal(st["vel"][k][sl], a["vel"][ka])
+        assert np.array_equal(st["rho"][k][sl], a["rho"][ka])
+
+
+def test_scheme_entry_points_are_exclusive():
+    sym = S.Simulation.from_case(cases.random_block(200, seed=3))
+    ver = S.Simulation.from_case(_paper(cases.random_block(200, seed=3)))
+    for sim in (sym, ver):
+        sim.build_cells()
+        sim.interact()
+    with pytest.raises(S.SphError, match="SPH_ERR_STATE"):
+        sym.verlet()
+    with pytest.raises(S.SphError, match="SPH_ERR_STATE"):
+        ver.predict()
+    # no earlier state on a symplectic context
+    assert S.lib().sph_array_bytes(sym.ctx, S.SPH_ARRAY_PREV) == 0
+    assert S.lib().sph_array_bytes(ver.ctx, S.SPH_ARRAY_PREV) == 16 * ver.n
+    # one evaluation per Verlet step, two per symplectic step
+    assert sym.kernels_per_step() - ver.kernels_per_step() == 2 + (sym.kernels_per_step() - 6) // 2
+    sym.close()
+    ver.close()
+
+
+def test_verlet_graph_and_direct_launch_paths_agree():
+    """A Verlet step rebuilds once, so graph replays alternate between the
+    two state-buffer parities; both must equal kernel-by-kernel launches."""
+    import torch
+    case = _paper(cases.c1_dam_break(), every=3)
+    sims = [S.Simulation.from_case(case),
+            S.Simulation.from_case(case, stream=torch.cuda.default_stream(0))]
+    sts = []
+    for sim in sims:
+        sim.step(4)
+        sim.step(3)
+        sts.append(sim.download())
+        assert sim.diagnostics()["step"] == 7
+        sim.close()
+    for key in ("ids", "pos", "vel", "rho"):
+        assert np.array_equal(sts[0][key], sts[1][key])
