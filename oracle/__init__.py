@@ -89,6 +89,9 @@ def lib():
         L.or_verlet_step.argtypes = [P, C.c_int64] + [dp] * 11 + [u32, C.c_double,
                                                                   C.c_int, C.c_int, i64]
         L.or_verlet_step.restype = C.c_double
+        L.or_subdomain_labels.argtypes = [P, C.c_int64, dp, dp, dp, C.c_int, C.c_double,
+                                          C.c_double, u32]
+        L.or_subdomain_labels.restype = C.c_int64
         L.or_diagnostics.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp,
                                      u32, dp]
         L.or_num_threads.restype = C.c_int
@@ -308,6 +311,28 @@ class Oracle:
             dt, _ = self.verlet_step(st, prev, k % every == 0, dt_fixed=dt_fixed)
             dts.append(dt)
         return dts, prev
+
+    def subdomain_labels(self, pos, mode, xlo, xhi):
+        """Sec. 4.2-4.3 labels (mode 0: edge, 1: migration) of a 1-D
+        decomposition along x for the sub-domain [xlo, xhi)."""
+        pos = np.asarray(pos, dtype=np.float64)
+        x, y, z = (np.ascontiguousarray(pos[:, a]) for a in range(3))
+        lab = np.zeros(pos.shape[0], dtype=np.uint32)
+        self.L.or_subdomain_labels(C.byref(self.P), pos.shape[0], _d(x), _d(y), _d(z),
+                                   int(mode), float(xlo), float(xhi), _u(lab))
+        return lab
+
+    def subdomain_select(self, pos, ids, mode, xlo, xhi):
+        """Labels, then the paper's (label, id) order; returns the labels,
+        the counts per label and the input indices of the particles labelled
+        1 or 2 in that order (the data a sub-domain sends)."""
+        lab = self.subdomain_labels(pos, mode, xlo, xhi)
+        perm = self.sort_by_key_id(lab, ids)
+        key, _ = self.cell_keys(pos)
+        inside = key != self.ncells          # particles of the cell-grid domain
+        counts = np.array([np.sum((lab == v) & inside) for v in range(3)], dtype=np.int64)
+        sel = perm[lab[perm] != 0]
+        return lab, counts, sel
 
     def diagnostics(self, st: State):
         out = np.zeros(8, dtype=np.float64)

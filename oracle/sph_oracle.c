@@ -603,6 +603,43 @@ double or_verlet_step(const or_params *P, int64_t n, double *x, double *y,
     return dt;
 }
 
+/* Sec. 4.2-4.3: labels of a one-dimensional decomposition along x, for the
+ * sub-domain [xlo, xhi) that holds this particle set.
+ *   mode 0, edge (the data that builds the neighbours' halos):
+ *       1 if xlo <= x < xlo + 2h   (left edge)
+ *       2 if xhi - 2h <= x < xhi   (right edge)
+ *       0 otherwise
+ *   mode 1, migration: 1 if x < xlo (moved to the left neighbour),
+ *       2 if x >= xhi (moved to the right neighbour), 0 otherwise.
+ * xlo + 2h and xhi - 2h are each rounded once.  The edge mode needs
+ * xhi - xlo >= 4h, so that no particle belongs to both edges.  Particles
+ * outside the cell-grid domain get 0.  Returns the number labelled 1 or 2. */
+int64_t or_subdomain_labels(const or_params *P, int64_t n, const double *x,
+                            const double *y, const double *z, int mode,
+                            double xlo, double xhi, uint32_t *label)
+{
+    int64_t nc[3];
+    or_grid_dims(P, nc);
+    const double cs = 2.0 * P->h;
+    const double lo_edge = xlo + cs, hi_edge = xhi - cs;
+    int64_t sel = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t l = 0;
+        if (is_in(P, nc, x[i], y[i], z[i])) {
+            if (mode == 0) {
+                if (x[i] >= xlo && x[i] < lo_edge) l = 1;
+                else if (x[i] >= hi_edge && x[i] < xhi) l = 2;
+            } else {
+                if (x[i] < xlo) l = 1;
+                else if (x[i] >= xhi) l = 2;
+            }
+        }
+        label[i] = l;
+        sel += l != 0;
+    }
+    return sel;
+}
+
 /* Conservation diagnostics over in-domain particles:
  * out[0] total mass, out[1..3] fluid momentum, out[4] fluid kinetic energy,
  * out[5] fluid potential energy -m g.r, out[6] internal energy sum m e(rho)
