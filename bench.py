@@ -383,6 +383,8 @@ def run_ours(args):
            "ms_upload_step_download": [round(v / e2e_steps * 1e3, 3) for v in parts],
            "note": "per step: sph_upload (pinned host) + sph_step(1) + sph_download (pinned host)"}
 
+    sub = subdomain_timing(sim, case, args.subdomains, S, torch) if args.subdomains else None
+
     kps = sim.kernels_per_step()
     if is_ensemble(case):
         ist = sim.instance_state()
@@ -410,6 +412,8 @@ def run_ours(args):
             "member_steps_per_s": steps_per_s * getattr(sim, "n_inst", 1),
             "roofline": roofline, "e2e": e2e, "gpu_launches": kps * args.steps,
             "clocks": clocks}
+    if sub is not None:
+        line["subdomain_select"] = sub
     pk, src = peaks()
     line["peaks_source"] = src
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -423,6 +427,40 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def subdomain_timing(sim, case, nsub, S, torch):
+    """Sec. 4.3 selection on the current state for nsub equal slabs along
+    x of the particles' range: per slab, the edge particles that would build
+    the neighbours' halos (labels, (label, id) sort, copy into device
+    buffers).  Wall time per call (the call synchronises; it includes the
+    host read of the counts)."""
+    if is_ensemble(case):
+        return None
+    sim.build_cells()
+    st = sim.download()
+    x0, x1 = float(st["pos"][:, 0].min()), float(st["pos"][:, 0].max()) * (1 + 1e-12) + 1e-9
+    edges = np.linspace(x0, x1, nsub + 1)
+    n = case.n
+    dev = sim.device
+    out = dict(pos=torch.empty((n, 3), dtype=torch.float64, device=dev),
+               vel=torch.empty((n, 3), dtype=torch.float32, device=dev),
+               rho=torch.empty(n, dtype=torch.float32, device=dev),
+               ids=torch.empty(n, dtype=torch.int32, device=dev))
+    ms, sel = [], []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        args = (sim.ctx, S.SPH_SUBDOMAIN_EDGE, lo, hi, n, out["pos"], out["vel"], out["rho"],
+                out["ids"])
+        S.sph_subdomain_select(*args)                       # warm
+        reps = 5
+        t = time.perf_counter()
+        for _ in range(reps):
+            c = S.sph_subdomain_select(*args)
+        ms.append(round((time.perf_counter() - t) / reps * 1e3, 3))
+        sel.append(int(c[1]) + int(c[2]))
+    return {"slabs": nsub, "mode": "edge", "ms_per_call": ms, "selected": sel,
+            "note": "labels of all particles, (label, id) radix sort of the selected, copy "
+                    "into device buffers; wall time per synchronous call"}
 
 
 def run_surrogate(args):
@@ -532,6 +570,8 @@ def main():
     ap.add_argument("--workload", default="dam_break_32m", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--formulation", default="default", choices=sorted(FORMULATIONS))
+    ap.add_argument("--subdomains", type=int, default=0,
+                    help="also time the Sec. 4.3 edge selection for this many slabs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

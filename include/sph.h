@@ -280,6 +280,33 @@ int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
 uint64_t sph_array_bytes(const sph_ctx *ctx, int which);
 int sph_read_array(sph_ctx *ctx, int which, void *host, uint64_t bytes);
 
+/* Sec. 4.2-4.3: the data a sub-domain of a one-dimensional decomposition
+ * along x sends to its neighbours, selected on the GPU as the paper does it:
+ * label every particle, order by (label, id) with the radix sort, copy the
+ * labelled ones out.  The sub-domain is [xlo, xhi) and holds the context's
+ * particles.  Labels (FP64 x, xlo + 2h and xhi - 2h each rounded once):
+ *   SPH_SUBDOMAIN_EDGE     1 if xlo <= x < xlo + 2h (left edge), 2 if
+ *                          xhi - 2h <= x < xhi (right edge), else 0: the
+ *                          edge particles that build the neighbours' halos.
+ *                          Needs xhi - xlo >= 4h (no particle in both edges)
+ *   SPH_SUBDOMAIN_MIGRATE  1 if x < xlo (moved to the left neighbour), 2 if
+ *                          x >= xhi (moved to the right one), else 0
+ * Particles outside the cell-grid domain are not labelled.  counts[3]
+ * receives the number of in-domain particles with label 0, 1 and 2.  The
+ * m = counts[1] + counts[2] labelled particles are copied, label 1 first,
+ * each label in ascending id (the order of the worked example of Sec. 4.3),
+ * into pos[3m] (float64 x,y,z), vel[3m] (float32), rho[m], ids[m]: host or
+ * device arrays owned by the caller, any of them NULL to skip it.
+ * capacity < m returns SPH_ERR_CAPACITY with counts filled and nothing
+ * copied.  The state itself is not reordered (the cell order stays).
+ * Needs built cells and a single simulation (SPH_ERR_STATE otherwise).
+ * Sync; a radix-sort look-back that gave up shows in sph_check. */
+#define SPH_SUBDOMAIN_EDGE     0
+#define SPH_SUBDOMAIN_MIGRATE  1
+int sph_subdomain_select(sph_ctx *ctx, int mode, double xlo, double xhi,
+                         uint32_t *counts, uint32_t capacity, double *pos,
+                         float *vel, float *rho, uint32_t *ids);
+
 /* Sec. 3.2 neighbour counts with the FP64 predicate |r_ij|^2 < (2h)^2,
  * |r|^2 = (dx*dx + dy*dy) + dz*dz without contraction, on the current
  * cells (for bit-exact comparison; not used by the time step).  Async. */

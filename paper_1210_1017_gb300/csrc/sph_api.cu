@@ -216,6 +216,14 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->os_bytes = 4 * sizeof(uint32_t) + (size_t)passes * tiles * 256 * sizeof(uint32_t);
     c->tilectr = cv.take<uint32_t>(c->os_bytes / sizeof(uint32_t));
     c->os_status = c->tilectr ? c->tilectr + 4 : nullptr;
+    for (int b = 0; b < 2; ++b) {
+        c->sub_key[b] = cv.take<uint32_t>(n);
+        c->sub_val[b] = cv.take<uint32_t>(n);
+    }
+    c->sub_hist = cv.take<uint32_t>(5 * 256);
+    c->sub_os_bytes = 5 * sizeof(uint32_t) + (size_t)5 * tiles * 256 * sizeof(uint32_t);
+    c->sub_os = cv.take<uint32_t>(c->sub_os_bytes / sizeof(uint32_t));
+    c->sub_cnt = cv.take<uint32_t>(4);
     c->csum = cv.take<uint32_t>(t.ncells + t.nrows + 1);
     c->ucnt = cv.take<uint32_t>(t.nrows + 1);
     c->uoff = cv.take<uint32_t>(t.nrows + 2);

@@ -51,6 +51,13 @@ struct sph_ctx {
     unsigned long long* lvl2_q;
     uint32_t *done, *status;
     uint32_t* id_flag;       // set by the upload when some id >= n
+    // sub-domain selection (Sec. 4.3): ping-pong (key, value) arrays of the
+    // selected particles for the radix sorts, their digit histograms (4
+    // passes by id + 1 by label), tile counters and look-back status, and
+    // the label counters
+    uint32_t *sub_key[2], *sub_val[2];
+    uint32_t *sub_hist, *sub_os, *sub_cnt;
+    size_t sub_os_bytes = 0;
     double *diag_out, *diag_part;
     unsigned long long* counters;
     // ensemble table and per-member state (device)

@@ -24,6 +24,7 @@ SPH_INTERACT_COUNTS = 1
 SPH_ARRAY_KEY, SPH_ARRAY_CELL_OFF, SPH_ARRAY_ACE, SPH_ARRAY_NNB = 0, 1, 2, 3
 SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT, SPH_ARRAY_PREV = 4, 5, 6, 7
 SPH_SCHEME_CUBIC, SPH_SCHEME_VERLET = 1, 2
+SPH_SUBDOMAIN_EDGE, SPH_SUBDOMAIN_MIGRATE = 0, 1
 ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
           -4: "SPH_ERR_TIMEOUT", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_CAPACITY",
           -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE"}
@@ -36,7 +37,8 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_kernels_per_step", "sph_last_error", "sph_destroy",
             "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
             "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
-            "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune"]
+            "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune",
+            "sph_subdomain_select"]
 
 
 class SphParams(C.Structure):
@@ -145,6 +147,7 @@ def lib(build: bool = False):
     L.sph_num_variants.restype = u32
     L.sph_set_variant.argtypes = [vp, u32]
     L.sph_autotune.argtypes = [vp, u32, vp, vp]
+    L.sph_subdomain_select.argtypes = [vp, i32, C.c_double, C.c_double, vp, u32, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -313,6 +316,17 @@ def sph_read_array(ctx, which: int, out: np.ndarray):
     return out
 
 
+def sph_subdomain_select(ctx, mode, xlo, xhi, capacity, pos=None, vel=None, rho=None,
+                         ids=None):
+    """Returns the per-label counts; fills the caller's arrays (host numpy
+    or device tensors) with the selected particles' state."""
+    counts = np.zeros(3, np.uint32)
+    _check(lib().sph_subdomain_select(ctx, int(mode), float(xlo), float(xhi), _ptr(counts),
+                                      int(capacity), _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)),
+           ctx, "sph_subdomain_select")
+    return counts
+
+
 def sph_neighbour_counts_fp64(ctx):
     _check(lib().sph_neighbour_counts_fp64(ctx), ctx, "sph_neighbour_counts_fp64")
 
@@ -474,6 +488,20 @@ class Simulation:
 
     def rollout(self, nsteps, save_every=0, cb=None):
         sph_rollout(self.ctx, nsteps, save_every, cb)
+
+    def subdomain_select(self, mode, xlo, xhi, capacity=None):
+        """Sec. 4.3 selection for the sub-domain [xlo, xhi) (needs built
+        cells): counts per label and the labelled particles' state in
+        (label, id) order, in host arrays."""
+        cap = self.n if capacity is None else int(capacity)
+        pos = np.empty((max(cap, 1), 3), np.float64)
+        vel = np.empty((max(cap, 1), 3), np.float32)
+        rho = np.empty(max(cap, 1), np.float32)
+        ids = np.empty(max(cap, 1), np.uint32)
+        counts = sph_subdomain_select(self.ctx, mode, xlo, xhi, cap, pos, vel, rho, ids)
+        m = int(counts[1]) + int(counts[2])
+        return dict(counts=counts.astype(np.int64), pos=pos[:m], vel=vel[:m], rho=rho[:m],
+                    ids=ids[:m])
 
     def neighbour_counts_fp64(self):
         sph_neighbour_counts_fp64(self.ctx)
