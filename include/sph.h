@@ -315,8 +315,23 @@ int sph_neighbour_counts_fp64(sph_ctx *ctx);
 /* FP64 conservation sums, counters and status.  Sync. */
 int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
 
-/* Map the device status word to an error code (SPH_OK if clear).  Sync. */
+/* Map the device status word to an error code (SPH_OK if clear).  Sync.
+ * The word keeps its bits until sph_clear_status. */
 int sph_check(sph_ctx *ctx);
+
+/* Clear the device status word once the caller has handled what sph_check
+ * reported.  Sync. */
+int sph_clear_status(sph_ctx *ctx);
+
+/* Self-test of the failure path; the paper has no counterpart.  Bounded
+ * device waits must be testable without hanging a GPU: this runs the radix
+ * sort's decoupled look-back (the same device code as the sort) against a
+ * predecessor tile whose status nothing ever publishes, with a limit of
+ * `polls` polls (1 to 2^20).  The wait gives up and sets SPH_STATUS_TIMEOUT
+ * in the context's status word, as a stalled sort would, so sph_check
+ * returns SPH_ERR_TIMEOUT.  The particle state and cells are untouched (the
+ * sort's status words it borrows are cleared before every sort).  Sync. */
+int sph_selftest_timeout(sph_ctx *ctx, uint32_t polls);
 
 /* Block shapes of the interaction kernel ("variants": particles per work
  * unit, staged candidates per unit, neighbour-list slots per lane) and the

@@ -858,6 +858,23 @@ int sph_check(sph_ctx* c) {
     return SPH_OK;
 }
 
+int sph_clear_status(sph_ctx* c) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    int rc = cuda_check(c, cudaMemsetAsync(c->status, 0, sizeof(uint32_t), c->st), "clear status");
+    if (rc) return rc;
+    return cuda_check(c, cudaStreamSynchronize(c->st), "clear status sync");
+}
+
+int sph_selftest_timeout(sph_ctx* c, uint32_t polls) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (polls == 0 || polls > (1u << 20)) return fail(c, SPH_ERR_INVALID_ARG, "polls must be 1..2^20");
+    // the first pass's status words: cleared by every rebuild before use
+    launch_lookback_selftest(c->os_status, polls, c->status, c->st);
+    int rc = post_launch(c, "selftest");
+    if (rc) return rc;
+    return cuda_check(c, cudaStreamSynchronize(c->st), "selftest sync");
+}
+
 uint32_t sph_num_variants(void) { return (uint32_t)kNumVariants; }
 
 int sph_set_variant(sph_ctx* c, uint32_t v) {

@@ -98,6 +98,11 @@ constexpr int kOsTile = kOsThreads * kOsItems;
 inline uint32_t os_tiles(uint32_t n) { return (n + kOsTile - 1) / kOsTile; }
 void launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, int bits_total,
                        uint32_t* hist, cudaStream_t st);
+// Failure-path self-test: the radix sort's look-back waits on 256 status
+// words that nothing sets (zeroed here) and gives up after `limit` polls,
+// setting kStatusTimeout in *err.
+void launch_lookback_selftest(uint32_t* zeroed256, uint32_t limit, uint32_t* err,
+                              cudaStream_t st);
 void launch_onesweep_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                           uint32_t* vout, uint32_t n, int pass, int bits_total,
                           const uint32_t* hist, uint32_t* status, uint32_t* tilectr,

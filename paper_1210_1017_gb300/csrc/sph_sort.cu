@@ -87,6 +87,35 @@ __global__ void __launch_bounds__(256) k_digit_hist(const uint32_t* __restrict__
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+// Decoupled look-back for one digit: the sum of the counts of the tiles
+// before `tile` (status words of 256 digits per tile; a tile's word holds its
+// own count, kFlagAgg, or the inclusive prefix, kFlagPre, or 0 while it has
+// published nothing).  A predecessor that stays silent for `limit` polls
+// makes the wait give up: the timeout bit is set in *err and the partial sum
+// returned, which never exceeds the true prefix (so scatter addresses stay
+// inside the output).
+__device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* status, uint32_t tile,
+                                                    int digit, uint32_t limit, uint32_t* err) {
+    uint32_t excl = 0;
+    int64_t p = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (p >= 0) {
+        const uint32_t s = ld_relaxed(status + (size_t)p * 256 + digit);
+        const uint32_t flag = s & ~kValMask;
+        if (flag == 0u) {
+            if (++spins > limit) {
+                atomicOr(err, kStatusTimeout);
+                break;
+            }
+            continue;
+        }
+        excl += s & kValMask;
+        if (flag == kFlagPre) break;
+        --p;
+    }
+    return excl;
+}
+
 // One digit place.  hist holds the global count of each digit value for
 // this place; status holds one word per (tile, digit), zero on entry;
 // tilectr is a zeroed counter that hands out tiles in launch order, so every
@@ -154,22 +183,7 @@ __global__ void __launch_bounds__(kOsThreads) k_onesweep(
     // Decoupled look-back for digit tid.
     uint32_t excl = 0;
     if (tile > 0) {
-        int64_t p = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        while (p >= 0) {
-            const uint32_t s = ld_relaxed(status + (size_t)p * 256 + tid);
-            const uint32_t flag = s & ~kValMask;
-            if (flag == 0u) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(err, kStatusTimeout);
-                    break;
-                }
-                continue;
-            }
-            excl += s & kValMask;
-            if (flag == kFlagPre) break;
-            --p;
-        }
+        excl = lookback_prefix(status, tile, tid, kSpinLimit, err);
         st_relaxed(my, kFlagPre | (excl + cnt));
     }
     s_gbase[tid] = gofs + excl;
@@ -194,6 +208,14 @@ __global__ void __launch_bounds__(kOsThreads) k_onesweep(
         kout[g] = key;
         vout[g] = s_vals[i];
     }
+}
+
+// Self-test of the failure path: one block of 256 threads runs the look-back
+// of tile 1 against a tile 0 whose status words stay zero (nothing
+// publishes them), so every digit's wait gives up after `limit` polls.
+__global__ void __launch_bounds__(256) k_lookback_selftest(const uint32_t* status, uint32_t limit,
+                                                           uint32_t* err) {
+    lookback_prefix(status, 1u, (int)threadIdx.x, limit, err);
 }
 
 // --- exclusive scan of the per-cell counts into cell offsets --------------
@@ -287,6 +309,12 @@ void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaSt
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st) {
     launch_scan(cnt, (uint64_t)d.ncells + 1, bsum, off, st);   // counts incl. the excluded bin
+}
+
+void launch_lookback_selftest(uint32_t* zeroed256, uint32_t limit, uint32_t* err,
+                              cudaStream_t st) {
+    cudaMemsetAsync(zeroed256, 0, 256 * sizeof(uint32_t), st);
+    k_lookback_selftest<<<1, 256, 0, st>>>(zeroed256, limit, err);
 }
 
 void launch_digit_hist(const uint32_t* keys, uint32_t n, int passes, int bits_total,

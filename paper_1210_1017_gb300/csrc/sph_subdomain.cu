@@ -9,6 +9,8 @@
 // arbitrary), a four-pass sort by id and a stable one-pass sort by label then
 // give the (label, id) order of the paper's worked example for any 32-bit
 // ids.  The state itself keeps its cell order.
+#include <string.h>
+
 #include "sph_ctx.cuh"
 
 namespace sph {
@@ -19,28 +21,39 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kIdxBits = 26;                     // state index < 2^26
 constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 
+// Order-preserving integer image of a finite double: a < b exactly when
+// ordered(a) < ordered(b), with -0 and +0 both 0.  The labels compare these
+// on the integer pipe (GB300 issues FP64 instructions at 1/64 of the FP32
+// rate, which would bound this pass instead of HBM).
+__host__ __device__ __forceinline__ long long ordered(long long bits) {
+    const long long mag = bits & 0x7fffffffffffffffLL;
+    return bits < 0 ? -mag : mag;
+}
+
 struct SubLabelArgs {
     const double* x;
     const uint32_t* id;
     const uint32_t* off;      // cell offsets: off[ncells] = in-domain count
     uint32_t ncells, n;
     int mode;
-    double xlo, xhi, lo_edge, hi_edge;
+    long long xlo, xhi, lo_edge, hi_edge;   // ordered images of the bounds
     uint32_t* key;            // id of each selected particle
     uint32_t* val;            // (label << 26) | state index
-    uint32_t* cnt;            // [0..2] in-domain count per label, [3] selected
+    uint32_t* cnt;            // [0] in-domain count, [1..2] per label, [3] selected
 };
 
-// Label of state entry k (in-domain entries k < off[ncells] only).
+// Label of state entry k (in-domain entries k < off[ncells] only).  Only
+// warps holding labelled particles touch the counters (label 0 is the rest
+// of the in-domain count), so the pass stays a read of x.
 __global__ void __launch_bounds__(256) k_sub_label(const SubLabelArgs a) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t l = 0;
-    bool in = false;
     if (k < a.n) {
-        in = k < a.off[a.ncells];
-        if (in) {
-            const double x = a.x[k];
+        const uint32_t n_in = a.off[a.ncells];
+        if (k == 0) a.cnt[0] = n_in;
+        if (k < n_in) {
+            const long long x = ordered(__double_as_longlong(a.x[k]));
             if (a.mode == SPH_SUBDOMAIN_EDGE) {
                 if (x >= a.xlo && x < a.lo_edge) l = 1;
                 else if (x >= a.hi_edge && x < a.xhi) l = 2;
@@ -50,16 +63,15 @@ __global__ void __launch_bounds__(256) k_sub_label(const SubLabelArgs a) {
             }
         }
     }
-    const uint32_t m0 = __ballot_sync(kFull, in && l == 0u);
     const uint32_t m1 = __ballot_sync(kFull, l == 1u);
     const uint32_t m2 = __ballot_sync(kFull, l == 2u);
     const uint32_t sel = m1 | m2;
+    if (sel == 0u) return;                       // warp-uniform
     uint32_t base = 0;
     if (lane == 0) {
-        if (m0) atomicAdd(a.cnt + 0, __popc(m0));
         if (m1) atomicAdd(a.cnt + 1, __popc(m1));
         if (m2) atomicAdd(a.cnt + 2, __popc(m2));
-        if (sel) base = atomicAdd(a.cnt + 3, __popc(sel));
+        base = atomicAdd(a.cnt + 3, __popc(sel));
     }
     base = __shfl_sync(kFull, base, 0);
     if (l != 0u) {
@@ -149,10 +161,18 @@ extern "C" int sph_subdomain_select(sph_ctx* c, int mode, double xlo, double xhi
     la.ncells = (uint32_t)c->ncells;
     la.n = n;
     la.mode = mode;
-    la.xlo = xlo;
-    la.xhi = xhi;
-    la.lo_edge = xlo + cs;
-    la.hi_edge = xhi - cs;
+    // xlo + 2h and xhi - 2h rounded once in FP64, then mapped
+    const double bounds[4] = {xlo, xhi, xlo + cs, xhi - cs};
+    long long ob[4];
+    for (int i = 0; i < 4; ++i) {
+        long long b;
+        memcpy(&b, &bounds[i], sizeof(b));
+        ob[i] = ordered(b);
+    }
+    la.xlo = ob[0];
+    la.xhi = ob[1];
+    la.lo_edge = ob[2];
+    la.hi_edge = ob[3];
     la.key = c->sub_key[0];
     la.val = c->sub_val[0];
     la.cnt = c->sub_cnt;
@@ -164,7 +184,7 @@ extern "C" int sph_subdomain_select(sph_ctx* c, int mode, double xlo, double xhi
     cudaMemcpyAsync(cnt, c->sub_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
     rc = cuda_ok(c, cudaStreamSynchronize(st), "sub-domain counts");
     if (rc) return rc;
-    counts[0] = cnt[0];
+    counts[0] = cnt[0] - cnt[1] - cnt[2];
     counts[1] = cnt[1];
     counts[2] = cnt[2];
     const uint32_t m = cnt[3];

@@ -38,7 +38,7 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
             "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
             "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune",
-            "sph_subdomain_select"]
+            "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout"]
 
 
 class SphParams(C.Structure):
@@ -129,6 +129,8 @@ def lib(build: bool = False):
     L.sph_neighbour_counts_fp64.argtypes = [vp]
     L.sph_diagnostics.argtypes = [vp, C.POINTER(SphDiag)]
     L.sph_check.argtypes = [vp]
+    L.sph_clear_status.argtypes = [vp]
+    L.sph_selftest_timeout.argtypes = [vp, u32]
     L.sph_kernels_per_step.argtypes = [vp]
     L.sph_kernels_per_step.restype = u32
     L.sph_last_error.argtypes = [vp]
@@ -341,6 +343,14 @@ def sph_check(ctx):
     _check(lib().sph_check(ctx), ctx, "sph_check")
 
 
+def sph_clear_status(ctx):
+    _check(lib().sph_clear_status(ctx), ctx, "sph_clear_status")
+
+
+def sph_selftest_timeout(ctx, polls: int):
+    _check(lib().sph_selftest_timeout(ctx, polls), ctx, "sph_selftest_timeout")
+
+
 def sph_kernels_per_step(ctx) -> int:
     return int(lib().sph_kernels_per_step(ctx))
 
@@ -549,6 +559,9 @@ class Simulation:
 
     def check(self):
         sph_check(self.ctx)
+
+    def clear_status(self):
+        sph_clear_status(self.ctx)
 
     def kernels_per_step(self):
         return sph_kernels_per_step(self.ctx)

@@ -125,3 +125,26 @@ def test_capacity_empty_selection_and_argument_checks():
         sim.subdomain_select(S.SPH_SUBDOMAIN_EDGE, xlo, xhi)
     sim.check()
     sim.close()
+
+
+def test_labels_at_exactly_2h_and_signed_zero():
+    """Dyadic h = 1/4: every threshold is exact, so the strict and non-strict
+    bounds decide; -0.0 and +0.0 are the same x."""
+    h = 0.25
+    xlo, xhi = 0.0, 2.0
+    xs = [xlo - 2.0 ** -30, -0.0, xlo, xlo + 2 * h - 2.0 ** -40, xlo + 2 * h, 1.0,
+          xhi - 2 * h - 2.0 ** -40, xhi - 2 * h, xhi - 2.0 ** -40, xhi]
+    n = len(xs)
+    pos = np.array([[v, 0.1 * k - 0.45, 0.0] for k, v in enumerate(xs)])
+    case = cases.Case(name="thresholds", pos=pos, vel=np.zeros((n, 3), np.float32),
+                      rho=np.full(n, 1000.0, np.float32), ids=np.arange(n, dtype=np.uint32),
+                      n_bound=0, dp=0.2, h=h, rho0=1000.0, c0=20.0, alpha=0.01, cfl=0.2,
+                      gravity=(0.0, 0.0, -9.81), dmin=(-1.0, -1.0, -1.0), dmax=(3.0, 1.0, 1.0),
+                      fluid_height=0.0)
+    sim = S.Simulation.from_case(case)
+    sim.build_cells()
+    edge = _check_against_oracle(case, sim, S.SPH_SUBDOMAIN_EDGE, xlo, xhi)
+    assert sorted(edge["ids"].tolist()) == [1, 2, 3, 7, 8]
+    mig = _check_against_oracle(case, sim, S.SPH_SUBDOMAIN_MIGRATE, xlo, xhi)
+    assert mig["ids"].tolist() == [0, 9]
+    sim.close()
