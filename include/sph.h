@@ -178,6 +178,16 @@ int sph_init_batch(const sph_params *params, const sph_instance *inst,
 int sph_instance_state(sph_ctx *ctx, double *t, double *dt, uint32_t *done,
                        uint64_t *steps);
 
+/* Restore each member's simulated time and step count (host arrays of
+ * n_inst entries; steps may be NULL to keep the counts), e.g. after
+ * sph_upload of a checkpointed state.  A member whose t reaches its t_end is
+ * marked done again, one below it runs again.  With the symplectic
+ * scheme the next step size comes from the state alone, so a run resumed
+ * from (state, t, steps) repeats the uninterrupted run bit for bit; the
+ * Verlet scheme restarts with an Euler step (its earlier state is not part
+ * of a checkpoint).  Sync. */
+int sph_set_instance_state(sph_ctx *ctx, const double *t, const uint64_t *steps);
+
 /* Copy a particle state from host or device memory (any order; the arrays
  * may live on either side, unified addressing decides): pos[3n] float64
  * (x,y,z interleaved), vel[3n] float32, rho[n] float32, ids[n] uint32 (a

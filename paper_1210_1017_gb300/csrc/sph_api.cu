@@ -2,6 +2,8 @@
 // layout, the ensemble table, the step sequence and its CUDA-graph capture,
 // host transfers.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -563,6 +565,23 @@ int sph_instance_state(sph_ctx* c, double* t, double* dt, uint32_t* done, uint64
     if (done) cudaMemcpyAsync(done, c->i_done, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (steps) cudaMemcpyAsync(steps, c->i_steps, m * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     return cuda_check(c, cudaStreamSynchronize(st), "instance state");
+}
+
+int sph_set_instance_state(sph_ctx* c, const double* t, const uint64_t* steps) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!t) return fail(c, SPH_ERR_INVALID_ARG, "NULL time array");
+    const size_t m = c->n_inst;
+    std::vector<uint32_t> done(m);
+    for (size_t q = 0; q < m; ++q) {
+        if (!std::isfinite(t[q]) || t[q] < 0.0) return fail(c, SPH_ERR_INVALID_ARG, "bad member time");
+        done[q] = t[q] >= c->tab.inst[q].t_end ? 1u : 0u;
+    }
+    cudaStream_t st = c->st;
+    cudaMemcpyAsync(c->i_t, t, m * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->i_done, done.data(), m * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (steps)
+        cudaMemcpyAsync(c->i_steps, steps, m * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+    return cuda_check(c, cudaStreamSynchronize(st), "set instance state");
 }
 
 int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho,

@@ -38,7 +38,8 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_radix_sort_scratch_bytes", "sph_radix_sort_pairs",
             "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
             "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune",
-            "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout"]
+            "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout",
+            "sph_set_instance_state"]
 
 
 class SphParams(C.Structure):
@@ -145,6 +146,7 @@ def lib(build: bool = False):
     L.sph_query_sizes_batch.argtypes = [P, PI, u32, C.POINTER(SphSizes)]
     L.sph_init_batch.argtypes = [P, PI, u32, vp, u64, vp, C.POINTER(vp)]
     L.sph_instance_state.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_set_instance_state.argtypes = [vp, vp, vp]
     L.sph_num_variants.argtypes = []
     L.sph_num_variants.restype = u32
     L.sph_set_variant.argtypes = [vp, u32]
@@ -248,6 +250,62 @@ def sph_instance_state(ctx, n_inst: int):
     _check(lib().sph_instance_state(ctx, _ptr(t), _ptr(dt), _ptr(done), _ptr(steps)), ctx,
            "sph_instance_state")
     return dict(t=t, dt=dt, done=done.astype(bool), steps=steps)
+
+
+def sph_set_instance_state(ctx, t, steps=None):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    steps = None if steps is None else np.ascontiguousarray(steps, dtype=np.uint64)
+    _check(lib().sph_set_instance_state(ctx, _ptr(t), _ptr(steps)), ctx, "sph_set_instance_state")
+
+
+# --- checkpoints ---------------------------------------------------------------
+#
+# A checkpoint is one .npz file: a format tag and version, the parameter
+# dictionary and ensemble members as JSON, each member's time, step size,
+# step count and end flag, and the particle state as structure-of-arrays
+# (positions float64, velocities and densities float32, ids uint32, in the
+# library's (cell, id) order).  Writing and reading need no GPU.
+
+CHECKPOINT_FORMAT = "gb300-wcsph-checkpoint"
+CHECKPOINT_VERSION = 1
+
+
+def write_checkpoint(path, params: dict, members, inst: dict, state: dict):
+    import json
+    meta = dict(format=CHECKPOINT_FORMAT, version=CHECKPOINT_VERSION,
+                params={k: (list(v) if isinstance(v, tuple) else v) for k, v in params.items()},
+                members=members, n=int(state["ids"].shape[0]))
+    with open(path, "wb") as f:
+        np.savez(f, meta=np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8),
+                 t=np.asarray(inst["t"], np.float64), dt=np.asarray(inst["dt"], np.float64),
+                 steps=np.asarray(inst["steps"], np.uint64),
+                 done=np.asarray(inst["done"], np.uint8),
+                 pos=np.ascontiguousarray(state["pos"], np.float64),
+                 vel=np.ascontiguousarray(state["vel"], np.float32),
+                 rho=np.ascontiguousarray(state["rho"], np.float32),
+                 ids=np.ascontiguousarray(state["ids"], np.uint32))
+
+
+def read_checkpoint(path):
+    """Returns (params, members, member state, particle state); raises on a
+    file of another format or version, or with inconsistent sizes."""
+    import json
+    with np.load(path) as z:
+        meta = json.loads(bytes(z["meta"]).decode())
+        if meta.get("format") != CHECKPOINT_FORMAT or meta.get("version") != CHECKPOINT_VERSION:
+            raise ValueError(f"{path}: not a version-{CHECKPOINT_VERSION} checkpoint")
+        inst = {k: z[k].copy() for k in ("t", "dt", "steps", "done")}
+        state = {k: z[k].copy() for k in ("pos", "vel", "rho", "ids")}
+    n = meta["n"]
+    if any(state[k].shape[0] != n for k in state) or state["pos"].shape != (n, 3):
+        raise ValueError(f"{path}: particle arrays do not match n = {n}")
+    params = {k: (tuple(v) if isinstance(v, list) else v) for k, v in meta["params"].items()}
+    members = meta["members"]
+    nm = 1 if members is None else len(members)
+    if any(inst[k].shape[0] != nm for k in inst):
+        raise ValueError(f"{path}: member arrays do not match {nm} members")
+    inst["done"] = inst["done"].astype(bool)
+    return params, members, inst, state
 
 
 def sph_num_variants() -> int:
@@ -459,6 +517,30 @@ class Simulation:
 
     def instance_state(self):
         return sph_instance_state(self.ctx, self.n_inst)
+
+    def set_instance_state(self, t, steps=None):
+        sph_set_instance_state(self.ctx, t, steps)
+
+    def save_checkpoint(self, path):
+        """Write the state and each member's time and step count (sync)."""
+        members = None
+        if self.members is not None:
+            members = [dict(dmin=list(m.dmin), dmax=list(m.dmax), c0=m.c0, t_end=m.t_end,
+                            n_particles=int(m.n_particles), n_bound=int(m.n_bound))
+                       for m in self.members]
+        params = dict(self.params)
+        params["dt_fixed"] = float(self.P.dt_fixed)
+        write_checkpoint(path, params, members, self.instance_state(), self.download())
+
+    @classmethod
+    def load_checkpoint(cls, path, **kw):
+        """A new simulation resumed from a checkpoint: same parameters and
+        members, the saved state uploaded, times and step counts restored."""
+        params, members, inst, state = read_checkpoint(path)
+        sim = cls(params, int(state["ids"].shape[0]), members=members, **kw)
+        sim.upload(state["pos"], state["vel"], state["rho"], state["ids"])
+        sim.set_instance_state(inst["t"], inst["steps"])
+        return sim
 
     def autotune(self, reps=3, cache=True):
         """Pick the fastest interaction variant for this GPU and size (needs
