@@ -46,14 +46,16 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_the_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(sph_params),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sph_params),'
                     ' sizeof(sph_sizes), sizeof(sph_diag), offsetof(sph_params, dt_fixed),'
-                    ' offsetof(sph_diag, n_out));return 0;}\n')
+                    ' offsetof(sph_diag, n_out), offsetof(sph_params, scheme),'
+                    ' offsetof(sph_params, verlet_every), sizeof(sph_instance));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(S.SphParams), C.sizeof(S.SphSizes), C.sizeof(S.SphDiag),
-            S.SphParams.dt_fixed.offset, S.SphDiag.n_out.offset]
+            S.SphParams.dt_fixed.offset, S.SphDiag.n_out.offset, S.SphParams.scheme.offset,
+            S.SphParams.verlet_every.offset, C.sizeof(S.SphInstance)]
     assert got == want
 
 
