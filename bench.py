@@ -409,6 +409,9 @@ def run_ours(args):
             "fluid_pairs_per_step": pf / args.steps, "boundary_pairs_per_step": pb / args.steps,
             "candidates_per_step": cand / args.steps,
             "sim_time_per_step": (d1["t"] - d0["t"]) / args.steps,
+            # time to solution: wall seconds per simulated second (member 0)
+            "wall_s_per_simulated_s": ((t_max * 1e-3) / (d1["t"] - d0["t"])
+                                       if d1["t"] > d0["t"] else None),
             "member_steps_per_s": steps_per_s * getattr(sim, "n_inst", 1),
             "roofline": roofline, "e2e": e2e, "gpu_launches": kps * args.steps,
             "clocks": clocks}
