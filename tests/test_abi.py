@@ -97,3 +97,38 @@ def test_sort_scratch_size_grows_with_n(lib):
     b = lib.sph_radix_sort_scratch_bytes(1000000)
     assert 8000 <= a < b
     assert b >= 8 * 1000000
+
+
+def test_formulation_flags_and_their_validation(lib):
+    """The scheme bits follow the case's kernel and integrator names; the
+    library refuses unknown bits and a non-zero reserved field before any
+    GPU work (query runs the same validation as init)."""
+    case = cases.c1_dam_break()
+    p = case.params()
+    assert S.make_params(p).scheme == 0
+    both = dict(p, kernel="cubic", integrator="verlet", verlet_every=25)
+    P = S.make_params(both)
+    assert P.scheme == S.SPH_SCHEME_CUBIC | S.SPH_SCHEME_VERLET and P.verlet_every == 25
+    assert S.make_params(dict(p, integrator="verlet")).scheme == S.SPH_SCHEME_VERLET
+    assert S.sph_query_sizes(P, case.n).workspace_bytes > 0
+    with pytest.raises(ValueError):
+        S.make_params(dict(p, kernel="gaussian"))
+    bad = S.make_params(p)
+    bad.scheme = 4
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(bad, case.n)
+    bad = S.make_params(p)
+    bad.reserved = 1
+    with pytest.raises(S.SphError, match="INVALID_ARG"):
+        S.sph_query_sizes(bad, case.n)
+
+
+def test_entry_points_refuse_a_null_context(lib):
+    """Every context call checks its context pointer first (no GPU needed)."""
+    counts = (C.c_uint32 * 3)()
+    assert lib.sph_verlet(None) == -1
+    assert lib.sph_subdomain_select(None, 0, 0.0, 1.0, counts, 0, None, None, None, None) == -1
+    assert lib.sph_selftest_timeout(None, 10) == -1
+    assert lib.sph_clear_status(None) == -1
+    t = (C.c_double * 1)(0.0)
+    assert lib.sph_set_instance_state(None, t, None) == -1
