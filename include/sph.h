@@ -233,9 +233,10 @@ int sph_correct(sph_ctx *ctx);
  *                   v1 = v + dt a            (Euler step)
  *   every in-domain particle: rho1 = rho_prev + 2 dt drho/dt (leapfrog),
  *                   rho + dt drho/dt (Euler)
- * Each member counts its steps from its last sph_upload (or sph_init); step
- * k is an Euler step when k is a multiple of params.verlet_every, so the
- * first step after an upload, which has no earlier state, is one.  Boundary
+ * Each member counts its steps from its last sph_upload (or sph_init, or
+ * surrogate advance); step k is an Euler step when k is a multiple of
+ * params.verlet_every, so the first step after new state arrives, which has
+ * no earlier state, is one.  Boundary
  * particles keep r and v (Sec. 2.3).  Advances t and the step count and
  * recomputes the cell labels.  Async.  sph_predict / sph_correct return
  * SPH_ERR_STATE on these contexts. */

@@ -2,11 +2,10 @@
 // layout, the ensemble table, the step sequence and its CUDA-graph capture,
 // host transfers.
 #include <math.h>
-
-#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 

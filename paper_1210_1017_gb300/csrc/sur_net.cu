@@ -907,6 +907,9 @@ int sur_advance(sur_ctx* c, sph_ctx* s, float* d_hist) {
     s->cells_valid = false;
     s->keys_ready = false;
     s->pre_state = 0;
+    // a Verlet context has no earlier state for the surrogate's result: its
+    // next SPH step is an Euler step
+    cudaMemsetAsync(s->i_vphase, 0, s->n_inst * sizeof(uint32_t), c->st);
     return check(c, "sur_advance");
 }
 
