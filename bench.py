@@ -331,7 +331,8 @@ def run_ours(args):
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
-        if tr.get("kernel_rev") == S.KERNEL_REV:
+        # captured on the Wendland C2 build; the cubic-spline build has none
+        if tr.get("kernel_rev") == S.KERNEL_REV and args.formulation == "default":
             traffic = tr.get("bytes_per_launch", {}).get(args.workload)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
