@@ -180,7 +180,9 @@ int sph_instance_state(sph_ctx *ctx, double *t, double *dt, uint32_t *done,
 
 /* Restore each member's simulated time and step count (host arrays of
  * n_inst entries; steps may be NULL to keep the counts), e.g. after
- * sph_upload of a checkpointed state.  A member whose t reaches its t_end is
+ * sph_upload of a checkpointed state (the saved state of Sec. 3, copied to
+ * the host when saving, is what a run resumes from).  Times must be finite
+ * and non-negative (SPH_ERR_INVALID_ARG otherwise).  A member whose t reaches its t_end is
  * marked done again, one below it runs again.  With the symplectic
  * scheme the next step size comes from the state alone, so a run resumed
  * from (state, t, steps) repeats the uninterrupted run bit for bit; the
