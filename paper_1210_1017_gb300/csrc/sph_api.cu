@@ -94,16 +94,6 @@ __global__ void k_pack(uint32_t n, const double* __restrict__ x, const double* _
 
 namespace {
 
-int fail(sph_ctx* c, int code, const std::string& msg) {
-    if (c) c->err = msg;
-    return code;
-}
-
-int cuda_check(sph_ctx* c, cudaError_t e, const char* what) {
-    if (e == cudaSuccess) return SPH_OK;
-    return fail(c, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
 int validate_shared(const sph_params* p) {
     if (!p) return SPH_ERR_INVALID_ARG;
     if (!(p->h > 0.0) || !(p->rho0 > 0.0) || !(p->mass > 0.0) || !(p->cfl > 0.0) ||

@@ -84,3 +84,19 @@ struct sph_ctx {
     std::string err;
 };
 
+namespace sph {
+
+// Record a one-line error message on the context and return the code.
+inline int fail(sph_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+// SPH_OK, or SPH_ERR_CUDA with the runtime's message.
+inline int cuda_check(sph_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SPH_OK;
+    return fail(c, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace sph
+

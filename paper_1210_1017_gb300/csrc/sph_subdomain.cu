@@ -121,17 +121,6 @@ __global__ void __launch_bounds__(256) k_sub_gather(const uint32_t* __restrict__
 
 inline uint32_t blocks256(uint32_t n) { return n ? (n + 255u) / 256u : 1u; }
 
-int fail(sph_ctx* c, int code, const char* msg) {
-    c->err = msg;
-    return code;
-}
-
-int cuda_ok(sph_ctx* c, cudaError_t e, const char* what) {
-    if (e == cudaSuccess) return SPH_OK;
-    c->err = std::string(what) + ": " + cudaGetErrorString(e);
-    return SPH_ERR_CUDA;
-}
-
 }  // namespace
 
 }  // namespace sph
@@ -178,11 +167,11 @@ extern "C" int sph_subdomain_select(sph_ctx* c, int mode, double xlo, double xhi
     la.cnt = c->sub_cnt;
     cudaMemsetAsync(c->sub_cnt, 0, 4 * sizeof(uint32_t), st);
     k_sub_label<<<blocks256(n), 256, 0, st>>>(la);
-    int rc = cuda_ok(c, cudaGetLastError(), "sub-domain labels");
+    int rc = cuda_check(c, cudaGetLastError(), "sub-domain labels");
     if (rc) return rc;
     uint32_t cnt[4] = {0, 0, 0, 0};
     cudaMemcpyAsync(cnt, c->sub_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-    rc = cuda_ok(c, cudaStreamSynchronize(st), "sub-domain counts");
+    rc = cuda_check(c, cudaStreamSynchronize(st), "sub-domain counts");
     if (rc) return rc;
     counts[0] = cnt[0] - cnt[1] - cnt[2];
     counts[1] = cnt[1];
@@ -219,12 +208,12 @@ extern "C" int sph_subdomain_select(sph_ctx* c, int mode, double xlo, double xhi
     k_sub_gather<<<blocks256(m), 256, 0, st>>>(c->sub_val[0], m, c->x[c->cur], c->y[c->cur],
                                                c->z[c->cur], c->vr[c->cur], c->id[c->cur], spos,
                                                svel, srho, sids);
-    rc = cuda_ok(c, cudaGetLastError(), "sub-domain sort and gather");
+    rc = cuda_check(c, cudaGetLastError(), "sub-domain sort and gather");
     if (rc) return rc;
     // cudaMemcpyDefault: host or device destinations (unified addressing)
     if (pos) cudaMemcpyAsync(pos, spos, 3 * (size_t)m * sizeof(double), cudaMemcpyDefault, st);
     if (vel) cudaMemcpyAsync(vel, svel, 3 * (size_t)m * sizeof(float), cudaMemcpyDefault, st);
     if (rho) cudaMemcpyAsync(rho, srho, (size_t)m * sizeof(float), cudaMemcpyDefault, st);
     if (ids) cudaMemcpyAsync(ids, sids, (size_t)m * sizeof(uint32_t), cudaMemcpyDefault, st);
-    return cuda_ok(c, cudaStreamSynchronize(st), "sub-domain copy");
+    return cuda_check(c, cudaStreamSynchronize(st), "sub-domain copy");
 }
