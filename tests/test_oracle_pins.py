@@ -380,6 +380,119 @@ def test_viscosity_switch_linearity_and_scaling():
     assert np.allclose(b2, 2 * b1, rtol=1e-12, atol=1e-12 * np.abs(b1).max())
 
 
+# --- artificial viscosity and the viscous CFL term, worked by hand -----------
+#
+# Sec. 2.2 with the readings R2 (rho_ij = (rho_i + rho_j)/2), R3 (c_i =
+# c0 (rho_i/rho0)^3) and R7 (dt = CFL min(sqrt(h/|a|), h/(c_max + mu_max)),
+# mu_max = max over pairs of h |v_ij.r_ij| / (r_ij^2 + eta^2)).  Scale-free
+# constants make every factor a small rational: h = 1, rho0 = 1000, c0 = 10,
+# gamma = 7 (B = 10^5/7), alpha = 1/2, eta^2 = h^2/100, m = 1, no gravity.
+# The kernel gradient F(r) cancels from the ratios used below, so these pins
+# fix the viscosity and the pressure terms independently of the kernel.
+
+def _hand_params(alpha=0.5):
+    return dict(dp=0.5, h=1.0, rho0=1000.0, gamma=7.0, c0=10.0, alpha=alpha,
+                eta2_coef=0.01, gravity=(0.0, 0.0, 0.0), cfl=0.2, mass=1.0,
+                dmin=(-4.0, -4.0, -4.0), dmax=(4.0, 4.0, 4.0), n_bound=0)
+
+
+def test_viscosity_of_an_approaching_pair_worked_by_hand():
+    """Two fluid particles: i at the origin with v_i = (2, 0, 0) and rho_i =
+    rho0; j at (3/2, 0, 0) with v_j = (-1, 0, 0) and rho_j = 2 rho0.
+
+      r_ij = (-3/2, 0, 0), v_ij = (3, 0, 0), v_ij.r_ij = -9/2 (approaching)
+      nu    = h v_ij.r_ij / (r^2 + eta^2) = -(9/2) / (9/4 + 1/100) = -225/113
+      c_i = 10, c_j = 10 * 2^3 = 80: c_bar = 45;  rho_bar = 1500
+      Pi_ij = -alpha c_bar nu / rho_bar = 27/904
+      P_i = 0 (rho_i = rho0);  P_j = B (2^7 - 1) / rho_j^2 = 127/280
+      a_i,x = -m (P_i + P_j + Pi_ij) F (-3/2),  drho_i/dt = m (-9/2) F
+      => a_i,x / (drho_i/dt) = -(P_j + Pi_ij)/3 = -1912/11865
+                              = -0.161146228402865571...
+         (alpha = 0: -(127/280)/3 = -0.151190476190476190...)
+      particle j: r_ji = -r_ij, same v.r, so its ratio is +1912/11865
+      mu_max = 225/113 = 1.99115044247787610...;  c_max = 80
+      dt = 0.2 / (80 + 225/113) = 0.00243928764166216945...
+           (|a| is about 0.02 here, so sqrt(h/|a|) ~ 6.5 does not decide)
+
+    Wrong readings give, for a_i,x / (drho_i/dt): eta^2 = 0.1 h^2 ->
+    -0.16076494; rho_i for rho_bar -> -0.16612410; c0 (or c_i) for c_bar ->
+    -0.15340287; and dt without mu_max would be 0.0025."""
+    p = _hand_params()
+    pos = np.array([[0.0, 0.0, 0.0], [1.5, 0.0, 0.0]])
+    vel = np.array([[2.0, 0.0, 0.0], [-1.0, 0.0, 0.0]])
+    st = oracle.State(pos, vel, np.array([1000.0, 2000.0]), np.array([0, 1], np.uint32))
+    for brute in (True, False):
+        r = oracle.Oracle(p).interact(st, brute=brute)
+        assert r["pairs"] == 2
+        ratio_i = r["a"][0, 0] / r["drho"][0]
+        ratio_j = r["a"][1, 0] / r["drho"][1]
+        assert ratio_i == pytest.approx(-1912 / 11865, rel=1e-13)
+        assert ratio_j == pytest.approx(1912 / 11865, rel=1e-13)
+        assert ratio_i == pytest.approx(-0.161146228402865571, rel=1e-13)
+        assert np.all(r["a"][:, 1:] == 0.0)
+        assert r["drho"][0] == r["drho"][1]          # v.r and F are symmetric
+        assert r["terms"][2] == pytest.approx(225 / 113, rel=1e-14)
+        assert r["terms"][1] == 80.0
+        assert r["dt"] == pytest.approx(0.00243928764166216945, rel=1e-14)
+    # without viscosity only the pressure term is left
+    r0 = oracle.Oracle(_hand_params(alpha=0.0)).interact(st, brute=True)
+    assert r0["a"][0, 0] / r0["drho"][0] == pytest.approx(-127 / 840, rel=1e-13)
+    # the viscous part alone: Pi_ij = -3 (ratio(alpha) - ratio(0))
+    pi = -3.0 * (ratio_i - r0["a"][0, 0] / r0["drho"][0])
+    assert pi == pytest.approx(27 / 904, rel=1e-11)
+    # the literal discriminates each wrong reading by far more than the tolerance
+    for wrong in (-0.16076494427558257, -0.16612410450906026, -0.15340286557100716):
+        assert abs(wrong - ratio_i) > 1e-3 * abs(ratio_i)
+
+
+def test_viscous_cfl_term_from_a_receding_pair_worked_by_hand():
+    """Three fluid particles: i and j as in the two-particle case, plus k at
+    (0, 5/4, 0) with v_k = (0, 3, 0) and rho_k = rho0/2 (c_k = 10/8,
+    P_k = B (2^-7 - 1) / 500^2 = -127/2240).  Pairs (all within 2h = 2):
+
+      (i, j): |r|^2 = 9/4,   v.r = -9/2 (approaching), |nu| = 225/113
+      (i, k): |r|^2 = 25/16, v.r = 15/4 (receding),    |nu| = 1500/629
+      (j, k): |r|^2 = 61/16, v.r = 9/4  (receding),    |nu| = 0.5886...
+
+    mu_max is set by the receding pair (i, k): 1500/629 = 2.38473767885532591;
+    c_max = 80; dt = 0.2 / (80 + 1500/629) = 0.00242763411810111926.
+    The receding pair adds no viscosity, and (i, j) acts along x and (i, k)
+    along y only, so with P_i = 0 the kernel values follow from i's
+    acceleration, F_ij = a_i,x / ((3/2)(P_j + Pi_ij)) and
+    F_ik = a_i,y / ((5/4) P_k), and Eq. 7 must then give
+    drho_i/dt = (-9/2) F_ij + (15/4) F_ik with Pi_ij = 27/904 from the
+    two-particle case (a viscosity applied to the receding pair, or any
+    other Pi_ij, breaks this identity)."""
+    p = _hand_params()
+    pos = np.array([[0.0, 0.0, 0.0], [1.5, 0.0, 0.0], [0.0, 1.25, 0.0]])
+    vel = np.array([[2.0, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.0, 3.0, 0.0]])
+    rho = np.array([1000.0, 2000.0, 500.0])
+    st = oracle.State(pos, vel, rho, np.array([0, 1, 2], np.uint32))
+    r = oracle.Oracle(p).interact(st, brute=True)
+    assert r["pairs"] == 6
+    assert r["terms"][2] == pytest.approx(1500 / 629, rel=1e-14)
+    assert r["terms"][1] == 80.0
+    assert r["dt"] == pytest.approx(0.00242763411810111926, rel=1e-14)
+    Pj, Pk, Pij = 127 / 280, -127 / 2240, 27 / 904
+    F_ij = r["a"][0, 0] / (1.5 * (Pj + Pij))
+    F_ik = r["a"][0, 1] / (1.25 * Pk)
+    assert F_ij < 0 and F_ik < 0                       # the kernel decreases
+    assert r["drho"][0] == pytest.approx(-4.5 * F_ij + 3.75 * F_ik, rel=1e-12)
+    # the same identity with a viscosity on the receding pair would be off
+    nu_ik = 1500 / 629
+    Pik_wrong = -0.5 * (10 + 1.25) / 2 * nu_ik / 750
+    F_ik_wrong = r["a"][0, 1] / (1.25 * (Pk + Pik_wrong))
+    assert abs((-4.5 * F_ij + 3.75 * F_ik_wrong) - r["drho"][0]) > 1e-3 * abs(r["drho"][0])
+    # a boundary particle never sets mu_max by itself: with k a boundary
+    # particle (id below n_bound) mu_max comes from fluid i's pairs, which
+    # still include (i, k)
+    pb = dict(p, n_bound=1)
+    st_b = oracle.State(pos[[2, 0, 1]], vel[[2, 0, 1]], rho[[2, 0, 1]],
+                        np.array([0, 1, 2], np.uint32))
+    rb = oracle.Oracle(pb).interact(st_b, brute=True)
+    assert rb["terms"][2] == pytest.approx(1500 / 629, rel=1e-14)
+
+
 # --- time step and integrator ------------------------------------------------
 
 def _isolated(n=5, dp=0.02, v=None, n_bound=0):
