@@ -89,7 +89,7 @@ typedef struct sph_params {
 } sph_params;
 
 /* sph_params.scheme bits: the paper's own formulation.
- *   SPH_SCHEME_CUBIC   the cubic spline kernel of Sec. 2.1 (the kernel of
+ *   SPH_SCHEME_CUBIC   the cubic spline kernel of Sec. 2.2 (the kernel of
  *                      the paper's results) instead of Wendland C2:
  *                      W = aD (1 - 3/2 q^2 + 3/4 q^3) for q < 1,
  *                      aD/4 (2 - q)^3 for 1 <= q < 2, aD = 1/(pi h^3)
@@ -251,10 +251,14 @@ int sph_verlet(sph_ctx *ctx);
 int sph_step(sph_ctx *ctx, uint32_t nsteps);
 
 /* Run nsteps steps; after every save_every steps (and at the end) wait for
- * the stream and call cb(user, step, t), from which the caller may call
- * sph_download or sph_diagnostics (the paper's "copy to the host only when
- * saving", Sec. 3).  cb may be NULL.  A non-zero return from cb stops the
- * rollout early (still SPH_OK).  Sync. */
+ * the stream, read the device status word and call cb(user, step, t), from
+ * which the caller may call sph_download or sph_diagnostics (the paper's
+ * "copy to the host only when saving", Sec. 3).  cb may be NULL.  A non-zero
+ * return from cb stops the rollout early (still SPH_OK).  A status bit set
+ * during a chunk (non-finite rates, a bounded wait that gave up, a capacity
+ * overflow) ends the rollout at that save boundary, before cb, with the
+ * code sph_check returns; the state is that of the end of the chunk.
+ * Sync. */
 typedef int (*sph_snapshot_fn)(void *user, uint64_t step, double t);
 int sph_rollout(sph_ctx *ctx, uint32_t nsteps, uint32_t save_every,
                 sph_snapshot_fn cb, void *user);
@@ -328,6 +332,17 @@ int sph_neighbour_counts_fp64(sph_ctx *ctx);
 /* FP64 conservation sums, counters and status.  Sync. */
 int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
 
+/* Free-surface front of the dam-break flow (the test case of Sec. 6, Fig. 1;
+ * the paper plots it but does not define it): for each member, the largest
+ * FP64 x of the in-domain fluid particles with z_lo <= z < z_hi -- for a
+ * surge along +x over a floor at z_f, the band z_f <= z < z_f + 2 dp.
+ * front[n_inst] is a caller-owned host array; a member with no particle in
+ * the band gets -INFINITY.  Needs z_lo < z_hi (SPH_ERR_INVALID_ARG) and
+ * built cells (SPH_ERR_STATE).  A maximum does not depend on the order of
+ * the particles, so the value is exact (bit-identical to the same maximum
+ * taken on the host).  Sync. */
+int sph_front(sph_ctx *ctx, double z_lo, double z_hi, double *front);
+
 /* Map the device status word to an error code (SPH_OK if clear).  Sync.
  * The word keeps its bits until sph_clear_status. */
 int sph_check(sph_ctx *ctx);
@@ -364,6 +379,15 @@ int sph_autotune(sph_ctx *ctx, uint32_t reps, float *ms_per_variant,
 /* Number of kernels one sph_step(ctx, 1) launches. */
 uint32_t sph_kernels_per_step(const sph_ctx *ctx);
 
+/* FP32 issue-rate probe (a measurement helper; the paper has no
+ * counterpart): launches `blocks` blocks of 256 threads on stream, each
+ * thread running `iters` iterations of 128 independent fused multiply-adds
+ * (256 flop), and writes one float per thread to d_out (a caller-owned
+ * device array of blocks * 256 floats).  Timing it with events gives the
+ * measured FP32 peak used as the interaction's roofline denominator.
+ * Async. */
+int sph_fma_probe(float *d_out, uint32_t blocks, uint32_t iters, void *stream);
+
 const char *sph_last_error(const sph_ctx *ctx);
 void sph_destroy(sph_ctx *ctx);
 
@@ -381,20 +405,42 @@ int sph_radix_sort_pairs(const uint32_t *d_keys_in, const uint32_t *d_vals_in,
                          uint32_t n, uint32_t key_bits, void *d_scratch,
                          uint64_t scratch_bytes, void *stream);
 
+/* Outcome of the last sph_radix_sort_pairs call of n pairs on d_scratch:
+ * waits for stream, then SPH_OK, or SPH_ERR_TIMEOUT if a decoupled look-back
+ * wait gave up (its bounded spin ran out; the order is then not valid).
+ * Each sort clears the flag before it starts.  Arguments as for the sort
+ * (n >= 1).  Sync. */
+int sph_radix_sort_status(const void *d_scratch, uint64_t scratch_bytes,
+                          uint32_t n, void *stream);
+
+/* Self-test of that failure path; the paper has no counterpart.  Runs the
+ * sort's look-back on d_scratch (laid out for n pairs) against a
+ * predecessor tile whose status nothing publishes, with a limit of `polls`
+ * polls (1 to 2^20), so the wait gives up and the next
+ * sph_radix_sort_status reports SPH_ERR_TIMEOUT.  Sync. */
+int sph_radix_sort_selftest_timeout(void *d_scratch, uint64_t scratch_bytes,
+                                    uint32_t n, uint32_t polls, void *stream);
+
 /* The same stable radix sort without caller scratch.  The paper has no
  * counterpart: this is for callers that cannot give the library device
  * memory -- C code with no device allocator of its own, a process whose
  * device memory belongs to another allocator's pool, or a latency-critical
  * loop that must not call cudaMalloc/cudaFree (they can synchronise the
  * device).  The scratch lives in a fixed array inside libsph.so, about
- * 9 MB per device, held until the process exits; nothing is allocated per
- * call.  Limits and behaviour:
+ * 9.4 MB per device: it is reserved on every device whose context loads the
+ * library's module, whether or not this entry point is ever called, and
+ * held until the process exits; nothing is allocated per call.  Limits and
+ * behaviour:
  *   - n <= SPH_RADIX_SORT_STATIC_MAX_N, else SPH_ERR_TOO_LARGE (no work done)
  *   - arrays as for sph_radix_sort_pairs (device, n uint32 each, outputs not
  *     aliasing inputs, d_vals_in may be NULL for values 0..n-1)
  *   - the first call with a given device current looks up the array's
  *     device address (a CUDA runtime query): make that first call before
- *     any stream capture
+ *     any stream capture.  The address is kept for the life of the process:
+ *     after cudaDeviceReset (or any teardown of the device's primary
+ *     context) it is stale, so do not use this entry point after one
+ *   - a look-back wait that gave up is reported by
+ *     sph_radix_sort_static_status, not by the return value
  *   - all calls on one device share the array and it keeps the last call's
  *     contents (each call clears what must start at zero); calls that overlap
  *     on the GPU race, so serialise them (e.g. one stream)
@@ -404,6 +450,18 @@ int sph_radix_sort_pairs_static(const uint32_t *d_keys_in,
                                 const uint32_t *d_vals_in,
                                 uint32_t *d_keys_out, uint32_t *d_vals_out,
                                 uint32_t n, uint32_t key_bits, void *stream);
+
+/* Outcome of the last sph_radix_sort_pairs_static call on the current
+ * device: waits for stream, then SPH_OK or SPH_ERR_TIMEOUT (a look-back
+ * wait gave up; the order is then not valid).  Reads the fixed array; the
+ * same first-call and overlap rules apply.  Sync. */
+int sph_radix_sort_static_status(void *stream);
+
+/* Self-test of that failure path on the fixed array (the paper has no
+ * counterpart), as sph_radix_sort_selftest_timeout: afterwards
+ * sph_radix_sort_static_status reports SPH_ERR_TIMEOUT until the next
+ * sort.  polls 1 to 2^20.  Sync. */
+int sph_radix_sort_static_selftest_timeout(uint32_t polls, void *stream);
 
 #ifdef __cplusplus
 }

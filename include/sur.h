@@ -145,6 +145,13 @@ int sur_rollout(sur_ctx *ctx, struct sph_ctx *sph, float *d_hist,
                 void *user);
 
 uint32_t sur_num_edges(const sur_ctx *ctx);
+/* The graph of the last sur_forward, in the particle order of the SPH
+ * context at that call (its cell order): rowptr[n + 1] (CSR row starts of
+ * the receiving particles i) and col[sur_num_edges] (the sending particles
+ * j of each row, with |r_i - r_j| < 2h by the FP64 predicate of Sec. 3.1),
+ * both caller-owned host arrays.  SPH_ERR_STATE before the first forward.
+ * Sync. */
+int sur_read_graph(sur_ctx *ctx, uint32_t *rowptr, uint32_t *col);
 const char *sur_last_error(const sur_ctx *ctx);
 void sur_destroy(sur_ctx *ctx);
 

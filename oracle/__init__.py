@@ -39,7 +39,7 @@ class _Params(C.Structure):
                 ("dmax", C.c_double * 3), ("n_bound", C.c_int64),
                 ("kernel", C.c_int64)]
 
-# Smoothing kernels the oracle knows (Sec. 2.1), by the name a case uses.
+# Smoothing kernels the oracle knows (Sec. 2.2), by the name a case uses.
 KERNELS = {"wendland": 0, "cubic": 1}
 
 

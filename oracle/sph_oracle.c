@@ -26,7 +26,7 @@
  *   - rho_ij in Pi_ij is the pair mean (rho_i + rho_j)/2.
  *   - c_i = sqrt(dp/drho at rho_i) = c0 (rho_i/rho0)^((gamma-1)/2).
  *   - Kernel: Wendland C2 with h = 1.3 dp, or the paper's own cubic spline
- *     (Sec. 2.1, or_params.kernel = 1); support |r_ij| < 2h strictly.
+ *     (Sec. 2.2, or_params.kernel = 1); support |r_ij| < 2h strictly.
  *   - Integrator: the symplectic predictor-corrector (position-Verlet
  *     midpoint form) with two force evaluations per step; the step size is
  *     set from the first evaluation of each step.  Or the paper's own
@@ -57,7 +57,7 @@ typedef struct {
     double cfl, mass;
     double dmin[3], dmax[3];
     int64_t n_bound;          /* ids below n_bound are boundary particles */
-    int64_t kernel;           /* 0: Wendland C2, 1: cubic spline (Sec. 2.1) */
+    int64_t kernel;           /* 0: Wendland C2, 1: cubic spline (Sec. 2.2) */
 } or_params;
 
 /* ---------------------------------------------------------------- grid -- */
@@ -266,7 +266,7 @@ void or_neighbour_counts(const or_params *P, int64_t n, const double *x,
 
 /* ------------------------------------------------------------- physics -- */
 
-/* Smoothing kernels, q = r/h, compact support q < 2 (Sec. 2.1).
+/* Smoothing kernels, q = r/h, compact support q < 2 (Sec. 2.2).
  *
  * Wendland C2:  W = aD (1 - q/2)^4 (2q + 1),  aD = 21/(16 pi h^3).
  * Cubic spline (the kernel of the paper's results), aD = 1/(pi h^3):

@@ -8,7 +8,7 @@ imports this module, and it shares no code with the CUDA path.
 
 The surrogate is not part of the paper.  It learns the particle update that
 the paper's WCSPH method computes (Sec. 2-3): the graph is the paper's
-neighbour relation (pairs closer than the kernel support 2h, Sec. 2.1 and
+neighbour relation (pairs closer than the kernel support 2h, Sec. 2.2 and
 Sec. 3.1), and the network is the plain definition below, written with plain
 PyTorch CPU ops in float64:
 

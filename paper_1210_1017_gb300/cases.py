@@ -87,7 +87,7 @@ class Case:
     fluid_height: float
     eta2_coef: float = 0.01
     gamma: float = 7.0
-    kernel: str = "wendland"          # or "cubic" (the paper's, Sec. 2.1)
+    kernel: str = "wendland"          # or "cubic" (the paper's, Sec. 2.2)
     integrator: str = "symplectic"    # or "verlet" (the paper's, Sec. 3.3)
     verlet_every: int = 40            # Verlet: an Euler step every this many
     meta: dict = field(default_factory=dict)

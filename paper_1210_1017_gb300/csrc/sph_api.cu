@@ -227,6 +227,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->id_flag = cv.take<uint32_t>(1);
     c->diag_out = cv.take<double>(8);
     c->diag_part = cv.take<double>(8 * kDiagBlocks);
+    c->front = cv.take<unsigned long long>(n_inst);
     c->counters = cv.take<unsigned long long>(8);
     c->d_inst = cv.take<Inst>(n_inst);
     c->d_cell_base = cv.take<uint32_t>(n_inst + 1);
@@ -708,6 +709,10 @@ int sph_rollout(sph_ctx* c, uint32_t nsteps, uint32_t save_every, sph_snapshot_f
         done += k;
         rc = cuda_check(c, cudaStreamSynchronize(c->st), "rollout sync");
         if (rc) return rc;
+        // the device status word at every save boundary: a non-finite rate,
+        // a wait that gave up or a capacity overflow ends the rollout here
+        rc = sph_check(c);
+        if (rc) return rc;
         if (cb) {
             double t = 0.0;
             unsigned long long s = 0;
@@ -853,6 +858,32 @@ int sph_diagnostics(sph_ctx* c, sph_diag* out) {
     return SPH_OK;
 }
 
+int sph_front(sph_ctx* c, double z_lo, double z_hi, double* front) {
+    if (!c || !front) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
+    if (!(z_lo < z_hi)) return fail(c, SPH_ERR_INVALID_ARG, "need z_lo < z_hi");
+    if (!c->have_state || !c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
+    launch_front(c->d, c->x[c->cur], c->z[c->cur], c->id[c->cur], c->off, z_lo, z_hi, c->front,
+                 c->st);
+    int rc = post_launch(c, "front");
+    if (rc) return rc;
+    std::vector<unsigned long long> img(c->n_inst);
+    rc = cuda_check(c, cudaMemcpyAsync(img.data(), c->front, c->n_inst * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost, c->st), "front copy");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaStreamSynchronize(c->st), "front sync");
+    if (rc) return rc;
+    for (uint32_t q = 0; q < c->n_inst; ++q) {
+        const unsigned long long u = img[q];
+        if (u == 0) {
+            front[q] = -INFINITY;
+            continue;
+        }
+        const unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u;
+        memcpy(&front[q], &b, sizeof(double));
+    }
+    return SPH_OK;
+}
+
 int sph_check(sph_ctx* c) {
     if (!c) return SPH_ERR_INVALID_ARG;
     uint32_t status = 0;
@@ -860,7 +891,8 @@ int sph_check(sph_ctx* c) {
     if (rc) return rc;
     rc = cuda_check(c, cudaStreamSynchronize(c->st), "check sync");
     if (rc) return rc;
-    if (status & SPH_STATUS_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "radix sort look-back gave up");
+    if (status & SPH_STATUS_TIMEOUT)
+        return fail(c, SPH_ERR_TIMEOUT, "a bounded device wait gave up (radix-sort look-back or staging copy)");
     if (status & SPH_STATUS_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite interaction result");
     if (status & SPH_STATUS_CAPACITY) return fail(c, SPH_ERR_CAPACITY, "a cell exceeded the id tie-break capacity");
     return SPH_OK;
@@ -1011,6 +1043,57 @@ int sph_radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kou
         cv_ = ov;
     }
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+// The error word of a scratch laid out by sph_radix_sort_pairs for n pairs.
+static uint32_t* sort_err_word(void* scratch, uint32_t n) {
+    Carver cv(scratch);
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(4 * 256);
+    cv.take<uint32_t>(4 + (size_t)4 * os_tiles(n) * 256);
+    return cv.take<uint32_t>(1);
+}
+
+static int sort_scratch_args(const void* scratch, uint64_t scratch_bytes, uint32_t n) {
+    if (!scratch || n == 0 || n >= (1u << 30)) return SPH_ERR_INVALID_ARG;
+    if (((uintptr_t)scratch % kAlign) != 0 || scratch_bytes < sph_radix_sort_scratch_bytes(n))
+        return SPH_ERR_WORKSPACE;
+    return SPH_OK;
+}
+
+int sph_radix_sort_status(const void* d_scratch, uint64_t scratch_bytes, uint32_t n,
+                          void* stream) {
+    int rc = sort_scratch_args(d_scratch, scratch_bytes, n);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, sort_err_word(const_cast<void*>(d_scratch), n), sizeof(word),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    return (word & kStatusTimeout) ? SPH_ERR_TIMEOUT : SPH_OK;
+}
+
+int sph_radix_sort_selftest_timeout(void* d_scratch, uint64_t scratch_bytes, uint32_t n,
+                                    uint32_t polls, void* stream) {
+    int rc = sort_scratch_args(d_scratch, scratch_bytes, n);
+    if (rc) return rc;
+    if (polls == 0 || polls > (1u << 20)) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    Carver cv(d_scratch);
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(4 * 256);
+    uint32_t* tilectr = cv.take<uint32_t>(4 + (size_t)4 * os_tiles(n) * 256);
+    uint32_t* err = cv.take<uint32_t>(1);
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+    // tile 1 of the first pass waits on tile 0's status words, zeroed here
+    // and published by nobody
+    launch_lookback_selftest(tilectr + 4, polls, err, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    return SPH_OK;
 }
 
 }  // extern "C"

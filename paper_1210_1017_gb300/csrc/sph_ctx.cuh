@@ -59,6 +59,7 @@ struct sph_ctx {
     uint32_t *sub_hist, *sub_os, *sub_cnt;
     size_t sub_os_bytes = 0;
     double *diag_out, *diag_part;
+    unsigned long long* front;   // per-member front images (sph_front)
     unsigned long long* counters;
     // ensemble table and per-member state (device)
     sph::Inst* d_inst;

@@ -75,7 +75,7 @@ struct Dev {
     float eta2;            // eta^2
     float fc;              // gradient factor: -5 aD/h^2 (Wendland C2) or aD/h^2
                            // (cubic spline, aD = 1/(pi h^3))
-    int kern;              // 0: Wendland C2, 1: cubic spline (Sec. 2.1)
+    int kern;              // 0: Wendland C2, 1: cubic spline (Sec. 2.2)
     uint32_t verlet_every; // Verlet: an Euler step every this many steps
     float alpha, rho0, inv_rho0, mass;
     float gx, gy, gz;
@@ -205,5 +205,8 @@ constexpr int kDiagBlocks = 152;
 void launch_diag(const Dev& d, const double* x, const double* y, const double* z,
                  const float4* vr, const uint32_t* id, const uint32_t* off,
                  double* partial, double* out, cudaStream_t st);
+void launch_front(const Dev& d, const double* x, const double* z, const uint32_t* id,
+                  const uint32_t* off, double zlo, double zhi, unsigned long long* out,
+                  cudaStream_t st);
 
 }  // namespace sph

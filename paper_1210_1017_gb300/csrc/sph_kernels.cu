@@ -308,7 +308,7 @@ __constant__ KeepTable c_keep = make_keep_table();
 // itself, placed 4 cells away) contributes exactly nothing and is not
 // counted, which lets lane work be padded with it.  Masks are products with
 // 0 or 1 rather than selects, keeping the integer/logic pipe free.
-// KERN: 0 Wendland C2, 1 cubic spline (Sec. 2.1).
+// KERN: 0 Wendland C2, 1 cubic spline (Sec. 2.2).
 template <int KERN, bool MOM, bool CHECK = false>
 __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4& pi,
                                            const float4& vi, float ci, float dx, float dy, float dz,
@@ -1315,6 +1315,51 @@ __global__ void k_diag_final(const double* __restrict__ part, int nparts, double
     out[threadIdx.x] = a;
 }
 
+// Free-surface front (the front position of the dam-break results): per
+// instance, the largest x of the in-domain fluid particles with zlo <= z <
+// zhi.  Maxima are kept as order-preserving 64-bit images of the FP64 x (a
+// maximum does not depend on the order of the updates); 0 stands for "no
+// particle".  Each thread folds its particles of one instance before an
+// atomic, and a warp whose lanes agree on the instance folds once more.
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void __launch_bounds__(256) k_front(const Dev d, const double* __restrict__ x,
+                                               const double* __restrict__ z,
+                                               const uint32_t* __restrict__ id,
+                                               const uint32_t* __restrict__ off, double zlo,
+                                               double zhi, unsigned long long* __restrict__ out) {
+    const uint32_t n_in = off[d.ncells];
+    uint32_t qc = 0xffffffffu;
+    unsigned long long best = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_in; k += gridDim.x * blockDim.x) {
+        const double zk = z[k];
+        if (!(zk >= zlo && zk < zhi)) continue;
+        const uint32_t pid = id[k];
+        const uint32_t q = find_instance(d.id_base, d.n_inst, pid);
+        if (pid < d.inst[q].id_fluid) continue;
+        if (q != qc) {
+            if (best) atomicMax(out + qc, best);
+            qc = q;
+            best = 0;
+        }
+        const unsigned long long b = ordered_bits(x[k]);
+        best = b > best ? b : best;
+    }
+    const uint32_t q0 = __shfl_sync(kFull, qc, 0);
+    if (__all_sync(kFull, qc == q0 || best == 0)) {
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(kFull, best, o);
+            best = t > best ? t : best;
+        }
+        if ((threadIdx.x & 31) == 0 && best) atomicMax(out + q0, best);
+    } else if (best) {
+        atomicMax(out + qc, best);
+    }
+}
+
 inline uint32_t blocks_for(uint32_t n, uint32_t t) { return n ? (n + t - 1) / t : 1; }
 
 }  // namespace
@@ -1443,6 +1488,13 @@ void launch_diag(const Dev& d, const double* x, const double* y, const double* z
                  double* out, cudaStream_t st) {
     k_diag_part<<<kDiagBlocks, 256, 0, st>>>(d, x, y, z, vr, id, off, partial);
     k_diag_final<<<1, 32, 0, st>>>(partial, kDiagBlocks, out);
+}
+
+void launch_front(const Dev& d, const double* x, const double* z, const uint32_t* id,
+                  const uint32_t* off, double zlo, double zhi, unsigned long long* out,
+                  cudaStream_t st) {
+    cudaMemsetAsync(out, 0, d.n_inst * sizeof(unsigned long long), st);
+    k_front<<<kDiagBlocks, 256, 0, st>>>(d, x, z, id, off, zlo, zhi, out);
 }
 
 }  // namespace sph

@@ -95,3 +95,30 @@ extern "C" int sph_radix_sort_pairs_static(const uint32_t* d_keys_in, const uint
     }
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }
+
+extern "C" int sph_radix_sort_static_status(void* stream) {
+    uint32_t* s = nullptr;
+    const int rc = scratch_for_current_device(&s);
+    if (rc != SPH_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, s + kErr, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    return (word & kStatusTimeout) ? SPH_ERR_TIMEOUT : SPH_OK;
+}
+
+extern "C" int sph_radix_sort_static_selftest_timeout(uint32_t polls, void* stream) {
+    if (polls == 0 || polls > (1u << 20)) return SPH_ERR_INVALID_ARG;
+    uint32_t* s = nullptr;
+    const int rc = scratch_for_current_device(&s);
+    if (rc != SPH_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(s + kErr, 0, sizeof(uint32_t), st);
+    // tile 1 of the first pass waits on tile 0's status words (zeroed by the
+    // self-test launch), which nothing publishes
+    launch_lookback_selftest(s + kStatus, polls, s + kErr, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    return SPH_OK;
+}

@@ -953,6 +953,25 @@ int sur_rollout(sur_ctx* c, sph_ctx* s, float* d_hist, uint32_t ncalls, uint32_t
 
 uint32_t sur_num_edges(const sur_ctx* c) { return c ? c->E : 0; }
 
+int sur_read_graph(sur_ctx* c, uint32_t* rowptr, uint32_t* col) {
+    if (!c || !rowptr || !col) return SPH_ERR_INVALID_ARG;
+    if (!c->have_forward) {
+        c->err = "no graph yet (call sur_forward first)";
+        return SPH_ERR_STATE;
+    }
+    cudaError_t e = cudaMemcpyAsync(rowptr, c->rowptr, ((size_t)c->n + 1) * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && c->E)
+        e = cudaMemcpyAsync(col, c->col, (size_t)c->E * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        c->err = std::string("read graph: ") + cudaGetErrorString(e);
+        return SPH_ERR_CUDA;
+    }
+    return SPH_OK;
+}
+
 const char* sur_last_error(const sur_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
 void sur_destroy(sur_ctx* c) { delete c; }

@@ -39,7 +39,9 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_radix_sort_pairs_static", "sph_query_sizes_batch", "sph_init_batch",
             "sph_instance_state", "sph_num_variants", "sph_set_variant", "sph_autotune",
             "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout",
-            "sph_set_instance_state"]
+            "sph_set_instance_state", "sph_front", "sph_radix_sort_status",
+            "sph_radix_sort_selftest_timeout", "sph_radix_sort_static_status",
+            "sph_radix_sort_static_selftest_timeout", "sph_fma_probe"]
 
 
 class SphParams(C.Structure):
@@ -142,6 +144,12 @@ def lib(build: bool = False):
     L.sph_radix_sort_scratch_bytes.restype = u64
     L.sph_radix_sort_pairs.argtypes = [vp, vp, vp, vp, u32, u32, vp, u64, vp]
     L.sph_radix_sort_pairs_static.argtypes = [vp, vp, vp, vp, u32, u32, vp]
+    L.sph_radix_sort_status.argtypes = [vp, u64, u32, vp]
+    L.sph_radix_sort_selftest_timeout.argtypes = [vp, u64, u32, u32, vp]
+    L.sph_radix_sort_static_status.argtypes = [vp]
+    L.sph_radix_sort_static_selftest_timeout.argtypes = [u32, vp]
+    L.sph_front.argtypes = [vp, C.c_double, C.c_double, vp]
+    L.sph_fma_probe.argtypes = [vp, u32, u32, vp]
     PI = C.POINTER(SphInstance)
     L.sph_query_sizes_batch.argtypes = [P, PI, u32, C.POINTER(SphSizes)]
     L.sph_init_batch.argtypes = [P, PI, u32, vp, u64, vp, C.POINTER(vp)]
@@ -397,6 +405,44 @@ def sph_diagnostics(ctx) -> dict:
     return d.as_dict()
 
 
+def sph_front(ctx, n_inst: int, z_lo: float, z_hi: float) -> np.ndarray:
+    """Per member, the largest x of fluid particles with z_lo <= z < z_hi
+    (-inf where none)."""
+    out = np.zeros(n_inst, np.float64)
+    _check(lib().sph_front(ctx, float(z_lo), float(z_hi), _ptr(out)), ctx, "sph_front")
+    return out
+
+
+FMA_PROBE_FLOP_PER_THREAD_ITER = 256
+
+
+def fp32_peak_tflops(torch, device, reps=10, iters=2000, blocks_per_sm=8, sms=None):
+    """Measured FP32 peak: sph_fma_probe over every SM (blocks_per_sm blocks
+    of 256 threads each), timed with CUDA events on a private stream after
+    one warm-up launch; returns (best, median) TFLOP/s over reps launches."""
+    if sms is None:
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * blocks_per_sm
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=device)
+    st = torch.cuda.Stream(device=device)
+    flop = float(blocks) * 256 * iters * FMA_PROBE_FLOP_PER_THREAD_ITER
+    L = lib()
+    ms = []
+    with torch.cuda.stream(st):
+        _check(L.sph_fma_probe(_ptr(out), blocks, iters, st.cuda_stream), what="sph_fma_probe")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(L.sph_fma_probe(_ptr(out), blocks, iters, st.cuda_stream),
+                   what="sph_fma_probe")
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    st.synchronize()
+    tf = sorted(flop / (m * 1e-3) / 1e12 for m in ms)
+    return tf[-1], tf[len(tf) // 2]
+
+
 def sph_check(ctx):
     _check(lib().sph_check(ctx), ctx, "sph_check")
 
@@ -422,6 +468,27 @@ def sph_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, scra
     _check(lib().sph_radix_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
                                       _ptr(vals_out), n, key_bits, _ptr(scratch),
                                       scratch_bytes, stream), what="sph_radix_sort_pairs")
+
+
+def sph_radix_sort_status(scratch, scratch_bytes, n, stream):
+    """Raises SphError (SPH_ERR_TIMEOUT) if the last sort on this scratch
+    gave up a look-back wait."""
+    _check(lib().sph_radix_sort_status(_ptr(scratch), scratch_bytes, n, stream),
+           what="sph_radix_sort_status")
+
+
+def sph_radix_sort_selftest_timeout(scratch, scratch_bytes, n, polls, stream):
+    _check(lib().sph_radix_sort_selftest_timeout(_ptr(scratch), scratch_bytes, n, polls, stream),
+           what="sph_radix_sort_selftest_timeout")
+
+
+def sph_radix_sort_static_status(stream):
+    _check(lib().sph_radix_sort_static_status(stream), what="sph_radix_sort_static_status")
+
+
+def sph_radix_sort_static_selftest_timeout(polls, stream):
+    _check(lib().sph_radix_sort_static_selftest_timeout(polls, stream),
+           what="sph_radix_sort_static_selftest_timeout")
 
 
 def sph_radix_sort_pairs_static(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream):
@@ -638,6 +705,10 @@ class Simulation:
 
     def diagnostics(self):
         return sph_diagnostics(self.ctx)
+
+    def front(self, z_lo, z_hi):
+        """Free-surface front per member (see sph_front)."""
+        return sph_front(self.ctx, self.n_inst, z_lo, z_hi)
 
     def check(self):
         sph_check(self.ctx)

@@ -18,7 +18,7 @@ EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_edge_laye
             "sur_param_count",
             "sur_query_bytes", "sur_init", "sur_set_params", "sur_get_params", "sur_get_grads",
             "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_rollout", "sur_make_sample",
-            "sur_num_edges",
+            "sur_num_edges", "sur_read_graph",
             "sur_last_error", "sur_destroy"]
 SUR_EPI_NONE, SUR_EPI_RELU, SUR_EPI_RESIDUAL, SUR_EPI_RELU_MASK = 0, 1, 2, 4
 
@@ -52,6 +52,7 @@ def lib():
         L.sur_rollout.argtypes = [vp, vp, vp, u32, u32, _sph.SNAPSHOT_FN, vp]
         L.sur_num_edges.argtypes = [vp]
         L.sur_num_edges.restype = u32
+        L.sur_read_graph.argtypes = [vp, vp, vp]
         L.sur_last_error.argtypes = [vp]
         L.sur_last_error.restype = C.c_char_p
         L.sur_destroy.argtypes = [vp]
@@ -251,6 +252,16 @@ class Surrogate:
     @property
     def num_edges(self):
         return sur_num_edges(self.ctx)
+
+    def read_graph(self):
+        """(rowptr, col) of the last forward's graph, in the SPH context's
+        particle order at that call."""
+        E = sur_num_edges(self.ctx)
+        rowptr = np.zeros(self.sim.n + 1, np.uint32)
+        col = np.zeros(max(E, 1), np.uint32)
+        _chk(lib().sur_read_graph(self.ctx, rowptr.ctypes.data, col.ctypes.data), self.ctx,
+             "sur_read_graph")
+        return rowptr, col[:E]
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -132,3 +132,25 @@ def test_entry_points_refuse_a_null_context(lib):
     assert lib.sph_clear_status(None) == -1
     t = (C.c_double * 1)(0.0)
     assert lib.sph_set_instance_state(None, t, None) == -1
+
+
+def test_new_entry_points_check_their_arguments_before_any_gpu_work(lib):
+    assert lib.sph_front(None, 0.0, 1.0, None) == -1
+    # standalone-sort status and self-test: scratch pointer, alignment and
+    # size are checked first, then the poll limit
+    assert lib.sph_radix_sort_status(None, 0, 8, None) == -1
+    assert lib.sph_radix_sort_status(0x1001, 1 << 20, 8, None) == -3
+    assert lib.sph_radix_sort_status(0x1000, 16, 1000, None) == -3
+    assert lib.sph_radix_sort_status(0x1000, 1 << 20, 0, None) == -1
+    need = int(lib.sph_radix_sort_scratch_bytes(1000))
+    assert lib.sph_radix_sort_selftest_timeout(0x1000, need - 1, 1000, 10, None) == -3
+    assert lib.sph_radix_sort_selftest_timeout(0x1000, need, 1000, 0, None) == -1
+    assert lib.sph_radix_sort_selftest_timeout(0x1000, need, 1000, (1 << 20) + 1, None) == -1
+    assert lib.sph_radix_sort_static_selftest_timeout(0, None) == -1
+
+
+def test_static_sort_maximum_in_the_binding_matches_the_header():
+    src = open(HEADERS[0]).read()
+    m = re.search(r"#define\s+SPH_RADIX_SORT_STATIC_MAX_N\s+\(1u\s*<<\s*(\d+)\)", src)
+    assert m, "SPH_RADIX_SORT_STATIC_MAX_N not found in sph.h"
+    assert S.SPH_RADIX_SORT_STATIC_MAX_N == 1 << int(m.group(1))

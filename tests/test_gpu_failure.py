@@ -58,3 +58,54 @@ def test_selftest_rejects_an_unbounded_poll_count():
             S.sph_selftest_timeout(sim.ctx, polls)
     sim.check()
     sim.close()
+
+
+def test_standalone_sort_reports_a_lookback_that_gave_up():
+    """sph_radix_sort_pairs keeps its look-back flag in the caller's scratch:
+    sph_radix_sort_status reads it (OK after a good sort, SPH_ERR_TIMEOUT
+    after the self-test made the bounded wait run out, OK again once the
+    next sort has cleared it)."""
+    import torch
+    L = S.lib()
+    n = 50000
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 1 << 16, n, dtype=np.uint64).astype(np.uint32)
+    kin = torch.from_numpy(keys.view(np.int32)).cuda()
+    kout, vout = torch.empty_like(kin), torch.empty_like(kin)
+    nb = int(L.sph_radix_sort_scratch_bytes(n))
+    scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    S.sph_radix_sort_pairs(kin, None, kout, vout, n, 16, scratch, nb, stream.cuda_stream)
+    S.sph_radix_sort_status(scratch, nb, n, stream.cuda_stream)
+    S.sph_radix_sort_selftest_timeout(scratch, nb, n, 500, stream.cuda_stream)
+    with pytest.raises(S.SphError, match="SPH_ERR_TIMEOUT"):
+        S.sph_radix_sort_status(scratch, nb, n, stream.cuda_stream)
+    S.sph_radix_sort_pairs(kin, None, kout, vout, n, 16, scratch, nb, stream.cuda_stream)
+    S.sph_radix_sort_status(scratch, nb, n, stream.cuda_stream)
+    stream.synchronize()
+    order = np.argsort(keys, kind="stable").astype(np.uint32)
+    assert np.array_equal(vout.cpu().numpy().view(np.uint32), order)
+
+
+def test_rollout_stops_at_the_save_boundary_where_the_status_is_set():
+    """A non-finite density makes the interaction flag SPH_STATUS_NONFINITE;
+    sph_rollout reads the status word at its first save boundary and
+    returns the error before calling the snapshot callback."""
+    case = cases.random_block(500, seed=21)
+    sim = S.Simulation.from_case(case)
+    rho = case.rho.copy()
+    rho[17] = np.nan
+    sim.upload(case.pos, case.vel, rho, case.ids)
+    calls = []
+    with pytest.raises(S.SphError, match="SPH_ERR_NONFINITE"):
+        sim.rollout(10, save_every=5, cb=lambda s, t: calls.append(s))
+    assert calls == []
+    assert sim.diagnostics()["step"] == 5
+    sim.clear_status()
+    sim.close()
+    # a clean rollout calls back at every boundary and returns normally
+    sim = S.Simulation.from_case(case)
+    calls = []
+    sim.rollout(10, save_every=5, cb=lambda s, t: calls.append(s))
+    assert calls == [5, 10]
+    sim.close()

@@ -73,3 +73,54 @@ def test_full_size_parity(name):
     assert worst <= REL_TOL
     sim.check()
     sim.close()
+
+
+def test_moving_obstacle_case_every_particle_in_the_bench_launch_shape():
+    """The 1.39M-particle dam break with obstacles after 200 symplectic steps
+    (t ~ 17 ms: the block has started to slump, velocities ~0.1 m/s, so the
+    artificial viscosity and the viscous CFL term are active), every
+    particle's rates against the FP64 oracle on the same state, in the
+    autotuned interaction shape; also the CFL terms.  Regions reported
+    separately: obstacle shells (boundary particles inside the tank, x > 1.3 m), the free
+    surface (the top 2 dp of the fluid) and the floor layer."""
+    case = cases.c2_dam_break_obstacles()
+    sim = S.Simulation.from_case(case)
+    sim.build_cells()
+    sim.autotune(reps=1)
+    sim.step(200)
+    sim.interact()
+    ace = sim.read(S.SPH_ARRAY_ACE)
+    d = sim.diagnostics()
+    dt = float(sim.read(S.SPH_ARRAY_DT)[0])
+    st = sim.download()
+    O = oracle.Oracle(case.params())
+    ref = O.interact(oracle.State(st["pos"], st["vel"], st["rho"], st["ids"]))
+    fluid = st["ids"] >= case.n_bound
+    assert np.abs(st["vel"][fluid]).max() > 0.02
+    assert ref["terms"][2] > 0.0
+    ea = np.zeros(case.n)
+    ea[fluid] = np.linalg.norm(ace[fluid, :3] - ref["a"][fluid], axis=1) / \
+        np.maximum(ref["sa"][fluid], 1e-300)
+    sd = ref["sd"]
+    ed = np.abs(ace[:, 3] - ref["drho"]) / np.where(sd > 0, sd, 1.0)
+    gl = np.linalg.norm(ace[fluid, :3] - ref["a"][fluid]) / np.linalg.norm(ref["a"][fluid])
+    z = st["pos"][:, 2]
+    regions = {
+        "obstacle shells": (~fluid) & (st["pos"][:, 0] > 1.3) & (st["pos"][:, 0] < 3.2) &
+                           (st["pos"][:, 1] > 0.0) & (st["pos"][:, 1] < 1.0) & (z > 0.0),
+        "free surface": fluid & (z > z[fluid].max() - 2 * case.dp),
+        "floor layer": fluid & (z < 2 * case.dp),
+    }
+    for name, sel in regions.items():
+        assert sel.sum() > 100, name
+        print(f"{name}: {int(sel.sum())} particles, max scaled |a| {ea[sel].max():.2e}, "
+              f"drho {ed[sel].max():.2e}")
+    print(f"all: max scaled |a| {ea.max():.2e}, drho {ed.max():.2e}, global {gl:.2e}")
+    assert ea.max() <= REL_TOL and ed.max() <= REL_TOL and gl <= REL_TOL
+    assert np.array_equal(ace[~fluid, :3], np.tile(np.float32(case.gravity), ((~fluid).sum(), 1)))
+    assert dt == pytest.approx(ref["dt"], rel=1e-5)
+    assert d["amax"] == pytest.approx(ref["terms"][0], rel=1e-5)
+    assert d["cmax"] == pytest.approx(ref["terms"][1], rel=1e-6)
+    assert d["mumax"] == pytest.approx(ref["terms"][2], rel=1e-5)
+    sim.check()
+    sim.close()

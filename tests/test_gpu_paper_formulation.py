@@ -1,5 +1,5 @@
 """The paper's own formulation on the GPU, through the C ABI, against the FP64
-oracle: the cubic spline kernel (Sec. 2.1) in the interaction and the
+oracle: the cubic spline kernel (Sec. 2.2) in the interaction and the
 second-order Verlet integrator (Sec. 3.3).
 
 Bars as for the default formulation: density rates and accelerations within

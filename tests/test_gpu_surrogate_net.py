@@ -74,15 +74,28 @@ def _rel(a, b):
 def test_graph_and_forward_match_reference(torch, n, layers):
     s = Setup(torch, n, layers, seed=n + layers)
     got = s.gpu_forward(torch)
-    # the graph: the same FP64 predicate, so the same number of edges
+    # the graph: the same FP64 predicate, so the same ordered pairs; the GPU's
+    # CSR rows are in cell order, mapped to particle ids here
     assert s.sur.num_edges == len(s.src)
+    rowptr, col = s.sur.read_graph()
+    ids = s.sim.download()["ids"].astype(np.int64)
+    g_src = ids[np.repeat(np.arange(s.n), np.diff(rowptr.astype(np.int64)))]
+    g_dst = ids[col.astype(np.int64)]
+    order = np.lexsort((g_dst, g_src))
+    assert np.array_equal(g_src[order], s.src)
+    assert np.array_equal(g_dst[order], s.dst)
     out, _, _ = s.ref(bf16=True)
     ref = out[:, :3]
     assert _cos(got, ref) >= 0.9999, _cos(got, ref)
     assert _rel(got, ref) <= 1e-2, _rel(got, ref)
-    # element-wise against the output scale
-    scale = np.abs(ref).max()
-    assert np.abs(got - ref).max() <= 5e-2 * scale
+    # element by element against a per-row scale: the row's largest
+    # component, floored at the median of those over rows (rows whose
+    # output nearly vanishes are judged at the typical output size)
+    row = np.abs(ref).max(axis=1)
+    scale = np.maximum(row, np.median(row))
+    worst = float((np.abs(got - ref) / scale[:, None]).max())
+    print(f"n={n} layers={layers}: per-row scaled element error {worst:.2e}")
+    assert worst <= 1e-2
     # the bf16 storage error itself, for the record (FP64 without rounding)
     out64, _, _ = s.ref(bf16=False)
     assert _rel(got, out64[:, :3]) <= 5e-2

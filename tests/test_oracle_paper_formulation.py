@@ -1,4 +1,4 @@
-"""Pins of the oracle's paper formulation: the cubic spline kernel (Sec. 2.1)
+"""Pins of the oracle's paper formulation: the cubic spline kernel (Sec. 2.2)
 and the second-order Verlet integrator (Sec. 3.3).
 
 As with the other pins, nothing here compares the oracle with itself: the
@@ -29,7 +29,7 @@ def _oracle(case, **over):
     return oracle.Oracle(p)
 
 
-# --- cubic spline (Sec. 2.1) -------------------------------------------------
+# --- cubic spline (Sec. 2.2) -------------------------------------------------
 
 def test_cubic_spline_integrates_to_one_with_compact_support():
     c = _cubic(cases.c1_dam_break())

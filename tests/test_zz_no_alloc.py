@@ -70,3 +70,43 @@ def test_static_scratch_sort_rejects_sizes_above_its_maximum(torch):
     assert L.sph_radix_sort_pairs_static(p, p, p, p, n, 8, None) == -8
     with pytest.raises(S.SphError, match="TOO_LARGE"):
         S.sph_radix_sort_pairs_static(small, small, small, small, n, 8, 0)
+
+
+def test_static_scratch_sort_32_bit_keys_at_the_maximum_and_implicit_values(torch):
+    """Four passes over the largest n (the status region sized for the
+    maximum tiles and passes) and d_vals_in = NULL (values 0..n-1), each
+    bit for bit against the workspace sort."""
+    L = S.lib()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(21)
+    for n, bits, with_vals in ((S.SPH_RADIX_SORT_STATIC_MAX_N, 32, True), (70001, 32, False)):
+        keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        kin = _dev(torch, keys)
+        vin = _dev(torch, rng.permutation(n).astype(np.uint32)) if with_vals else None
+        nb = int(L.sph_radix_sort_scratch_bytes(n))
+        scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        kref, vref = torch.empty_like(kin), torch.empty_like(kin)
+        S.sph_radix_sort_pairs(kin, vin, kref, vref, n, bits, scratch, nb, stream.cuda_stream)
+        kout, vout = torch.empty_like(kin), torch.empty_like(kin)
+        rc = L.sph_radix_sort_pairs_static(kin.data_ptr(), None if vin is None else vin.data_ptr(),
+                                           kout.data_ptr(), vout.data_ptr(), n, bits,
+                                           stream.cuda_stream)
+        assert rc == 0
+        assert L.sph_radix_sort_static_status(stream.cuda_stream) == 0
+        assert np.array_equal(_host(kout), _host(kref))
+        assert np.array_equal(_host(vout), _host(vref))
+        if not with_vals:
+            assert np.array_equal(_host(vout), np.argsort(keys, kind="stable").astype(np.uint32))
+
+
+def test_static_scratch_sort_reports_a_lookback_that_gave_up(torch):
+    L = S.lib()
+    stream = torch.cuda.current_stream()
+    assert L.sph_radix_sort_static_selftest_timeout(500, stream.cuda_stream) == 0
+    assert L.sph_radix_sort_static_status(stream.cuda_stream) == -4
+    keys = np.arange(1000, 0, -1, dtype=np.uint32)
+    kin = _dev(torch, keys)
+    kout, vout = torch.empty_like(kin), torch.empty_like(kin)
+    S.sph_radix_sort_pairs_static(kin, None, kout, vout, 1000, 10, stream.cuda_stream)
+    S.sph_radix_sort_static_status(stream.cuda_stream)      # cleared by the sort
+    assert np.array_equal(_host(vout), np.arange(999, -1, -1, dtype=np.uint32))
