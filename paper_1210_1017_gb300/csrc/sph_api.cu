@@ -143,6 +143,7 @@ int build_table(const sph_params* p, const sph_instance* inst, uint32_t n_inst, 
         I.id_end = (uint32_t)(ids + s.n_particles);
         I.c0 = (float)s.c0;
         I.B = (float)(s.c0 * s.c0 * p->rho0 / p->gamma);
+        I.B_d = s.c0 * s.c0 * p->rho0 / p->gamma;
         t->cell_base[q] = I.cell_base;
         t->row_base[q] = I.row_base;
         t->id_base[q] = I.id_base;

@@ -33,6 +33,7 @@ struct Inst {
     uint32_t id_end;
     float c0;               // reference speed of sound
     float B;                // Tait stiffness c0^2 rho0 / gamma
+    double B_d;             // the same in FP64 (conservation sums)
 };
 
 // Per-instance device state.

@@ -1285,7 +1285,7 @@ __global__ void __launch_bounds__(256) k_diag_part(const Dev d, const double* __
         const Inst& I = d.inst[find_instance(d.id_base, d.n_inst, pid)];
         const float4 v = vr[k];
         const double rho = v.w;
-        const double B = (double)I.c0 * (double)I.c0 * rho0 / 7.0;
+        const double B = I.B_d;
         acc[0] += m;
         // e(rho) = B [ ((rho/rho0)^6 - 1) / (6 rho0) + 1/rho - 1/rho0 ]
         const double rr = rho / rho0, r2 = rr * rr, r6 = r2 * r2 * r2;
