@@ -45,8 +45,8 @@ extern "C" {
 #define SPH_ERR_TIMEOUT       -4   /* a bounded device spin gave up         */
 #define SPH_ERR_NONFINITE     -5   /* NaN/Inf in the interaction results    */
 #define SPH_ERR_CAPACITY      -6   /* a cell held more particles than the
-                                      id tie-break handles (order within it
-                                      then follows the sort's stable order) */
+                                      id tie-break handles (the order within
+                                      it is then not the (label, id) order) */
 #define SPH_ERR_STATE         -7   /* call out of order (e.g. no state yet) */
 #define SPH_ERR_TOO_LARGE     -8   /* n above the fixed maximum of a call    */
 
@@ -103,7 +103,8 @@ typedef struct sph_sizes {
     uint64_t workspace_bytes;   /* device bytes sph_init needs            */
     uint64_t ncells;            /* ncx * ncy * ncz                        */
     uint32_t ncx, ncy, ncz;
-    uint32_t sort_passes;       /* 8-bit radix passes per cell sort        */
+    uint32_t sort_passes;       /* passes of the cell sort: 1 (a counting
+                                   sort whose one digit is the whole label) */
 } sph_sizes;
 
 typedef struct sph_diag {
@@ -198,8 +199,12 @@ int sph_set_instance_state(sph_ctx *ctx, const double *t, const uint64_t *steps)
 int sph_upload(sph_ctx *ctx, const double *pos, const float *vel,
                const float *rho, const uint32_t *ids);
 
-/* Sec. 3.1: cell label of every particle (FP64, x fastest), radix sort by
- * (label, id), first index per cell, and reorder of all state arrays.
+/* Sec. 3.1: cell label of every particle (FP64, x fastest), sort by
+ * (label, id), first index per cell, and reorder of all state arrays.  The
+ * sort is a radix sort with a single digit, the whole label (a counting
+ * sort: the per-cell counts are its histogram, the first indices its scan,
+ * one scatter places every particle in its cell); the reorder then ranks the
+ * particles of each cell by id, the tie-break of the Sec. 4.3 example.
  * Async. */
 int sph_build_cells(sph_ctx *ctx);
 
@@ -358,7 +363,7 @@ int sph_clear_status(sph_ctx *ctx);
  * `polls` polls (1 to 2^20).  The wait gives up and sets SPH_STATUS_TIMEOUT
  * in the context's status word, as a stalled sort would, so sph_check
  * returns SPH_ERR_TIMEOUT.  The particle state and cells are untouched (the
- * sort's status words it borrows are cleared before every sort).  Sync. */
+ * look-back runs on status words reserved for this test).  Sync. */
 int sph_selftest_timeout(sph_ctx *ctx, uint32_t polls);
 
 /* Block shapes of the interaction kernel ("variants": particles per work

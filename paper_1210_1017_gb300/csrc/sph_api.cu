@@ -205,7 +205,9 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->bsum = cv.take<uint32_t>(scan_bsum_count(t.ncells + 1));
     c->hist = cv.take<uint32_t>(4 * 256);
     const uint32_t tiles = os_tiles(n);
-    c->os_bytes = 4 * sizeof(uint32_t) + (size_t)passes * tiles * 256 * sizeof(uint32_t);
+    (void)passes;
+    // status words the failure-path self-test runs its look-back against
+    c->os_bytes = 4 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
     c->tilectr = cv.take<uint32_t>(c->os_bytes / sizeof(uint32_t));
     c->os_status = c->tilectr ? c->tilectr + 4 : nullptr;
     for (int b = 0; b < 2; ++b) {
@@ -307,14 +309,10 @@ Dev make_dev(const sph_ctx* c) {
 void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     cudaStream_t st = c->st;
     launch_scan_cells(c->d, c->cnt, c->bsum, c->off, st);
-    cudaMemsetAsync(c->tilectr, 0, c->os_bytes, st);
-    int src = 0;
-    for (int p = 0; p < c->passes; ++p) {
-        launch_onesweep_pass(c->key[src], p == 0 ? nullptr : c->val[src], c->key[1 - src],
-                             c->val[1 - src], c->n, p, c->bits, c->hist,
-                             c->os_status, c->tilectr, c->status, st);
-        src = 1 - src;
-    }
+    // the labels are in key[0]; one counting-sort pass groups the particles
+    // by cell into (key[1], val[1]) and the reorder applies the id tie-break
+    launch_cell_scatter(c->key[0], c->n, c->off, c->cnt, c->key[1], c->val[1], st);
+    const int src = 1;
     c->skey = src;
     launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, st);
     ReorderArgs ra;
@@ -394,14 +392,14 @@ IntegrateArgs integrate_args(sph_ctx* c, int pre) {
     a.key = c->key[0];
     a.cnt = c->cnt;
     a.hist = c->hist;
-    a.passes = c->passes;
+    a.passes = 0;   // the cell sort needs the per-cell counts only
     return a;
 }
 
 void enqueue_build(sph_ctx* c) {
     if (!c->keys_ready) {
         launch_keys(c->d, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->id[c->cur], c->n,
-                    c->key[0], c->cnt, c->hist, c->passes, c->st);
+                    c->key[0], c->cnt, c->hist, 0, c->st);
     }
     const bool with_pre = c->pre_state == 1;
     rebuild_after_keys(c, with_pre);
@@ -447,7 +445,7 @@ int query(const sph_params* params, const sph_instance* inst, uint32_t n_inst, s
     out->ncx = (uint32_t)tmp.tab.inst[0].ncx;
     out->ncy = (uint32_t)tmp.tab.inst[0].ncy;
     out->ncz = (uint32_t)tmp.tab.inst[0].ncz;
-    out->sort_passes = (uint32_t)passes;
+    out->sort_passes = 1u;   // one counting-sort pass over the whole label
     return SPH_OK;
 }
 
@@ -909,7 +907,7 @@ int sph_clear_status(sph_ctx* c) {
 int sph_selftest_timeout(sph_ctx* c, uint32_t polls) {
     if (!c) return SPH_ERR_INVALID_ARG;
     if (polls == 0 || polls > (1u << 20)) return fail(c, SPH_ERR_INVALID_ARG, "polls must be 1..2^20");
-    // the first pass's status words: cleared by every rebuild before use
+    // status words reserved for this test (zeroed by the launch)
     launch_lookback_selftest(c->os_status, polls, c->status, c->st);
     int rc = post_launch(c, "selftest");
     if (rc) return rc;
@@ -983,9 +981,9 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
-    // one rebuild: 3 cell scan + passes + 6 unit list (row sums, count, 3 scan,
-    // fill) + reorder
-    const uint32_t rebuild = 3u + (uint32_t)c->passes + 6u + 1u;
+    // one rebuild: 3 cell scan + 1 counting-sort scatter + 6 unit list (row
+    // sums, count, 3 scan, fill) + reorder
+    const uint32_t rebuild = 3u + 1u + 6u + 1u;
     // Verlet: interact + reduce + update + member advance + rebuild
     if (c->verlet) return 2u + 2u + rebuild;
     // symplectic: 2 x (interact + reduce) + predict + correct + 2 rebuilds

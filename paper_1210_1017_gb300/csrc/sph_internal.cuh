@@ -88,8 +88,15 @@ void launch_keys(const Dev& d, const double* x, const double* y, const double* z
                  int passes, cudaStream_t st);
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st);
-// out[i] = in[0] + ... + in[i-1] for i = 0..m (m + 1 outputs); clears in[].
-void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st);
+// out[i] = in[0] + ... + in[i-1] for i = 0..m (m + 1 outputs); clears in[]
+// unless zero_in is false.
+void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st,
+                 bool zero_in = true);
+// One-pass counting sort of the cell labels (keys; values = input index)
+// into (kout, vout), from the per-cell counts cnt (counted back to zero) and
+// the cell offsets off.  Order inside a cell is arbitrary.
+void launch_cell_scatter(const uint32_t* key, uint32_t n, const uint32_t* off, uint32_t* cnt,
+                         uint32_t* kout, uint32_t* vout, cudaStream_t st);
 uint32_t scan_bsum_count(uint64_t m);
 
 // Radix sort

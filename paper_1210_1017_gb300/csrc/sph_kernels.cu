@@ -128,11 +128,12 @@ __device__ __forceinline__ float p_over_rho2(const Dev& d, float B, float rho) {
 
 constexpr uint32_t kMaxSeg = 4096;   // largest cell the id tie-break handles
 
-// Sec. 3.1 reorder.  Thread k takes the k-th pair of the radix sort (stable
-// by the previous order), ranks its particle by id among the particles of
-// the same cell, and moves the particle's state to (cell start + rank): the
-// result is ordered by (label, id) whatever the previous order was.  Also
-// writes the FP32 position relative to the cell's origin and P = p/rho^2.
+// Sec. 3.1 reorder.  Thread k takes the k-th pair of the cell sort (grouped
+// by cell, any order inside a cell), ranks its particle by id among the
+// particles of the same cell, and moves the particle's state to (cell start
+// + rank): the result is ordered by (label, id) whatever the order inside
+// the cells was.  Also writes the FP32 position relative to the cell's
+// origin and P = p/rho^2.
 __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs a) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;

@@ -90,28 +90,47 @@ __global__ void __launch_bounds__(256) k_digit_hist(const uint32_t* __restrict__
 // Decoupled look-back for one digit: the sum of the counts of the tiles
 // before `tile` (status words of 256 digits per tile; a tile's word holds its
 // own count, kFlagAgg, or the inclusive prefix, kFlagPre, or 0 while it has
-// published nothing).  A predecessor that stays silent for `limit` polls
-// makes the wait give up: the timeout bit is set in *err and the partial sum
-// returned, which never exceeds the true prefix (so scatter addresses stay
-// inside the output).
+// published nothing).  The predecessors are polled kLookWin at a time (the
+// loads of one window are in flight together), and the walk takes their
+// counts in order until an inclusive prefix ends it or a silent tile stops
+// it, where the next window starts.  A predecessor that stays silent for
+// `limit` windows makes the wait give up: the timeout bit is set in *err and
+// the partial sum returned, which never exceeds the true prefix (so scatter
+// addresses stay inside the output).  Tile 0 always publishes an inclusive
+// prefix, so no window reads before it.
+constexpr int kLookWin = 8;
+
 __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* status, uint32_t tile,
                                                     int digit, uint32_t limit, uint32_t* err) {
     uint32_t excl = 0;
     int64_t p = (int64_t)tile - 1;
     uint32_t spins = 0;
     while (p >= 0) {
-        const uint32_t s = ld_relaxed(status + (size_t)p * 256 + digit);
-        const uint32_t flag = s & ~kValMask;
-        if (flag == 0u) {
-            if (++spins > limit) {
-                atomicOr(err, kStatusTimeout);
-                break;
+        uint32_t s[kLookWin];
+#pragma unroll
+        for (int j = 0; j < kLookWin; ++j)
+            s[j] = p - j >= 0 ? ld_relaxed(status + (size_t)(p - j) * 256 + digit) : kFlagPre;
+        bool stop = false, fin = false;
+        int taken = 0;
+#pragma unroll
+        for (int j = 0; j < kLookWin; ++j) {
+            if (!stop) {
+                const uint32_t flag = s[j] & ~kValMask;
+                if (flag == 0u) {
+                    stop = true;
+                } else {
+                    excl += s[j] & kValMask;
+                    ++taken;
+                    if (flag == kFlagPre) stop = fin = true;
+                }
             }
-            continue;
         }
-        excl += s & kValMask;
-        if (flag == kFlagPre) break;
-        --p;
+        if (fin) break;
+        p -= taken;
+        if (taken == 0 && ++spins > limit) {
+            atomicOr(err, kStatusTimeout);
+            break;
+        }
     }
     return excl;
 }
@@ -266,7 +285,8 @@ __global__ void __launch_bounds__(256) k_scan_top(uint32_t* bsum, uint32_t nb) {
 // next use.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ in, uint64_t m,
                                                             const uint32_t* __restrict__ bsum,
-                                                            uint32_t* __restrict__ out) {
+                                                            uint32_t* __restrict__ out,
+                                                            int zero_in) {
     __shared__ uint32_t s_w[8];
     const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
     const uint64_t t0 = b0 + (uint64_t)threadIdx.x * kScanItems;
@@ -285,7 +305,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
         const uint64_t i = t0 + r;
         if (i < m) {
             out[i] = run;
-            in[i] = 0u;
+            if (zero_in) in[i] = 0u;
         }
         if (i == m) out[m] = run;
         run += v[r];
@@ -299,16 +319,52 @@ uint32_t scan_bsum_count(uint64_t m) {
     return (uint32_t)((m + 1 + kScanChunk - 1) / kScanChunk);
 }
 
-void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st) {
+void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st,
+                 bool zero_in) {
     const uint32_t nb = scan_bsum_count(m);
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, m, bsum);
     k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
-    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, m, bsum, out);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, m, bsum, out, zero_in ? 1 : 0);
 }
 
+// The per-cell counts (incl. the excluded bin) stay in cnt: the scatter of
+// the cell sort counts them back down to zero.
 void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
                        cudaStream_t st) {
-    launch_scan(cnt, (uint64_t)d.ncells + 1, bsum, off, st);   // counts incl. the excluded bin
+    launch_scan(cnt, (uint64_t)d.ncells + 1, bsum, off, st, false);
+}
+
+// Sec. 3.1 cell sort as one counting-sort pass (a radix sort whose single
+// digit is the whole cell label): the label kernel's per-cell counts are the
+// histogram, the cell offsets its exclusive scan, and each particle takes a
+// slot of its cell's range by a warp-aggregated atomic decrement of its
+// cell's count (which leaves the counts at zero for the next rebuild).  The
+// order inside a cell is left arbitrary: the reorder ranks every particle by
+// id within its cell, which makes the result the (label, id) order.
+__global__ void __launch_bounds__(256) k_cell_scatter(const uint32_t* __restrict__ key, uint32_t n,
+                                                      const uint32_t* __restrict__ off,
+                                                      uint32_t* cnt, uint32_t* __restrict__ kout,
+                                                      uint32_t* __restrict__ vout) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t act = __ballot_sync(kFull, valid);
+    if (!valid) return;
+    const uint32_t k = key[i];
+    const uint32_t peers = __match_any_sync(act, k);
+    const int leader = __ffs(peers) - 1;
+    const uint32_t np = __popc(peers);
+    uint32_t old = 0;
+    if ((int)(threadIdx.x & 31) == leader) old = atomicSub(cnt + k, np);
+    old = __shfl_sync(peers, old, leader);
+    const uint32_t slot = off[k] + old - np + __popc(peers & lanemask_lt());
+    kout[slot] = k;
+    vout[slot] = i;
+}
+
+void launch_cell_scatter(const uint32_t* key, uint32_t n, const uint32_t* off, uint32_t* cnt,
+                         uint32_t* kout, uint32_t* vout, cudaStream_t st) {
+    if (n == 0) return;
+    k_cell_scatter<<<(n + 255) / 256, 256, 0, st>>>(key, n, off, cnt, kout, vout);
 }
 
 void launch_lookback_selftest(uint32_t* zeroed256, uint32_t limit, uint32_t* err,
