@@ -353,6 +353,70 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
     }
 }
 
+// Packed accumulators of two pair streams (the two pairs a lane evaluates
+// per step of the pair phase), one in each half of a float2.  The momentum
+// sums hold +sum f r_ij (the caller negates once at the end; negation is
+// exact, so this equals summing the negated terms).
+struct PairAcc2 {
+    float2 ax, ay, az, dr, npf;
+    float mu;
+};
+
+__device__ __forceinline__ float2 ff2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// pair_terms<KERN, true, true> for two pairs at once, with the Blackwell
+// packed FP32 operations (__ffma2_rn, __fadd2_rn, __fmul2_rn: two FP32
+// results per instruction, each rounded as the scalar operation); the
+// square roots, reciprocals, min/max and the saturated support test stay
+// scalar.  Same arithmetic per pair as pair_terms.
+template <int KERN, bool MOM>
+__device__ __forceinline__ void pair_terms2(const Dev& d, float c0, const float4& pi,
+                                            const float4& vi, float ci, float2 dx, float2 dy,
+                                            float2 dz, const float4& pa, const float4& va,
+                                            const float4& pb, const float4& vb, PairAcc2& s) {
+    const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float r2s = d.r2max * 0x1p100f;
+    const float2 use = ff2(__saturatef(fmaf(d2.x, -0x1p100f, r2s)),
+                           __saturatef(fmaf(d2.y, -0x1p100f, r2s)));
+    s.npf = __fadd2_rn(s.npf, use);
+    const float2 q = __fmul2_rn(ff2(sqrt_approx(d2.x), sqrt_approx(d2.y)), dup2(d.inv_h));
+    float2 shape;
+    if (KERN == 1) {
+        const float2 wo = __ffma2_rn(q, dup2(-1.0f), dup2(2.0f));
+        const float2 outer =
+            __fmul2_rn(__fmul2_rn(dup2(-0.75f), __fmul2_rn(wo, wo)), ff2(rcp_approx(q.x), rcp_approx(q.y)));
+        const float2 inner = __ffma2_rn(dup2(2.25f), q, dup2(-3.0f));
+        shape = ff2(q.x < 1.0f ? inner.x : outer.x, q.y < 1.0f ? inner.y : outer.y);
+    } else {
+        const float2 wq = __ffma2_rn(dup2(-0.5f), q, dup2(1.0f));
+        shape = __fmul2_rn(__fmul2_rn(wq, wq), wq);
+    }
+    const float2 F = __fmul2_rn(__fmul2_rn(dup2(d.fc), shape), use);
+    const float2 m1 = dup2(-1.0f);
+    const float2 dvx = __ffma2_rn(ff2(va.x, vb.x), m1, dup2(vi.x));
+    const float2 dvy = __ffma2_rn(ff2(va.y, vb.y), m1, dup2(vi.y));
+    const float2 dvz = __ffma2_rn(ff2(va.z, vb.z), m1, dup2(vi.z));
+    const float2 vr = __ffma2_rn(dvx, dx, __ffma2_rn(dvy, dy, __fmul2_rn(dvz, dz)));
+    s.dr = __ffma2_rn(vr, F, s.dr);                                 // Eq. 7
+    if (MOM) {
+        const float2 de = __fadd2_rn(d2, dup2(d.eta2));
+        const float2 nu = __fmul2_rn(__fmul2_rn(dup2(d.h), vr), ff2(rcp_approx(de.x), rcp_approx(de.y)));
+        const float2 rrj = __fmul2_rn(ff2(va.w, vb.w), dup2(d.inv_rho0));
+        const float2 cj = __fmul2_rn(__fmul2_rn(__fmul2_rn(dup2(c0), rrj), rrj), rrj);
+        const float2 rs = __fadd2_rn(dup2(vi.w), ff2(va.w, vb.w));
+        const float2 nmin = ff2(fminf(nu.x, 0.f), fminf(nu.y, 0.f));
+        const float2 visc = __fmul2_rn(
+            __fmul2_rn(__fmul2_rn(dup2(-d.alpha), __fadd2_rn(dup2(ci), cj)), nmin),
+            ff2(rcp_approx(rs.x), rcp_approx(rs.y)));
+        const float2 f = __fmul2_rn(__fadd2_rn(__fadd2_rn(dup2(pi.w), ff2(pa.w, pb.w)), visc), F);
+        s.ax = __ffma2_rn(f, dx, s.ax);                              // Eq. 9 (sign later)
+        s.ay = __ffma2_rn(f, dy, s.ay);
+        s.az = __ffma2_rn(f, dz, s.az);
+        s.mu = fmaxf(s.mu, fmaxf(fabsf(nu.x) * use.x, fabsf(nu.y) * use.y));
+    }
+}
+
 // Sec. 3.2.  One block takes work units in turn: up to W*32 consecutive
 // sorted particles of one row of cells (same instance, cy, cz) spanning at
 // most kSpan cells with no more than two empty cells in a row, so the
@@ -376,7 +440,7 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
 // keeps a similar share of its own neighbours in each part); the parts' sums
 // are added in a fixed order at the end.  More warps per block at the same
 // staging footprint.
-template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN>
+template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN, bool PK>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     constexpr int NT = W * SPLIT * 32;
     constexpr int FBCAP = Shape<W * SPLIT, STAGE, WCAP>::fb_cap;   // fallback list slots
@@ -559,6 +623,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             // within the support always tests negative.
             uint32_t* wl = s_words + w * (WCAP * 32) + lane;
             uint32_t* wd = s_desc + w * WCAP;
+            PairAcc2 acc2 = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), 0.f};
             const uint32_t self = valid ? s_base[4] + (i - s_rs[4]) : 0u;
             const bool anyfluid = __any_sync(kFull, fluid);
             const float inv_cs = 1.0f / d.csf;
@@ -583,39 +648,50 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 float qxw = 0.f;                         // i's x in the word's cell frame
                 const float qpad = fmaf(4.0f, d.csf, pi.x);   // pads: i itself, out of range
                 constexpr int kPop = 2;   // pairs per iteration (independent chains)
+                // the lane's next hit (its staged index and i's x in that
+                // word's cell frame), or the pad i itself, out of range
+                auto pop = [&](uint32_t& j, float& qx) {
+                    if (cm == 0 && nz != 0) {
+                        const uint32_t wi = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        cm = wl[wi * 32];
+                        const uint32_t dsc = wd[wi];
+                        jb = dsc & 0xffffu;
+                        qxw = fmaf((float)(cx - (ulo + (int)(dsc >> 16))), d.csf, pi.x);
+                    }
+                    if (cm) {
+                        const uint32_t b = 31u - __clz(cm);
+                        cm ^= 1u << b;
+                        j = jb + 4u * b - 31u * (b >> 3);
+                        qx = qxw;
+                    } else {
+                        j = self;
+                        qx = qpad;
+                    }
+                };
                 for (uint32_t t = 0; t < mx; t += kPop) {
                     uint32_t j2[kPop];
                     float qx2[kPop];
 #pragma unroll
-                    for (int k = 0; k < kPop; ++k) {
-                        // at most one step: the lane visits only its non-empty words
-                        if (cm == 0 && nz != 0) {
-                            const uint32_t wi = __ffs(nz) - 1;
-                            nz &= nz - 1;
-                            cm = wl[wi * 32];
-                            const uint32_t dsc = wd[wi];
-                            jb = dsc & 0xffffu;
-                            qxw = fmaf((float)(cx - (ulo + (int)(dsc >> 16))), d.csf, pi.x);
-                        }
-                        if (cm) {
-                            const uint32_t b = 31u - __clz(cm);
-                            cm ^= 1u << b;
-                            // bit b = 8k + j: candidate jb + 4j + k
-                            const uint32_t hi = b >> 3;
-                            j2[k] = jb + 4u * b - 31u * hi;
-                            qx2[k] = qxw;
-                        } else {
-                            j2[k] = self;
-                            qx2[k] = qpad;
-                        }
-                    }
+                    for (int k = 0; k < kPop; ++k) pop(j2[k], qx2[k]);
                     float4 pp[kPop], vv[kPop];
 #pragma unroll
                     for (int k = 0; k < kPop; ++k) {
                         pp[k] = s_p[j2[k]];
                         vv[k] = s_v[j2[k]];
                     }
-                    if (anyfluid) {
+                    if (PK) {
+                        const float2 m1 = dup2(-1.0f);
+                        const float2 dx2 = __ffma2_rn(ff2(pp[0].x, pp[1].x), m1, ff2(qx2[0], qx2[1]));
+                        const float2 dy2 = __ffma2_rn(ff2(pp[0].y, pp[1].y), m1, dup2(pi.y));
+                        const float2 dz2 = __ffma2_rn(ff2(pp[0].z, pp[1].z), m1, dup2(pi.z));
+                        if (anyfluid)
+                            pair_terms2<KERN, true>(d, c0, pi, vi, ci, dx2, dy2, dz2, pp[0], vv[0],
+                                                    pp[1], vv[1], acc2);
+                        else
+                            pair_terms2<KERN, false>(d, c0, pi, vi, ci, dx2, dy2, dz2, pp[0], vv[0],
+                                                     pp[1], vv[1], acc2);
+                    } else if (anyfluid) {
 #pragma unroll
                         for (int k = 0; k < kPop; ++k)
                             pair_terms<KERN, true, true>(d, c0, pi, vi, ci, qx2[k] - pp[k].x,
@@ -632,6 +708,10 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 __syncwarp();   // every lane is done reading before the words are reused
                 acc.np += (uint32_t)acc.npf;
                 acc.npf = 0.f;
+                if (PK) {
+                    acc.np += (uint32_t)acc2.npf.x + (uint32_t)acc2.npf.y;
+                    acc2.npf = dup2(0.f);
+                }
                 nw = 0;
                 lane_hits = 0;
                 lane_nz = 0;
@@ -694,6 +774,14 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 }
             }
             flush();
+            if (PK) {
+                // the two streams' sums, in a fixed order (momentum negated once)
+                acc.ax -= acc2.ax.x + acc2.ax.y;
+                acc.ay -= acc2.ay.x + acc2.ay.y;
+                acc.az -= acc2.az.x + acc2.az.y;
+                acc.dr += acc2.dr.x + acc2.dr.y;
+                acc.mu = fmaxf(acc.mu, acc2.mu);
+            }
         } else {
             // candidates straight from global memory (unit too large to stage)
             uint32_t* lst = reinterpret_cast<uint32_t*>(s_raw) + w * (FBCAP * 32);
@@ -1399,22 +1487,28 @@ struct Variant {
 
 // (warps, staged candidates, hit-mask words per lane, resident blocks per SM
 // that the shared memory allows -- also the register budget hint)
-#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv)                                               \
+#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv, PKv)                                          \
     Variant {                                                                        \
         Wv, Pv, Sv,                                                                  \
-            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0>, k_interact<Wv, Sv, Cv, Bv, true, Pv, 0>}, \
-             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1>, k_interact<Wv, Sv, Cv, Bv, true, Pv, 1>}}, \
+            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0, PKv>,                         \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 0, PKv>},                         \
+             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1, PKv>,                         \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 1, PKv>}},                        \
             Shape<Wv * Pv, Sv, Cv>::smem, 0                                          \
     }
 
 Variant g_variants[kNumVariants] = {
-    SPH_VARIANT(4, 2048, 24, 2, 2),   // 128-particle units, two warps per 32 particles
-    SPH_VARIANT(4, 2048, 32, 2, 1),   // 128-particle units
-    SPH_VARIANT(3, 1280, 16, 3, 2),   // 96-particle units, two warps per 32, three blocks per SM
-    SPH_VARIANT(3, 1408, 16, 3, 2),
-    SPH_VARIANT(2, 1280, 24, 3, 2),   // 64-particle units, two warps per 32 particles
-    SPH_VARIANT(4, 1792, 20, 2, 2),
-    SPH_VARIANT(3, 1152, 24, 4, 1),   // 96-particle units, four blocks per SM
+    SPH_VARIANT(4, 2048, 24, 2, 2, false),   // 128-particle units, two warps per 32 particles
+    SPH_VARIANT(4, 2048, 32, 2, 1, false),   // 128-particle units
+    SPH_VARIANT(3, 1280, 16, 3, 2, false),   // 96-particle units, two warps per 32, three per SM
+    SPH_VARIANT(3, 1408, 16, 3, 2, false),
+    SPH_VARIANT(2, 1280, 24, 3, 2, false),   // 64-particle units, two warps per 32 particles
+    SPH_VARIANT(4, 1792, 20, 2, 2, false),
+    SPH_VARIANT(3, 1152, 24, 4, 1, false),   // 96-particle units, four blocks per SM
+    // the same shapes with the pair terms of two pairs in packed FP32
+    SPH_VARIANT(4, 2048, 24, 2, 2, true),
+    SPH_VARIANT(3, 1408, 16, 3, 2, true),
+    SPH_VARIANT(4, 1792, 20, 2, 2, true),
 };
 
 }  // namespace
