@@ -393,6 +393,8 @@ def run_ours(args):
     sub = subdomain_timing(sim, case, args.subdomains, S, torch) if args.subdomains else None
 
     kps = sim.kernels_per_step()
+    # symplectic runs of two or more steps go through the device step loop
+    loop = args.formulation == "default" and args.steps >= 2
     if is_ensemble(case):
         ist = sim.instance_state()
         cfg = {"workload": args.workload, "members": len(case.members), "n_particles": case.n,
@@ -420,14 +422,24 @@ def run_ours(args):
             "wall_s_per_simulated_s": ((t_max * 1e-3) / (d1["t"] - d0["t"])
                                        if d1["t"] > d0["t"] else None),
             "member_steps_per_s": steps_per_s * getattr(sim, "n_inst", 1),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": kps * args.steps,
+            "roofline": roofline, "e2e": e2e,
+            # the step kernels, one loop-control kernel per step and the loop's
+            # arming kernel (sph_step with two or more steps is one graph launch)
+            "gpu_launches": (kps * args.steps + (args.steps + 1 if loop else 0)),
             "clocks": clocks}
     if sub is not None:
         line["subdomain_select"] = sub
     pk, src = peaks()
     line["peaks_source"] = src
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if args.workload == "dam_break_32m" and args.formulation == "default" and not args.no_ensemble:
         sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        sim = None
+        line["ensemble_256"] = ensemble_record(args, S, torch, local, args.steps)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        if sim is not None:
+            sim.close()
         del sim
         torch.cuda.empty_cache()
         line["cpu_baseline"] = (cpu_baseline_ensemble(case) if is_ensemble(case)
@@ -437,6 +449,52 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def ensemble_record(args, S, torch, device, steps):
+    """The batched configuration as a nested record of the default line: the
+    256-member ensemble of uneven dam breaks (fluid blocks drawn from
+    U[0.2, 0.6] m, 5.47M particles), ``steps`` lockstep steps issued as one
+    sph_step call (one launch of the step graph, whose conditional WHILE node
+    repeats the step on the device), timed with CUDA events on the
+    simulation's stream after a warm-up, with its own clock samples.
+    ``device`` is this rank's CUDA device index."""
+    from paper_1210_1017_gb300 import cases
+    ens = cases.dam_break_ensemble(256, t_end=1.0)
+    sim = S.Simulation.from_ensemble(ens, device=device)
+    sim.build_cells()
+    variant, _ = sim.autotune(reps=2, cache=False)
+    sim.step(args.warmup)
+    sim.synchronize()
+    d0 = sim.diagnostics()
+    i0 = sim.instance_state()
+    sampler = ClockSampler(device)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    sim.step(steps)
+    e1.record(sim.stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    d1 = sim.diagnostics()
+    i1 = sim.instance_state()
+    sim.check()
+    member_steps = int((i1["steps"] - i0["steps"]).sum())
+    pairs = d1["pairs_total"] - d0["pairs_total"]
+    rec = {"workload": "dam_break_ensemble_256", "members": len(ens.members),
+           "n_particles": ens.n,
+           "member_sizes": [int(min(c.n for c in ens.cases)), int(max(c.n for c in ens.cases))],
+           "steps": steps, "ms_per_step": ms / steps, "steps_per_s": steps / (ms * 1e-3),
+           "member_steps_per_s": member_steps / (ms * 1e-3),
+           "pairs_per_s": pairs / (ms * 1e-3), "interaction_variant": variant,
+           "gpu_launches": (sim.kernels_per_step() + 1) * steps + 1,
+           "launch": "one sph_step call: one CUDA graph launch whose conditional WHILE node "
+                     "runs the step body on the device",
+           "clocks": clocks}
+    sim.close()
+    return rec
 
 
 def subdomain_timing(sim, case, nsub, S, torch):
@@ -579,6 +637,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dam_break_32m", choices=WORKLOADS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the nested 256-member ensemble record of the default line")
     ap.add_argument("--formulation", default="default", choices=sorted(FORMULATIONS))
     ap.add_argument("--subdomains", type=int, default=0,
                     help="also time the Sec. 4.3 edge selection for this many slabs")

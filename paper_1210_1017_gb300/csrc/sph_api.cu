@@ -231,6 +231,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->diag_out = cv.take<double>(8);
     c->diag_part = cv.take<double>(8 * kDiagBlocks);
     c->front = cv.take<unsigned long long>(n_inst);
+    c->loop_ctr = cv.take<uint32_t>(4);
     c->counters = cv.take<unsigned long long>(8);
     c->d_inst = cv.take<Inst>(n_inst);
     c->d_cell_base = cv.take<uint32_t>(n_inst + 1);
@@ -655,6 +656,42 @@ int sph_verlet(sph_ctx* c) {
     return post_launch(c, "verlet");
 }
 
+// The loop graph of start parity g: a conditional WHILE node whose body is
+// `body` steps followed by k_loop_ctrl (captured from the same enqueue
+// functions as the single-step graphs).  The body must end on the parity it
+// started from.
+static int build_loop_graph(sph_ctx* c, int g, uint32_t body) {
+    cudaGraph_t graph = nullptr;
+    int rc = cuda_check(c, cudaGraphCreate(&graph, 0), "loop graph create");
+    if (rc) return rc;
+    cudaGraphConditionalHandle h;
+    rc = cuda_check(c, cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault),
+                    "conditional handle");
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (!rc) rc = cuda_check(c, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np),
+                             "conditional node");
+    if (!rc) {
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        rc = cuda_check(c, cudaStreamBeginCaptureToGraph(c->st, bodyg, nullptr, nullptr, 0,
+                                                         cudaStreamCaptureModeThreadLocal),
+                        "begin body capture");
+        if (!rc) {
+            for (uint32_t s = 0; s < body; ++s) enqueue_step(c);
+            launch_loop_ctrl(h, c->loop_ctr, c->i_done, c->n_inst, body, c->st);
+            rc = cuda_check(c, cudaStreamEndCapture(c->st, &bodyg), "end body capture");
+        }
+    }
+    if (!rc && c->cur != g) rc = fail(c, SPH_ERR_STATE, "loop body changed buffer parity");
+    if (!rc) rc = cuda_check(c, cudaGraphInstantiate(&c->loop_graph[g], graph, 0), "instantiate loop");
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
 int sph_step(sph_ctx* c, uint32_t nsteps) {
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
@@ -669,10 +706,30 @@ int sph_step(sph_ctx* c, uint32_t nsteps) {
         for (uint32_t s = 0; s < nsteps; ++s) enqueue_step(c);
         return post_launch(c, "step");
     }
+    // Two or more steps: one launch of the loop graph, whose WHILE node runs
+    // bodies of one symplectic step (which returns to its buffer parity) or
+    // two Verlet steps on the device until the steps asked are done or every
+    // member has reached its end time; a remaining odd Verlet step takes the
+    // single-step graph below.
+    const uint32_t body = c->verlet ? 2u : 1u;
+    uint32_t looped = 0;
+    if (nsteps >= 2u * body || (!c->verlet && nsteps >= 2u)) {
+        looped = nsteps / body * body;
+        const int g = c->cur;
+        if (!c->loop_graph[g]) {
+            int rc = build_loop_graph(c, g, body);
+            if (rc) return rc;
+        }
+        launch_loop_init(c->loop_ctr, looped, c->st);
+        int rc = post_launch(c, "loop init");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaGraphLaunch(c->loop_graph[g], c->st), "loop graph launch");
+        if (rc) return rc;
+    }
     // One graph per state-buffer parity the step starts from.  A symplectic
     // step rebuilds twice and ends on the parity it started from; a Verlet
     // step rebuilds once, so its steps alternate between the two graphs.
-    for (uint32_t s = 0; s < nsteps; ++s) {
+    for (uint32_t s = looped; s < nsteps; ++s) {
         const int g = c->cur;
         if (!c->graph[g]) {
             cudaGraph_t graph;
@@ -925,6 +982,8 @@ int sph_set_variant(sph_ctx* c, uint32_t v) {
     for (int g = 0; g < 2; ++g) {
         if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
         c->graph[g] = nullptr;
+        if (c->loop_graph[g]) cudaGraphExecDestroy(c->loop_graph[g]);
+        c->loop_graph[g] = nullptr;
     }
     // the work units depend on the block shape: recut them for the current cells
     if (c->cells_valid) launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->st);
@@ -981,9 +1040,12 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
-    // one rebuild: 3 cell scan + 1 counting-sort scatter + 6 unit list (row
-    // sums, count, 3 scan, fill) + reorder
-    const uint32_t rebuild = 3u + 1u + 6u + 1u;
+    // a scan is 3 kernels, or 1 when the array fits one scan block
+    const uint32_t cell_scan = scan_bsum_count(c->ncells + 1) == 1 ? 1u : 3u;
+    const uint32_t unit_scan = scan_bsum_count(c->tab.nrows) == 1 ? 1u : 3u;
+    // one rebuild: cell scan + 1 counting-sort scatter + unit list (row sums,
+    // count, scan, fill) + reorder
+    const uint32_t rebuild = cell_scan + 1u + 3u + unit_scan + 1u;
     // Verlet: interact + reduce + update + member advance + rebuild
     if (c->verlet) return 2u + 2u + rebuild;
     // symplectic: 2 x (interact + reduce) + predict + correct + 2 rebuilds
@@ -994,8 +1056,10 @@ const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "NULL
 
 void sph_destroy(sph_ctx* c) {
     if (!c) return;
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < 2; ++g) {
         if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
+        if (c->loop_graph[g]) cudaGraphExecDestroy(c->loop_graph[g]);
+    }
     delete c;
 }
 

@@ -82,6 +82,10 @@ struct sph_ctx {
     bool verlet = false;     // Verlet integrator: pvr[0] / pvr[1] hold (v, rho) one
                              // step earlier, before / after the reorder
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // sph_step(n): one graph per start parity whose conditional WHILE node
+    // repeats a body of loop_body steps on the device (see sph_step)
+    cudaGraphExec_t loop_graph[2] = {nullptr, nullptr};
+    uint32_t* loop_ctr = nullptr;   // [0] steps done in this launch, [1] steps asked
     std::string err;
 };
 

@@ -213,6 +213,12 @@ constexpr int kDiagBlocks = 152;
 void launch_diag(const Dev& d, const double* x, const double* y, const double* z,
                  const float4* vr, const uint32_t* id, const uint32_t* off,
                  double* partial, double* out, cudaStream_t st);
+// Device-side step loop: arm the counter (ctr[0] = 0, ctr[1] = nsteps); after
+// each body of `body` steps, count it and set the WHILE condition to "another
+// body fits and some member is still running".
+void launch_loop_init(uint32_t* ctr, uint32_t nsteps, cudaStream_t st);
+void launch_loop_ctrl(cudaGraphConditionalHandle h, uint32_t* ctr, const uint32_t* done,
+                      uint32_t n_inst, uint32_t body, cudaStream_t st);
 void launch_front(const Dev& d, const double* x, const double* z, const uint32_t* id,
                   const uint32_t* off, double zlo, double zhi, unsigned long long* out,
                   cudaStream_t st);

@@ -1449,6 +1449,28 @@ __global__ void __launch_bounds__(256) k_front(const Dev d, const double* __rest
     }
 }
 
+// Device-side step loop (sph_step): the conditional WHILE node of the step
+// graph runs its body (`body` steps) again while k_loop_ctrl leaves its
+// condition at 1.  k_loop_init arms the counter before each launch.
+__global__ void k_loop_init(uint32_t* ctr, uint32_t nsteps) {
+    ctr[0] = 0u;
+    ctr[1] = nsteps;
+}
+
+__global__ void __launch_bounds__(256) k_loop_ctrl(cudaGraphConditionalHandle h, uint32_t* ctr,
+                                                   const uint32_t* __restrict__ done,
+                                                   uint32_t n_inst, uint32_t body) {
+    int running = 0;
+    for (uint32_t q = threadIdx.x; q < n_inst; q += blockDim.x) running |= done[q] == 0u;
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const uint32_t k = ctr[0] + body;
+        ctr[0] = k;
+        // another body while it fits the steps asked and a member still runs
+        cudaGraphSetConditional(h, (running && k + body <= ctr[1]) ? 1u : 0u);
+    }
+}
+
 inline uint32_t blocks_for(uint32_t n, uint32_t t) { return n ? (n + t - 1) / t : 1; }
 
 }  // namespace
@@ -1583,6 +1605,15 @@ void launch_diag(const Dev& d, const double* x, const double* y, const double* z
                  double* out, cudaStream_t st) {
     k_diag_part<<<kDiagBlocks, 256, 0, st>>>(d, x, y, z, vr, id, off, partial);
     k_diag_final<<<1, 32, 0, st>>>(partial, kDiagBlocks, out);
+}
+
+void launch_loop_init(uint32_t* ctr, uint32_t nsteps, cudaStream_t st) {
+    k_loop_init<<<1, 1, 0, st>>>(ctr, nsteps);
+}
+
+void launch_loop_ctrl(cudaGraphConditionalHandle h, uint32_t* ctr, const uint32_t* done,
+                      uint32_t n_inst, uint32_t body, cudaStream_t st) {
+    k_loop_ctrl<<<1, 256, 0, st>>>(h, ctr, done, n_inst, body);
 }
 
 void launch_front(const Dev& d, const double* x, const double* z, const uint32_t* id,

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
         v[r] = i < m ? in[i] : 0u;
         tot += v[r];
     }
-    const uint32_t ex = block_excl_scan_256(tot, s_w) + bsum[blockIdx.x];
+    const uint32_t ex = block_excl_scan_256(tot, s_w) + (bsum ? bsum[blockIdx.x] : 0u);
     uint32_t run = ex;
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
@@ -322,6 +322,11 @@ uint32_t scan_bsum_count(uint64_t m) {
 void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st,
                  bool zero_in) {
     const uint32_t nb = scan_bsum_count(m);
+    if (nb == 1) {
+        // one block holds the whole array: no block sums needed
+        k_scan_down<<<1, kScanThreads, 0, st>>>(in, m, nullptr, out, zero_in ? 1 : 0);
+        return;
+    }
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, m, bsum);
     k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
     k_scan_down<<<nb, kScanThreads, 0, st>>>(in, m, bsum, out, zero_in ? 1 : 0);

@@ -101,3 +101,34 @@ def test_member_rates_match_the_oracle():
         ed = np.abs(a[:, 3] - ref["drho"]) / np.where(ref["sd"] > 0, ref["sd"], 1.0)
         print(f"member {q}: n={case.n} accel {ea.max():.2e} drho {ed.max():.2e}")
         assert ea.max() <= 2e-5 and ed.max() <= 2e-5
+
+
+def test_device_step_loop_stops_once_every_member_is_done():
+    """One sph_step call with far more steps than needed: the device loop
+    ends as soon as every member has reached its end time, each member with
+    the same step count as when stepping one step per call."""
+    members = _members(2, seed=5)
+    ens = cases.ensemble(members, t_end=2e-3)
+    ref = S.Simulation.from_ensemble(ens)
+    lock = 0
+    while not ref.instance_state()["done"].all():
+        ref.step(1)
+        lock += 1
+        assert lock < 100
+    want = ref.instance_state()
+    a = ref.download()
+    pairs_ref = ref.diagnostics()["pairs_total"]
+    ref.close()
+    sim = S.Simulation.from_ensemble(ens)
+    d0 = sim.diagnostics()
+    sim.step(100000)
+    got = sim.instance_state()
+    d1 = sim.diagnostics()
+    assert got["done"].all()
+    assert np.array_equal(got["steps"], want["steps"]) and np.array_equal(got["t"], want["t"])
+    b = sim.download()
+    for key in ("ids", "pos", "vel", "rho"):
+        assert np.array_equal(a[key], b[key])
+    # only the lockstep steps up to the last member's end were evaluated
+    assert d1["pairs_total"] - d0["pairs_total"] == pairs_ref
+    sim.close()
