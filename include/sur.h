@@ -65,9 +65,12 @@ int sur_edge_layer(const void *d_E, const void *d_W1t, const void *d_W2t,
 /* ---- the network -------------------------------------------------------
  * Nodes: the particles of an SPH context (sph.h) in its current sorted order,
  * with cells built.  Edges: every ordered pair within 2h (the FP64 predicate
- * of the cell list).  Node input: the particle's last five velocities (a
+ * of the cell list), or within radius * 2h for a sparser graph.  Node input: the particle's last five velocities (a
  * history array indexed by particle id: hist[id][15], oldest first) / v_scale
  * and its boundary flag; edge input: (r_i - r_j)/2h and |r_i - r_j|/2h.
+ * A sparser graph keeps only the pairs closer than radius * 2h (radius in
+ * (0, 1); 0 or 1 = the full support): fewer edges per node and a smaller
+ * receptive field per layer.
  * Latent width 128; `layers` message-passing layers of
  *   e' = e + W2 relu(W1a h_i + W1b h_j + W1c e + b1) + b2
  *   h' = h + W4 relu(W3 [h, sum_j e'_ij] + b3) + b4,
@@ -85,6 +88,8 @@ typedef struct sur_config {
     float v_scale;             /* velocity normalisation [m/s]               */
     float a_mean[3], a_std[3]; /* acceleration normalisation [m/s^2]         */
     float dt_s;                /* time advanced per sur_advance call [s]     */
+    float radius;              /* edge radius / 2h; 0 or 1 = 2h (the SPH
+                                  neighbour relation), else in (0, 1)       */
 } sur_config;
 
 typedef struct sur_ctx sur_ctx;

@@ -59,15 +59,17 @@ __global__ void k_refresh(const float* __restrict__ w, int kin, int kout, __nv_b
 
 // ----------------------------------------------------------------- graph --
 
-// Neighbours j != i with |r_ij|^2 < (2h)^2 (FP64 predicate, as the SPH
-// cell list defines them), visited in ascending sorted index: the 9 rows of
-// cells around i's cell in (z, y) order, cells in x order.
+// Neighbours j != i with |r_ij|^2 < r2 (FP64 predicate; r2 = (2h)^2 as the
+// SPH cell list defines neighbours, or (radius 2h)^2 for a sparser graph),
+// visited in ascending sorted index: the 9 rows of cells around i's cell in
+// (z, y) order, cells in x order.
 template <int MODE>
 __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const double* __restrict__ y,
                         const double* __restrict__ z, const uint32_t* __restrict__ key,
                         const uint32_t* __restrict__ off, uint32_t* __restrict__ cnt,
                         const uint32_t* __restrict__ rowptr, uint32_t* __restrict__ col,
-                        uint32_t* __restrict__ src, __nv_bfloat16* __restrict__ xe, double inv2h) {
+                        uint32_t* __restrict__ src, __nv_bfloat16* __restrict__ xe, double inv2h,
+                        double r2) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const uint32_t n_in = off[d.ncells];
@@ -103,7 +105,7 @@ __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const do
                 const double dz = __dsub_rn(zi, z[j]);
                 const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
                                             __dmul_rn(dz, dz));
-                if (d2 < d.r2max_d) {
+                if (d2 < r2) {
                     if (MODE) {
                         col[e] = j;
                         src[e] = i;
@@ -664,9 +666,14 @@ int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
     const sph::Dev& d = s->d;
     const int cur = s->cur;
     const double inv2h = 1.0 / (2.0 * s->p.h);
+    // the SPH predicate's (2h)^2 itself, or (radius 2h)^2 rounded once
+    const float rad = c->cfg.radius;
+    const double r2 = (rad > 0.f && rad < 1.f)
+                          ? ((double)rad * (2.0 * s->p.h)) * ((double)rad * (2.0 * s->p.h))
+                          : s->d.r2max_d;
     const uint32_t* key = s->key[s->skey];
     k_graph<0><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
-                                             c->cnt, nullptr, nullptr, nullptr, nullptr, inv2h);
+                                             c->cnt, nullptr, nullptr, nullptr, nullptr, inv2h, r2);
     sph::launch_scan(c->cnt, n, c->bsum, c->rowptr, st);
     uint32_t E = 0;
     cudaMemcpyAsync(&E, c->rowptr + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
@@ -674,7 +681,7 @@ int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
     if (E > c->cfg.max_edges) return fail(c, SPH_ERR_CAPACITY, "more edges than max_edges");
     c->E = E;
     k_graph<1><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
-                                             nullptr, c->rowptr, c->col, c->src, c->xe, inv2h);
+                                             nullptr, c->rowptr, c->col, c->src, c->xe, inv2h, r2);
     if (c->cfg.train && E) k_graph_rev<<<nblk(E, 256), 256, 0, st>>>(E, c->rowptr, c->col, c->src, c->rev);
     k_node_features<<<nblk(n, 256), 256, 0, st>>>(d, s->id[cur], hist, 1.0 / (double)c->cfg.v_scale, c->xn);
     const std::vector<Layer>& Ls = c->layers;
@@ -824,7 +831,8 @@ uint64_t sur_query_bytes(const sur_config* cfg) {
 
 int sur_init(const sur_config* cfg, void* ws, uint64_t bytes, void* stream, sur_ctx** out) {
     if (!cfg || !out || !ws || cfg->layers == 0 || cfg->layers > 64 || cfg->max_nodes == 0 ||
-        !(cfg->v_scale > 0.f) || ((uintptr_t)ws % 256) != 0)
+        !(cfg->v_scale > 0.f) || !(cfg->radius >= 0.f && cfg->radius <= 1.f) ||
+        ((uintptr_t)ws % 256) != 0)
         return SPH_ERR_INVALID_ARG;
     sur_ctx* c = new sur_ctx();
     c->cfg = *cfg;

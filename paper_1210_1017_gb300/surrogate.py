@@ -12,7 +12,7 @@ from . import sph as _sph
 class SurConfig(C.Structure):
     _fields_ = [("layers", C.c_uint32), ("max_nodes", C.c_uint32), ("max_edges", C.c_uint32),
                 ("train", C.c_uint32), ("v_scale", C.c_float), ("a_mean", C.c_float * 3),
-                ("a_std", C.c_float * 3), ("dt_s", C.c_float)]
+                ("a_std", C.c_float * 3), ("dt_s", C.c_float), ("radius", C.c_float)]
 
 EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_edge_layer",
             "sur_param_count",
@@ -92,10 +92,11 @@ def _chk(rc, ctx, what):
 
 
 def make_config(layers=10, max_nodes=0, max_edges=0, train=False, v_scale=1.0,
-                a_mean=(0.0, 0.0, 0.0), a_std=(1.0, 1.0, 1.0), dt_s=0.0) -> SurConfig:
+                a_mean=(0.0, 0.0, 0.0), a_std=(1.0, 1.0, 1.0), dt_s=0.0,
+                radius=1.0) -> SurConfig:
     c = SurConfig()
     c.layers, c.max_nodes, c.max_edges, c.train = layers, max_nodes, max_edges, int(bool(train))
-    c.v_scale, c.dt_s = v_scale, dt_s
+    c.v_scale, c.dt_s, c.radius = v_scale, dt_s, radius
     for a in range(3):
         c.a_mean[a], c.a_std[a] = a_mean[a], a_std[a]
     return c
@@ -183,7 +184,7 @@ class Surrogate:
 
     def __init__(self, sim, layers=10, max_edges=None, train=False, v_scale=1.0,
                  a_mean=(0.0, 0.0, 0.0), a_std=(1.0, 1.0, 1.0), dt_s=0.0, edges_per_node=90,
-                 max_nodes=None):
+                 max_nodes=None, radius=1.0):
         import torch
         self.sim = sim
         self.torch = torch
@@ -191,7 +192,7 @@ class Surrogate:
         if max_edges is None:
             max_edges = max_nodes * edges_per_node
         self.cfg = make_config(layers, max_nodes, int(max_edges), train, v_scale, a_mean, a_std,
-                               dt_s)
+                               dt_s, radius)
         self.nparams = sur_param_count(self.cfg)
         nbytes = sur_query_bytes(self.cfg)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=sim.device)

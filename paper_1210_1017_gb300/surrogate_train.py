@@ -181,11 +181,12 @@ class Trainer:
     """One surrogate context serving several groups (same stream)."""
 
     def __init__(self, groups, layers=10, sigma=3e-4, seed=0, edges_per_node=80, stats=None,
-                 train=True, max_nodes=0):
+                 train=True, max_nodes=0, radius=1.0):
         import torch
         self.torch = torch
         self.groups = groups
         self.layers = layers
+        self.radius = radius
         self.sigma = sigma
         self.rng = np.random.default_rng(seed)
         self.seed = seed
@@ -197,7 +198,7 @@ class Trainer:
         dev = groups[0].sim.device
         self.sur = U.Surrogate(groups[0].sim, layers=layers, train=train, v_scale=self.v_scale,
                                a_mean=self.a_mean, a_std=self.a_std, dt_s=self.dt_s,
-                               max_nodes=nmax, max_edges=nmax * edges_per_node)
+                               max_nodes=nmax, max_edges=nmax * edges_per_node, radius=radius)
         self.sur.set_params(init_params(layers, seed))
         f64, f32 = torch.float64, torch.float32
         self.pos = torch.empty((nmax, 3), dtype=f64, device=dev)
@@ -356,34 +357,35 @@ def evaluate_group(trainer: Trainer, g: Group, k0: int, n_calls: int, every: int
 
 
 def evaluate_case(trainer: Trainer, case, t_sim: float, every: int = 10, pilot_t: float = None,
-                  edges_per_node: int = 80, sph_steps_timed: int = 200):
+                  edges_per_node: int = 80, sph_steps_timed: int = 200, steps_per_call: int = 4):
     """The trained network on a standalone case (its own resolution and
     step) against the GPU SPH on the same case: both start from rest, the
     SPH runs with the fixed step dt (smallest adaptive step of a pilot run)
-    and the surrogate advances 4 dt per call.  Returns per saved call the
-    position RMSE / dp and front error, and the simulated seconds per wall
-    second of both."""
+    and the surrogate advances steps_per_call dt per call.  Returns per saved
+    call the position RMSE / dp and front error, and the simulated seconds
+    per wall second of both."""
+    K = int(steps_per_call)
     import torch
     st = trainer.groups[0].sim.stream
     g = Group(ens=cases.ensemble([case]), sim=None)
     g.sim = S.Simulation(case.params(), case.n, stream=st)
     dt = pilot_dt(g, pilot_t if pilot_t is not None else min(t_sim, 0.2))
-    n_calls = int(round(t_sim / (4 * dt)))
-    # SPH frames: 6 initial frames 4 steps apart, then every `every` calls
+    n_calls = int(round(t_sim / (K * dt)))
+    # SPH frames: 6 initial frames K steps apart, then every `every` calls
     sim = S.Simulation(case.params(), case.n, stream=st, dt_fixed=dt)
     sim.upload(case.pos, case.vel, case.rho, case.ids)
     dev = sim.device
     first = torch.empty((7, case.n, 3), dtype=torch.float64, device=dev)
     for f in range(7):
         if f:
-            sim.step(4)
+            sim.step(K)
         sim.download_by_id(pos=first[f])
     ref = {}
     c = 1                      # frame 6 = call 1 after frame 5
     ref[1] = first[6].clone()
     while c < n_calls:
         k = min(every - (c % every) if c % every else every, n_calls - c)
-        sim.step(4 * k)
+        sim.step(K * k)
         c += k
         p = torch.empty((case.n, 3), dtype=torch.float64, device=dev)
         sim.download_by_id(pos=p)
@@ -398,11 +400,12 @@ def evaluate_case(trainer: Trainer, case, t_sim: float, every: int = 10, pilot_t
     sph_sps = dt * sph_steps_timed / (e0.elapsed_time(e1) / 1e3)
     sim.close()
     # surrogate on the case, same weights and normalisation, this case's step
-    g.frames, g.dt, g.steps_per_frame = first, dt, 4
+    g.frames, g.dt, g.steps_per_frame = first, dt, K
     g.fluid = torch.tensor(np.arange(case.n) >= case.n_bound, device=dev)   # by id
     sur = U.Surrogate(g.sim, layers=trainer.layers, train=False, v_scale=trainer.v_scale,
-                      a_mean=trainer.a_mean, a_std=trainer.a_std, dt_s=4 * dt,
-                      max_nodes=case.n, max_edges=case.n * edges_per_node)
+                      a_mean=trainer.a_mean, a_std=trainer.a_std, dt_s=K * dt,
+                      max_nodes=case.n, max_edges=case.n * edges_per_node,
+                      radius=getattr(trainer, "radius", 1.0))
     sur.set_params(trainer.sur.params())
     ev = Trainer.__new__(Trainer)
     ev.torch, ev.sur = torch, sur
@@ -421,8 +424,8 @@ def evaluate_case(trainer: Trainer, case, t_sim: float, every: int = 10, pilot_t
         if c not in ref:
             continue
         m = metrics(g.ens, p, ref[c], fluid, dp)
-        rows.append(dict(call=c, t=c * 4 * dt, rmse_dp=m["rmse_dp"], front_err=m["front_err"]))
-    sur_sps = 4 * dt / spc
+        rows.append(dict(call=c, t=c * K * dt, rmse_dp=m["rmse_dp"], front_err=m["front_err"]))
+    sur_sps = K * dt / spc
     sur.close()
     g.sim.close()
     return dict(dt=dt, calls=n_calls, rows=rows, sur_seconds_per_call=spc, sur_sim_per_s=sur_sps,
@@ -448,6 +451,12 @@ def main(argv=None):
     ap.add_argument("--case-seconds", type=float, default=0.1)
     ap.add_argument("--case", default="c2", choices=["c2", "none"])
     ap.add_argument("--save-params", default=None)
+    ap.add_argument("--steps-per-call", type=int, default=4,
+                    help="SPH steps one surrogate call advances (frames are this many apart)")
+    ap.add_argument("--radius", type=float, default=1.0,
+                    help="graph edge radius as a fraction of 2h (sparser graph below 1)")
+    ap.add_argument("--case-every", type=int, default=10,
+                    help="surrogate calls between the compared frames of the case")
     a = ap.parse_args(argv)
     report = dict(args=vars(a))
     t0 = time.perf_counter()
@@ -457,15 +466,17 @@ def main(argv=None):
     groups = [make_group(specs[i * gs:(i + 1) * gs], t_end=a.t_end, stream=st)
               for i in range(a.train_groups + 1)]
     dt = min(pilot_dt(g, a.t_end) for g in groups)
-    n_frames = int(a.t_end / (4 * dt)) + 1
+    K = a.steps_per_call
+    n_frames = int(a.t_end / (K * dt)) + 1
     for g in groups:
-        record(g, dt, n_frames)
+        record(g, dt, n_frames, steps_per_frame=K)
     train, held = groups[:-1], groups[-1]
-    report["data"] = dict(dt=dt, dt_s=4 * dt, frames=n_frames,
+    report["data"] = dict(dt=dt, dt_s=K * dt, frames=n_frames,
                           train_particles=[g.n for g in train], held_particles=held.n,
                           seconds=time.perf_counter() - t0)
     print(json.dumps(report["data"]), flush=True)
-    tr = Trainer(train, layers=a.layers, sigma=a.sigma, seed=0, max_nodes=held.n)
+    tr = Trainer(train, layers=a.layers, sigma=a.sigma, seed=0, max_nodes=held.n,
+                 radius=a.radius)
     report["stats"] = dict(v_scale=tr.v_scale, a_mean=tr.a_mean, a_std=tr.a_std)
     ks = range(10, n_frames - 2, max(1, (n_frames - 12) // 8))
     report["untrained_held_one_step"], report["zero_held_one_step"] = tr.one_step_loss(held, ks)
@@ -482,7 +493,8 @@ def main(argv=None):
     report["held_rollout"] = dict(rows=rows, seconds_per_call=spc)
     print(json.dumps(report["held_rollout"]["rows"][-1]), flush=True)
     if a.case == "c2":
-        report["c2"] = evaluate_case(tr, cases.c2_dam_break_obstacles(), a.case_seconds)
+        report["c2"] = evaluate_case(tr, cases.c2_dam_break_obstacles(), a.case_seconds,
+                                     every=a.case_every, steps_per_call=K)
         print(json.dumps({k: v for k, v in report["c2"].items() if k != "rows"}), flush=True)
     report["seconds"] = time.perf_counter() - t0
     with open(a.out, "w") as f:

@@ -336,3 +336,29 @@ def test_rollout_equals_repeated_calls_and_reports_snapshots(torch):
     assert np.array_equal(a["pos"][oa], b["pos"][ob]) and np.array_equal(a["vel"][oa], b["vel"][ob])
     assert torch.equal(h1, h2)
     assert [k for k, _ in seen] == [2, 3] and abs(seen[-1][1] - 3 * dt) < 1e-9
+
+
+def test_sparser_graph_keeps_the_pairs_within_its_radius(torch):
+    """radius < 1: the edges are exactly the ordered pairs closer than
+    radius * 2h (the reference graph at smoothing length radius * h), and
+    the network still runs on them."""
+    s = Setup(torch, 1500, 1, seed=31)
+    for radius in (0.5, 0.75):
+        sur = U.Surrogate(s.sim, layers=1, train=False, v_scale=s.v_scale, radius=radius)
+        sur.set_params(s.w)
+        acc = torch.zeros((s.n, 3), dtype=torch.float32, device="cuda")
+        sur.forward(s.d_hist, acc)
+        s.sim.synchronize()
+        rowptr, col = sur.read_graph()
+        ids = s.sim.download()["ids"].astype(np.int64)
+        g_src = ids[np.repeat(np.arange(s.n), np.diff(rowptr.astype(np.int64)))]
+        g_dst = ids[col.astype(np.int64)]
+        order = np.lexsort((g_dst, g_src))
+        ref_src, ref_dst = so.graph(s.pos, radius * s.case.h)
+        assert np.array_equal(g_src[order], ref_src)
+        assert np.array_equal(g_dst[order], ref_dst)
+        assert 0 < len(ref_src) < len(s.src)
+        assert np.isfinite(acc.cpu().numpy()).all()
+        sur.close()
+    with pytest.raises(S.SphError):
+        U.Surrogate(s.sim, layers=1, v_scale=1.0, radius=1.5)
