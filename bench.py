@@ -45,7 +45,7 @@ SMS, FP32_LANES, MAX_CLOCK_GHZ = 152, 128, 2.07
 
 
 WORKLOADS = ("dam_break_32m", "dam_break_obstacles_1m", "dam_break_6k", "dam_break_ensemble_256",
-             "surrogate_obstacles_1m")
+             "surrogate_obstacles_1m", "surrogate_block_50k")
 
 
 def workload(name):
@@ -547,7 +547,12 @@ def run_surrogate(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     S.lib(build=True)
-    case = cases.c2_dam_break_obstacles()
+    # surrogate_block_50k: a 50,000-particle jittered block (about 3.5M
+    # edges, a few GB of workspace) for kernel captures; it skips the
+    # standalone 16M-edge kernel timing below
+    small = args.workload == "surrogate_block_50k"
+    case = cases.random_block(50000, seed=41, jitter=0.3) if small else \
+        cases.c2_dam_break_obstacles()
     st = torch.cuda.Stream()
     sim = S.Simulation.from_case(case, device=local, stream=st)
     sim.build_cells()
@@ -589,7 +594,7 @@ def run_surrogate(args):
     # run on its own over 16M edges with 2M-node tables (inputs larger than
     # L2); algorithmic bytes per edge: e read 256 + e' written 256 (the
     # gathered node rows are counted once per node)
-    M, nodes = 1 << 24, 1 << 21
+    M, nodes = (1 << 24, 1 << 21) if not small else (1 << 20, 1 << 17)
     dev = sim.device
     E = torch.randn((M, 128), device=dev).to(torch.bfloat16)
     Eo = torch.empty((M, 128), dtype=torch.bfloat16, device=dev)
@@ -614,14 +619,15 @@ def run_surrogate(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sur_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "surrogate_obstacles_1m", "n_particles": case.n, "edges": n_edges,
+            "config": {"workload": args.workload, "n_particles": case.n, "edges": n_edges,
                        "layers": 10, "latent": 128, "sph_steps_per_call": 4, "dt": dt,
                        "weights": "random initialisation"},
             "sph_sim_per_s": sph_sim / sph_s, "speedup_vs_sph": value / (sph_sim / sph_s),
             "edges_per_s": n_edges * args.steps / sur_s,
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
                          "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None,
-                         "kernel": "k_edge_layer (fused edge update), 16M edges, 2M nodes",
+                         "kernel": (f"k_edge_layer (fused edge update), {M >> 20}M edges, "
+                                    f"{nodes >> 10}k nodes"),
                          "ms_per_launch": round(t_gemm * 1e3, 4)},
             "gpu_launches": None, "clocks": clocks, "peaks_source": src_pk}
     if rank == 0:
@@ -647,7 +653,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "surrogate_obstacles_1m":
+    if args.workload in ("surrogate_obstacles_1m", "surrogate_block_50k"):
         return run_surrogate(args)
     return run_ours(args)
 
