@@ -179,7 +179,7 @@ struct ReduceArgs {
     unsigned long long* counters;
     uint32_t* status;
 };
-constexpr int kReduceBlocks = 152;
+constexpr int kReduceBlocks = 1;   // the partials are a few hundred per-block words
 void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st);
 
 struct IntegrateArgs {
