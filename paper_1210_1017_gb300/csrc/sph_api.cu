@@ -224,8 +224,7 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->ubsum = cv.take<uint32_t>(scan_bsum_count(t.nrows + 1));
     c->units = cv.take<uint2>(max_units(n, (uint32_t)t.nrows, t.ncells));
     c->part_u = cv.take<uint4>(kMaxGridBlocks);
-    c->lvl2_q = cv.take<unsigned long long>(4 * kReduceBlocks);
-    c->done = cv.take<uint32_t>(1);
+    c->done = cv.take<uint32_t>(1);   // ticket of the interaction's last block
     c->status = cv.take<uint32_t>(1);
     c->id_flag = cv.take<uint32_t>(1);
     c->diag_out = cv.take<double>(8);
@@ -365,15 +364,14 @@ void enqueue_interact(sph_ctx* c, bool counts, bool set_dt) {
     ia.ace = c->ace;
     ia.nnb = c->nnb;
     ia.part_u = c->part_u;
+    // the Sec. 3.3 reductions run in the interaction's last block
+    ia.ticket = c->done;
+    ia.red.part_u = c->part_u;
+    ia.red.nparts = c->nparts;
+    ia.red.counters = c->counters;
+    ia.red.status = c->status;
+    ia.set_dt = set_dt ? 1 : 0;
     launch_interact(c->d, ia, counts, c->st);
-    ReduceArgs ra;
-    ra.part_u = c->part_u;
-    ra.nparts = c->nparts;
-    ra.lvl2_q = c->lvl2_q;
-    ra.done = c->done;
-    ra.counters = c->counters;
-    ra.status = c->status;
-    launch_dt_reduce(c->d, ra, set_dt, c->st);
 }
 
 IntegrateArgs integrate_args(sph_ctx* c, int pre) {
@@ -1015,6 +1013,7 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
         ia.ace = c->ace;
         ia.nnb = c->nnb;
         ia.part_u = c->part_u;
+        ia.ticket = nullptr;   // timing only: no counters, no step size
         launch_interact(c->d, ia, false, c->st);   // warm
         cudaEventRecord(e0, c->st);
         for (uint32_t r = 0; r < reps; ++r) launch_interact(c->d, ia, false, c->st);
@@ -1042,14 +1041,15 @@ uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
     // a scan is 3 kernels, or 1 when the array fits one scan block
     const uint32_t cell_scan = scan_bsum_count(c->ncells + 1) == 1 ? 1u : 3u;
+    // the unit list: row sums, count, scan, fill
     const uint32_t unit_scan = scan_bsum_count(c->tab.nrows) == 1 ? 1u : 3u;
-    // one rebuild: cell scan + 1 counting-sort scatter + unit list (row sums,
-    // count, scan, fill) + reorder
-    const uint32_t rebuild = cell_scan + 1u + 3u + unit_scan + 1u;
-    // Verlet: interact + reduce + update + member advance + rebuild
-    if (c->verlet) return 2u + 2u + rebuild;
-    // symplectic: 2 x (interact + reduce) + predict + correct + 2 rebuilds
-    return 2u * 2u + 2u + 2u * rebuild;
+    const uint32_t unit_list = 3u + unit_scan;
+    // one rebuild: cell scan + 1 counting-sort scatter + unit list + reorder
+    const uint32_t rebuild = cell_scan + 1u + unit_list + 1u;
+    // Verlet: interact (with the CFL reduction) + update + member advance + rebuild
+    if (c->verlet) return 1u + 2u + rebuild;
+    // symplectic: 2 interactions (with the CFL reduction) + predict + correct + 2 rebuilds
+    return 2u + 2u + 2u * rebuild;
 }
 
 const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "NULL context"; }

@@ -48,7 +48,6 @@ struct sph_ctx {
     uint32_t* csum;                  // staged-candidate prefix sums per row
     uint2* units;
     uint4* part_u;
-    unsigned long long* lvl2_q;
     uint32_t *done, *status;
     uint32_t* id_flag;       // set by the upload when some id >= n
     // sub-domain selection (Sec. 4.3): ping-pong (key, value) arrays of the

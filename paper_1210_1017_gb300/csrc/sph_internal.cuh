@@ -143,6 +143,16 @@ constexpr int kSpan = 32;
 constexpr int kMinUnit = 32;
 constexpr int kNumVariants = 10;
 
+struct ReduceArgs {
+    const uint4* part_u;
+    uint32_t nparts;
+    // [0] pairs total, [1] candidates total, [2] pairs last, [3] candidates
+    // last, [4] fluid-i pairs last, [5] boundary-i pairs last, [6] fluid-i
+    // pairs total, [7] boundary-i pairs total
+    unsigned long long* counters;
+    uint32_t* status;
+};
+
 struct InteractArgs {
     const uint2* units;
     const uint32_t* n_units;
@@ -156,6 +166,10 @@ struct InteractArgs {
     uint32_t* nnb;        // may be null
     uint4* part_u;        // per block (persistent grid): fluid-i pairs, candidates,
                           // status bits, boundary-i pairs
+    uint32_t* ticket;     // non-null: the last block runs the Sec. 3.3 reductions
+                          // (zero on entry, left at zero)
+    ReduceArgs red;
+    int set_dt;
 };
 uint32_t max_units(uint32_t n, uint32_t nrows, uint64_t ncells);   // bound on units
 int variant_unit(int variant);               // particles per unit of a variant
@@ -168,19 +182,6 @@ void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* u
 void prepare_interact();
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
 
-struct ReduceArgs {
-    const uint4* part_u;
-    uint32_t nparts;
-    unsigned long long* lvl2_q;     // 4 per block: fluid pairs, boundary pairs, cands, status
-    uint32_t* done;
-    // [0] pairs total, [1] candidates total, [2] pairs last, [3] candidates
-    // last, [4] fluid-i pairs last, [5] boundary-i pairs last, [6] fluid-i
-    // pairs total, [7] boundary-i pairs total
-    unsigned long long* counters;
-    uint32_t* status;
-};
-constexpr int kReduceBlocks = 1;   // the partials are a few hundred per-block words
-void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st);
 
 struct IntegrateArgs {
     const uint32_t* off;     // for the in-domain count

@@ -353,6 +353,86 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
     }
 }
 
+// Sec. 3.3 reductions, by one block once every interaction block has
+// published its counters (pairs, candidates, status bits) and atomically
+// raised the per-instance maxima: the counters are summed (integer sums and
+// maxima do not depend on the order), then per instance
+//   dt = CFL min( sqrt(h / max|a|), h / (max c + max mu) )
+// (0 for instances that are done), and the maxima are cleared for the next
+// evaluation.  Loads bypass L1 (the partials may come from the same kernel).
+__device__ void reduce_counters_and_dt(const Dev& d, const ReduceArgs& a, int set_dt) {
+    __shared__ unsigned long long s_u[32][3];
+    __shared__ uint32_t s_b[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    unsigned long long pf = 0, pb = 0, nc = 0;
+    uint32_t bad = 0;
+    for (uint32_t i = threadIdx.x; i < a.nparts; i += blockDim.x) {
+        const uint4 u = __ldcg(a.part_u + i);
+        pf += u.x;
+        nc += u.y;
+        bad |= u.z;
+        pb += u.w;
+    }
+    for (int o = 16; o; o >>= 1) {
+        pf += __shfl_xor_sync(kFull, pf, o);
+        pb += __shfl_xor_sync(kFull, pb, o);
+        nc += __shfl_xor_sync(kFull, nc, o);
+        bad |= __shfl_xor_sync(kFull, bad, o);
+    }
+    if (lane == 0) {
+        s_u[w][0] = pf;
+        s_u[w][1] = pb;
+        s_u[w][2] = nc;
+        s_b[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long qf = 0, qb = 0, qc = 0;
+        uint32_t bb = 0;
+        for (int k = 0; k < nw; ++k) {
+            qf += s_u[k][0];
+            qb += s_u[k][1];
+            qc += s_u[k][2];
+            bb |= s_b[k];
+        }
+        a.counters[0] += qf + qb;
+        a.counters[1] += qc;
+        a.counters[2] = qf + qb;
+        a.counters[3] = qc;
+        a.counters[4] = qf;
+        a.counters[5] = qb;
+        a.counters[6] += qf;
+        a.counters[7] += qb;
+        if (bb) atomicOr(a.status, bb);
+    }
+    for (uint32_t q = threadIdx.x; q < d.n_inst; q += blockDim.x) {
+        uint32_t* tm = d.is.terms + 3 * q;
+        const float fa = __uint_as_float(__ldcg(tm + 0));
+        const float fc = __uint_as_float(__ldcg(tm + 1));
+        const float fm = __uint_as_float(__ldcg(tm + 2));
+        const double amax = sqrt((double)fa);
+        if (set_dt) {
+            double dt = 0.0;
+            if (!d.is.done[q]) {
+                if (d.dt_fixed > 0.0) {
+                    dt = d.dt_fixed;
+                } else {
+                    const double dtf = amax > 0.0 ? sqrt(d.h_d / amax) : INFINITY;
+                    const double dtc = d.h_d / ((double)fc + (double)fm);
+                    dt = d.cfl * (dtf < dtc ? dtf : dtc);
+                }
+            }
+            d.is.dt[q] = dt;
+            d.is.last[3 * q + 0] = (float)amax;
+            d.is.last[3 * q + 1] = fc;
+            d.is.last[3 * q + 2] = fm;
+        }
+        tm[0] = 0u;
+        tm[1] = 0u;
+        tm[2] = 0u;
+    }
+}
+
 // Packed accumulators of two pair streams (the two pairs a lane evaluates
 // per step of the pair phase), one in each half of a float2.  The momentum
 // sums hold +sum f r_ij (the caller negates once at the end; negation is
@@ -927,6 +1007,20 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
         }
         a.part_u[blockIdx.x] = u;
     }
+    if (a.ticket) {
+        // the last block to finish runs the Sec. 3.3 reductions (every
+        // thread's maxima atomics and thread 0's partials fenced first)
+        __shared__ bool s_lastblk;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_lastblk = atomicAdd(a.ticket, 1u) == gridDim.x - 1u;
+        __syncthreads();
+        if (s_lastblk) {
+            __threadfence();
+            reduce_counters_and_dt(d, a.red, a.set_dt);
+            if (tid == 0) *a.ticket = 0u;
+        }
+    }
 }
 
 // Staged-candidate prefix sums of each row: for row r and x in [0, ncx],
@@ -967,20 +1061,18 @@ __global__ void __launch_bounds__(128) k_row_csum(const Dev d, const uint32_t* _
 // row, mode 1 writes them at the row's offset (uint2: first particle, end).
 constexpr int kUnitChunk = 16;
 
+// The walk of row r: its units (mode 1 writes them from units[out]).
 template <int MODE>
-__global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __restrict__ off,
-                                               const uint32_t* __restrict__ csum,
-                                               uint32_t* __restrict__ ucnt,
-                                               const uint32_t* __restrict__ uoff,
-                                               uint2* __restrict__ units) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.nrows) return;
+__device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __restrict__ off,
+                                              const uint32_t* __restrict__ csum, uint32_t r,
+                                              uint32_t out,
+                                              uint2* __restrict__ units) {
     const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
     const int ncx = I.ncx;
     const uint32_t lr = r - I.row_base;
     const uint32_t* o = off + I.cell_base + (size_t)lr * (uint32_t)ncx;
     const uint32_t* cs = csum + I.cell_base + (size_t)lr * (uint32_t)ncx + r;
-    uint32_t n = 0, out = MODE ? uoff[r] : 0u;
+    uint32_t n = 0;
     uint32_t start = 0xffffffffu;
     uint32_t base = 0;   // cs[first - 1] of the open unit (clamped at 0)
     int lo = 0, last = 0;
@@ -1031,109 +1123,19 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
         if (MODE) units[out + n] = make_uint2(start, a);
         ++n;
     }
-    if (!MODE) ucnt[r] = n;
+    return n;
 }
 
-// Sec. 3.3 reductions.  The interaction leaves per-block counters (pairs,
-// candidates, status) and per-instance maxima; the last block to finish here
-// combines the counters in block order and, per instance,
-//   dt = CFL min( sqrt(h / max|a|), h / (max c + max mu) )
-// (0 for instances that are done), then clears the maxima for the next
-// evaluation.  Maxima and integer sums do not depend on the order.
-__global__ void __launch_bounds__(256) k_dt_reduce(const Dev d, const ReduceArgs a, int set_dt) {
-    __shared__ unsigned long long s_u[8][3];
-    __shared__ uint32_t s_b[8];
-    __shared__ bool s_last;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long pf = 0, pb = 0, nc = 0;
-    uint32_t bad = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nparts;
-         i += gridDim.x * blockDim.x) {
-        const uint4 u = a.part_u[i];
-        pf += u.x;
-        nc += u.y;
-        bad |= u.z;
-        pb += u.w;
-    }
-    for (int o = 16; o; o >>= 1) {
-        pf += __shfl_xor_sync(kFull, pf, o);
-        pb += __shfl_xor_sync(kFull, pb, o);
-        nc += __shfl_xor_sync(kFull, nc, o);
-        bad |= __shfl_xor_sync(kFull, bad, o);
-    }
-    if (lane == 0) {
-        s_u[w][0] = pf;
-        s_u[w][1] = pb;
-        s_u[w][2] = nc;
-        s_b[w] = bad;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long q0 = 0, q1 = 0, q2 = 0;
-        uint32_t b = 0;
-        for (int k = 0; k < 8; ++k) {
-            q0 += s_u[k][0];
-            q1 += s_u[k][1];
-            q2 += s_u[k][2];
-            b |= s_b[k];
-        }
-        a.lvl2_q[4 * blockIdx.x + 0] = q0;
-        a.lvl2_q[4 * blockIdx.x + 1] = q1;
-        a.lvl2_q[4 * blockIdx.x + 2] = q2;
-        a.lvl2_q[4 * blockIdx.x + 3] = b;
-        __threadfence();
-        const uint32_t ticket = atomicAdd(a.done, 1u);
-        s_last = ticket == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) {
-        unsigned long long qf = 0, qb = 0, qc = 0;
-        uint32_t b = 0;
-        for (uint32_t k = 0; k < gridDim.x; ++k) {
-            qf += __ldcg(a.lvl2_q + 4 * k + 0);
-            qb += __ldcg(a.lvl2_q + 4 * k + 1);
-            qc += __ldcg(a.lvl2_q + 4 * k + 2);
-            b |= (uint32_t)__ldcg(a.lvl2_q + 4 * k + 3);
-        }
-        a.counters[0] += qf + qb;
-        a.counters[1] += qc;
-        a.counters[2] = qf + qb;
-        a.counters[3] = qc;
-        a.counters[4] = qf;
-        a.counters[5] = qb;
-        a.counters[6] += qf;
-        a.counters[7] += qb;
-        if (b) atomicOr(a.status, b);
-        *a.done = 0u;
-    }
-    for (uint32_t q = threadIdx.x; q < d.n_inst; q += blockDim.x) {
-        uint32_t* tm = d.is.terms + 3 * q;
-        const float fa = __uint_as_float(__ldcg(tm + 0));
-        const float fc = __uint_as_float(__ldcg(tm + 1));
-        const float fm = __uint_as_float(__ldcg(tm + 2));
-        const double amax = sqrt((double)fa);
-        if (set_dt) {
-            double dt = 0.0;
-            if (!d.is.done[q]) {
-                if (d.dt_fixed > 0.0) {
-                    dt = d.dt_fixed;
-                } else {
-                    const double dtf = amax > 0.0 ? sqrt(d.h_d / amax) : INFINITY;
-                    const double dtc = d.h_d / ((double)fc + (double)fm);
-                    dt = d.cfl * (dtf < dtc ? dtf : dtc);
-                }
-            }
-            d.is.dt[q] = dt;
-            d.is.last[3 * q + 0] = (float)amax;
-            d.is.last[3 * q + 1] = fc;
-            d.is.last[3 * q + 2] = fm;
-        }
-        tm[0] = 0u;
-        tm[1] = 0u;
-        tm[2] = 0u;
-    }
+template <int MODE>
+__global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __restrict__ off,
+                                               const uint32_t* __restrict__ csum,
+                                               uint32_t* __restrict__ ucnt,
+                                               const uint32_t* __restrict__ uoff,
+                                               uint2* __restrict__ units) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.nrows) return;
+    const uint32_t n = unit_walk<MODE>(d, off, csum, r, MODE ? uoff[r] : 0u, units);
+    if (!MODE) ucnt[r] = n;
 }
 
 // Symplectic predictor (half step) for sorted particle k, then its new
@@ -1574,10 +1576,6 @@ void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* u
     k_units<0><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
     launch_scan(ucnt, d.nrows, ubsum, uoff, st);
     k_units<1><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
-}
-
-void launch_dt_reduce(const Dev& d, const ReduceArgs& a, bool set_dt, cudaStream_t st) {
-    k_dt_reduce<<<kReduceBlocks, 256, 0, st>>>(d, a, set_dt ? 1 : 0);
 }
 
 void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
