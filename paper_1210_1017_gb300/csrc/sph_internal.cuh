@@ -141,7 +141,7 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 // size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
 constexpr int kMinUnit = 32;
-constexpr int kNumVariants = 10;
+constexpr int kNumVariants = 12;
 
 struct ReduceArgs {
     const uint4* part_u;

@@ -360,9 +360,10 @@ __device__ __forceinline__ void pair_terms(const Dev& d, float c0, const float4&
 //   dt = CFL min( sqrt(h / max|a|), h / (max c + max mu) )
 // (0 for instances that are done), and the maxima are cleared for the next
 // evaluation.  Loads bypass L1 (the partials may come from the same kernel).
+// Run by a block of at most 256 threads (an interaction block).
 __device__ void reduce_counters_and_dt(const Dev& d, const ReduceArgs& a, int set_dt) {
-    __shared__ unsigned long long s_u[32][3];
-    __shared__ uint32_t s_b[32];
+    __shared__ unsigned long long s_u[8][3];
+    __shared__ uint32_t s_b[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     unsigned long long pf = 0, pb = 0, nc = 0;
     uint32_t bad = 0;
@@ -520,7 +521,8 @@ __device__ __forceinline__ void pair_terms2(const Dev& d, float c0, const float4
 // keeps a similar share of its own neighbours in each part); the parts' sums
 // are added in a fixed order at the end.  More warps per block at the same
 // staging footprint.
-template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN, bool PK>
+template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN, bool PK,
+          bool TU>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     constexpr int NT = W * SPLIT * 32;
     constexpr int FBCAP = Shape<W * SPLIT, STAGE, WCAP>::fb_cap;   // fallback list slots
@@ -833,8 +835,21 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                             return *reinterpret_cast<const uint32_t*>(&r2t);
                         };
                         uint32_t m = 0;
+                        // TU: a word of five or more candidate pairs tests its
+                        // first eight pairs without a bound test between them
+                        // (their loads can all be in flight), then the rest
+                        uint32_t jj0 = 0;
+                        if (TU && npair >= 5) {
+#pragma unroll
+                            for (uint32_t jj = 0; jj < 4; ++jj) {
+                                const uint32_t sa = test_pair(hp[2 * jj]), sb = test_pair(hp[2 * jj + 1]);
+                                m |= sign_bytes(sa, sb) & (0x01010101u << jj);
+                            }
+                            jj0 = 4;
+                        }
 #pragma unroll
                         for (uint32_t jj = 0; jj < 8; ++jj) {
+                            if (jj < jj0) continue;
                             if (2 * jj >= npair) break;
                             const uint32_t sa = test_pair(hp[2 * jj]), sb = test_pair(hp[2 * jj + 1]);
                             m |= sign_bytes(sa, sb) & (0x01010101u << jj);
@@ -1511,15 +1526,16 @@ struct Variant {
 
 // (warps, staged candidates, hit-mask words per lane, resident blocks per SM
 // that the shared memory allows -- also the register budget hint)
-#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv, PKv)                                          \
+#define SPH_VARIANT_T(Wv, Sv, Cv, Bv, Pv, PKv, TUv)                                   \
     Variant {                                                                        \
         Wv, Pv, Sv,                                                                  \
-            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0, PKv>,                         \
-              k_interact<Wv, Sv, Cv, Bv, true, Pv, 0, PKv>},                         \
-             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1, PKv>,                         \
-              k_interact<Wv, Sv, Cv, Bv, true, Pv, 1, PKv>}},                        \
+            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0, PKv, TUv>,                    \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 0, PKv, TUv>},                    \
+             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1, PKv, TUv>,                    \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 1, PKv, TUv>}},                   \
             Shape<Wv * Pv, Sv, Cv>::smem, 0                                          \
     }
+#define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv, PKv) SPH_VARIANT_T(Wv, Sv, Cv, Bv, Pv, PKv, false)
 
 Variant g_variants[kNumVariants] = {
     SPH_VARIANT(4, 2048, 24, 2, 2, false),   // 128-particle units, two warps per 32 particles
@@ -1533,6 +1549,9 @@ Variant g_variants[kNumVariants] = {
     SPH_VARIANT(4, 2048, 24, 2, 2, true),
     SPH_VARIANT(3, 1408, 16, 3, 2, true),
     SPH_VARIANT(4, 1792, 20, 2, 2, true),
+    // packed, and the candidate test's first eight pairs of a word unconditional
+    SPH_VARIANT_T(4, 2048, 24, 2, 2, true, true),
+    SPH_VARIANT_T(3, 1408, 16, 3, 2, true, true),
 };
 
 }  // namespace
