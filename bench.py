@@ -409,7 +409,8 @@ def run_ours(args):
     cfg.update(formulation_config(args.formulation))
     cfg.update({"formulation": args.formulation, "position_dtype": "f64", "l2": "inputs larger than L2",
                 "parallelism": f"replicas x{ws}", "interaction_variant": variant,
-                "variant_ms": [round(float(v), 3) for v in variant_ms]})
+                "variant_ms": [round(float(v), 3) for v in variant_ms],
+                "programmatic_dependent_launch": S.pdl_enabled()})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

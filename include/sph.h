@@ -384,6 +384,15 @@ int sph_autotune(sph_ctx *ctx, uint32_t reps, float *ms_per_variant,
 /* Number of kernels one sph_step(ctx, 1) launches. */
 uint32_t sph_kernels_per_step(const sph_ctx *ctx);
 
+/* 1 when the step's kernels are launched with programmatic dependent launch
+ * (each may be scheduled while its predecessor drains and waits for it on
+ * the device before touching memory; results are the same either way), 0
+ * when not.  Decided once per process by the first sph_init or
+ * sph_init_batch: off when the environment sets SPH_PDL=0, or when the
+ * driver refuses such launches inside a captured conditional node (checked
+ * with a graph whose loop body never runs).  0 before the first context. */
+int sph_pdl_enabled(void);
+
 /* FP32 issue-rate probe (a measurement helper; the paper has no
  * counterpart): launches `blocks` blocks of 256 threads on stream, each
  * thread running `iters` iterations of 128 independent fused multiply-adds

@@ -971,6 +971,8 @@ int sph_selftest_timeout(sph_ctx* c, uint32_t polls) {
 
 uint32_t sph_num_variants(void) { return (uint32_t)kNumVariants; }
 
+int sph_pdl_enabled(void) { return pdl_enabled() ? 1 : 0; }
+
 int sph_set_variant(sph_ctx* c, uint32_t v) {
     if (!c || v >= (uint32_t)kNumVariants) return fail(c, SPH_ERR_INVALID_ARG, "bad variant");
     if ((int)v == c->variant) return SPH_OK;

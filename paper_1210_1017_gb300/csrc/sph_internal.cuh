@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace sph {
 
 constexpr uint32_t kStatusTimeout = 1u;
@@ -141,7 +143,7 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 // size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
 constexpr int kMinUnit = 32;
-constexpr int kNumVariants = 12;
+constexpr int kNumVariants = 13;
 
 struct ReduceArgs {
     const uint4* part_u;
@@ -181,6 +183,32 @@ void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* u
 // the persistent grid from the device's SM count and occupancy.
 void prepare_interact();
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
+
+// Programmatic dependent launch of the step's kernels: a kernel launched
+// with it may be scheduled while the previous kernel of its stream drains,
+// and it calls pdl_wait() before touching global memory; that returns once
+// the previous kernel has completed and its writes are visible.  Since every
+// such kernel waits first, each also completes after all earlier work of the
+// stream.  pdl_enabled() is decided once per process by prepare_interact:
+// off when the environment sets SPH_PDL=0 or when the driver does not accept
+// the launches inside a captured conditional node's body.
+bool pdl_enabled();
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... K, typename... A>
+inline cudaError_t launch_pdl(void (*k)(K...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, A&&... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1u : 0u;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 
 struct IntegrateArgs {

@@ -7,6 +7,9 @@
 // simulation is the ensemble of one.
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdlib.h>
+
+#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -135,6 +138,7 @@ constexpr uint32_t kMaxSeg = 4096;   // largest cell the id tie-break handles
 // the cells was.  Also writes the FP32 position relative to the cell's
 // origin and P = p/rho^2.
 __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs a) {
+    pdl_wait();
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = k < d.n;
@@ -524,6 +528,7 @@ __device__ __forceinline__ void pair_terms2(const Dev& d, float c0, const float4
 template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN, bool PK,
           bool TU>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
+    pdl_wait();
     constexpr int NT = W * SPLIT * 32;
     constexpr int FBCAP = Shape<W * SPLIT, STAGE, WCAP>::fb_cap;   // fallback list slots
     extern __shared__ __align__(128) unsigned char s_raw[];
@@ -1045,6 +1050,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
 // row, threads along x (coalesced).
 __global__ void __launch_bounds__(128) k_row_csum(const Dev d, const uint32_t* __restrict__ off,
                                                   uint32_t* __restrict__ csum) {
+    pdl_wait();
     const uint32_t r = blockIdx.x;
     const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
     const int ncx = I.ncx;
@@ -1147,6 +1153,7 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
                                                uint32_t* __restrict__ ucnt,
                                                const uint32_t* __restrict__ uoff,
                                                uint2* __restrict__ units) {
+    pdl_wait();
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.nrows) return;
     const uint32_t n = unit_walk<MODE>(d, off, csum, r, MODE ? uoff[r] : 0u, units);
@@ -1158,6 +1165,7 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
 // (k >= in-domain count) are left untouched.  Each particle uses its
 // instance's step size (0 once the instance is done).
 __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArgs a) {
+    pdl_wait();
     __shared__ uint32_t s_hist[4 * 256];
     zero_hist(s_hist);
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1203,6 +1211,7 @@ __global__ void __launch_bounds__(256) k_predict(const Dev d, const IntegrateArg
 // current state) and the half-step rates, then the new label.  Threads
 // k < n_inst also advance instance k's time and step count.
 __global__ void __launch_bounds__(256) k_correct(const Dev d, const IntegrateArgs a) {
+    pdl_wait();
     __shared__ uint32_t s_hist[4 * 256];
     zero_hist(s_hist);
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1263,6 +1272,7 @@ __global__ void __launch_bounds__(256) k_correct(const Dev d, const IntegrateArg
 // receives the (v, rho) on entry.  Members that are done (dt = 0) and
 // excluded particles keep their state.
 __global__ void __launch_bounds__(256) k_verlet(const Dev d, const IntegrateArgs a) {
+    pdl_wait();
     __shared__ uint32_t s_hist[4 * 256];
     zero_hist(s_hist);
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1312,6 +1322,7 @@ __global__ void __launch_bounds__(256) k_verlet(const Dev d, const IntegrateArgs
 // After k_verlet: each running member's time, step count and Verlet phase
 // (0 again after verlet_every steps) advance.
 __global__ void __launch_bounds__(256) k_verlet_advance(const Dev d) {
+    pdl_wait();
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < d.n_inst && !d.is.done[q]) {
         const double t = d.is.t[q] + d.is.dt[q];
@@ -1477,6 +1488,7 @@ __global__ void k_loop_init(uint32_t* ctr, uint32_t nsteps) {
 __global__ void __launch_bounds__(256) k_loop_ctrl(cudaGraphConditionalHandle h, uint32_t* ctr,
                                                    const uint32_t* __restrict__ done,
                                                    uint32_t n_inst, uint32_t body) {
+    pdl_wait();
     int running = 0;
     for (uint32_t q = threadIdx.x; q < n_inst; q += blockDim.x) running |= done[q] == 0u;
     running = __syncthreads_or(running);
@@ -1499,7 +1511,7 @@ void launch_keys(const Dev& d, const double* x, const double* y, const double* z
 }
 
 void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st) {
-    k_reorder<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
+    launch_pdl(k_reorder, blocks_for(d.n, 256), 256, 0, st, d, a);
 }
 
 // Upper bound on the number of units: every unit but the last of its row
@@ -1552,6 +1564,9 @@ Variant g_variants[kNumVariants] = {
     // packed, and the candidate test's first eight pairs of a word unconditional
     SPH_VARIANT_T(4, 2048, 24, 2, 2, true, true),
     SPH_VARIANT_T(3, 1408, 16, 3, 2, true, true),
+    // 32-particle units shared by four warps, four blocks per SM: shorter
+    // dependent chains per unit for small systems (fewer units than SMs)
+    SPH_VARIANT_T(1, 1024, 12, 4, 4, true, true),
 };
 
 }  // namespace
@@ -1563,7 +1578,72 @@ int variant_stage(int v) { return g_variants[v].stage; }
 // Persistent grid: every resident block of the variant on this GPU.
 uint32_t interact_grid(int v) { return (uint32_t)g_variants[v].grid; }
 
+namespace {
+
+__global__ void k_pdl_probe() { pdl_wait(); }
+
+bool g_pdl = false;
+std::once_flag g_pdl_once;
+
+// Whether the driver takes programmatic launches inside a captured
+// conditional node's body (the device-side step loop): capture two of them
+// into a WHILE node whose condition starts at 0 (the body never runs), then
+// instantiate and launch the graph.  Every failure here is a host-side error
+// code, cleared before returning.
+bool probe_pdl() {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    do {
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 0u, cudaGraphCondAssignDefault) !=
+            cudaSuccess)
+            break;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            break;
+        g_pdl = true;   // launch_pdl reads it
+        const cudaError_t e1 = launch_pdl(k_pdl_probe, 1, 32, 0, s);
+        const cudaError_t e2 = launch_pdl(k_pdl_probe, 1, 32, 0, s);
+        g_pdl = false;
+        const cudaError_t e3 = cudaStreamEndCapture(s, &body);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) break;
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) break;
+        if (cudaStreamSynchronize(s) != cudaSuccess) break;
+        ok = true;
+    } while (false);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(s);
+    cudaGetLastError();
+    return ok;
+}
+
+}  // namespace
+
+bool pdl_enabled() { return g_pdl; }
+
 void prepare_interact() {
+    std::call_once(g_pdl_once, [] {
+        const char* e = getenv("SPH_PDL");
+        const bool want = !(e && e[0] == '0');
+        g_pdl = want && probe_pdl();
+    });
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1586,29 +1666,30 @@ void prepare_interact() {
 
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st) {
     const Variant& v = g_variants[d.variant];
-    v.fn[d.kern == 1 ? 1 : 0][counts ? 1 : 0]<<<v.grid, v.warps * v.split * 32, v.smem, st>>>(d, a);
+    launch_pdl(v.fn[d.kern == 1 ? 1 : 0][counts ? 1 : 0], v.grid, v.warps * v.split * 32, v.smem,
+               st, d, a);
 }
 
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
                   uint32_t* ubsum, uint32_t* uoff, uint2* units, cudaStream_t st) {
-    k_row_csum<<<d.nrows, 128, 0, st>>>(d, off, csum);
-    k_units<0><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
+    launch_pdl(k_row_csum, d.nrows, 128, 0, st, d, off, csum);
+    launch_pdl(k_units<0>, blocks_for(d.nrows, 128), 128, 0, st, d, off, csum, ucnt, uoff, units);
     launch_scan(ucnt, d.nrows, ubsum, uoff, st);
-    k_units<1><<<blocks_for(d.nrows, 128), 128, 0, st>>>(d, off, csum, ucnt, uoff, units);
+    launch_pdl(k_units<1>, blocks_for(d.nrows, 128), 128, 0, st, d, off, csum, ucnt, uoff, units);
 }
 
 void launch_predict(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
-    k_predict<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
+    launch_pdl(k_predict, blocks_for(d.n, 256), 256, 0, st, d, a);
 }
 
 void launch_correct(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
     const uint32_t n = d.n > d.n_inst ? d.n : d.n_inst;
-    k_correct<<<blocks_for(n, 256), 256, 0, st>>>(d, a);
+    launch_pdl(k_correct, blocks_for(n, 256), 256, 0, st, d, a);
 }
 
 void launch_verlet(const Dev& d, const IntegrateArgs& a, cudaStream_t st) {
-    k_verlet<<<blocks_for(d.n, 256), 256, 0, st>>>(d, a);
-    k_verlet_advance<<<blocks_for(d.n_inst, 256), 256, 0, st>>>(d);
+    launch_pdl(k_verlet, blocks_for(d.n, 256), 256, 0, st, d, a);
+    launch_pdl(k_verlet_advance, blocks_for(d.n_inst, 256), 256, 0, st, d);
 }
 
 void launch_counts_fp64(const Dev& d, const double* x, const double* y, const double* z,
@@ -1630,7 +1711,7 @@ void launch_loop_init(uint32_t* ctr, uint32_t nsteps, cudaStream_t st) {
 
 void launch_loop_ctrl(cudaGraphConditionalHandle h, uint32_t* ctr, const uint32_t* done,
                       uint32_t n_inst, uint32_t body, cudaStream_t st) {
-    k_loop_ctrl<<<1, 256, 0, st>>>(h, ctr, done, n_inst, body);
+    launch_pdl(k_loop_ctrl, 1, 256, 0, st, h, ctr, done, n_inst, body);
 }
 
 void launch_front(const Dev& d, const double* x, const double* z, const uint32_t* id,

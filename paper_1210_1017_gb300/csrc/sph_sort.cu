@@ -246,6 +246,7 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
                                                               uint64_t m,
                                                               uint32_t* __restrict__ bsum) {
+    pdl_wait();
     __shared__ uint32_t s_w[8];
     const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
     uint32_t s = 0;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 
 // Exclusive scan of the block sums in place (one block).
 __global__ void __launch_bounds__(256) k_scan_top(uint32_t* bsum, uint32_t nb) {
+    pdl_wait();
     __shared__ uint32_t s_w[8];
     __shared__ uint32_t s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
                                                             const uint32_t* __restrict__ bsum,
                                                             uint32_t* __restrict__ out,
                                                             int zero_in) {
+    pdl_wait();
     __shared__ uint32_t s_w[8];
     const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
     const uint64_t t0 = b0 + (uint64_t)threadIdx.x * kScanItems;
@@ -324,12 +327,12 @@ void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaSt
     const uint32_t nb = scan_bsum_count(m);
     if (nb == 1) {
         // one block holds the whole array: no block sums needed
-        k_scan_down<<<1, kScanThreads, 0, st>>>(in, m, nullptr, out, zero_in ? 1 : 0);
+        launch_pdl(k_scan_down, 1, kScanThreads, 0, st, in, m, nullptr, out, zero_in ? 1 : 0);
         return;
     }
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, m, bsum);
-    k_scan_top<<<1, 256, 0, st>>>(bsum, nb);
-    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, m, bsum, out, zero_in ? 1 : 0);
+    launch_pdl(k_scan_reduce, nb, kScanThreads, 0, st, in, m, bsum);
+    launch_pdl(k_scan_top, 1, 256, 0, st, bsum, nb);
+    launch_pdl(k_scan_down, nb, kScanThreads, 0, st, in, m, bsum, out, zero_in ? 1 : 0);
 }
 
 // The per-cell counts (incl. the excluded bin) stay in cnt: the scatter of
@@ -350,6 +353,7 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ off,
                                                       uint32_t* cnt, uint32_t* __restrict__ kout,
                                                       uint32_t* __restrict__ vout) {
+    pdl_wait();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     const uint32_t act = __ballot_sync(kFull, valid);
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const uint32_t* __restrict
 void launch_cell_scatter(const uint32_t* key, uint32_t n, const uint32_t* off, uint32_t* cnt,
                          uint32_t* kout, uint32_t* vout, cudaStream_t st) {
     if (n == 0) return;
-    k_cell_scatter<<<(n + 255) / 256, 256, 0, st>>>(key, n, off, cnt, kout, vout);
+    launch_pdl(k_cell_scatter, (n + 255) / 256, 256, 0, st, key, n, off, cnt, kout, vout);
 }
 
 void launch_lookback_selftest(uint32_t* zeroed256, uint32_t limit, uint32_t* err,

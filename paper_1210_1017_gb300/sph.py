@@ -17,7 +17,7 @@ from . import _build
 
 # Revision tag of the interaction kernel; DRAM-traffic figures captured with
 # ncu are only quoted while they were taken on this revision.
-KERNEL_REV = "interact-v4.12"
+KERNEL_REV = "interact-v4.13"
 
 SPH_OK = 0
 SPH_INTERACT_COUNTS = 1
@@ -41,7 +41,7 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout",
             "sph_set_instance_state", "sph_front", "sph_radix_sort_status",
             "sph_radix_sort_selftest_timeout", "sph_radix_sort_static_status",
-            "sph_radix_sort_static_selftest_timeout", "sph_fma_probe"]
+            "sph_radix_sort_static_selftest_timeout", "sph_fma_probe", "sph_pdl_enabled"]
 
 
 class SphParams(C.Structure):
@@ -157,6 +157,8 @@ def lib(build: bool = False):
     L.sph_set_instance_state.argtypes = [vp, vp, vp]
     L.sph_num_variants.argtypes = []
     L.sph_num_variants.restype = u32
+    L.sph_pdl_enabled.argtypes = []
+    L.sph_pdl_enabled.restype = C.c_int
     L.sph_set_variant.argtypes = [vp, u32]
     L.sph_autotune.argtypes = [vp, u32, vp, vp]
     L.sph_subdomain_select.argtypes = [vp, i32, C.c_double, C.c_double, vp, u32, vp, vp, vp, vp]
@@ -318,6 +320,12 @@ def read_checkpoint(path):
 
 def sph_num_variants() -> int:
     return int(lib().sph_num_variants())
+
+
+def pdl_enabled() -> bool:
+    """Whether the step's kernels use programmatic dependent launch (decided
+    by the first context of the process; SPH_PDL=0 turns it off)."""
+    return bool(lib().sph_pdl_enabled())
 
 
 def sph_set_variant(ctx, v: int):
