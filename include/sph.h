@@ -290,7 +290,17 @@ int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
  *   SPH_ARRAY_POSC     float32[4n] cell-relative position and p/rho^2
  *   SPH_ARRAY_DT       float64[n_inst] current step size of each member
  *   SPH_ARRAY_PREV     float32[4n] (vx, vy, vz, rho) one step earlier, in the
- *                      order of the state (Verlet contexts after a step) */
+ *                      order of the state (Verlet contexts after a step)
+ *   SPH_ARRAY_UNITS    uint32[1 + 2 cap]: the number of interaction work units
+ *                      m, then m (first sorted index, end) pairs, each a run
+ *                      of particles of one row of cells (Sec. 3.2; cut for
+ *                      the interaction variant in use); the words past 1 + 2m
+ *                      are unspecified.  cap bounds m for the context.  Needs
+ *                      built cells (SPH_ERR_STATE otherwise).  The list is
+ *                      built in one launch when the grid has at most 8,192
+ *                      rows of at most 1,023 cells, unless the environment
+ *                      sets SPH_UNITS_FUSED=0 when the context is created;
+ *                      the list is the same either way. */
 #define SPH_ARRAY_KEY      0
 #define SPH_ARRAY_CELL_OFF 1
 #define SPH_ARRAY_ACE      2
@@ -299,6 +309,7 @@ int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
 #define SPH_ARRAY_POSC     5
 #define SPH_ARRAY_DT       6
 #define SPH_ARRAY_PREV     7
+#define SPH_ARRAY_UNITS    8
 uint64_t sph_array_bytes(const sph_ctx *ctx, int which);
 int sph_read_array(sph_ctx *ctx, int which, void *host, uint64_t bytes);
 
@@ -365,6 +376,13 @@ int sph_clear_status(sph_ctx *ctx);
  * returns SPH_ERR_TIMEOUT.  The particle state and cells are untouched (the
  * look-back runs on status words reserved for this test).  Sync. */
 int sph_selftest_timeout(sph_ctx *ctx, uint32_t polls);
+
+/* The same for the one-launch unit list's row look-back (see
+ * SPH_ARRAY_UNITS): one warp waits, with a limit of `polls` polls (1 to
+ * 2^20), on the word of a preceding row that nothing publishes, gives up and
+ * sets SPH_STATUS_TIMEOUT, so sph_check returns SPH_ERR_TIMEOUT.  The state,
+ * cells and unit list are untouched.  Sync. */
+int sph_units_selftest_timeout(sph_ctx *ctx, uint32_t polls);
 
 /* Block shapes of the interaction kernel ("variants": particles per work
  * unit, staged candidates per unit, neighbour-list slots per lane) and the

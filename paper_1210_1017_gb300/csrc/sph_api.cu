@@ -202,7 +202,8 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->nnb64 = cv.take<uint32_t>(n);
     c->cnt = cv.take<uint32_t>(t.ncells + 1);
     c->off = cv.take<uint32_t>(t.ncells + 2);
-    c->bsum = cv.take<uint32_t>(scan_bsum_count(t.ncells + 1));
+    c->cscan_words = cv.take<unsigned long long>(scan_bsum_count(t.ncells + 1));
+    c->cscan_ctl = cv.take<uint32_t>(2);
     c->hist = cv.take<uint32_t>(4 * 256);
     const uint32_t tiles = os_tiles(n);
     (void)passes;
@@ -222,7 +223,10 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->ucnt = cv.take<uint32_t>(t.nrows + 1);
     c->uoff = cv.take<uint32_t>(t.nrows + 2);
     c->ubsum = cv.take<uint32_t>(scan_bsum_count(t.nrows + 1));
-    c->units = cv.take<uint2>(max_units(n, (uint32_t)t.nrows, t.ncells));
+    c->urow = cv.take<unsigned long long>(t.nrows);
+    c->uctl = cv.take<uint32_t>(2);
+    c->units_cap = max_units(n, (uint32_t)t.nrows, t.ncells);
+    c->units = cv.take<uint2>(c->units_cap);
     c->part_u = cv.take<uint4>(kMaxGridBlocks);
     c->done = cv.take<uint32_t>(1);   // ticket of the interaction's last block
     c->status = cv.take<uint32_t>(1);
@@ -279,6 +283,7 @@ Dev make_dev(const sph_ctx* c) {
     d.variant = c->variant;
     d.unit = variant_unit(c->variant);
     d.stage = variant_stage(c->variant);
+    d.units_fused = c->units_one ? 1 : 0;
     d.csf = (float)cs;
     d.h = (float)p->h;
     d.inv_h = (float)(1.0 / p->h);
@@ -308,13 +313,14 @@ Dev make_dev(const sph_ctx* c) {
 // units and reorder the state (and the start state when with_pre).
 void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     cudaStream_t st = c->st;
-    launch_scan_cells(c->d, c->cnt, c->bsum, c->off, st);
+    launch_scan_cells(c->d, c->cnt, c->off, c->cscan_words, c->cscan_ctl, c->status, st);
     // the labels are in key[0]; one counting-sort pass groups the particles
     // by cell into (key[1], val[1]) and the reorder applies the id tie-break
     launch_cell_scatter(c->key[0], c->n, c->off, c->cnt, c->key[1], c->val[1], st);
     const int src = 1;
     c->skey = src;
-    launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, st);
+    launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->urow,
+                 c->uctl, c->status, st);
     ReorderArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.skey = c->key[src];
@@ -476,6 +482,13 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
         return SPH_ERR_WORKSPACE;
     }
     c->tiles = os_tiles(c->n);
+    {
+        // the one-launch unit list for grids of few, short rows, unless the
+        // environment sets SPH_UNITS_FUSED=0 when the context is created
+        const char* e = getenv("SPH_UNITS_FUSED");
+        c->units_one = !(e && e[0] == '0') &&
+                       units_fit_one_launch((uint32_t)c->tab.nrows, c->tab.max_ncx);
+    }
     prepare_interact();
     for (int v = 0; v < kNumVariants; ++v) {
         if (interact_grid(v) == 0 || interact_grid(v) > kMaxGridBlocks) {
@@ -506,6 +519,11 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
     cudaMemsetAsync(c->done, 0, sizeof(uint32_t), st);
     cudaMemsetAsync(c->status, 0, sizeof(uint32_t), st);
     cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(c->urow, 0, (size_t)c->tab.nrows * sizeof(unsigned long long), st);
+    cudaMemsetAsync(c->uctl, 0, 2 * sizeof(uint32_t), st);
+    cudaMemsetAsync(c->cscan_words, 0, scan_bsum_count(c->ncells + 1) * sizeof(unsigned long long),
+                    st);
+    cudaMemsetAsync(c->cscan_ctl, 0, 2 * sizeof(uint32_t), st);
     rc = cuda_check(c, cudaStreamSynchronize(st), "sph_init");
     if (rc) {
         delete c;
@@ -828,6 +846,7 @@ uint64_t sph_array_bytes(const sph_ctx* c, int which) {
         case SPH_ARRAY_POSC: return (uint64_t)c->n * 16;
         case SPH_ARRAY_PREV: return c->verlet ? (uint64_t)c->n * 16 : 0;
         case SPH_ARRAY_DT: return 8ull * c->n_inst;
+        case SPH_ARRAY_UNITS: return 4ull + 8ull * c->units_cap;
         default: return 0;
     }
 }
@@ -836,6 +855,17 @@ int sph_read_array(sph_ctx* c, int which, void* host, uint64_t bytes) {
     if (!c || !host) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
     const uint64_t want = sph_array_bytes(c, which);
     if (want == 0 || bytes != want) return fail(c, SPH_ERR_INVALID_ARG, "bad array id or size");
+    if (which == SPH_ARRAY_UNITS) {
+        if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
+        // the count, then the units; entries past the count are left as they are
+        uint32_t* h = static_cast<uint32_t*>(host);
+        int rc = cuda_check(c, cudaMemcpyAsync(h, c->uoff + c->tab.nrows, 4, cudaMemcpyDeviceToHost,
+                                               c->st), "read unit count");
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(h + 1, c->units, 8ull * c->units_cap,
+                                                    cudaMemcpyDeviceToHost, c->st), "read units");
+        if (rc) return rc;
+        return cuda_check(c, cudaStreamSynchronize(c->st), "read array sync");
+    }
     const void* src = nullptr;
     switch (which) {
         case SPH_ARRAY_KEY: src = c->key[c->skey]; break;
@@ -969,6 +999,17 @@ int sph_selftest_timeout(sph_ctx* c, uint32_t polls) {
     return cuda_check(c, cudaStreamSynchronize(c->st), "selftest sync");
 }
 
+int sph_units_selftest_timeout(sph_ctx* c, uint32_t polls) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (polls == 0 || polls > (1u << 20)) return fail(c, SPH_ERR_INVALID_ARG, "polls must be 1..2^20");
+    // a word of the sort self-test's reserved status area (zeroed by the launch)
+    launch_row_lookback_selftest(reinterpret_cast<unsigned long long*>(c->os_status), polls,
+                                 c->status, c->st);
+    int rc = post_launch(c, "units selftest");
+    if (rc) return rc;
+    return cuda_check(c, cudaStreamSynchronize(c->st), "units selftest sync");
+}
+
 uint32_t sph_num_variants(void) { return (uint32_t)kNumVariants; }
 
 int sph_pdl_enabled(void) { return pdl_enabled() ? 1 : 0; }
@@ -986,7 +1027,8 @@ int sph_set_variant(sph_ctx* c, uint32_t v) {
         c->loop_graph[g] = nullptr;
     }
     // the work units depend on the block shape: recut them for the current cells
-    if (c->cells_valid) launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->st);
+    if (c->cells_valid) launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units,
+                                     c->urow, c->uctl, c->status, c->st);
     return post_launch(c, "set variant");
 }
 
@@ -1041,11 +1083,13 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
 
 uint32_t sph_kernels_per_step(const sph_ctx* c) {
     if (!c) return 0;
-    // a scan is 3 kernels, or 1 when the array fits one scan block
-    const uint32_t cell_scan = scan_bsum_count(c->ncells + 1) == 1 ? 1u : 3u;
-    // the unit list: row sums, count, scan, fill
+    // the cell scan is one launch; another scan is 3 kernels, or 1 when the
+    // array fits one scan block
+    const uint32_t cell_scan = 1u;
+    // the unit list: one launch for a grid of few rows, else row sums, count,
+    // scan, fill
     const uint32_t unit_scan = scan_bsum_count(c->tab.nrows) == 1 ? 1u : 3u;
-    const uint32_t unit_list = 3u + unit_scan;
+    const uint32_t unit_list = c->units_one ? 1u : 3u + unit_scan;
     // one rebuild: cell scan + 1 counting-sort scatter + unit list + reorder
     const uint32_t rebuild = cell_scan + 1u + unit_list + 1u;
     // Verlet: interact (with the CFL reduction) + update + member advance + rebuild

@@ -43,9 +43,15 @@ struct sph_ctx {
     double* stage_pos;       // host transfer staging: 3n doubles
     float* stage_vr;         // 4n floats (velocity, then density)
     uint32_t *key[2], *val[2];
-    uint32_t *cnt, *off, *bsum, *hist, *tilectr, *os_status, *nnb, *nnb64;
+    uint32_t *cnt, *off, *hist, *tilectr, *os_status, *nnb, *nnb64;
     uint32_t *ucnt, *uoff, *ubsum;   // work units of the interaction
     uint32_t* csum;                  // staged-candidate prefix sums per row
+    unsigned long long* cscan_words; // one-launch cell scan: look-back word per tile
+    uint32_t* cscan_ctl;             // one-launch cell scan: tile ticket, launch epoch
+    unsigned long long* urow;        // one-launch unit list: look-back word per row
+    uint32_t* uctl;                  // one-launch unit list: row ticket, launch epoch
+    bool units_one = false;          // build the unit list in one launch
+    uint32_t units_cap = 0;          // capacity of `units`
     uint2* units;
     uint4* part_u;
     uint32_t *done, *status;

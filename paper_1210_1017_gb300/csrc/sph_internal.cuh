@@ -72,6 +72,7 @@ struct Dev {
     int variant;           // interaction variant (block shape) in use
     int unit;              // its unit size in particles
     int stage;             // its staging capacity in candidates
+    int units_fused;       // the unit list is built in one launch (k_units_fused)
     float csf;             // 2h
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
@@ -88,12 +89,22 @@ struct Dev {
 void launch_keys(const Dev& d, const double* x, const double* y, const double* z,
                  const uint32_t* id, uint32_t n, uint32_t* key, uint32_t* cnt, uint32_t* hist,
                  int passes, cudaStream_t st);
-void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
-                       cudaStream_t st);
+// Cell offsets from the per-cell counts (kept: the cell sort's scatter
+// counts them back down) in one launch (launch_scan_onepass).
+void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* off, unsigned long long* words,
+                       uint32_t* ctl, uint32_t* err, cudaStream_t st);
 // out[i] = in[0] + ... + in[i-1] for i = 0..m (m + 1 outputs); clears in[]
 // unless zero_in is false.
 void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaStream_t st,
                  bool zero_in = true);
+// The same in one launch, with a decoupled look-back between tiles: words
+// holds scan_bsum_count(m) look-back words and ctl a ticket and an epoch,
+// all zero before the first launch and kept by the caller between launches
+// (one set per stream of successive scans).  A look-back that gives up sets
+// kStatusTimeout in *err.
+void launch_scan_onepass(uint32_t* in, uint64_t m, uint32_t* out, bool zero_in,
+                         unsigned long long* words, uint32_t* ctl, uint32_t* err,
+                         cudaStream_t st);
 // One-pass counting sort of the cell labels (keys; values = input index)
 // into (kout, vout), from the per-cell counts cnt (counted back to zero) and
 // the cell offsets off.  Order inside a cell is arbitrary.
@@ -177,12 +188,78 @@ uint32_t max_units(uint32_t n, uint32_t nrows, uint64_t ncells);   // bound on u
 int variant_unit(int variant);               // particles per unit of a variant
 int variant_stage(int variant);              // staged candidates of a variant
 uint32_t interact_grid(int variant);         // blocks of its persistent launch
+// Grids of few, short rows build the unit list in one launch (row sums,
+// counts, a look-back over rows, the fill); others take row sums, counts, a
+// scan and the fill as separate launches.
+struct UnitsFusedArgs {
+    uint2* units;
+    uint32_t* total;                 // number of units (uoff[nrows])
+    unsigned long long* words;       // per-row look-back words (nrows)
+    uint32_t* ctl;                   // row ticket, launch epoch (zero at init)
+    uint32_t* err;                   // device status word
+};
+bool units_fused(const Dev& d);
+bool units_fit_one_launch(uint32_t nrows, int max_ncx);   // the grid qualifies
+// Failure-path self-test: the one-launch unit list's row look-back waits on
+// a word that nothing publishes (zeroed here) and gives up after `limit`
+// polls, setting kStatusTimeout in *err.
+void launch_row_lookback_selftest(unsigned long long* zeroed, uint32_t limit, uint32_t* err,
+                                  cudaStream_t st);
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
-                  uint32_t* ubsum, uint32_t* uoff, uint2* units, cudaStream_t st);
+                  uint32_t* ubsum, uint32_t* uoff, uint2* units, unsigned long long* urow,
+                  uint32_t* uctl, uint32_t* err, cudaStream_t st);
 // Once per context (current device): opt in to the shared memory and size
 // the persistent grid from the device's SM count and occupancy.
 void prepare_interact();
 void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStream_t st);
+
+// Decoupled look-back over tiles handed out in launch order (the one-launch
+// unit list's rows, the one-launch scan's tiles).  A tile's word is
+// epoch << 34 | flag << 32 | value, flag 1 for the tile's own total and 2
+// for the inclusive prefix through it; the epoch (launch number mod 2^30)
+// makes words of earlier launches read as not yet published, so the words
+// are never cleared.  tile_lookback returns the sum over tiles 0 .. r-1 (the
+// whole warp; lane j reads tile p - j of a window of 32 below the next
+// unread tile p).  A wait that sees no progress for `limit` polls sets
+// kStatusTimeout in *err and returns the partial sum, which never exceeds
+// the true one.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t tile_lookback(const unsigned long long* words, uint32_t r,
+                                                  uint32_t ep, uint32_t limit, uint32_t* err) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t excl = 0, spins = 0;
+    int64_t p = (int64_t)r - 1;
+    while (true) {
+        const int64_t q = p - lane;
+        uint32_t flag = 2u, val = 0u;   // before tile 0: a prefix of 0
+        if (q >= 0) {
+            const unsigned long long s = ld_relaxed64(words + q);
+            flag = (uint32_t)(s >> 34) == ep ? (uint32_t)(s >> 32) & 3u : 0u;
+            val = (uint32_t)s;
+        }
+        const uint32_t waiting = __ballot_sync(kAll, flag == 0u);
+        const uint32_t prefix = __ballot_sync(kAll, flag == 2u);
+        const int fw = waiting ? __ffs(waiting) - 1 : 32;
+        const int fp = prefix ? __ffs(prefix) - 1 : 32;
+        if (fp < fw) return excl + __reduce_add_sync(kAll, lane <= fp ? val : 0u);
+        excl += __reduce_add_sync(kAll, lane < fw ? val : 0u);
+        p -= fw;
+        if (fw == 0 && ++spins > limit) {
+            if (lane == 0) atomicOr(err, kStatusTimeout);
+            return excl;
+        }
+    }
+}
 
 // Programmatic dependent launch of the step's kernels: a kernel launched
 // with it may be scheduled while the previous kernel of its stream drains,

@@ -1082,8 +1082,10 @@ __global__ void __launch_bounds__(128) k_row_csum(const Dev d, const uint32_t* _
 // row, mode 1 writes them at the row's offset (uint2: first particle, end).
 constexpr int kUnitChunk = 16;
 
-// The walk of row r: its units (mode 1 writes them from units[out]).
-template <int MODE>
+// The walk of row r: its units (mode 1 writes them from units[out]).  With
+// SCS the row's staged-candidate sums are read from `csum` itself (the
+// caller's shared-memory copy, indexes 0..ncx) instead of the global array.
+template <int MODE, bool SCS = false>
 __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __restrict__ off,
                                               const uint32_t* __restrict__ csum, uint32_t r,
                                               uint32_t out,
@@ -1092,7 +1094,7 @@ __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __re
     const int ncx = I.ncx;
     const uint32_t lr = r - I.row_base;
     const uint32_t* o = off + I.cell_base + (size_t)lr * (uint32_t)ncx;
-    const uint32_t* cs = csum + I.cell_base + (size_t)lr * (uint32_t)ncx + r;
+    const uint32_t* cs = SCS ? csum : csum + I.cell_base + (size_t)lr * (uint32_t)ncx + r;
     uint32_t n = 0;
     uint32_t start = 0xffffffffu;
     uint32_t base = 0;   // cs[first - 1] of the open unit (clamped at 0)
@@ -1110,7 +1112,8 @@ __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __re
 #pragma unroll
         for (int k = 0; k < kUnitChunk + 3; ++k) {
             const int xi = x0 - 1 + k;
-            cc[k] = __ldg(cs + (xi < 0 ? 0 : (xi < ncx ? xi : ncx)));
+            const int xc = xi < 0 ? 0 : (xi < ncx ? xi : ncx);
+            cc[k] = SCS ? cs[xc] : __ldg(cs + xc);
         }
 #pragma unroll
         for (int k = 0; k < kUnitChunk; ++k) {
@@ -1158,6 +1161,81 @@ __global__ void __launch_bounds__(128) k_units(const Dev d, const uint32_t* __re
     if (r >= d.nrows) return;
     const uint32_t n = unit_walk<MODE>(d, off, csum, r, MODE ? uoff[r] : 0u, units);
     if (!MODE) ucnt[r] = n;
+}
+
+// The unit list of a grid of few rows in one launch (d.nrows <= kFusedRows,
+// rows of at most kFusedNcx cells): one warp per row, rows taken in launch
+// order from a ticket.  The warp sums the row's 9 neighbour-row offsets into
+// shared memory (k_row_csum's sums), lane 0 counts the row's units, a
+// decoupled look-back over the rows before it (tile_lookback, one word per
+// row holding its unit count) gives the row's first unit, and lane 0 writes
+// the units.  The warp of the last row writes the total and rearms the
+// ticket and the epoch: its look-back ended on a prefix, so every row has
+// taken its ticket and read the epoch by then.  A look-back that gave up
+// leaves a partial prefix, never above the true one, so every write stays
+// inside the unit array.
+constexpr uint32_t kFusedRows = 8192;
+constexpr int kFusedNcx = 1023;
+constexpr int kFusedWarps = 4;
+constexpr uint32_t kRowSpinLimit = 1u << 20;   // polls of a row's look-back
+
+// Self-test of the failure path: one warp runs the look-back of row 1
+// against a row 0 whose word stays zero (never published), so the wait gives
+// up after `limit` polls.
+__global__ void k_row_lookback_selftest(const unsigned long long* zeroed, uint32_t limit,
+                                        uint32_t* err) {
+    tile_lookback(zeroed, 1u, 1u, limit, err);
+}
+
+__global__ void __launch_bounds__(kFusedWarps * 32) k_units_fused(const Dev d,
+                                                                   const uint32_t* __restrict__ off,
+                                                                   const UnitsFusedArgs a) {
+    pdl_wait();
+    __shared__ uint32_t s_cs[kFusedWarps][kFusedNcx + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x * kFusedWarps + w >= d.nrows) return;   // exactly nrows tickets
+    uint32_t r = 0, ep = 0;
+    if (lane == 0) {
+        r = atomicAdd(a.ctl, 1u);
+        ep = *reinterpret_cast<volatile uint32_t*>(a.ctl + 1) & 0x3fffffffu;
+    }
+    r = __shfl_sync(kFull, r, 0);
+    ep = __shfl_sync(kFull, ep, 0);
+    const Inst& I = d.inst[find_instance(d.row_base, d.n_inst, r)];
+    const int ncx = I.ncx;
+    const uint32_t lr = r - I.row_base;
+    const int cy = (int)(lr % (uint32_t)I.ncy), cz = (int)(lr / (uint32_t)I.ncy);
+    uint32_t* cs = s_cs[w];
+    for (int x = lane; x <= ncx; x += 32) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int yy = cy + k % 3 - 1, zz = cz + k / 3 - 1;
+            if (yy >= 0 && yy < I.ncy && zz >= 0 && zz < I.ncz)
+                t += __ldg(off + I.cell_base +
+                           ((size_t)zz * (uint32_t)I.ncy + (uint32_t)yy) * (uint32_t)ncx + x);
+        }
+        cs[x] = t;
+    }
+    __syncwarp();
+    uint32_t n = 0;
+    if (lane == 0) n = unit_walk<0, true>(d, off, cs, r, 0u, nullptr);
+    n = __shfl_sync(kFull, n, 0);
+    const unsigned long long tag = (unsigned long long)ep << 34;
+    uint32_t excl = 0;
+    if (r > 0) {
+        if (lane == 0) st_relaxed64(a.words + r, tag | (1ull << 32) | n);
+        excl = tile_lookback(a.words, r, ep, kRowSpinLimit, a.err);
+    }
+    if (lane == 0) {
+        st_relaxed64(a.words + r, tag | (2ull << 32) | (excl + n));
+        unit_walk<1, true>(d, off, cs, r, excl, a.units);
+        if (r == d.nrows - 1) {
+            *a.total = excl + n;
+            a.ctl[0] = 0u;
+            a.ctl[1] = ep + 1u;
+        }
+    }
 }
 
 // Symplectic predictor (half step) for sorted particle k, then its new
@@ -1670,8 +1748,27 @@ void launch_interact(const Dev& d, const InteractArgs& a, bool counts, cudaStrea
                st, d, a);
 }
 
+void launch_row_lookback_selftest(unsigned long long* zeroed, uint32_t limit, uint32_t* err,
+                                  cudaStream_t st) {
+    cudaMemsetAsync(zeroed, 0, sizeof(unsigned long long), st);
+    k_row_lookback_selftest<<<1, 32, 0, st>>>(zeroed, limit, err);
+}
+
+bool units_fit_one_launch(uint32_t nrows, int max_ncx) {
+    return nrows <= kFusedRows && max_ncx <= kFusedNcx;
+}
+
+bool units_fused(const Dev& d) { return d.units_fused != 0; }
+
 void launch_units(const Dev& d, const uint32_t* off, uint32_t* csum, uint32_t* ucnt,
-                  uint32_t* ubsum, uint32_t* uoff, uint2* units, cudaStream_t st) {
+                  uint32_t* ubsum, uint32_t* uoff, uint2* units, unsigned long long* urow,
+                  uint32_t* uctl, uint32_t* err, cudaStream_t st) {
+    if (units_fused(d)) {
+        const UnitsFusedArgs a = {units, uoff + d.nrows, urow, uctl, err};
+        launch_pdl(k_units_fused, (d.nrows + kFusedWarps - 1) / kFusedWarps, kFusedWarps * 32, 0,
+                   st, d, off, a);
+        return;
+    }
     launch_pdl(k_row_csum, d.nrows, 128, 0, st, d, off, csum);
     launch_pdl(k_units<0>, blocks_for(d.nrows, 128), 128, 0, st, d, off, csum, ucnt, uoff, units);
     launch_scan(ucnt, d.nrows, ubsum, uoff, st);

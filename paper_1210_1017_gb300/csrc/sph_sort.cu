@@ -315,7 +315,80 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
     }
 }
 
+// The same scan in one launch: tiles of kScanChunk entries taken in launch
+// order from a ticket (ctl[0]), each publishing its total, finding the sum
+// of the tiles before it by a decoupled look-back (tile_lookback, epoch in
+// ctl[1]) and publishing its inclusive prefix.  The block of the last tile
+// rearms the ticket and the epoch: its look-back ended on a prefix, so every
+// tile has taken its ticket and read the epoch by then.
+constexpr uint32_t kScanSpinLimit = 1u << 20;   // polls of a tile's look-back
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(uint32_t* __restrict__ in,
+                                                               uint64_t m,
+                                                               uint32_t* __restrict__ out,
+                                                               int zero_in,
+                                                               unsigned long long* words,
+                                                               uint32_t* ctl, uint32_t* err) {
+    pdl_wait();
+    __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_tile, s_ep, s_tot, s_excl;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(ctl, 1u);
+        s_ep = *reinterpret_cast<volatile uint32_t*>(ctl + 1) & 0x3fffffffu;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile, ep = s_ep;
+    const uint64_t t0 = (uint64_t)tile * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint64_t i = t0 + r;
+        v[r] = i < m ? in[i] : 0u;
+        tot += v[r];
+    }
+    const uint32_t ex = block_excl_scan_256(tot, s_w);
+    if (threadIdx.x == kScanThreads - 1) s_tot = ex + tot;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t btot = s_tot;
+        const unsigned long long tag = (unsigned long long)ep << 34;
+        uint32_t excl = 0;
+        if (tile > 0) {
+            if (threadIdx.x == 0) st_relaxed64(words + tile, tag | (1ull << 32) | btot);
+            excl = tile_lookback(words, tile, ep, kScanSpinLimit, err);
+        }
+        if (threadIdx.x == 0) {
+            st_relaxed64(words + tile, tag | (2ull << 32) | (excl + btot));
+            s_excl = excl;
+            if ((uint64_t)tile == m / kScanChunk) {   // the tile that holds index m
+                ctl[0] = 0u;
+                ctl[1] = ep + 1u;
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t run = s_excl + ex;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint64_t i = t0 + r;
+        if (i < m) {
+            out[i] = run;
+            if (zero_in) in[i] = 0u;
+        }
+        if (i == m) out[m] = run;
+        run += v[r];
+    }
+}
+
 }  // namespace
+
+void launch_scan_onepass(uint32_t* in, uint64_t m, uint32_t* out, bool zero_in,
+                         unsigned long long* words, uint32_t* ctl, uint32_t* err,
+                         cudaStream_t st) {
+    launch_pdl(k_scan_onepass, scan_bsum_count(m), kScanThreads, 0, st, in, m, out,
+               zero_in ? 1 : 0, words, ctl, err);
+}
 
 uint32_t scan_bsum_count(uint64_t m) {
     // m + 1 outputs: the block that holds index m writes the total
@@ -337,9 +410,9 @@ void launch_scan(uint32_t* in, uint64_t m, uint32_t* bsum, uint32_t* out, cudaSt
 
 // The per-cell counts (incl. the excluded bin) stay in cnt: the scatter of
 // the cell sort counts them back down to zero.
-void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* bsum, uint32_t* off,
-                       cudaStream_t st) {
-    launch_scan(cnt, (uint64_t)d.ncells + 1, bsum, off, st, false);
+void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* off, unsigned long long* words,
+                       uint32_t* ctl, uint32_t* err, cudaStream_t st) {
+    launch_scan_onepass(cnt, (uint64_t)d.ncells + 1, off, false, words, ctl, err, st);
 }
 
 // Sec. 3.1 cell sort as one counting-sort pass (a radix sort whose single

@@ -23,6 +23,7 @@ SPH_OK = 0
 SPH_INTERACT_COUNTS = 1
 SPH_ARRAY_KEY, SPH_ARRAY_CELL_OFF, SPH_ARRAY_ACE, SPH_ARRAY_NNB = 0, 1, 2, 3
 SPH_ARRAY_NNB64, SPH_ARRAY_POSC, SPH_ARRAY_DT, SPH_ARRAY_PREV = 4, 5, 6, 7
+SPH_ARRAY_UNITS = 8
 SPH_SCHEME_CUBIC, SPH_SCHEME_VERLET = 1, 2
 SPH_SUBDOMAIN_EDGE, SPH_SUBDOMAIN_MIGRATE = 0, 1
 ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
@@ -41,7 +42,8 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_subdomain_select", "sph_clear_status", "sph_selftest_timeout",
             "sph_set_instance_state", "sph_front", "sph_radix_sort_status",
             "sph_radix_sort_selftest_timeout", "sph_radix_sort_static_status",
-            "sph_radix_sort_static_selftest_timeout", "sph_fma_probe", "sph_pdl_enabled"]
+            "sph_radix_sort_static_selftest_timeout", "sph_fma_probe", "sph_pdl_enabled",
+            "sph_units_selftest_timeout"]
 
 
 class SphParams(C.Structure):
@@ -134,6 +136,7 @@ def lib(build: bool = False):
     L.sph_check.argtypes = [vp]
     L.sph_clear_status.argtypes = [vp]
     L.sph_selftest_timeout.argtypes = [vp, u32]
+    L.sph_units_selftest_timeout.argtypes = [vp, u32]
     L.sph_kernels_per_step.argtypes = [vp]
     L.sph_kernels_per_step.restype = u32
     L.sph_last_error.argtypes = [vp]
@@ -463,6 +466,10 @@ def sph_selftest_timeout(ctx, polls: int):
     _check(lib().sph_selftest_timeout(ctx, polls), ctx, "sph_selftest_timeout")
 
 
+def sph_units_selftest_timeout(ctx, polls: int):
+    _check(lib().sph_units_selftest_timeout(ctx, polls), ctx, "sph_units_selftest_timeout")
+
+
 def sph_kernels_per_step(ctx) -> int:
     return int(lib().sph_kernels_per_step(ctx))
 
@@ -710,6 +717,14 @@ class Simulation:
                   SPH_ARRAY_PREV: ((n, 4), np.float32)}
         shape, dt = shapes[which]
         return sph_read_array(self.ctx, which, np.empty(shape, dt))
+
+    def units(self):
+        """The interaction's work units, uint32 (m, 2): first sorted index and
+        end of each (SPH_ARRAY_UNITS)."""
+        nbytes = int(lib().sph_array_bytes(self.ctx, SPH_ARRAY_UNITS))
+        buf = sph_read_array(self.ctx, SPH_ARRAY_UNITS, np.empty(nbytes // 4, np.uint32))
+        m = int(buf[0])
+        return buf[1:1 + 2 * m].reshape(m, 2).copy()
 
     def diagnostics(self):
         return sph_diagnostics(self.ctx)

@@ -129,6 +129,7 @@ def test_entry_points_refuse_a_null_context(lib):
     assert lib.sph_verlet(None) == -1
     assert lib.sph_subdomain_select(None, 0, 0.0, 1.0, counts, 0, None, None, None, None) == -1
     assert lib.sph_selftest_timeout(None, 10) == -1
+    assert lib.sph_units_selftest_timeout(None, 10) == -1
     assert lib.sph_clear_status(None) == -1
     t = (C.c_double * 1)(0.0)
     assert lib.sph_set_instance_state(None, t, None) == -1

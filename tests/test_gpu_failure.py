@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a fault: a bounded device wait (the
-radix sort's decoupled look-back) runs against a predecessor that never
-publishes, gives up after a short poll limit, and reports SPH_ERR_TIMEOUT
-through the context's status word; the context then keeps working."""
+radix sort's decoupled look-back, or the unit list's look-back over rows)
+runs against a predecessor that never publishes, gives up after a short poll
+limit, and reports SPH_ERR_TIMEOUT through the context's status word; the
+context then keeps working."""
 import numpy as np
 import pytest
 
@@ -49,6 +50,39 @@ def test_bounded_wait_gives_up_reports_timeout_and_the_context_recovers():
     ref.close()
     for key in ("ids", "pos", "vel", "rho"):
         assert np.array_equal(got[key], want[key])
+
+
+def test_row_lookback_gives_up_reports_timeout_and_the_context_recovers():
+    """The same for the one-launch unit list's bounded look-back over rows."""
+    case = cases.c1_dam_break()
+    sim = S.Simulation.from_case(case)
+    sim.step(3)
+    before = sim.download()
+    units = sim.units()
+    sim.check()
+    S.sph_units_selftest_timeout(sim.ctx, 1000)
+    with pytest.raises(S.SphError, match="SPH_ERR_TIMEOUT"):
+        sim.check()
+    after = sim.download()
+    for key in ("ids", "pos", "vel", "rho"):
+        assert np.array_equal(before[key], after[key])
+    assert np.array_equal(units, sim.units())
+    sim.clear_status()
+    sim.step(3)
+    sim.check()
+    got = sim.download()
+    sim.close()
+    ref = S.Simulation.from_case(case)
+    ref.step(6)
+    want = ref.download()
+    ref.close()
+    for key in ("ids", "pos", "vel", "rho"):
+        assert np.array_equal(got[key], want[key])
+    for polls in (0, (1 << 20) + 1):
+        s2 = S.Simulation.from_case(cases.random_block(200, seed=4))
+        with pytest.raises(S.SphError, match="SPH_ERR_INVALID_ARG"):
+            S.sph_units_selftest_timeout(s2.ctx, polls)
+        s2.close()
 
 
 def test_selftest_rejects_an_unbounded_poll_count():
