@@ -228,7 +228,9 @@ size_t carve(sph_ctx* c, void* base, uint32_t n, const Table& t, int passes) {
     c->units_cap = max_units(n, (uint32_t)t.nrows, t.ncells);
     c->units = cv.take<uint2>(c->units_cap);
     c->part_u = cv.take<uint4>(kMaxGridBlocks);
-    c->done = cv.take<uint32_t>(1);   // ticket of the interaction's last block
+    // ticket of the interaction's last block, then the unit counter and
+    // finish ticket of the counter-scheduled interaction variants
+    c->done = cv.take<uint32_t>(4);
     c->status = cv.take<uint32_t>(1);
     c->id_flag = cv.take<uint32_t>(1);
     c->diag_out = cv.take<double>(8);
@@ -372,6 +374,7 @@ void enqueue_interact(sph_ctx* c, bool counts, bool set_dt) {
     ia.part_u = c->part_u;
     // the Sec. 3.3 reductions run in the interaction's last block
     ia.ticket = c->done;
+    ia.sched = c->done + 1;
     ia.red.part_u = c->part_u;
     ia.red.nparts = c->nparts;
     ia.red.counters = c->counters;
@@ -516,7 +519,7 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
     cudaMemsetAsync(c->i_vphase, 0, n_inst * sizeof(uint32_t), st);
     cudaMemsetAsync(c->cnt, 0, (c->ncells + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(c->hist, 0, 4 * 256 * sizeof(uint32_t), st);
-    cudaMemsetAsync(c->done, 0, sizeof(uint32_t), st);
+    cudaMemsetAsync(c->done, 0, 4 * sizeof(uint32_t), st);
     cudaMemsetAsync(c->status, 0, sizeof(uint32_t), st);
     cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned long long), st);
     cudaMemsetAsync(c->urow, 0, (size_t)c->tab.nrows * sizeof(unsigned long long), st);
@@ -1058,6 +1061,7 @@ int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* bes
         ia.nnb = c->nnb;
         ia.part_u = c->part_u;
         ia.ticket = nullptr;   // timing only: no counters, no step size
+        ia.sched = c->done + 1;
         launch_interact(c->d, ia, false, c->st);   // warm
         cudaEventRecord(e0, c->st);
         for (uint32_t r = 0; r < reps; ++r) launch_interact(c->d, ia, false, c->st);

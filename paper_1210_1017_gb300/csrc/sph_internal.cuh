@@ -154,7 +154,7 @@ void launch_reorder(const Dev& d, const ReorderArgs& a, cudaStream_t st);
 // size is the block size of the interaction variant in use.
 constexpr int kSpan = 32;
 constexpr int kMinUnit = 32;
-constexpr int kNumVariants = 13;
+constexpr int kNumVariants = 16;
 
 struct ReduceArgs {
     const uint4* part_u;
@@ -181,6 +181,8 @@ struct InteractArgs {
                           // status bits, boundary-i pairs
     uint32_t* ticket;     // non-null: the last block runs the Sec. 3.3 reductions
                           // (zero on entry, left at zero)
+    uint32_t* sched;      // unit counter and finish ticket of the variants that
+                          // take units from a counter (zero on entry, left at zero)
     ReduceArgs red;
     int set_dt;
 };

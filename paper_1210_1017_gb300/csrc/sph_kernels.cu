@@ -526,7 +526,7 @@ __device__ __forceinline__ void pair_terms2(const Dev& d, float c0, const float4
 // are added in a fixed order at the end.  More warps per block at the same
 // staging footprint.
 template <int W, int STAGE, int WCAP, int MINB, bool COUNTS, int SPLIT, int KERN, bool PK,
-          bool TU>
+          bool TU, bool DYN>
 __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, const InteractArgs a) {
     pdl_wait();
     constexpr int NT = W * SPLIT * 32;
@@ -539,8 +539,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     uint32_t* s_desc = s_words + W * SPLIT * WCAP * 32;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_rs[9], s_len[9], s_base[10];
-    __shared__ uint32_t s_off[9][kSpan + 3];    // cell offsets of the 9 runs
-    __shared__ int s_ok[9];
+    // cell offsets of the 9 runs (DYN: two buffers, the next unit's filled
+    // by asynchronous copies while this one is worked on)
+    __shared__ uint32_t s_offb[DYN ? 2 : 1][9][kSpan + 3];
+    __shared__ int s_okb[DYN ? 2 : 1][9];
+    __shared__ uint32_t s_nui[2];                // DYN: next unit, by parity of k
     __shared__ int s_mode;
     __shared__ uint32_t s_ru[W * SPLIT][4];
     __shared__ float s_comb[SPLIT > 1 ? (SPLIT - 1) * W * 32 : 1][8];   // parts 1.. sums
@@ -551,12 +554,45 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     const uint32_t nunits = *a.n_units;
     uint32_t phase = 0;
     uint32_t t_np = 0, t_nb = 0, t_nc = 0, t_bad = 0;   // counters over this block's units
-    for (uint32_t ui = blockIdx.x; ui < nunits; ui += gridDim.x) {
-    const uint2 unit = a.units[ui];
+    // DYN: units are taken from a counter (the first one is blockIdx.x), and
+    // the next unit's record, end labels and cell offsets are fetched while
+    // this one is worked on.  pf: the next unit's record is in nx_*; pf_off:
+    // its offsets are in buffer sb ^ 1.  Every value is block-uniform.
+    uint32_t k_unit = 0;
+    bool pf = false, pf_off = false;
+    int sb = 0;
+    uint2 nx_unit = make_uint2(0u, 0u);
+    uint32_t nx_k0 = 0u, nx_kl = 0u;
+    for (uint32_t ui = blockIdx.x; ui < nunits;) {
+    uint32_t (*s_off)[kSpan + 3] = s_offb[DYN ? sb : 0];
+    int* s_ok = s_okb[DYN ? sb : 0];
+    if (DYN && tid == 0) s_nui[k_unit & 1u] = gridDim.x + atomicAdd(a.sched, 1u);
+    uint2 unit;
+    uint32_t key0, keyl = 0u;
+    if (DYN && pf) {
+        unit = nx_unit;
+        key0 = nx_k0;
+        keyl = nx_kl;
+    } else {
+        unit = a.units[ui];
+        key0 = __ldg(a.key + unit.x);
+        if (DYN) keyl = __ldg(a.key + unit.y - 1);
+    }
+    const bool have_off = DYN && pf_off;
+    pf = false;
+    pf_off = false;
     const uint32_t i0 = unit.x, i1 = unit.y;
-    const uint32_t key0 = __ldg(a.key + i0);
     const uint32_t q = find_instance(d.cell_base, d.n_inst, key0);
-    if (__ldg(d.is.done + q)) continue;             // block-uniform
+    if (__ldg(d.is.done + q)) {                      // block-uniform
+        if (DYN) {
+            __syncthreads();                         // s_nui written
+            ui = s_nui[k_unit & 1u];
+            ++k_unit;
+        } else {
+            ui += gridDim.x;
+        }
+        continue;
+    }
     const Inst& I = d.inst[q];
     const int ncx = I.ncx, ncy = I.ncy, ncz = I.ncz;
     const float c0 = I.c0;
@@ -565,22 +601,24 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     const uint32_t rowbase = I.cell_base + lrow * (uint32_t)ncx;   // global label of (0, cy, cz)
     const int cy = (int)(lrow % (uint32_t)ncy), cz = (int)(lrow / (uint32_t)ncy);
     const int xb = (int)(key0 - rowbase);
-    const int xe = (int)(__ldg(a.key + i1 - 1) - rowbase);
+    const int xe = (int)((DYN ? keyl : __ldg(a.key + i1 - 1)) - rowbase);
     const int ulo = xb > 0 ? xb - 1 : 0;
     const int uhi = xe + 1 < ncx ? xe + 1 : ncx - 1;
     const int nce = uhi - ulo + 2;                 // offsets per neighbour row
-    // cell offsets of the 9 neighbour rows (each thread derives its row's
-    // base label itself: no barrier before the loads)
-    for (int r9 = tid; r9 < 9 * nce; r9 += NT) {
-        const int r = r9 / nce, c = r9 - r * nce;
-        const int yy = cy + r % 3 - 1, zz = cz + r / 3 - 1;
-        const bool ok = yy >= 0 && yy < ncy && zz >= 0 && zz < ncz;
-        const uint32_t rb =
-            I.cell_base + (uint32_t)ncx * ((uint32_t)yy + (uint32_t)ncy * (uint32_t)zz);
-        s_off[r][c] = ok ? __ldg(a.off + rb + ulo + c) : 0u;
-        if (c == 0) s_ok[r] = ok;
+    if (!have_off) {
+        // cell offsets of the 9 neighbour rows (each thread derives its
+        // row's base label itself: no barrier before the loads)
+        for (int r9 = tid; r9 < 9 * nce; r9 += NT) {
+            const int r = r9 / nce, c = r9 - r * nce;
+            const int yy = cy + r % 3 - 1, zz = cz + r / 3 - 1;
+            const bool ok = yy >= 0 && yy < ncy && zz >= 0 && zz < ncz;
+            const uint32_t rb =
+                I.cell_base + (uint32_t)ncx * ((uint32_t)yy + (uint32_t)ncy * (uint32_t)zz);
+            s_off[r][c] = ok ? __ldg(a.off + rb + ulo + c) : 0u;
+            if (c == 0) s_ok[r] = ok;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // staging plan and copies by the first warp: lane r < 9 owns run r
     if (w == 0) {
         const uint32_t len = lane < 9 ? s_off[lane][nce - 1] - s_off[lane][0] : 0u;
@@ -637,6 +675,13 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     uint32_t ncand = 0;
     __syncthreads();
     const bool staged = s_mode != 0;
+    // DYN: the next unit (taken by thread 0 at the top of this one) and its
+    // record; its end labels follow once the record has landed
+    uint32_t nui = 0u;
+    if (DYN) {
+        nui = s_nui[k_unit & 1u];
+        if (nui < nunits) nx_unit = a.units[nui];
+    }
     if (staged) {
         const bool got = mbar_wait_bounded(&s_bar, phase);
         if (__syncthreads_or(!got) != 0) {
@@ -645,6 +690,11 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
             break;
         }
         phase ^= 1u;
+        if (DYN && nui < nunits) {
+            nx_k0 = __ldg(a.key + nx_unit.x);
+            nx_kl = __ldg(a.key + nx_unit.y - 1);
+            pf = true;
+        }
         // one pass over candidate pairs: shift the staged y, z into the
         // frame of this unit's row (the run r of a candidate gives the
         // offsets), then keep half-precision copies in cell units (cell =
@@ -686,6 +736,40 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                                 *reinterpret_cast<const uint32_t*>(&hk));
         }
         __syncthreads();
+        if (DYN && pf) {
+            // the next unit's cell offsets into the other buffer (asynchronous
+            // 4-byte copies, waited for before this unit's last barrier)
+            const uint32_t nq = find_instance(d.cell_base, d.n_inst, nx_k0);
+            const Inst& J = d.inst[nq];
+            const int jcx = J.ncx, jcy = J.ncy, jcz = J.ncz;
+            const uint32_t jrow = (nx_k0 - J.cell_base) / (uint32_t)jcx;
+            const uint32_t jbase = J.cell_base + jrow * (uint32_t)jcx;
+            const int jy = (int)(jrow % (uint32_t)jcy), jz = (int)(jrow / (uint32_t)jcy);
+            const int jxb = (int)(nx_k0 - jbase), jxe = (int)(nx_kl - jbase);
+            const int jlo = jxb > 0 ? jxb - 1 : 0;
+            const int jhi = jxe + 1 < jcx ? jxe + 1 : jcx - 1;
+            const int jnce = jhi - jlo + 2;
+            uint32_t (*o2)[kSpan + 3] = s_offb[sb ^ 1];
+            int* ok2 = s_okb[sb ^ 1];
+            for (int r9 = tid; r9 < 9 * jnce; r9 += NT) {
+                const int r = r9 / jnce, c = r9 - r * jnce;
+                const int yy = jy + r % 3 - 1, zz = jz + r / 3 - 1;
+                const bool ok = yy >= 0 && yy < jcy && zz >= 0 && zz < jcz;
+                if (ok) {
+                    const uint32_t rb =
+                        J.cell_base + (uint32_t)jcx * ((uint32_t)yy + (uint32_t)jcy * (uint32_t)zz);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                     smem_u32(&o2[r][c])),
+                                 "l"(a.off + rb + jlo + c)
+                                 : "memory");
+                } else {
+                    o2[r][c] = 0u;
+                }
+                if (c == 0) ok2[r] = ok;
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            pf_off = true;
+        }
     }
 
     const uint32_t act = __ballot_sync(kFull, valid);
@@ -1000,7 +1084,24 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     t_np += fluid ? npairs : 0u;
     t_nb += fluid ? 0u : npairs;
     t_nc += owner ? ncand : 0u;
+    if (DYN && pf_off) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();   // the next unit overwrites the shared staging
+    if (DYN) {
+        ui = nui;
+        ++k_unit;
+        if (pf_off) sb ^= 1;
+    } else {
+        ui += gridDim.x;
+    }
+    }
+    if (DYN) {
+        // the last block to finish rearms the unit counter for the next launch
+        // (every block's last take precedes its finish ticket)
+        __threadfence();
+        if (tid == 0 && atomicAdd(a.sched + 1, 1u) == gridDim.x - 1u) {
+            a.sched[0] = 0u;
+            a.sched[1] = 0u;
+        }
     }
 
     uint32_t np = t_np, nb = t_nb, nc = t_nc, bad = t_bad;
@@ -1616,15 +1717,17 @@ struct Variant {
 
 // (warps, staged candidates, hit-mask words per lane, resident blocks per SM
 // that the shared memory allows -- also the register budget hint)
-#define SPH_VARIANT_T(Wv, Sv, Cv, Bv, Pv, PKv, TUv)                                   \
+#define SPH_VARIANT_D(Wv, Sv, Cv, Bv, Pv, PKv, TUv, Dv)                               \
     Variant {                                                                        \
         Wv, Pv, Sv,                                                                  \
-            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0, PKv, TUv>,                    \
-              k_interact<Wv, Sv, Cv, Bv, true, Pv, 0, PKv, TUv>},                    \
-             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1, PKv, TUv>,                    \
-              k_interact<Wv, Sv, Cv, Bv, true, Pv, 1, PKv, TUv>}},                   \
+            {{k_interact<Wv, Sv, Cv, Bv, false, Pv, 0, PKv, TUv, Dv>,                \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 0, PKv, TUv, Dv>},                \
+             {k_interact<Wv, Sv, Cv, Bv, false, Pv, 1, PKv, TUv, Dv>,                \
+              k_interact<Wv, Sv, Cv, Bv, true, Pv, 1, PKv, TUv, Dv>}},               \
             Shape<Wv * Pv, Sv, Cv>::smem, 0                                          \
     }
+#define SPH_VARIANT_T(Wv, Sv, Cv, Bv, Pv, PKv, TUv) \
+    SPH_VARIANT_D(Wv, Sv, Cv, Bv, Pv, PKv, TUv, false)
 #define SPH_VARIANT(Wv, Sv, Cv, Bv, Pv, PKv) SPH_VARIANT_T(Wv, Sv, Cv, Bv, Pv, PKv, false)
 
 Variant g_variants[kNumVariants] = {
@@ -1645,6 +1748,11 @@ Variant g_variants[kNumVariants] = {
     // 32-particle units shared by four warps, four blocks per SM: shorter
     // dependent chains per unit for small systems (fewer units than SMs)
     SPH_VARIANT_T(1, 1024, 12, 4, 4, true, true),
+    // units taken from a counter, the next unit's record and cell offsets
+    // fetched during the current one
+    SPH_VARIANT_D(4, 2048, 24, 2, 2, true, true, true),
+    SPH_VARIANT_D(3, 1408, 16, 3, 2, true, true, true),
+    SPH_VARIANT_D(1, 1024, 12, 4, 4, true, true, true),
 };
 
 }  // namespace

@@ -17,7 +17,7 @@ from . import _build
 
 # Revision tag of the interaction kernel; DRAM-traffic figures captured with
 # ncu are only quoted while they were taken on this revision.
-KERNEL_REV = "interact-v4.13"
+KERNEL_REV = "interact-v4.14"
 
 SPH_OK = 0
 SPH_INTERACT_COUNTS = 1

@@ -397,3 +397,28 @@ def test_device_step_loop_equals_single_step_graphs():
         assert np.array_equal(a.download()[key], b.download()[key])
     a.close()
     b.close()
+
+
+def test_counter_scheduled_variants_equal_their_static_shapes():
+    """The variants that take work units from a counter (and fetch the next
+    unit's record and offsets during the current one) compute every unit as
+    the round-robin variant of the same block shape does, so their rates are
+    bit-identical.  Three launches in a row check that the last block rearms
+    the counter (a stale counter would skip units)."""
+    case = cases.c2_dam_break_obstacles(dp=0.012)     # ~330k particles: many units per block
+    sim = S.Simulation.from_case(case)
+    sim.step(20)
+    nv = S.sph_num_variants()
+    pairs = [(10, 13), (11, 14), (12, 15)]
+    assert nv == 16
+    for vs, vd in pairs:
+        sim.set_variant(vs)
+        sim.interact()
+        ref = sim.read(S.SPH_ARRAY_ACE).copy()
+        sim.set_variant(vd)
+        for _ in range(3):
+            sim.interact()
+            sim.check()
+            got = sim.read(S.SPH_ARRAY_ACE)
+            assert np.array_equal(got, ref), (vs, vd)
+    sim.close()
