@@ -252,6 +252,23 @@ def run_reference(args):
     return 0
 
 
+def pinned_copy_gbs(torch, host, stream):
+    """GB/s of one torch copy of a pinned host tensor to the device (best of
+    3, CUDA events on `stream`): the host link the e2e transfers share."""
+    dev = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            dev.copy_(host, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        best = max(best, host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e6))
+    del dev
+    return best
+
+
 def run_ours(args):
     import torch
 
@@ -367,9 +384,12 @@ def run_ours(args):
     S.sph_step(sim.ctx, 1)
     S.sph_download(sim.ctx, out["pos"], out["vel"], out["rho"], out["ids"])
     de0 = sim.diagnostics()
+    # the link itself: one plain copy of the pinned positions (torch, events)
+    link = pinned_copy_gbs(torch, pin["pos"], stream)
     barrier()
     t0 = time.perf_counter()
     parts = np.zeros(3)
+    each = []
     for _ in range(e2e_steps):
         ta = time.perf_counter()
         S.sph_upload(sim.ctx, pin["pos"], pin["vel"], pin["rho"], pin["ids"])
@@ -378,7 +398,9 @@ def run_ours(args):
         sim.synchronize()
         tc = time.perf_counter()
         S.sph_download(sim.ctx, out["pos"], out["vel"], out["rho"], out["ids"])
-        parts += (tb - ta, tc - tb, time.perf_counter() - tc)
+        td = time.perf_counter()
+        parts += (tb - ta, tc - tb, td - tc)
+        each.append([round((tb - ta) * 1e3, 3), round((tc - tb) * 1e3, 3), round((td - tc) * 1e3, 3)])
     t_e2e = time.perf_counter() - t0
     de1 = sim.diagnostics()
     barrier()
@@ -388,6 +410,8 @@ def run_ours(args):
            "d2h_bytes_per_step": bytes_h2d, "steps": e2e_steps,
            "ms_per_step": round(t_e2e / e2e_steps * 1e3, 3),
            "ms_upload_step_download": [round(v / e2e_steps * 1e3, 3) for v in parts],
+           "ms_each_step": each,
+           "pinned_copy_h2d_gbs": round(link, 1),
            "note": "per step: sph_upload (pinned host) + sph_step(1) + sph_download (pinned host)"}
 
     sub = subdomain_timing(sim, case, args.subdomains, S, torch) if args.subdomains else None
