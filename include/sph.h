@@ -278,6 +278,48 @@ int sph_download(sph_ctx *ctx, double *pos, float *vel, float *rho,
  * n (SPH_ERR_STATE otherwise).  Sync. */
 int sph_download_by_id(sph_ctx *ctx, double *pos, float *vel, float *rho);
 
+/* Pipelined transfers.  Sec. 3 keeps the whole simulation on the GPU and
+ * copies to the host only when saving; these calls let those copies (and
+ * the uploads of new states) run on copy engines while the GPU keeps
+ * stepping, instead of stalling the caller and the stream.
+ *
+ * sph_async_transfer_bytes: bytes of the device buffer the calls need: three
+ * staging slots of 44 B per particle (two for uploads, one for downloads),
+ * each rounded to 256 bytes.
+ * sph_enable_async_transfers: attach that caller-owned buffer (device,
+ * 256-byte aligned, at least the bytes above; SPH_ERR_WORKSPACE otherwise)
+ * and create the context's two copy streams (one per direction) and their
+ * events; they are destroyed by sph_destroy.  The library allocates no
+ * device memory for them.  Calling it again with another buffer first waits
+ * for every transfer.  Sync. */
+uint64_t sph_async_transfer_bytes(const sph_ctx *ctx);
+int sph_enable_async_transfers(sph_ctx *ctx, void *d_buf, uint64_t bytes);
+
+/* As sph_upload, but only enqueued: the copies of the arrays into an upload
+ * slot run on the host-to-device copy stream (after that slot's previous
+ * upload was unpacked), and the unpack that replaces the state is ordered on
+ * the context's stream after them, so the copies overlap whatever the stream
+ * is still running.  The arrays must stay unchanged until
+ * sph_sync_transfers.  The id check of sph_upload (every id below n, needed
+ * by sph_download_by_id) is read at the next sph_sync_transfers.
+ * SPH_ERR_STATE if sph_enable_async_transfers was not called.  Async. */
+int sph_upload_async(sph_ctx *ctx, const double *pos, const float *vel,
+                     const float *rho, const uint32_t *ids);
+
+/* As sph_download, but only enqueued: the state is packed into the download
+ * slot on the context's stream (after the previous download's copies left
+ * the slot), and the copies to the arrays run on the device-to-host copy
+ * stream, overlapping the work enqueued after this call.  The arrays hold
+ * the state of this point of the stream after sph_sync_transfers.  Any
+ * pointer may be NULL.  SPH_ERR_STATE without a state or without
+ * sph_enable_async_transfers.  Async. */
+int sph_download_async(sph_ctx *ctx, double *pos, float *vel, float *rho,
+                       uint32_t *ids);
+
+/* Wait for both copy streams and the context's stream, then read the id
+ * check of the last pipelined upload.  Sync. */
+int sph_sync_transfers(sph_ctx *ctx);
+
 /* Copy an internal device array to host memory for inspection.  bytes must
  * equal the array's size (see sph_array_bytes).  Sync.
  *   SPH_ARRAY_KEY      uint32[n]  cell label of each particle, sorted order

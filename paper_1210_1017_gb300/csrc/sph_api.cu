@@ -57,6 +57,22 @@ __global__ void k_unpack(uint32_t n, const double* __restrict__ pos, const float
     vr[i] = make_float4(vel[3 * (size_t)i], vel[3 * (size_t)i + 1], vel[3 * (size_t)i + 2], rho[i]);
 }
 
+// k_unpack for a pipelined upload: the ids come from the staging slot too.
+__global__ void k_unpack_ids(uint32_t n, const double* __restrict__ pos,
+                             const float* __restrict__ vel, const float* __restrict__ rho,
+                             const uint32_t* __restrict__ ids, double* x, double* y, double* z,
+                             float4* vr, uint32_t* id, uint32_t* id_flag) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = ids[i];
+    if (k >= n) atomicOr(id_flag, 1u);
+    id[i] = k;
+    x[i] = pos[3 * (size_t)i];
+    y[i] = pos[3 * (size_t)i + 1];
+    z[i] = pos[3 * (size_t)i + 2];
+    vr[i] = make_float4(vel[3 * (size_t)i], vel[3 * (size_t)i + 1], vel[3 * (size_t)i + 2], rho[i]);
+}
+
 // Scatter by id (every id < n, distinct).
 __global__ void k_pack_by_id(uint32_t n, const double* __restrict__ x, const double* __restrict__ y,
                              const double* __restrict__ z, const float4* __restrict__ vr,
@@ -77,9 +93,11 @@ __global__ void k_pack_by_id(uint32_t n, const double* __restrict__ x, const dou
 
 __global__ void k_pack(uint32_t n, const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const float4* __restrict__ vr, double* pos,
-                       float* vel, float* rho) {
+                       float* vel, float* rho, const uint32_t* __restrict__ id = nullptr,
+                       uint32_t* ids = nullptr) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (ids) ids[i] = id[i];
     pos[3 * (size_t)i] = x[i];
     pos[3 * (size_t)i + 1] = y[i];
     pos[3 * (size_t)i + 2] = z[i];
@@ -623,6 +641,7 @@ int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho
     c->pre_state = 0;
     rc = cuda_check(c, cudaStreamSynchronize(st), "upload sync");
     c->ids_dense = rc == SPH_OK && flag == 0;
+    c->ids_pending = false;
     return rc;
 }
 
@@ -822,6 +841,10 @@ int sph_download(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids)
 int sph_download_by_id(sph_ctx* c, double* pos, float* vel, float* rho) {
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
+    if (c->ids_pending) {
+        const int rc = sph_sync_transfers(c);
+        if (rc) return rc;
+    }
     if (!c->ids_dense) return fail(c, SPH_ERR_STATE, "ids are not all below n");
     const size_t n = c->n;
     cudaStream_t st = c->st;
@@ -1104,12 +1127,170 @@ uint32_t sph_kernels_per_step(const sph_ctx* c) {
 
 const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
+// --- pipelined transfers -------------------------------------------------
+
+namespace {
+
+// One staging slot: positions (3n f64), velocities (3n f32), densities (n
+// f32), ids (n u32), each sub-array 256-byte aligned.
+struct XferSlot {
+    double* pos;
+    float *vel, *rho;
+    uint32_t* ids;
+};
+
+uint64_t xfer_slot_bytes(uint32_t n) {
+    Carver cv(nullptr);
+    cv.take<double>(3 * (size_t)n);
+    cv.take<float>(3 * (size_t)n);
+    cv.take<float>(n);
+    cv.take<uint32_t>(n);
+    return (cv.used + kAlign - 1) / kAlign * kAlign;
+}
+
+XferSlot xfer_slot(sph_ctx* c, int s) {
+    Carver cv(c->xfer + (size_t)s * c->xfer_slot);
+    XferSlot x;
+    x.pos = cv.take<double>(3 * (size_t)c->n);
+    x.vel = cv.take<float>(3 * (size_t)c->n);
+    x.rho = cv.take<float>(c->n);
+    x.ids = cv.take<uint32_t>(c->n);
+    return x;
+}
+
+}  // namespace
+
+static void release_transfer_streams(sph_ctx* c) {
+    if (!c->s_h2d) return;
+    cudaStreamSynchronize(c->s_h2d);
+    cudaStreamSynchronize(c->s_d2h);
+    for (int s = 0; s < 2; ++s) {
+        cudaEventDestroy(c->ev_up_loaded[s]);
+        cudaEventDestroy(c->ev_up_free[s]);
+    }
+    cudaEventDestroy(c->ev_dn_packed);
+    cudaEventDestroy(c->ev_dn_free);
+    cudaStreamDestroy(c->s_h2d);
+    cudaStreamDestroy(c->s_d2h);
+    c->s_h2d = c->s_d2h = nullptr;
+    c->xfer = nullptr;
+}
+
+uint64_t sph_async_transfer_bytes(const sph_ctx* c) {
+    if (!c) return 0;
+    return 3 * xfer_slot_bytes(c->n);
+}
+
+int sph_enable_async_transfers(sph_ctx* c, void* d_buf, uint64_t bytes) {
+    if (!c || !d_buf) return SPH_ERR_INVALID_ARG;
+    if (((uintptr_t)d_buf % kAlign) != 0 || bytes < sph_async_transfer_bytes(c))
+        return fail(c, SPH_ERR_WORKSPACE, "transfer buffer too small or not 256-byte aligned");
+    if (c->s_h2d) {
+        // a new buffer: everything that used the old one has finished
+        int rc = sph_sync_transfers(c);
+        if (rc) return rc;
+    } else {
+        const unsigned fl = cudaEventDisableTiming;
+        bool ok = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
+        for (int s = 0; s < 2 && ok; ++s)
+            ok = cudaEventCreateWithFlags(&c->ev_up_loaded[s], fl) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_up_free[s], fl) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&c->ev_dn_packed, fl) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_dn_free, fl) == cudaSuccess;
+        if (!ok) return cuda_check(c, cudaGetLastError(), "transfer streams");
+    }
+    c->xfer = static_cast<unsigned char*>(d_buf);
+    c->xfer_slot = xfer_slot_bytes(c->n);
+    c->up_slot = 0;
+    return SPH_OK;
+}
+
+int sph_upload_async(sph_ctx* c, const double* pos, const float* vel, const float* rho,
+                     const uint32_t* ids) {
+    if (!c || !pos || !vel || !rho || !ids) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
+    if (!c->xfer) return fail(c, SPH_ERR_STATE, "pipelined transfers not enabled");
+    const size_t n = c->n;
+    const int s = c->up_slot;
+    const XferSlot u = xfer_slot(c, s);
+    cudaStream_t st = c->st, h = c->s_h2d;
+    // the slot's previous upload has been unpacked
+    cudaStreamWaitEvent(h, c->ev_up_free[s], 0);
+    int rc = cuda_check(c, cudaMemcpyAsync(u.pos, pos, 3 * n * sizeof(double), cudaMemcpyDefault, h),
+                        "upload pos");
+    if (rc) return rc;
+    cudaMemcpyAsync(u.vel, vel, 3 * n * sizeof(float), cudaMemcpyDefault, h);
+    cudaMemcpyAsync(u.rho, rho, n * sizeof(float), cudaMemcpyDefault, h);
+    cudaMemcpyAsync(u.ids, ids, n * sizeof(uint32_t), cudaMemcpyDefault, h);
+    cudaEventRecord(c->ev_up_loaded[s], h);
+    // the unpack replaces the state in stream order, after the copies
+    cudaStreamWaitEvent(st, c->ev_up_loaded[s], 0);
+    cudaMemsetAsync(c->id_flag, 0, sizeof(uint32_t), st);
+    cudaMemsetAsync(c->i_vphase, 0, c->n_inst * sizeof(uint32_t), st);
+    k_unpack_ids<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(
+        c->n, u.pos, u.vel, u.rho, u.ids, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->vr[c->cur],
+        c->id[c->cur], c->id_flag);
+    rc = post_launch(c, "upload_async");
+    if (rc) return rc;
+    cudaEventRecord(c->ev_up_free[s], st);
+    c->up_slot ^= 1;
+    c->have_state = true;
+    c->cells_valid = false;
+    c->keys_ready = false;
+    c->pre_state = 0;
+    c->ids_pending = true;
+    return cuda_check(c, cudaGetLastError(), "upload_async");
+}
+
+int sph_download_async(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
+    if (!c->xfer) return fail(c, SPH_ERR_STATE, "pipelined transfers not enabled");
+    const size_t n = c->n;
+    const XferSlot dn = xfer_slot(c, 2);
+    cudaStream_t st = c->st, h = c->s_d2h;
+    // the previous download's copies out of the slot have finished
+    cudaStreamWaitEvent(st, c->ev_dn_free, 0);
+    k_pack<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(c->n, c->x[c->cur], c->y[c->cur],
+                                                       c->z[c->cur], c->vr[c->cur], dn.pos, dn.vel,
+                                                       dn.rho, c->id[c->cur], dn.ids);
+    int rc = post_launch(c, "download_async pack");
+    if (rc) return rc;
+    cudaEventRecord(c->ev_dn_packed, st);
+    cudaStreamWaitEvent(h, c->ev_dn_packed, 0);
+    if (pos) cudaMemcpyAsync(pos, dn.pos, 3 * n * sizeof(double), cudaMemcpyDefault, h);
+    if (vel) cudaMemcpyAsync(vel, dn.vel, 3 * n * sizeof(float), cudaMemcpyDefault, h);
+    if (rho) cudaMemcpyAsync(rho, dn.rho, n * sizeof(float), cudaMemcpyDefault, h);
+    if (ids) cudaMemcpyAsync(ids, dn.ids, n * sizeof(uint32_t), cudaMemcpyDefault, h);
+    cudaEventRecord(c->ev_dn_free, h);
+    return cuda_check(c, cudaGetLastError(), "download_async");
+}
+
+int sph_sync_transfers(sph_ctx* c) {
+    if (!c) return SPH_ERR_INVALID_ARG;
+    int rc = SPH_OK;
+    if (c->s_h2d) {
+        rc = cuda_check(c, cudaStreamSynchronize(c->s_h2d), "h2d stream");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->s_d2h), "d2h stream");
+    }
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->st), "stream");
+    if (!rc && c->ids_pending) {
+        uint32_t flag = 1;
+        rc = cuda_check(c, cudaMemcpy(&flag, c->id_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost),
+                        "id check");
+        c->ids_dense = rc == SPH_OK && flag == 0;
+        c->ids_pending = false;
+    }
+    return rc;
+}
+
 void sph_destroy(sph_ctx* c) {
     if (!c) return;
     for (int g = 0; g < 2; ++g) {
         if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
         if (c->loop_graph[g]) cudaGraphExecDestroy(c->loop_graph[g]);
     }
+    release_transfer_streams(c);
     delete c;
 }
 

@@ -91,6 +91,16 @@ struct sph_ctx {
     // repeats a body of loop_body steps on the device (see sph_step)
     cudaGraphExec_t loop_graph[2] = {nullptr, nullptr};
     uint32_t* loop_ctr = nullptr;   // [0] steps done in this launch, [1] steps asked
+    // pipelined transfers (sph_enable_async_transfers): a caller-owned buffer
+    // of three staging slots (two for uploads, one for downloads), a copy
+    // stream per direction and the events that order them with c->st
+    unsigned char* xfer = nullptr;
+    uint64_t xfer_slot = 0;          // bytes per slot
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_up_loaded[2] = {nullptr, nullptr}, ev_up_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_dn_packed = nullptr, ev_dn_free = nullptr;
+    int up_slot = 0;                 // upload slot of the next sph_upload_async
+    bool ids_pending = false;        // ids_dense not yet read back after an async upload
     std::string err;
 };
 

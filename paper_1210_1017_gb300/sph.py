@@ -43,7 +43,9 @@ EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph
             "sph_set_instance_state", "sph_front", "sph_radix_sort_status",
             "sph_radix_sort_selftest_timeout", "sph_radix_sort_static_status",
             "sph_radix_sort_static_selftest_timeout", "sph_fma_probe", "sph_pdl_enabled",
-            "sph_units_selftest_timeout"]
+            "sph_units_selftest_timeout", "sph_async_transfer_bytes",
+            "sph_enable_async_transfers", "sph_upload_async", "sph_download_async",
+            "sph_sync_transfers"]
 
 
 class SphParams(C.Structure):
@@ -128,6 +130,12 @@ def lib(build: bool = False):
     L.sph_rollout.argtypes = [vp, u32, u32, SNAPSHOT_FN, vp]
     L.sph_download.argtypes = [vp, vp, vp, vp, vp]
     L.sph_download_by_id.argtypes = [vp, vp, vp, vp]
+    L.sph_async_transfer_bytes.argtypes = [vp]
+    L.sph_async_transfer_bytes.restype = u64
+    L.sph_enable_async_transfers.argtypes = [vp, vp, u64]
+    L.sph_upload_async.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_download_async.argtypes = [vp, vp, vp, vp, vp]
+    L.sph_sync_transfers.argtypes = [vp]
     L.sph_array_bytes.argtypes = [vp, i32]
     L.sph_array_bytes.restype = u64
     L.sph_read_array.argtypes = [vp, i32, vp, u64]
@@ -381,6 +389,29 @@ def sph_rollout(ctx, nsteps: int, save_every: int = 0, cb=None):
 def sph_download(ctx, pos=None, vel=None, rho=None, ids=None):
     _check(lib().sph_download(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx,
            "sph_download")
+
+
+def sph_async_transfer_bytes(ctx) -> int:
+    return int(lib().sph_async_transfer_bytes(ctx))
+
+
+def sph_enable_async_transfers(ctx, buf, nbytes):
+    _check(lib().sph_enable_async_transfers(ctx, _ptr(buf), int(nbytes)), ctx,
+           "sph_enable_async_transfers")
+
+
+def sph_upload_async(ctx, pos, vel, rho, ids):
+    _check(lib().sph_upload_async(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx,
+           "sph_upload_async")
+
+
+def sph_download_async(ctx, pos=None, vel=None, rho=None, ids=None):
+    _check(lib().sph_download_async(ctx, _ptr(pos), _ptr(vel), _ptr(rho), _ptr(ids)), ctx,
+           "sph_download_async")
+
+
+def sph_sync_transfers(ctx):
+    _check(lib().sph_sync_transfers(ctx), ctx, "sph_sync_transfers")
 
 
 def sph_download_by_id(ctx, pos=None, vel=None, rho=None):
@@ -699,6 +730,13 @@ class Simulation:
         self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
         sph_download(self.ctx, pos, vel, rho, ids)
         self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def enable_async_transfers(self):
+        """Attach a device staging buffer (allocated here, owned by this
+        object) for sph_upload_async / sph_download_async."""
+        nb = sph_async_transfer_bytes(self.ctx)
+        self._xfer = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
+        sph_enable_async_transfers(self.ctx, self._xfer, nb)
 
     def download_by_id(self, pos=None, vel=None, rho=None):
         """State indexed by particle id into caller-owned arrays or device

@@ -133,6 +133,12 @@ def test_entry_points_refuse_a_null_context(lib):
     assert lib.sph_clear_status(None) == -1
     t = (C.c_double * 1)(0.0)
     assert lib.sph_set_instance_state(None, t, None) == -1
+    # pipelined transfers
+    assert lib.sph_async_transfer_bytes(None) == 0
+    assert lib.sph_enable_async_transfers(None, 0x1000, 1 << 20) == -1
+    assert lib.sph_upload_async(None, 0x1000, 0x1000, 0x1000, 0x1000) == -1
+    assert lib.sph_download_async(None, None, None, None, None) == -1
+    assert lib.sph_sync_transfers(None) == -1
 
 
 def test_new_entry_points_check_their_arguments_before_any_gpu_work(lib):
