@@ -269,6 +269,33 @@ def pinned_copy_gbs(torch, host, stream):
     return best
 
 
+def phase_split(sim, torch, paper, reps=3):
+    """Per-phase device time of one step (ms), the step issued call by call
+    with CUDA events between the calls on the simulation's stream: the
+    rebuilds (labels, counting sort, offsets, unit list, reorder), the
+    force evaluations (interaction and CFL step) and the integrator.
+    Median over reps steps."""
+    stream = sim.stream
+    seq = ([("rebuild", sim.build_cells), ("interact", sim.interact), ("verlet", sim.verlet)]
+           if paper else
+           [("rebuild", sim.build_cells), ("interact", sim.interact), ("predict", sim.predict),
+            ("rebuild", sim.build_cells), ("interact", sim.interact), ("correct", sim.correct)])
+    rows = []
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(seq) + 1)]
+        ev[0].record(stream)
+        for k, (_, fn) in enumerate(seq):
+            fn()
+            ev[k + 1].record(stream)
+        ev[-1].synchronize()
+        row = {}
+        for k, (name, _) in enumerate(seq):
+            row[name] = row.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
+        rows.append(row)
+    sim.check()
+    return {name: round(float(np.median([r[name] for r in rows])), 4) for name in rows[0]}
+
+
 def run_ours(args):
     import torch
 
@@ -361,6 +388,9 @@ def run_ours(args):
                 "peak_median": round(peak_median, 2),
                 "peak_derived": round(peak_derived, 2),
                 "frac_of_derived": round(achieved / peak_derived, 4)}
+
+    # --- per-phase split of one step (call by call, events between) ---------
+    phases = phase_split(sim, torch, args.formulation == "paper")
 
     # --- end to end through the C ABI with pinned host buffers ---------------
     n = case.n
@@ -474,7 +504,7 @@ def run_ours(args):
             "wall_s_per_simulated_s": ((t_max * 1e-3) / (d1["t"] - d0["t"])
                                        if d1["t"] > d0["t"] else None),
             "member_steps_per_s": steps_per_s * getattr(sim, "n_inst", 1),
-            "roofline": roofline, "e2e": e2e,
+            "roofline": roofline, "e2e": e2e, "phases_ms": phases,
             # the step kernels, one loop-control kernel per step and the loop's
             # arming kernel (sph_step with two or more steps is one graph launch)
             "gpu_launches": (kps * args.steps + (args.steps + 1 if loop else 0)),

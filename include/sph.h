@@ -49,11 +49,17 @@ extern "C" {
                                       it is then not the (label, id) order) */
 #define SPH_ERR_STATE         -7   /* call out of order (e.g. no state yet) */
 #define SPH_ERR_TOO_LARGE     -8   /* n above the fixed maximum of a call    */
+#define SPH_ERR_BOUNDS        -9   /* checked build: a kernel index was out of
+                                      range (the access was skipped)          */
 
 /* Bits of the device status word. */
 #define SPH_STATUS_TIMEOUT    1u
 #define SPH_STATUS_NONFINITE  2u
 #define SPH_STATUS_CAPACITY   4u
+/* Set only by the checked build of the library (libsph_checked.so, compiled
+ * with -DSPH_CHECKED), whose kernels test the indexes they compute and skip
+ * an out-of-range access instead of making it. */
+#define SPH_STATUS_BOUNDS     8u
 
 /* Physical and numerical constants of one simulation (Sec. 2.2, 2.3, 3).
  *   dp        particle spacing [m]; mass is given separately

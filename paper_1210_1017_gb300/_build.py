@@ -12,6 +12,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libsph.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+# The checked build: the same sources with -DSPH_CHECKED, whose kernels test
+# the indexes they compute and report an out-of-range one in the status word.
+LIB_CHECKED = os.path.join(HERE, "libsph_checked.so")
+BUILD_DIR_CHECKED = os.path.join(HERE, "_build_checked")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
               "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -28,25 +32,29 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libsph.so next to this file."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libsph.so next to this file
+    (checked=True: libsph_checked.so, with -DSPH_CHECKED)."""
+    lib = LIB_CHECKED if checked else LIB
+    build_dir = BUILD_DIR_CHECKED if checked else BUILD_DIR
+    extra = ["-DSPH_CHECKED"] if checked else []
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -56,10 +64,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(sources()) or 1) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, "-shared", "-o", tmp, *objs]
+    tmp = lib + ".tmp"
+    cmd = [nvcc, "-shared", "-o", tmp, *objs, "-ldl"]   # -ldl: NVTX loads its tool library
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib

@@ -274,6 +274,8 @@ Dev make_dev(const sph_ctx* c) {
     const sph_params* p = &c->p;
     Dev d;
     memset(&d, 0, sizeof(d));
+    d.status = c->status;
+    d.units_cap = c->units_cap;
     const double cs = 2.0 * p->h;
     d.inst = c->d_inst;
     d.cell_base = c->d_cell_base;
@@ -336,7 +338,7 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     launch_scan_cells(c->d, c->cnt, c->off, c->cscan_words, c->cscan_ctl, c->status, st);
     // the labels are in key[0]; one counting-sort pass groups the particles
     // by cell into (key[1], val[1]) and the reorder applies the id tie-break
-    launch_cell_scatter(c->key[0], c->n, c->off, c->cnt, c->key[1], c->val[1], st);
+    launch_cell_scatter(c->key[0], c->n, c->off, c->cnt, c->key[1], c->val[1], c->status, st);
     const int src = 1;
     c->skey = src;
     launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->urow,
@@ -613,6 +615,7 @@ int sph_set_instance_state(sph_ctx* c, const double* t, const uint64_t* steps) {
 
 int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho,
                const uint32_t* ids) {
+    const TraceRange trace("sph_upload");
     if (!c || !pos || !vel || !rho || !ids) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
     const size_t n = c->n;
     cudaStream_t st = c->st;
@@ -628,6 +631,7 @@ int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho
     cudaMemsetAsync(c->id_flag, 0, sizeof(uint32_t), st);
     // Verlet: the first step after an upload has no earlier state (Euler)
     cudaMemsetAsync(c->i_vphase, 0, c->n_inst * sizeof(uint32_t), st);
+    drop_pending_counts(c, st);
     k_unpack<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(c->n, dpos, dvel, drho, c->x[c->cur],
                                                          c->y[c->cur], c->z[c->cur], c->vr[c->cur],
                                                          c->id[c->cur], c->id_flag);
@@ -646,6 +650,7 @@ int sph_upload(sph_ctx* c, const double* pos, const float* vel, const float* rho
 }
 
 int sph_build_cells(sph_ctx* c) {
+    const TraceRange trace("sph_build_cells");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
     enqueue_build(c);
@@ -653,6 +658,7 @@ int sph_build_cells(sph_ctx* c) {
 }
 
 int sph_interact(sph_ctx* c, uint32_t flags) {
+    const TraceRange trace("sph_interact");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
     // at the half step (predictor pending) the step size stays the one set
@@ -662,6 +668,7 @@ int sph_interact(sph_ctx* c, uint32_t flags) {
 }
 
 int sph_predict(sph_ctx* c) {
+    const TraceRange trace("sph_predict");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (c->verlet) return fail(c, SPH_ERR_STATE, "predict on a Verlet context");
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
@@ -673,6 +680,7 @@ int sph_predict(sph_ctx* c) {
 }
 
 int sph_correct(sph_ctx* c) {
+    const TraceRange trace("sph_correct");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (c->verlet) return fail(c, SPH_ERR_STATE, "correct on a Verlet context");
     if (!c->cells_valid || c->pre_state != 2)
@@ -685,6 +693,7 @@ int sph_correct(sph_ctx* c) {
 }
 
 int sph_verlet(sph_ctx* c) {
+    const TraceRange trace("sph_verlet");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->verlet) return fail(c, SPH_ERR_STATE, "verlet on a symplectic context");
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "verlet needs build_cells and interact first");
@@ -731,6 +740,7 @@ static int build_loop_graph(sph_ctx* c, int g, uint32_t body) {
 }
 
 int sph_step(sph_ctx* c, uint32_t nsteps) {
+    const TraceRange trace("sph_step");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
     c->pre_state = 0;
@@ -793,6 +803,7 @@ int sph_step(sph_ctx* c, uint32_t nsteps) {
 
 int sph_rollout(sph_ctx* c, uint32_t nsteps, uint32_t save_every, sph_snapshot_fn cb,
                 void* user) {
+    const TraceRange trace("sph_rollout");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (save_every == 0) save_every = nsteps ? nsteps : 1;
     uint32_t done = 0;
@@ -819,6 +830,7 @@ int sph_rollout(sph_ctx* c, uint32_t nsteps, uint32_t save_every, sph_snapshot_f
 }
 
 int sph_download(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids) {
+    const TraceRange trace("sph_download");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
     const size_t n = c->n;
@@ -839,6 +851,7 @@ int sph_download(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids)
 }
 
 int sph_download_by_id(sph_ctx* c, double* pos, float* vel, float* rho) {
+    const TraceRange trace("sph_download_by_id");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
     if (c->ids_pending) {
@@ -910,6 +923,7 @@ int sph_read_array(sph_ctx* c, int which, void* host, uint64_t bytes) {
 }
 
 int sph_neighbour_counts_fp64(sph_ctx* c) {
+    const TraceRange trace("sph_neighbour_counts_fp64");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
     launch_counts_fp64(c->d, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->key[c->skey], c->off,
@@ -918,6 +932,7 @@ int sph_neighbour_counts_fp64(sph_ctx* c) {
 }
 
 int sph_diagnostics(sph_ctx* c, sph_diag* out) {
+    const TraceRange trace("sph_diagnostics");
     if (!c || !out) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
     memset(out, 0, sizeof(*out));
     if (c->have_state && c->cells_valid) {
@@ -969,6 +984,7 @@ int sph_diagnostics(sph_ctx* c, sph_diag* out) {
 }
 
 int sph_front(sph_ctx* c, double z_lo, double z_hi, double* front) {
+    const TraceRange trace("sph_front");
     if (!c || !front) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
     if (!(z_lo < z_hi)) return fail(c, SPH_ERR_INVALID_ARG, "need z_lo < z_hi");
     if (!c->have_state || !c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
@@ -1005,6 +1021,8 @@ int sph_check(sph_ctx* c) {
         return fail(c, SPH_ERR_TIMEOUT, "a bounded device wait gave up (radix-sort look-back or staging copy)");
     if (status & SPH_STATUS_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite interaction result");
     if (status & SPH_STATUS_CAPACITY) return fail(c, SPH_ERR_CAPACITY, "a cell exceeded the id tie-break capacity");
+    if (status & SPH_STATUS_BOUNDS)
+        return fail(c, SPH_ERR_BOUNDS, "a kernel index was out of range (checked build)");
     return SPH_OK;
 }
 
@@ -1059,6 +1077,7 @@ int sph_set_variant(sph_ctx* c, uint32_t v) {
 }
 
 int sph_autotune(sph_ctx* c, uint32_t reps, float* ms_per_variant, uint32_t* best) {
+    const TraceRange trace("sph_autotune");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->cells_valid) return fail(c, SPH_ERR_STATE, "cells not built");
     if (reps == 0) reps = 3;
@@ -1208,6 +1227,7 @@ int sph_enable_async_transfers(sph_ctx* c, void* d_buf, uint64_t bytes) {
 
 int sph_upload_async(sph_ctx* c, const double* pos, const float* vel, const float* rho,
                      const uint32_t* ids) {
+    const TraceRange trace("sph_upload_async");
     if (!c || !pos || !vel || !rho || !ids) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
     if (!c->xfer) return fail(c, SPH_ERR_STATE, "pipelined transfers not enabled");
     const size_t n = c->n;
@@ -1227,6 +1247,7 @@ int sph_upload_async(sph_ctx* c, const double* pos, const float* vel, const floa
     cudaStreamWaitEvent(st, c->ev_up_loaded[s], 0);
     cudaMemsetAsync(c->id_flag, 0, sizeof(uint32_t), st);
     cudaMemsetAsync(c->i_vphase, 0, c->n_inst * sizeof(uint32_t), st);
+    drop_pending_counts(c, st);
     k_unpack_ids<<<(uint32_t)((n + 255) / 256), 256, 0, st>>>(
         c->n, u.pos, u.vel, u.rho, u.ids, c->x[c->cur], c->y[c->cur], c->z[c->cur], c->vr[c->cur],
         c->id[c->cur], c->id_flag);
@@ -1243,6 +1264,7 @@ int sph_upload_async(sph_ctx* c, const double* pos, const float* vel, const floa
 }
 
 int sph_download_async(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t* ids) {
+    const TraceRange trace("sph_download_async");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!c->have_state) return fail(c, SPH_ERR_STATE, "no state uploaded");
     if (!c->xfer) return fail(c, SPH_ERR_STATE, "pipelined transfers not enabled");
@@ -1267,6 +1289,7 @@ int sph_download_async(sph_ctx* c, double* pos, float* vel, float* rho, uint32_t
 }
 
 int sph_sync_transfers(sph_ctx* c) {
+    const TraceRange trace("sph_sync_transfers");
     if (!c) return SPH_ERR_INVALID_ARG;
     int rc = SPH_OK;
     if (c->s_h2d) {

@@ -1,6 +1,7 @@
 // The SPH context (private to libsph.so; shared by the SPH and surrogate
 // translation units).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +106,25 @@ struct sph_ctx {
 };
 
 namespace sph {
+
+// Host-side range around a C-ABI call (NVTX, header-only): profilers that
+// read NVTX (nsys timelines, ncu --nvtx-include) see which call enqueued
+// which kernels.  Without an attached tool a push/pop is a null check.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// The state is being replaced (an upload, a surrogate advance): labels that
+// sph_predict / sph_correct / sph_verlet computed and counted into the
+// per-cell counts for the next rebuild no longer apply.  Clear those counts,
+// since the next rebuild counts the new labels from zero.
+inline void drop_pending_counts(sph_ctx* c, cudaStream_t st) {
+    if (c->keys_ready) cudaMemsetAsync(c->cnt, 0, (c->ncells + 1) * sizeof(uint32_t), st);
+    c->keys_ready = false;
+}
 
 // Record a one-line error message on the context and return the code.
 inline int fail(sph_ctx* c, int code, const std::string& msg) {

@@ -19,6 +19,29 @@ namespace sph {
 constexpr uint32_t kStatusTimeout = 1u;
 constexpr uint32_t kStatusNonFinite = 2u;
 constexpr uint32_t kStatusCapacity = 4u;
+constexpr uint32_t kStatusBounds = 8u;
+
+// The checked build (compiled with -DSPH_CHECKED, loaded as
+// libsph_checked.so) tests the array indexes its kernels compute (staged
+// and global candidate indexes, gather and scatter slots, cell offsets, the
+// unit list) before using them.  An index out of range sets kStatusBounds
+// in the context's status word and the access is skipped (the index is
+// replaced by a safe one), so a wrong index is reported, never followed and
+// never trapped.  In the normal build the tests compile away.
+#ifdef SPH_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// True when ok; otherwise (checked build only) records kStatusBounds.
+__device__ __forceinline__ bool in_bounds(bool ok, uint32_t* status) {
+    if (kChecked && !ok) {
+        atomicOr(status, kStatusBounds);
+        return false;
+    }
+    return true;
+}
 
 // Largest particle count (FP64 counts and ids stay within 32 bits with room).
 constexpr uint32_t kMaxParticles = 1u << 26;
@@ -73,6 +96,8 @@ struct Dev {
     int unit;              // its unit size in particles
     int stage;             // its staging capacity in candidates
     int units_fused;       // the unit list is built in one launch (k_units_fused)
+    uint32_t units_cap;    // capacity of the unit list
+    uint32_t* status;      // the context's device status word
     float csf;             // 2h
     float h, inv_h;
     float r2max;           // (2h)^2 in FP32
@@ -109,7 +134,7 @@ void launch_scan_onepass(uint32_t* in, uint64_t m, uint32_t* out, bool zero_in,
 // into (kout, vout), from the per-cell counts cnt (counted back to zero) and
 // the cell offsets off.  Order inside a cell is arbitrary.
 void launch_cell_scatter(const uint32_t* key, uint32_t n, const uint32_t* off, uint32_t* cnt,
-                         uint32_t* kout, uint32_t* vout, cudaStream_t st);
+                         uint32_t* kout, uint32_t* vout, uint32_t* status, cudaStream_t st);
 uint32_t scan_bsum_count(uint64_t m);
 
 // Radix sort

@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
     if (valid) {
         c = a.skey[k];
         v = a.sval[k];
+        if (!in_bounds(c <= d.ncells && v < d.n, d.status)) {
+            c = d.ncells;
+            v = k;
+        }
         myid = a.sid[v];
         s = a.off[c];
         e = a.off[c + 1];
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(256) k_reorder(const Dev d, const ReorderArgs 
         atomicOr(a.status, kStatusCapacity);
     }
     const uint32_t dst = s + rank;
+    if (!in_bounds(dst < d.n, d.status)) return;
     const double x = a.sx[v], y = a.sy[v], z = a.sz[v];
     const float4 vr = a.svr[v];
     a.dx[dst] = x;
@@ -582,6 +587,7 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
     pf = false;
     pf_off = false;
     const uint32_t i0 = unit.x, i1 = unit.y;
+    if (!in_bounds(i0 < i1 && i1 <= d.n && i1 - i0 <= (uint32_t)(W * 32), d.status)) break;
     const uint32_t q = find_instance(d.cell_base, d.n_inst, key0);
     if (__ldg(d.is.done + q)) {                      // block-uniform
         if (DYN) {
@@ -848,6 +854,10 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                     float4 pp[kPop], vv[kPop];
 #pragma unroll
                     for (int k = 0; k < kPop; ++k) {
+                        if (!in_bounds(j2[k] < s_base[9], d.status)) {
+                            j2[k] = self;
+                            qx2[k] = qpad;
+                        }
                         pp[k] = s_p[j2[k]];
                         vv[k] = s_v[j2[k]];
                     }
@@ -974,7 +984,8 @@ __global__ void __launch_bounds__(W * SPLIT * 32, MINB) k_interact(const Dev d, 
                 for (uint32_t t = 0; t < mx; ++t) {
                     if (t < cnt) {
                         const uint32_t e = lst[t * 32 + lane];
-                        const uint32_t j = e & kIdxMask;
+                        uint32_t j = e & kIdxMask;
+                        if (!in_bounds(j < d.n, d.status)) j = i;
                         const float ox = (float)((int)((e >> 26) & 3u) - 1);
                         const float oy = (float)((int)((e >> 28) & 3u) - 1);
                         const float oz = (float)((int)(e >> 30) - 1);
@@ -1223,7 +1234,7 @@ __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __re
             if (x < ncx && a != b) {
                 if (start != 0xffffffffu &&
                     (x - last > 3 || x - lo >= kSpan || cc[k + 3] - base > (uint32_t)d.stage)) {
-                    if (MODE) units[out + n] = make_uint2(start, a);
+                    if (MODE && in_bounds(out + n < d.units_cap, d.status)) units[out + n] = make_uint2(start, a);
                     ++n;
                     start = 0xffffffffu;
                 }
@@ -1234,7 +1245,7 @@ __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __re
                 }
                 last = x;
                 while (b - start > (uint32_t)d.unit) {
-                    if (MODE) units[out + n] = make_uint2(start, start + d.unit);
+                    if (MODE && in_bounds(out + n < d.units_cap, d.status)) units[out + n] = make_uint2(start, start + d.unit);
                     ++n;
                     start += d.unit;
                     lo = x;
@@ -1245,7 +1256,7 @@ __device__ __forceinline__ uint32_t unit_walk(const Dev& d, const uint32_t* __re
         }
     }
     if (start != 0xffffffffu) {
-        if (MODE) units[out + n] = make_uint2(start, a);
+        if (MODE && in_bounds(out + n < d.units_cap, d.status)) units[out + n] = make_uint2(start, a);
         ++n;
     }
     return n;

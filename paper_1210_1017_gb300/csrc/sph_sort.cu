@@ -425,7 +425,8 @@ void launch_scan_cells(const Dev& d, uint32_t* cnt, uint32_t* off, unsigned long
 __global__ void __launch_bounds__(256) k_cell_scatter(const uint32_t* __restrict__ key, uint32_t n,
                                                       const uint32_t* __restrict__ off,
                                                       uint32_t* cnt, uint32_t* __restrict__ kout,
-                                                      uint32_t* __restrict__ vout) {
+                                                      uint32_t* __restrict__ vout,
+                                                      uint32_t* status) {
     pdl_wait();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
@@ -439,14 +440,15 @@ __global__ void __launch_bounds__(256) k_cell_scatter(const uint32_t* __restrict
     if ((int)(threadIdx.x & 31) == leader) old = atomicSub(cnt + k, np);
     old = __shfl_sync(peers, old, leader);
     const uint32_t slot = off[k] + old - np + __popc(peers & lanemask_lt());
+    if (!in_bounds(slot < n, status)) return;
     kout[slot] = k;
     vout[slot] = i;
 }
 
 void launch_cell_scatter(const uint32_t* key, uint32_t n, const uint32_t* off, uint32_t* cnt,
-                         uint32_t* kout, uint32_t* vout, cudaStream_t st) {
+                         uint32_t* kout, uint32_t* vout, uint32_t* status, cudaStream_t st) {
     if (n == 0) return;
-    launch_pdl(k_cell_scatter, (n + 255) / 256, 256, 0, st, key, n, off, cnt, kout, vout);
+    launch_pdl(k_cell_scatter, (n + 255) / 256, 256, 0, st, key, n, off, cnt, kout, vout, status);
 }
 
 void launch_lookback_selftest(uint32_t* zeroed256, uint32_t limit, uint32_t* err,

@@ -130,6 +130,7 @@ using namespace sph;
 extern "C" int sph_subdomain_select(sph_ctx* c, int mode, double xlo, double xhi,
                                     uint32_t* counts, uint32_t capacity, double* pos, float* vel,
                                     float* rho, uint32_t* ids) {
+    const TraceRange trace("sph_subdomain_select");
     if (!c) return SPH_ERR_INVALID_ARG;
     if (!counts) return fail(c, SPH_ERR_INVALID_ARG, "NULL counts");
     if (mode != SPH_SUBDOMAIN_EDGE && mode != SPH_SUBDOMAIN_MIGRATE)

@@ -913,7 +913,7 @@ int sur_advance(sur_ctx* c, sph_ctx* s, float* d_hist) {
     k_advance<<<nblk(s->n, 256), 256, 0, c->st>>>(s->d, s->id[cur], s->x[cur], s->y[cur], s->z[cur],
                                                   s->vr[cur], s->off, c->acc, d_hist, c->cfg.dt_s);
     s->cells_valid = false;
-    s->keys_ready = false;
+    sph::drop_pending_counts(s, c->st);
     s->pre_state = 0;
     // a Verlet context has no earlier state for the surrogate's result: its
     // next SPH step is an Euler step

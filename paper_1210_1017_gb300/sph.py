@@ -28,7 +28,7 @@ SPH_SCHEME_CUBIC, SPH_SCHEME_VERLET = 1, 2
 SPH_SUBDOMAIN_EDGE, SPH_SUBDOMAIN_MIGRATE = 0, 1
 ERRORS = {-1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_WORKSPACE",
           -4: "SPH_ERR_TIMEOUT", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_CAPACITY",
-          -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE"}
+          -7: "SPH_ERR_STATE", -8: "SPH_ERR_TOO_LARGE", -9: "SPH_ERR_BOUNDS"}
 SPH_RADIX_SORT_STATIC_MAX_N = 1 << 20
 
 EXPORTED = ["sph_query_sizes", "sph_init", "sph_upload", "sph_build_cells", "sph_download_by_id",
@@ -103,16 +103,24 @@ SNAPSHOT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_uint64, C.c_double)
 _lib = None
 
 
+def checked() -> bool:
+    """SPH_CHECKED=1 in the environment selects the checked build
+    (libsph_checked.so: every kernel index tested, an out-of-range one
+    reported as SPH_ERR_BOUNDS by sph_check)."""
+    return os.environ.get("SPH_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def lib(build: bool = False):
-    """Load libsph.so (building it first if asked).  Raises if it is missing."""
+    """Load libsph.so, or libsph_checked.so under SPH_CHECKED=1 (building
+    it first if asked).  Raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    path = _build.build(checked=checked()) if build else library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"libsph.so not built ({path}); run __graft_entry__.build()")
     L = C.CDLL(path)

@@ -422,3 +422,50 @@ def test_counter_scheduled_variants_equal_their_static_shapes():
             got = sim.read(S.SPH_ARRAY_ACE)
             assert np.array_equal(got, ref), (vs, vd)
     sim.close()
+
+
+def test_upload_after_a_predict_or_correct_without_rebuild():
+    """sph_predict / sph_correct count the new labels into the per-cell
+    counts for the next rebuild.  When new state is uploaded instead, those
+    counts must not carry over: the next step equals the same step on a
+    fresh context, bit for bit (stale counts would double the cell sizes and
+    misplace the scatter)."""
+    case = cases.c1_dam_break(shuffle_seed=8)
+    ref = S.Simulation.from_case(case)
+    ref.step(3)
+    want = ref.download()
+    for stop in ("predict", "correct"):
+        sim = S.Simulation.from_case(case)
+        sim.step(2)
+        sim.build_cells()
+        sim.interact()
+        sim.predict()
+        if stop == "correct":
+            sim.build_cells()
+            sim.interact()
+            sim.correct()
+        sim.check()
+        # the pending counts are dropped by the upload; the same for the
+        # pipelined upload
+        sim.upload(case.pos, case.vel, case.rho, case.ids)
+        sim.step(3)
+        sim.check()
+        got = sim.download()
+        for key in ("ids", "pos", "vel", "rho"):
+            assert np.array_equal(got[key], want[key]), (stop, key)
+        sim.enable_async_transfers()
+        sim.build_cells()
+        sim.interact()
+        sim.predict()
+        S.sph_upload_async(sim.ctx, np.ascontiguousarray(case.pos, np.float64),
+                           np.ascontiguousarray(case.vel, np.float32),
+                           np.ascontiguousarray(case.rho, np.float32),
+                           np.ascontiguousarray(case.ids, np.uint32))
+        S.sph_sync_transfers(sim.ctx)
+        sim.step(3)
+        sim.check()
+        got = sim.download()
+        for key in ("ids", "pos", "vel", "rho"):
+            assert np.array_equal(got[key], want[key]), (stop, "async", key)
+        sim.close()
+    ref.close()
