@@ -469,6 +469,10 @@ int sph_pdl_enabled(void);
 int sph_fma_probe(float *d_out, uint32_t blocks, uint32_t iters, void *stream);
 
 const char *sph_last_error(const sph_ctx *ctx);
+
+/* Wait for the context's stream and its copy streams, then free the context
+ * (its graphs, streams and events).  The workspace and the transfer buffer
+ * may be freed once this returns.  Sync. */
 void sph_destroy(sph_ctx *ctx);
 
 /* Sec. 3.1 / Sec. 4.3: stable LSD radix sort of (key, value) pairs by the

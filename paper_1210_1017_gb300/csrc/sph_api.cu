@@ -1309,6 +1309,9 @@ int sph_sync_transfers(sph_ctx* c) {
 
 void sph_destroy(sph_ctx* c) {
     if (!c) return;
+    // work still queued may read the workspace or the transfer buffer, which
+    // the caller frees after this call
+    cudaStreamSynchronize(c->st);
     for (int g = 0; g < 2; ++g) {
         if (c->graph[g]) cudaGraphExecDestroy(c->graph[g]);
         if (c->loop_graph[g]) cudaGraphExecDestroy(c->loop_graph[g]);
