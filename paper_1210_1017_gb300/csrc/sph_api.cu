@@ -336,13 +336,24 @@ Dev make_dev(const sph_ctx* c) {
 void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     cudaStream_t st = c->st;
     launch_scan_cells(c->d, c->cnt, c->off, c->cscan_words, c->cscan_ctl, c->status, st);
+    // the interaction's unit list needs only the cell offsets: on the fork
+    // stream it runs beside the scatter and the reorder (joined below)
+    const bool fork = c->st_units != nullptr;
+    if (fork) {
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->st_units, c->ev_fork, 0);
+        launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->urow,
+                     c->uctl, c->status, c->st_units);
+        cudaEventRecord(c->ev_join, c->st_units);
+    }
     // the labels are in key[0]; one counting-sort pass groups the particles
     // by cell into (key[1], val[1]) and the reorder applies the id tie-break
     launch_cell_scatter(c->key[0], c->n, c->off, c->cnt, c->key[1], c->val[1], c->status, st);
     const int src = 1;
     c->skey = src;
-    launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->urow,
-                 c->uctl, c->status, st);
+    if (!fork)
+        launch_units(c->d, c->off, c->csum, c->ucnt, c->ubsum, c->uoff, c->units, c->urow,
+                     c->uctl, c->status, st);
     ReorderArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.skey = c->key[src];
@@ -376,6 +387,7 @@ void rebuild_after_keys(sph_ctx* c, bool with_pre) {
     ra.hist_to_zero = c->hist;
     ra.status = c->status;
     launch_reorder(c->d, ra, st);
+    if (fork) cudaStreamWaitEvent(st, c->ev_join, 0);
     c->cur = d;
 }
 
@@ -455,6 +467,17 @@ void enqueue_step(sph_ctx* c) {
     c->keys_ready = true;
     c->pre_state = 0;
     enqueue_build(c);
+}
+
+void release_fork_stream(sph_ctx* c) {
+    if (c->st_units) {
+        cudaStreamSynchronize(c->st_units);
+        cudaStreamDestroy(c->st_units);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->st_units = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
 }
 
 int post_launch(sph_ctx* c, const char* what) {
@@ -551,6 +574,21 @@ int init(const sph_params* params, const sph_instance* inst, uint32_t n_inst, vo
     if (rc) {
         delete c;
         return rc;
+    }
+    {
+        // the unit-list fork stream (not on the legacy default stream, or
+        // when the environment sets SPH_FORK_UNITS=0 at context creation)
+        const char* e = getenv("SPH_FORK_UNITS");
+        if (st != nullptr && !(e && e[0] == '0')) {
+            const bool ok =
+                cudaStreamCreateWithFlags(&c->st_units, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                release_fork_stream(c);
+            }
+        }
     }
     *out = c;
     return SPH_OK;
@@ -1317,6 +1355,7 @@ void sph_destroy(sph_ctx* c) {
         if (c->loop_graph[g]) cudaGraphExecDestroy(c->loop_graph[g]);
     }
     release_transfer_streams(c);
+    release_fork_stream(c);
     delete c;
 }
 

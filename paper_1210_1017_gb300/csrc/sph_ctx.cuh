@@ -92,6 +92,12 @@ struct sph_ctx {
     // repeats a body of loop_body steps on the device (see sph_step)
     cudaGraphExec_t loop_graph[2] = {nullptr, nullptr};
     uint32_t* loop_ctr = nullptr;   // [0] steps done in this launch, [1] steps asked
+    // a second stream for the unit list: after the cell scan each rebuild
+    // forks the unit-list kernels onto it and joins them before the
+    // interaction, so they run beside the cell scatter and the reorder (both
+    // only need the cell offsets); null on the legacy default stream
+    cudaStream_t st_units = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // pipelined transfers (sph_enable_async_transfers): a caller-owned buffer
     // of three staging slots (two for uploads, one for downloads), a copy
     // stream per direction and the events that order them with c->st

@@ -90,3 +90,34 @@ def test_one_launch_unit_list_of_an_ensemble():
     _check_tiling(one, u1)
     one.close()
     many.close()
+
+
+def test_forked_unit_list_equals_the_serial_one():
+    """Each rebuild builds the unit list on a second stream, beside the cell
+    scatter and the reorder, and joins it before the interaction; a context
+    created with SPH_FORK_UNITS=0 builds it in line.  Both give the same
+    steps, bit for bit, in the device loop and call by call."""
+    import os
+    case = cases.c1_dam_break(shuffle_seed=12)
+    forked = S.Simulation.from_case(case)
+    os.environ["SPH_FORK_UNITS"] = "0"
+    try:
+        serial = S.Simulation.from_case(case)
+    finally:
+        del os.environ["SPH_FORK_UNITS"]
+    for sim in (forked, serial):
+        sim.step(20)
+        sim.build_cells()
+        sim.interact()
+        sim.predict()
+        sim.build_cells()
+        sim.interact()
+        sim.correct()
+        sim.step(1)
+        sim.check()
+    a, b = forked.download(), serial.download()
+    for key in ("ids", "pos", "vel", "rho"):
+        assert np.array_equal(a[key], b[key])
+    assert np.array_equal(forked.units(), serial.units())
+    forked.close()
+    serial.close()
