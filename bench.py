@@ -519,6 +519,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         sim = None
         line["ensemble_256"] = ensemble_record(args, S, torch, local, args.steps)
+        torch.cuda.empty_cache()
+        line["surrogate_1m"] = surrogate_record(args, S, torch, local)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         if sim is not None:
             sim.close()
@@ -531,6 +533,66 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def surrogate_record(args, S, torch, device, calls=5):
+    """The learned surrogate's speed against plain GPU SPH, as a nested record
+    of the default line: the fastest variant (2 message-passing layers, 16
+    SPH steps per call, edges only within 0.65 2h) on the 1.39M-particle dam
+    break with obstacles, random initial weights (the speed does not depend
+    on them).  Plain SPH steps and surrogate calls (graph, layers, Euler step,
+    cell rebuild) are timed with CUDA events on the simulation's stream;
+    both sides advance the same simulated time per SPH step.  Accuracy needs
+    trained weights and comes from the training runs, not from here."""
+    from paper_1210_1017_gb300 import cases
+    from paper_1210_1017_gb300 import surrogate as U
+    from paper_1210_1017_gb300 import surrogate_train as T
+    layers, per_call, radius = 2, 16, 0.65
+    case = cases.c2_dam_break_obstacles()
+    st = torch.cuda.Stream(device)
+    sim = S.Simulation.from_case(case, device=device, stream=st)
+    sim.build_cells()
+    sim.autotune(reps=2, cache=False)
+    sim.step(args.warmup)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0 = sim.diagnostics()
+    e0.record(st)
+    sim.step(per_call * calls)
+    e1.record(st)
+    e1.synchronize()
+    d1 = sim.diagnostics()
+    sph_s = e0.elapsed_time(e1) / 1e3
+    dt = (d1["t"] - d0["t"]) / (per_call * calls)
+    sur = U.Surrogate(sim, layers=layers, train=False, v_scale=1.0, dt_s=per_call * dt,
+                      edges_per_node=30, radius=radius)
+    sur.set_params(T.init_params(layers, 0))
+    hist = torch.zeros((case.n, 15), dtype=torch.float32, device=sim.device)
+    sim.build_cells()
+    for _ in range(2):
+        sur.advance(hist)
+        sim.build_cells()
+    sim.synchronize()
+    e0.record(st)
+    for _ in range(calls):
+        sur.advance(hist)
+        sim.build_cells()
+    e1.record(st)
+    e1.synchronize()
+    sur_s = e0.elapsed_time(e1) / 1e3
+    sph_rate = per_call * calls * dt / sph_s
+    sur_rate = per_call * calls * dt / sur_s
+    rec = {"workload": "dam_break_obstacles_1m", "n_particles": case.n, "layers": layers,
+           "latent": 128, "sph_steps_per_call": per_call, "edge_radius_2h": radius,
+           "edges": sur.num_edges, "calls": calls, "ms_per_call": round(sur_s / calls * 1e3, 3),
+           "sph_ms_per_step": round(sph_s / (per_call * calls) * 1e3, 4),
+           "sim_s_per_wall_s": sur_rate, "sph_sim_s_per_wall_s": sph_rate,
+           "speedup_vs_sph": sur_rate / sph_rate, "weights": "random initialisation",
+           "note": ("speed only; accuracy of the trained variant (RMSE / dp, front) is "
+                    "measured by surrogate_train.py runs")}
+    sur.close()
+    sim.close()
+    return rec
 
 
 def ensemble_record(args, S, torch, device, steps):
