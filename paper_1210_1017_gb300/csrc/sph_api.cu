@@ -1217,19 +1217,23 @@ XferSlot xfer_slot(sph_ctx* c, int s) {
 
 }  // namespace
 
+// Waits for the copy streams and destroys them and their events (each
+// handle only if it was created).
 static void release_transfer_streams(sph_ctx* c) {
-    if (!c->s_h2d) return;
-    cudaStreamSynchronize(c->s_h2d);
-    cudaStreamSynchronize(c->s_d2h);
-    for (int s = 0; s < 2; ++s) {
-        cudaEventDestroy(c->ev_up_loaded[s]);
-        cudaEventDestroy(c->ev_up_free[s]);
+    for (cudaStream_t* s : {&c->s_h2d, &c->s_d2h}) {
+        if (*s) {
+            cudaStreamSynchronize(*s);
+            cudaStreamDestroy(*s);
+            *s = nullptr;
+        }
     }
-    cudaEventDestroy(c->ev_dn_packed);
-    cudaEventDestroy(c->ev_dn_free);
-    cudaStreamDestroy(c->s_h2d);
-    cudaStreamDestroy(c->s_d2h);
-    c->s_h2d = c->s_d2h = nullptr;
+    for (cudaEvent_t* e : {&c->ev_up_loaded[0], &c->ev_up_loaded[1], &c->ev_up_free[0],
+                           &c->ev_up_free[1], &c->ev_dn_packed, &c->ev_dn_free}) {
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    }
     c->xfer = nullptr;
 }
 
@@ -1255,7 +1259,11 @@ int sph_enable_async_transfers(sph_ctx* c, void* d_buf, uint64_t bytes) {
                  cudaEventCreateWithFlags(&c->ev_up_free[s], fl) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&c->ev_dn_packed, fl) == cudaSuccess &&
              cudaEventCreateWithFlags(&c->ev_dn_free, fl) == cudaSuccess;
-        if (!ok) return cuda_check(c, cudaGetLastError(), "transfer streams");
+        if (!ok) {
+            const cudaError_t e = cudaGetLastError();
+            release_transfer_streams(c);   // what was created; pipelined calls stay off
+            return cuda_check(c, e != cudaSuccess ? e : cudaErrorUnknown, "transfer streams");
+        }
     }
     c->xfer = static_cast<unsigned char*>(d_buf);
     c->xfer_slot = xfer_slot_bytes(c->n);
