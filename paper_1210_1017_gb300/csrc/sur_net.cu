@@ -63,13 +63,26 @@ __global__ void k_refresh(const float* __restrict__ w, int kin, int kout, __nv_b
 // SPH cell list defines neighbours, or (radius 2h)^2 for a sparser graph),
 // visited in ascending sorted index: the 9 rows of cells around i's cell in
 // (z, y) order, cells in x order.
+//
+// The predicate is decided in FP32 where that is exact: with the positions
+// relative to their own cell origins (posc, rounded once from FP64) and
+// whole-cell offsets, each coordinate difference is within 6 roundings of
+// 2^-24 of a cell (3.6e-7 cs), so |d2_32 - d2_64| < 2 sqrt(3) r 3.6e-7 cs +
+// 1.8e-7 r^2, below 1.3e-5 r2 for r >= 0.1 cs.  So d2_32 < `inside` (r2
+// (1 - 2^-12)) is inside and d2_32 >= `outside` (r2 (1 + 2^-12)) or not
+// finite is outside;
+// the caller widens both to "always ask FP64" for radii below 0.1 cell.
+// Candidates in between, and the features of the accepted edges, take the
+// FP64 arithmetic of the predicate as written.  FP64 instructions run at
+// 1/64 of the FP32 rate on this GPU.
 template <int MODE>
 __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const double* __restrict__ y,
-                        const double* __restrict__ z, const uint32_t* __restrict__ key,
-                        const uint32_t* __restrict__ off, uint32_t* __restrict__ cnt,
-                        const uint32_t* __restrict__ rowptr, uint32_t* __restrict__ col,
-                        uint32_t* __restrict__ src, __nv_bfloat16* __restrict__ xe, double inv2h,
-                        double r2) {
+                        const double* __restrict__ z, const float4* __restrict__ posc,
+                        const uint32_t* __restrict__ key, const uint32_t* __restrict__ off,
+                        uint32_t* __restrict__ cnt, const uint32_t* __restrict__ rowptr,
+                        uint32_t* __restrict__ col, uint32_t* __restrict__ src,
+                        __nv_bfloat16* __restrict__ xe, double inv2h, double r2, float inside,
+                        float outside) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const uint32_t n_in = off[d.ncells];
@@ -90,22 +103,36 @@ __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const do
     const uint32_t t = lk / (uint32_t)I.ncx;
     const int cy = (int)(t % (uint32_t)I.ncy), cz = (int)(t / (uint32_t)I.ncy);
     const double xi = x[i], yi = y[i], zi = z[i];
+    const float4 pi = posc[i];
     const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < I.ncx ? cx + 1 : I.ncx - 1;
     uint32_t c = 0, e = MODE ? rowptr[i] : 0u;
     for (int zz = cz - 1; zz <= cz + 1; ++zz) {
         if (zz < 0 || zz >= I.ncz) continue;
+        const float qz = fmaf((float)(cz - zz), d.csf, pi.z);
         for (int yy = cy - 1; yy <= cy + 1; ++yy) {
             if (yy < 0 || yy >= I.ncy) continue;
+            const float qy = fmaf((float)(cy - yy), d.csf, pi.y);
             const uint32_t rb = I.cell_base + (uint32_t)I.ncx * ((uint32_t)yy + (uint32_t)I.ncy * zz);
-            const uint32_t s = off[rb + xlo], en = off[rb + xhi + 1];
-            for (uint32_t j = s; j < en; ++j) {
-                if (j == i) continue;
-                const double dx = __dsub_rn(xi, x[j]);
-                const double dy = __dsub_rn(yi, y[j]);
-                const double dz = __dsub_rn(zi, z[j]);
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                            __dmul_rn(dz, dz));
-                if (d2 < r2) {
+            for (int xx = xlo; xx <= xhi; ++xx) {
+                const float qx = fmaf((float)(cx - xx), d.csf, pi.x);
+                const uint32_t s = off[rb + xx], en = off[rb + xx + 1];
+                for (uint32_t j = s; j < en; ++j) {
+                    if (j == i) continue;
+                    const float4 pj = posc[j];
+                    const float fx = qx - pj.x, fy = qy - pj.y, fz = qz - pj.z;
+                    const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                    // outside, or not finite (the FP64 predicate rejects those too)
+                    if (!(d2f < outside)) continue;
+                    const bool sure = d2f < inside;
+                    double dx = 0.0, dy = 0.0, dz = 0.0, d2 = 0.0;
+                    if (MODE || !sure) {
+                        dx = __dsub_rn(xi, x[j]);
+                        dy = __dsub_rn(yi, y[j]);
+                        dz = __dsub_rn(zi, z[j]);
+                        d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                       __dmul_rn(dz, dz));
+                        if (!sure && !(d2 < r2)) continue;
+                    }
                     if (MODE) {
                         col[e] = j;
                         src[e] = i;
@@ -672,16 +699,23 @@ int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
                           ? ((double)rad * (2.0 * s->p.h)) * ((double)rad * (2.0 * s->p.h))
                           : s->d.r2max_d;
     const uint32_t* key = s->key[s->skey];
-    k_graph<0><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
-                                             c->cnt, nullptr, nullptr, nullptr, nullptr, inv2h, r2);
+    // the FP32 decision margins of k_graph (FP64 for every candidate below
+    // a tenth of a cell)
+    const bool fp32_ok = r2 >= 0.01 * (2.0 * s->p.h) * (2.0 * s->p.h);
+    const float inside = fp32_ok ? (float)r2 * (1.0f - 0x1p-12f) : -1.0f;
+    const float outside = fp32_ok ? (float)r2 * (1.0f + 0x1p-12f) : INFINITY;
+    k_graph<0><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], s->posc, key,
+                                             s->off, c->cnt, nullptr, nullptr, nullptr, nullptr,
+                                             inv2h, r2, inside, outside);
     sph::launch_scan(c->cnt, n, c->bsum, c->rowptr, st);
     uint32_t E = 0;
     cudaMemcpyAsync(&E, c->rowptr + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check(c, "graph count");
     if (E > c->cfg.max_edges) return fail(c, SPH_ERR_CAPACITY, "more edges than max_edges");
     c->E = E;
-    k_graph<1><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], key, s->off,
-                                             nullptr, c->rowptr, c->col, c->src, c->xe, inv2h, r2);
+    k_graph<1><<<nblk(n, 128), 128, 0, st>>>(d, s->x[cur], s->y[cur], s->z[cur], s->posc, key,
+                                             s->off, nullptr, c->rowptr, c->col, c->src, c->xe,
+                                             inv2h, r2, inside, outside);
     if (c->cfg.train && E) k_graph_rev<<<nblk(E, 256), 256, 0, st>>>(E, c->rowptr, c->col, c->src, c->rev);
     k_node_features<<<nblk(n, 256), 256, 0, st>>>(d, s->id[cur], hist, 1.0 / (double)c->cfg.v_scale, c->xn);
     const std::vector<Layer>& Ls = c->layers;

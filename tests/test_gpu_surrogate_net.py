@@ -362,3 +362,52 @@ def test_sparser_graph_keeps_the_pairs_within_its_radius(torch):
         sur.close()
     with pytest.raises(S.SphError):
         U.Surrogate(s.sim, layers=1, v_scale=1.0, radius=1.5)
+
+
+def test_graph_pairs_at_the_radius_follow_the_fp64_predicate(torch):
+    """The graph builder decides most candidates in FP32 and defers to the
+    FP64 predicate within 2^-12 of the radius: pairs placed at r (1 + delta),
+    delta from -3e-4 to 3e-4 down to 1e-12 and exactly 0, come out exactly as
+    the FP64 brute-force reference has them, for the full and a sparser
+    radius."""
+    rng = np.random.default_rng(77)
+    h = 0.026
+    cs = 2 * h
+    g = np.stack(np.meshgrid(np.arange(7), np.arange(6), np.arange(5), indexing="ij"), -1)
+    base = 0.5 + 3.0 * cs * g.reshape(-1, 3).astype(np.float64)
+    deltas = np.array([0.0, 1e-12, -1e-12, 1e-9, -1e-9, 1e-6, -1e-6, 1e-4, -1e-4, 3e-4, -3e-4])
+    for radius in (1.0, 0.5):
+        d = deltas[np.arange(base.shape[0]) % len(deltas)]
+        u = rng.normal(size=base.shape)
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        partner = base + (radius * cs * (1.0 + d))[:, None] * u
+        pos = np.concatenate([base, partner])
+        n = pos.shape[0]
+        case = cases.Case(name="radius", pos=pos, vel=np.zeros((n, 3), np.float32),
+                          rho=np.full(n, 1000.0, np.float32), ids=np.arange(n, dtype=np.uint32),
+                          n_bound=0, dp=h / 1.3, h=h, rho0=1000.0, c0=20.0, alpha=0.01, cfl=0.2,
+                          gravity=(0.0, 0.0, -9.81),
+                          dmin=tuple(float(v) for v in pos.min(0) - cs),
+                          dmax=tuple(float(v) for v in pos.max(0) + 2 * cs),
+                          fluid_height=float(pos[:, 2].max()))
+        sim = S.Simulation.from_case(case)
+        sim.build_cells()
+        sur = U.Surrogate(sim, layers=1, train=False, v_scale=1.0, radius=radius)
+        sur.set_params(so.init_params(1, seed=3))
+        hist = torch.zeros((n, 15), dtype=torch.float32, device="cuda")
+        acc = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        sur.forward(hist, acc)
+        sim.synchronize()
+        rowptr, col = sur.read_graph()
+        ids = sim.download()["ids"].astype(np.int64)
+        g_src = ids[np.repeat(np.arange(n), np.diff(rowptr.astype(np.int64)))]
+        g_dst = ids[col.astype(np.int64)]
+        order = np.lexsort((g_dst, g_src))
+        ref_src, ref_dst = so.graph(pos, radius * h)
+        assert np.array_equal(g_src[order], ref_src), radius
+        assert np.array_equal(g_dst[order], ref_dst), radius
+        # both sides of the radius occur
+        inside = ((pos[:base.shape[0]] - partner) ** 2).sum(1) < (2 * radius * h) ** 2
+        assert inside.any() and (~inside).any()
+        sur.close()
+        sim.close()
