@@ -72,9 +72,9 @@ __global__ void k_refresh(const float* __restrict__ w, int kin, int kout, __nv_b
 // (1 - 2^-12)) is inside and d2_32 >= `outside` (r2 (1 + 2^-12)) or not
 // finite is outside;
 // the caller widens both to "always ask FP64" for radii below 0.1 cell.
-// Candidates in between, and the features of the accepted edges, take the
-// FP64 arithmetic of the predicate as written.  FP64 instructions run at
-// 1/64 of the FP32 rate on this GPU.
+// Candidates in between take the FP64 arithmetic of the predicate as
+// written.  The edge features (bfloat16) come from the FP32 differences.
+// FP64 instructions run at 1/64 of the FP32 rate on this GPU.
 template <int MODE>
 __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const double* __restrict__ y,
                         const double* __restrict__ z, const float4* __restrict__ posc,
@@ -104,6 +104,7 @@ __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const do
     const int cy = (int)(t % (uint32_t)I.ncy), cz = (int)(t / (uint32_t)I.ncy);
     const double xi = x[i], yi = y[i], zi = z[i];
     const float4 pi = posc[i];
+    const float inv2hf = (float)inv2h;
     const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < I.ncx ? cx + 1 : I.ncx - 1;
     uint32_t c = 0, e = MODE ? rowptr[i] : 0u;
     for (int zz = cz - 1; zz <= cz + 1; ++zz) {
@@ -123,24 +124,26 @@ __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const do
                     const float d2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     // outside, or not finite (the FP64 predicate rejects those too)
                     if (!(d2f < outside)) continue;
-                    const bool sure = d2f < inside;
-                    double dx = 0.0, dy = 0.0, dz = 0.0, d2 = 0.0;
-                    if (MODE || !sure) {
-                        dx = __dsub_rn(xi, x[j]);
-                        dy = __dsub_rn(yi, y[j]);
-                        dz = __dsub_rn(zi, z[j]);
-                        d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                       __dmul_rn(dz, dz));
-                        if (!sure && !(d2 < r2)) continue;
+                    if (!(d2f < inside)) {
+                        const double dx = __dsub_rn(xi, x[j]);
+                        const double dy = __dsub_rn(yi, y[j]);
+                        const double dz = __dsub_rn(zi, z[j]);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                    __dmul_rn(dz, dz));
+                        if (!(d2 < r2)) continue;
                     }
                     if (MODE) {
+                        // the edge inputs are bfloat16: the FP32 differences (within
+                        // 3.6e-7 of a cell of the FP64 ones) round to the bfloat16 of
+                        // the FP64 value except where that lies within this error of
+                        // a rounding midpoint (one bfloat16 step then)
                         col[e] = j;
                         src[e] = i;
                         __nv_bfloat16* f = xe + (size_t)e * KIN;
-                        f[0] = __double2bfloat16(dx * inv2h);
-                        f[1] = __double2bfloat16(dy * inv2h);
-                        f[2] = __double2bfloat16(dz * inv2h);
-                        f[3] = __double2bfloat16(sqrt(d2) * inv2h);
+                        f[0] = __float2bfloat16_rn(fx * inv2hf);
+                        f[1] = __float2bfloat16_rn(fy * inv2hf);
+                        f[2] = __float2bfloat16_rn(fz * inv2hf);
+                        f[3] = __float2bfloat16_rn(sqrtf(d2f) * inv2hf);
 #pragma unroll
                         for (int q = 4; q < KIN; ++q) f[q] = __float2bfloat16_rn(0.f);
                         ++e;
