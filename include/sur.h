@@ -62,6 +62,20 @@ int sur_edge_layer(const void *d_E, const void *d_W1t, const void *d_W2t,
                    const void *d_Q, const uint32_t *d_src, const uint32_t *d_dst,
                    uint32_t M, void *d_Z, void *d_Eout, void *stream);
 
+/* The network's edge encoder (its first two layers) in one kernel, over M
+ * edges (all arrays device, 16-byte aligned):
+ *   z  = relu(X W1 + b1)   -> Z (M x 128 bf16; may be NULL)
+ *   E0 = z W2 + b2         -> Eout (M x 128 bf16)
+ * X: M x 16 bf16 edge features; W1t: 128 x 16 and W2t: 128 x 128 bf16 (the
+ * weights transposed: row n holds output n); b1, b2: float[128].  z is
+ * rounded to bf16 before the second product, so the results are those of
+ * two sur_linear calls (SUR_EPI_RELU, then SUR_EPI_NONE with bf16 output)
+ * without the round trip of z through memory.  Async on `stream`.
+ * SPH_ERR_INVALID_ARG for NULL or unaligned pointers. */
+int sur_edge_encoder(const void *d_X, const void *d_W1t, const void *d_W2t,
+                     const float *d_b1, const float *d_b2, uint32_t M, void *d_Z,
+                     void *d_Eout, void *stream);
+
 /* ---- the network -------------------------------------------------------
  * Nodes: the particles of an SPH context (sph.h) in its current sorted order,
  * with cells built.  Edges: every ordered pair within 2h (the FP64 predicate

@@ -80,4 +80,24 @@ int sur_edge_layer(const void* E, const void* W1t, const void* W2t, const float*
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }
 
+int sur_edge_encoder(const void* X, const void* W1t, const void* W2t, const float* b1,
+                     const float* b2, uint32_t M, void* Z, void* Eout, void* stream) {
+    if (!X || !W1t || !W2t || !b1 || !b2 || !Eout) return SPH_ERR_INVALID_ARG;
+    const void* ptrs[] = {X, W1t, W2t, Eout};
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16u) return SPH_ERR_INVALID_ARG;
+    if (Z && reinterpret_cast<uintptr_t>(Z) % 16u) return SPH_ERR_INVALID_ARG;
+    EdgeArgs g = {};
+    g.E = static_cast<const __nv_bfloat16*>(X);
+    g.W1t = static_cast<const __nv_bfloat16*>(W1t);
+    g.W2t = static_cast<const __nv_bfloat16*>(W2t);
+    g.b1 = b1;
+    g.b2 = b2;
+    g.M = M;
+    g.Z = static_cast<__nv_bfloat16*>(Z);
+    g.Eout = static_cast<__nv_bfloat16*>(Eout);
+    launch_edge_encoder(g, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
 }  // extern "C"

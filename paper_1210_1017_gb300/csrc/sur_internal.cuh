@@ -71,6 +71,9 @@ struct EdgeArgs {
 int num_sms();
 bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st);
 void launch_edge_layer(const EdgeArgs& g, cudaStream_t st);
+// The edge encoder in one kernel: E (M x 16) -> Eout = relu(E W1 + b1) W2 + b2
+// (z = relu(E W1 + b1) to Z when Z != null); P, Q, src, dst unused.
+void launch_edge_encoder(const EdgeArgs& g, cudaStream_t st);
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st);
 
 }  // namespace sur

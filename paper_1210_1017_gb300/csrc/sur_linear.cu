@@ -386,38 +386,45 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, in
 }
 
 
-// Fused edge update (see EdgeArgs): per 128-edge tile, tcgen05 MMA 1 (e W1c)
-// into TMEM columns [0, 128), the first epilogue writes z = relu(...) as the
-// K-major A operand of MMA 2 in shared memory (and to global memory for the
-// backward pass), MMA 2 (z W2) into columns [128, 256), and the second
-// epilogue adds the bias and the residual e, read back from the staged e
-// tile, so z is never re-read from HBM.  The e tile is double-buffered and
-// the gathered rows P[src], Q[dst] of the next tile are copied in with
-// cp.async while MMA 2 and the second epilogue run.
-constexpr size_t kEdgeSmem = (size_t)7 * 128 * 128 * 2;   // W1c, W2, z, 2 x e, P, Q
+// Fused two-layer edge MLP (see EdgeArgs), per 128-edge tile: tcgen05 MMA 1
+// (e W1) into TMEM columns [0, 128); the first epilogue writes z =
+// relu(...) as the K-major A operand of MMA 2 in shared memory (and to
+// global memory for the backward pass); MMA 2 (z W2) into columns
+// [128, 256); the second epilogue adds the bias (and, in a layer, the
+// residual e read back from the staged tile), so z is never re-read from
+// HBM.  Two forms:
+//   a message-passing layer's edge update (ENC = false, K1 = 128):
+//       z = relu(e W1c + b1 + P[src] + Q[dst]),  e' = e + z W2 + b2;
+//   the edge encoder (ENC = true, K1 = 16, the edge features x):
+//       z = relu(x W1 + b1),                     e0 = z W2 + b2.
+// In a layer, z overwrites the tile's P[src] rows in place (each thread
+// writes z where it read P), and that buffer is doubled: the e and P[src]
+// copies of the next tile are issued right after MMA 1, the Q[dst] copies
+// after the first epilogue, and the row indices of the tile after next are
+// loaded a whole tile ahead, so no copy waits for its index.  The NT / 128
+// warps that share a TMEM lane quarter (the tile's rows) split the 128
+// columns of each epilogue between them.
+template <bool ENC>
+__host__ __device__ constexpr int edge_k1() { return ENC ? 16 : 128; }
 
-__device__ __forceinline__ void issue_gather(unsigned char* dst, const __nv_bfloat16* table,
-                                             const uint32_t* idx, uint32_t row0, uint32_t nrows) {
-    // threads t and t + 128 copy row t of the tile: 8 pieces of 16 bytes each
-    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
-    const bool ok = row0 + r < nrows;
-    const __nv_bfloat16* p = ok ? table + (size_t)idx[row0 + r] * 128 : table;
-#pragma unroll
-    for (int gk = 8 * h; gk < 8 * h + 8; ++gk)
-        cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
+template <bool ENC>
+__host__ __device__ constexpr size_t edge_smem() {
+    // W1^T (128 x K1), W2^T, z (encoder) or 2 x P[src]/z and Q[dst] (layer), 2 x e (128 x K1)
+    return (size_t)128 * edge_k1<ENC>() * 2 * 3 + (size_t)128 * 128 * 2 * (ENC ? 2 : 4);
 }
 
-// issue_rows for a 256-thread block
-template <int K>
-__device__ __forceinline__ void issue_rows256(unsigned char* dst, const __nv_bfloat16* src,
-                                              uint32_t row0, uint32_t nrows, uint32_t ld) {
+// Rows of P[src] (or Q[dst]) for one tile: the NT / 128 threads of row
+// t = threadIdx.x % 128 copy its 16 pieces of 16 bytes from table row `row`
+// (zero-filled when !ok).
+template <int NT>
+__device__ __forceinline__ void issue_gather(unsigned char* dst, const __nv_bfloat16* table,
+                                             uint32_t row, bool ok) {
+    constexpr int PP = 16 / (NT / 128);
+    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
+    const __nv_bfloat16* p = ok ? table + (size_t)row * 128 : table;
 #pragma unroll
-    for (int c = threadIdx.x; c < 128 * (K / 8); c += 256) {
-        const int r = c & 127, gk = c >> 7;
-        const bool ok = row0 + r < nrows;
-        const __nv_bfloat16* p = ok ? src + (size_t)(row0 + r) * ld + gk * 8 : src;
-        cp_async16(dst + kmajor_offset(r, gk * 8, K), p, ok);
-    }
+    for (int gk = PP * h; gk < PP * h + PP; ++gk)
+        cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
 }
 
 __device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, float* f) {
@@ -425,18 +432,20 @@ __device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, 
     unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0 + 8, 128)), f + 8);
 }
 
-// 256 threads: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (the
-// tile's rows) and split the 128 columns of each epilogue between them.
-__global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
-    constexpr int K = 128, N = 128;
+template <bool ENC, int NT>
+__global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) {
+    constexpr int K1 = edge_k1<ENC>(), N = 128;
     constexpr uint32_t T = 128 * 128 * 2;          // bytes of one 128 x 128 bf16 tile
+    constexpr uint32_t T1 = 128 * K1 * 2;          // bytes of one 128 x K1 tile
+    constexpr int NG = NT / 128;                   // warps per TMEM lane quarter
+    constexpr int CW = N / NG;                     // epilogue columns per thread
+    static_assert(NT == 256 || NT == 512, "two or four warps per lane quarter");
     extern __shared__ __align__(128) unsigned char s_raw[];
-    unsigned char* sw1 = s_raw;                    // W1c^T, N x K
-    unsigned char* sw2 = sw1 + T;                  // W2^T
-    unsigned char* sz = sw2 + T;                   // z tile
-    unsigned char* sp = sz + T;                    // P[src] rows
-    unsigned char* sq = sp + T;                    // Q[dst] rows
-    unsigned char* sa0 = sq + T;                   // 2 x e tile
+    unsigned char* sw1 = s_raw;                    // W1^T, N x K1
+    unsigned char* sw2 = sw1 + T1;                 // W2^T, N x N
+    unsigned char* spz0 = sw2 + T;                 // z (encoder); 2 x P[src] rows, then z (layer)
+    unsigned char* sq = spz0 + (ENC ? T : 2 * T);  // Q[dst] rows (layer only)
+    unsigned char* sa0 = sq + (ENC ? 0 : T);       // 2 x e tile
     __shared__ __align__(16) float s_b1[128], s_b2[128];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
@@ -444,47 +453,78 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
     if (w == 0) tmem_alloc(&s_tmem, 256);
     if (tid == 0) mbar_init1(&s_bar);
     const uint32_t ntiles = (g.M + 127) / 128;
-    for (int c = tid; c < N * (K / 8); c += 256) {
+    for (int c = tid; c < N * (K1 / 8); c += NT) {
         const int r = c % N, gk = c / N;
-        cp_async16(sw1 + kmajor_offset(r, gk * 8, K), g.W1t + (size_t)r * K + gk * 8, true);
-        cp_async16(sw2 + kmajor_offset(r, gk * 8, K), g.W2t + (size_t)r * K + gk * 8, true);
+        cp_async16(sw1 + kmajor_offset(r, gk * 8, K1), g.W1t + (size_t)r * K1 + gk * 8, true);
+    }
+    for (int c = tid; c < N * (N / 8); c += NT) {
+        const int r = c % N, gk = c / N;
+        cp_async16(sw2 + kmajor_offset(r, gk * 8, N), g.W2t + (size_t)r * N + gk * 8, true);
     }
     if (tid < 128) {
         s_b1[tid] = g.b1[tid];
         s_b2[tid] = g.b2[tid];
     }
+    // gather row of this thread (issue_gather's row mapping) and the table
+    // rows of the next tile (loaded one tile ahead)
+    const uint32_t gr = (uint32_t)(tid & 127);
+    uint32_t nsrc = 0, ndst = 0;
     if (blockIdx.x < ntiles) {
-        issue_rows256<K>(sa0, g.E, blockIdx.x * 128, g.M, K);
-        issue_gather(sp, g.P, g.src, blockIdx.x * 128, g.M);
-        issue_gather(sq, g.Q, g.dst, blockIdx.x * 128, g.M);
+        issue_rows<K1, NT>(sa0, g.E, blockIdx.x * 128, g.M, K1);
+        if (!ENC) {
+            const uint32_t m0 = blockIdx.x * 128 + gr;
+            const bool ok0 = m0 < g.M;
+            issue_gather<NT>(spz0, g.P, ok0 ? g.src[m0] : 0u, ok0);
+            issue_gather<NT>(sq, g.Q, ok0 ? g.dst[m0] : 0u, ok0);
+            const uint32_t m1 = m0 + gridDim.x * 128;
+            if (m1 < g.M) {
+                nsrc = g.src[m1];
+                ndst = g.dst[m1];
+            }
+        }
     }
     cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int wq = w & 3, half = w >> 2;                 // lane quarter, column half
+    const int wq = w & 3, part = w >> 2;                 // lane quarter, column part
     const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
     uint32_t phase = 0, buf = 0;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= 1u) {
-        unsigned char* sa = sa0 + buf * T;
-        cp_async_wait_all();                       // e, P, Q of this tile
+        unsigned char* sa = sa0 + buf * T1;
+        unsigned char* spz = spz0 + (ENC ? 0u : buf * T);
+        cp_async_wait_all();                       // e (and P, Q) of this tile
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
 #pragma unroll
-            for (int s = 0; s < K / 16; ++s) {
-                const uint64_t ad = smem_desc(sm_addr(sa) + s * 256, kLBO, (K / 8) * 128);
-                const uint64_t bd = smem_desc(sm_addr(sw1) + s * 256, kLBO, (K / 8) * 128);
+            for (int s = 0; s < K1 / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sa) + s * 256, kLBO, (K1 / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw1) + s * 256, kLBO, (K1 / 8) * 128);
                 tc_mma(tmem, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
             }
             tc_commit(&s_bar);
         }
+        // the next tile's e and P[src] rows into the other buffers (their last
+        // readers, the previous tile's MMAs, have completed)
         const uint32_t next = tile + gridDim.x;
-        if (next < ntiles) issue_rows256<K>(sa0 + (buf ^ 1u) * T, g.E, next * 128, g.M, K);
+        const bool ok_next = next * 128 + gr < g.M;
+        if (next < ntiles) {
+            issue_rows<K1, NT>(sa0 + (buf ^ 1u) * T1, g.E, next * 128, g.M, K1);
+            if (!ENC) issue_gather<NT>(spz0 + (buf ^ 1u) * T, g.P, nsrc, ok_next);
+        }
         cp_async_commit();
+        uint32_t nsrc2 = 0, ndst2 = 0;             // rows of the tile after next
+        if (!ENC) {
+            const uint32_t m2 = (next + gridDim.x) * 128 + gr;
+            if (next + gridDim.x < ntiles && m2 < g.M) {
+                nsrc2 = __ldg(g.src + m2);
+                ndst2 = __ldg(g.dst + m2);
+            }
+        }
         const int r = wq * 32 + lane;              // this thread's row of the tile
         const uint32_t m = tile * 128 + r;
         const bool valid = m < g.M;
@@ -493,31 +533,32 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
         if (!ok) break;
         phase ^= 1u;
         tc_fence_after();
-        // epilogue 1: z = relu(acc + b1 + P[src] + Q[dst]) -> shared (MMA 2) and global
+        // epilogue 1: z = relu(acc + b1 [+ P[src] + Q[dst]]) -> shared (MMA 2; in
+        // a layer over the P[src] rows just read) and global
 #pragma unroll 2
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+        for (int c0 = part * CW; c0 < part * CW + CW; c0 += 16) {
+            // ((acc + b1) + P) + Q per element, two elements per packed FP32 add
             float v[16], t[16], u[16];
             tmem_ld16(lane_base + c0, v);
-            const float4* b4 = reinterpret_cast<const float4*>(s_b1 + c0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 b = b4[q];
-                v[4 * q] += b.x;
-                v[4 * q + 1] += b.y;
-                v[4 * q + 2] += b.z;
-                v[4 * q + 3] += b.w;
+            if (!ENC) {
+                lds16(spz, r, c0, t);
+                lds16(sq, r, c0, u);
             }
-            lds16(sp, r, c0, t);
-            lds16(sq, r, c0, u);
+            const float2* b2v = reinterpret_cast<const float2*>(s_b1 + c0);
             __nv_bfloat162 hh[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                hh[q] = __floats2bfloat162_rn(fmaxf(v[2 * q] + t[2 * q] + u[2 * q], 0.f),
-                                              fmaxf(v[2 * q + 1] + t[2 * q + 1] + u[2 * q + 1], 0.f));
+            for (int q = 0; q < 8; ++q) {
+                float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
+                if (!ENC) {
+                    a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
+                    a = __fadd2_rn(a, make_float2(u[2 * q], u[2 * q + 1]));
+                }
+                hh[q] = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+            }
             const uint4 z0 = *reinterpret_cast<uint4*>(&hh[0]);
             const uint4 z1 = *reinterpret_cast<uint4*>(&hh[4]);
-            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0, K)) = z0;
-            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0 + 8, K)) = z1;
+            *reinterpret_cast<uint4*>(spz + kmajor_offset(r, c0, N)) = z0;
+            *reinterpret_cast<uint4*>(spz + kmajor_offset(r, c0 + 8, N)) = z1;
             if (g.Z && valid) {
                 uint4* o = reinterpret_cast<uint4*>(g.Z + (size_t)m * N + c0);
                 o[0] = z0;
@@ -526,51 +567,46 @@ __global__ void __launch_bounds__(256, 1) k_edge_layer(const EdgeArgs g) {
         }
         fence_async_shared();
         tc_fence_before();
-        __syncthreads();                           // z complete; P, Q tiles free
+        __syncthreads();                           // z complete; the Q tile free
         if (tid == 0) {
             tc_fence_after();
 #pragma unroll
-            for (int s = 0; s < K / 16; ++s) {
-                const uint64_t ad = smem_desc(sm_addr(sz) + s * 256, kLBO, (K / 8) * 128);
-                const uint64_t bd = smem_desc(sm_addr(sw2) + s * 256, kLBO, (K / 8) * 128);
+            for (int s = 0; s < N / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(spz) + s * 256, kLBO, (N / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw2) + s * 256, kLBO, (N / 8) * 128);
                 tc_mma(tmem + 128, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
             }
             tc_commit(&s_bar);
         }
-        if (next < ntiles) {
-            issue_gather(sp, g.P, g.src, next * 128, g.M);
-            issue_gather(sq, g.Q, g.dst, next * 128, g.M);
-        }
+        if (!ENC && next < ntiles) issue_gather<NT>(sq, g.Q, ndst, ok_next);
         cp_async_commit();
         got = mbar_wait(&s_bar, phase);
         ok = __syncthreads_and(got) != 0;
         if (!ok) break;
         phase ^= 1u;
         tc_fence_after();
-        // epilogue 2: e' = e + acc + b2 (e from the staged tile)
+        // epilogue 2: e' = acc + b2 [+ e, from the staged tile]
 #pragma unroll 2
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+        for (int c0 = part * CW; c0 < part * CW + CW; c0 += 16) {
+            // (acc + b2) + e per element, two elements per packed FP32 add
             float v[16], t[16];
             tmem_ld16(lane_base + 128 + c0, v);
             if (!valid) continue;
-            const float4* b4 = reinterpret_cast<const float4*>(s_b2 + c0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 b = b4[q];
-                v[4 * q] += b.x;
-                v[4 * q + 1] += b.y;
-                v[4 * q + 2] += b.z;
-                v[4 * q + 3] += b.w;
-            }
-            lds16(sa, r, c0, t);
+            if (!ENC) lds16(sa, r, c0, t);
+            const float2* b2v = reinterpret_cast<const float2*>(s_b2 + c0);
             __nv_bfloat162 hh[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                hh[q] = __floats2bfloat162_rn(v[2 * q] + t[2 * q], v[2 * q + 1] + t[2 * q + 1]);
+            for (int q = 0; q < 8; ++q) {
+                float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
+                if (!ENC) a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
+                hh[q] = __floats2bfloat162_rn(a.x, a.y);
+            }
             uint4* o = reinterpret_cast<uint4*>(g.Eout + (size_t)m * N + c0);
             o[0] = *reinterpret_cast<uint4*>(&hh[0]);
             o[1] = *reinterpret_cast<uint4*>(&hh[4]);
         }
+        nsrc = nsrc2;
+        ndst = ndst2;
         tc_fence_before();
         __syncthreads();
     }
@@ -653,19 +689,27 @@ bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st) {
     return true;
 }
 
-void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) {
+// The layer form: one 512-thread block per SM (its 224 KB of shared memory);
+// the encoder form: two 256-thread blocks per SM (76 KB each, 256 of the
+// SM's 512 TMEM columns each).
+template <bool ENC, int NT, int PER_SM>
+void launch_edge_mlp(const EdgeArgs& g, cudaStream_t st) {
     static bool init = false;
-    const size_t smem = kEdgeSmem;
+    constexpr size_t smem = edge_smem<ENC>();
     if (!init) {
-        cudaFuncSetAttribute(k_edge_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_edge_mlp<ENC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         init = true;
     }
     if (g.M == 0) return;
     const uint32_t tiles = (g.M + 127) / 128;
-    uint32_t grid = (uint32_t)num_sms();   // one block per SM (224 KB of shared memory)
+    uint32_t grid = (uint32_t)(num_sms() * PER_SM);
     if (grid > tiles) grid = tiles;
-    k_edge_layer<<<grid, 256, smem, st>>>(g);
+    k_edge_mlp<ENC, NT><<<grid, NT, smem, st>>>(g);
 }
+
+void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) { launch_edge_mlp<false, 512, 1>(g, st); }
+
+void launch_edge_encoder(const EdgeArgs& g, cudaStream_t st) { launch_edge_mlp<true, 256, 2>(g, st); }
 
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st) {
     if (N == 128) launch_wgrad_t<128>(g, num_sms(), st);

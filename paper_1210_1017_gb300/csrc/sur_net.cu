@@ -139,13 +139,14 @@ __global__ void k_graph(const sph::Dev d, const double* __restrict__ x, const do
                         // a rounding midpoint (one bfloat16 step then)
                         col[e] = j;
                         src[e] = i;
-                        __nv_bfloat16* f = xe + (size_t)e * KIN;
-                        f[0] = __float2bfloat16_rn(fx * inv2hf);
-                        f[1] = __float2bfloat16_rn(fy * inv2hf);
-                        f[2] = __float2bfloat16_rn(fz * inv2hf);
-                        f[3] = __float2bfloat16_rn(sqrtf(d2f) * inv2hf);
-#pragma unroll
-                        for (int q = 4; q < KIN; ++q) f[q] = __float2bfloat16_rn(0.f);
+                        // one 32-byte row: (x, y, z, |r|) / 2h, then zeros
+                        const __nv_bfloat162 f01 = __floats2bfloat162_rn(fx * inv2hf, fy * inv2hf);
+                        const __nv_bfloat162 f23 =
+                            __floats2bfloat162_rn(fz * inv2hf, sqrtf(d2f) * inv2hf);
+                        uint4* f = reinterpret_cast<uint4*>(xe + (size_t)e * KIN);
+                        f[0] = make_uint4(*reinterpret_cast<const uint32_t*>(&f01),
+                                          *reinterpret_cast<const uint32_t*>(&f23), 0u, 0u);
+                        f[1] = make_uint4(0u, 0u, 0u, 0u);
                         ++e;
                     }
                     ++c;
@@ -531,7 +532,7 @@ size_t carve(sur_ctx* c, void* base) {
     c->xn = cv.take<__nv_bfloat16>(N * KIN);
     c->xe = cv.take<__nv_bfloat16>(E * KIN);
     c->en1 = cv.take<__nv_bfloat16>(N * L);
-    c->ee1 = cv.take<__nv_bfloat16>(E * L);
+    c->ee1 = train ? cv.take<__nv_bfloat16>(E * L) : nullptr;   // encoder hidden layer (backward only)
     const int nx = train ? NL + 1 : 2, ne = train ? NL + 1 : 2, nz = train ? NL : 0;
     c->XN.assign(nx, nullptr);
     c->Ebuf.assign(ne, nullptr);
@@ -614,6 +615,21 @@ void edge_layer(sur_ctx* c, const Layer& l1, const Layer& l2, const __nv_bfloat1
     g.Z = z;
     g.Eout = e_out;
     launch_edge_layer(g, c->st);
+}
+
+// The two edge-encoder layers in one kernel: e0 = relu(xe W + b) W' + b'
+// (the hidden activation kept for the backward pass when z != null).
+void edge_encoder(sur_ctx* c, const Layer& l1, const Layer& l2, __nv_bfloat16* z, __nv_bfloat16* e0) {
+    EdgeArgs g = {};
+    g.E = c->xe;
+    g.W1t = l1.Wt;
+    g.W2t = l2.Wt;
+    g.b1 = c->w + l1.b_off;
+    g.b2 = c->w + l2.b_off;
+    g.M = c->E;
+    g.Z = z;
+    g.Eout = e0;
+    launch_edge_encoder(g, c->st);
 }
 
 // grad of W (kin x kout) += X^T dY over M rows (X: M x kin with stride ldx,
@@ -727,8 +743,7 @@ int forward(sur_ctx* c, sph_ctx* s, const float* hist) {
     // encoders
     if ((rc = linear(c, c->xn, 0, Ls[0], false, n, kEpiRelu, nullptr, 0, c->en1, nullptr, L))) return rc;
     if ((rc = linear(c, c->en1, 0, Ls[1], false, n, kEpiNone, nullptr, 0, c->XN[0], nullptr, 2 * L))) return rc;
-    if ((rc = linear(c, c->xe, 0, Ls[2], false, E, kEpiRelu, nullptr, 0, c->ee1, nullptr, L))) return rc;
-    if ((rc = linear(c, c->ee1, 0, Ls[3], false, E, kEpiNone, nullptr, 0, c->Ebuf[0], nullptr, L))) return rc;
+    edge_encoder(c, Ls[2], Ls[3], train ? c->ee1 : nullptr, c->Ebuf[0]);
     // message passing
     for (int l = 0; l < c->NL; ++l) {
         __nv_bfloat16* xn_cur = c->XN[train ? l : l % 2];

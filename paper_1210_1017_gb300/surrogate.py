@@ -15,6 +15,7 @@ class SurConfig(C.Structure):
                 ("a_std", C.c_float * 3), ("dt_s", C.c_float), ("radius", C.c_float)]
 
 EXPORTED = ["sur_linear", "sur_wgrad_scratch_bytes", "sur_wgrad", "sur_edge_layer",
+            "sur_edge_encoder",
             "sur_param_count",
             "sur_query_bytes", "sur_init", "sur_set_params", "sur_get_params", "sur_get_grads",
             "sur_forward", "sur_backward", "sur_adam", "sur_advance", "sur_rollout", "sur_make_sample",
@@ -35,6 +36,7 @@ def lib():
         L.sur_wgrad_scratch_bytes.restype = u64
         L.sur_wgrad.argtypes = [vp, vp, u32, u32, C.c_float, vp, vp, u64, vp]
         L.sur_edge_layer.argtypes = [vp] * 9 + [u32, vp, vp, vp]
+        L.sur_edge_encoder.argtypes = [vp] * 5 + [u32, vp, vp, vp]
         PC = C.POINTER(SurConfig)
         f = C.c_float
         L.sur_param_count.argtypes = [PC]
@@ -83,6 +85,11 @@ def sur_edge_layer(E, W1t, W2t, b1, b2, P, Q, src, dst, M, Z, Eout, stream):
     _sph._check(lib().sur_edge_layer(_p(E), _p(W1t), _p(W2t), _p(b1), _p(b2), _p(P), _p(Q),
                                      _p(src), _p(dst), M, _p(Z), _p(Eout), stream),
                 what="sur_edge_layer")
+
+
+def sur_edge_encoder(X, W1t, W2t, b1, b2, M, Z, Eout, stream):
+    _sph._check(lib().sur_edge_encoder(_p(X), _p(W1t), _p(W2t), _p(b1), _p(b2), M, _p(Z),
+                                       _p(Eout), stream), what="sur_edge_encoder")
 
 
 def _chk(rc, ctx, what):

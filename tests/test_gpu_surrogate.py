@@ -130,3 +130,36 @@ def test_fused_edge_layer_matches_numpy(torch, M):
     U.sur_edge_layer(E, W1t, W2t, b1, b2, P, Q, d_src, d_dst, M, None, Eo2, st.cuda_stream)
     st.synchronize()
     assert torch.equal(Eo, Eo2)
+
+
+@pytest.mark.parametrize("M", [1, 300, 5000, 100003])
+def test_fused_edge_encoder_equals_two_linear_calls(torch, M):
+    """The fused edge encoder, z = relu(X W1 + b1) (bf16), E0 = z W2 + b2
+    (bf16), bit for bit against the same two layers as separate sur_linear
+    calls (same MMA chains, same bf16 rounding of z), and E0 within its
+    rounding of numpy in float64 on the GPU's own z."""
+    rng = np.random.default_rng(M + 17)
+    X = _bf16(torch, rng.normal(size=(M, 16)))
+    W1 = rng.normal(size=(16, 128)) / 4.0
+    W2 = rng.normal(size=(128, 128)) / 11.3
+    W1t, W2t = _bf16(torch, W1.T), _bf16(torch, W2.T)
+    b1 = torch.tensor(rng.normal(size=128).astype(np.float32)).cuda()
+    b2 = torch.tensor(rng.normal(size=128).astype(np.float32)).cuda()
+    st = torch.cuda.current_stream()
+    Z = torch.empty((M, 128), dtype=torch.bfloat16, device="cuda")
+    E0 = torch.empty((M, 128), dtype=torch.bfloat16, device="cuda")
+    U.sur_edge_encoder(X, W1t, W2t, b1, b2, M, Z, E0, st.cuda_stream)
+    Z_ref = torch.empty_like(Z)
+    E0_ref = torch.empty_like(E0)
+    U.sur_linear(X, W1t, b1, M, 16, 128, U.SUR_EPI_RELU, None, Z_ref, None, st.cuda_stream)
+    U.sur_linear(Z_ref, W2t, b2, M, 128, 128, U.SUR_EPI_NONE, None, E0_ref, None, st.cuda_stream)
+    E0b = torch.empty_like(E0)
+    U.sur_edge_encoder(X, W1t, W2t, b1, b2, M, None, E0b, st.cuda_stream)
+    st.synchronize()
+    assert torch.equal(Z, Z_ref)
+    assert torch.equal(E0, E0_ref)
+    assert torch.equal(E0, E0b)
+    z, w2 = _np(Z), _np(W2t).T
+    ref = z @ w2 + b2.cpu().numpy()
+    scale = np.abs(z) @ np.abs(w2) + np.abs(b2.cpu().numpy())
+    assert np.all(np.abs(_np(E0) - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * scale)
