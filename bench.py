@@ -770,7 +770,7 @@ def run_surrogate(args):
             "edges_per_s": n_edges * args.steps / sur_s,
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
                          "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None,
-                         "kernel": (f"k_edge_mlp (fused edge update of a layer), {M >> 20}M edges, "
+                         "kernel": (f"k_edge_pp (fused edge update of a layer), {M >> 20}M edges, "
                                     f"{nodes >> 10}k nodes"),
                          "ms_per_launch": round(t_gemm * 1e3, 4)},
             "gpu_launches": None, "clocks": clocks, "peaks_source": src_pk}

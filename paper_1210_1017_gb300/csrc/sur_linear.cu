@@ -386,66 +386,27 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, int nparts, in
 }
 
 
-// Fused two-layer edge MLP (see EdgeArgs), per 128-edge tile: tcgen05 MMA 1
-// (e W1) into TMEM columns [0, 128); the first epilogue writes z =
-// relu(...) as the K-major A operand of MMA 2 in shared memory (and to
-// global memory for the backward pass); MMA 2 (z W2) into columns
-// [128, 256); the second epilogue adds the bias (and, in a layer, the
-// residual e read back from the staged tile), so z is never re-read from
-// HBM.  Two forms:
-//   a message-passing layer's edge update (ENC = false, K1 = 128):
-//       z = relu(e W1c + b1 + P[src] + Q[dst]),  e' = e + z W2 + b2;
-//   the edge encoder (ENC = true, K1 = 16, the edge features x):
-//       z = relu(x W1 + b1),                     e0 = z W2 + b2.
-// In a layer, z overwrites the tile's P[src] rows in place (each thread
-// writes z where it read P), and that buffer is doubled: the e and P[src]
-// copies of the next tile are issued right after MMA 1, the Q[dst] copies
-// after the first epilogue, and the row indices of the tile after next are
-// loaded a whole tile ahead, so no copy waits for its index.  The NT / 128
-// warps that share a TMEM lane quarter (the tile's rows) split the 128
-// columns of each epilogue between them.
-template <bool ENC>
-__host__ __device__ constexpr int edge_k1() { return ENC ? 16 : 128; }
+// The network's edge encoder (its two edge layers) in one kernel, per
+// 128-edge tile: tcgen05 MMA 1 (x W1, K = 16: the edge features) into TMEM
+// columns [0, 128); the first epilogue writes z = relu(acc + b1) as the
+// K-major A operand of MMA 2 in shared memory (and to global memory for the
+// backward pass); MMA 2 (z W2) into columns [128, 256); the second epilogue
+// writes e0 = acc + b2.  z never reaches HBM in inference.  The x tile is
+// double-buffered (the next tile's copies in flight during this one).  256
+// threads, two blocks per SM (76 KB of shared memory and 256 TMEM columns
+// each): the two warps that share a TMEM lane quarter split the columns.
+constexpr int kEncK = 16;
+constexpr size_t kEncSmem = (size_t)128 * kEncK * 2 * 3 + (size_t)128 * 128 * 2 * 2;   // W1, 2 x x; W2, z
 
-template <bool ENC>
-__host__ __device__ constexpr size_t edge_smem() {
-    // W1^T (128 x K1), W2^T, z (encoder) or 2 x P[src]/z and Q[dst] (layer), 2 x e (128 x K1)
-    return (size_t)128 * edge_k1<ENC>() * 2 * 3 + (size_t)128 * 128 * 2 * (ENC ? 2 : 4);
-}
-
-// Rows of P[src] (or Q[dst]) for one tile: the NT / 128 threads of row
-// t = threadIdx.x % 128 copy its 16 pieces of 16 bytes from table row `row`
-// (zero-filled when !ok).
-template <int NT>
-__device__ __forceinline__ void issue_gather(unsigned char* dst, const __nv_bfloat16* table,
-                                             uint32_t row, bool ok) {
-    constexpr int PP = 16 / (NT / 128);
-    const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
-    const __nv_bfloat16* p = ok ? table + (size_t)row * 128 : table;
-#pragma unroll
-    for (int gk = PP * h; gk < PP * h + PP; ++gk)
-        cp_async16(dst + kmajor_offset(r, gk * 8, 128), p + gk * 8, ok);
-}
-
-__device__ __forceinline__ void lds16(const unsigned char* tile, int r, int c0, float* f) {
-    unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0, 128)), f);
-    unpack8(*reinterpret_cast<const uint4*>(tile + kmajor_offset(r, c0 + 8, 128)), f + 8);
-}
-
-template <bool ENC, int NT>
-__global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) {
-    constexpr int K1 = edge_k1<ENC>(), N = 128;
+__global__ void __launch_bounds__(256, 2) k_edge_encoder(const EdgeArgs g) {
+    constexpr int K1 = kEncK, N = 128, NT = 256, CW = 64;   // CW: epilogue columns per thread
     constexpr uint32_t T = 128 * 128 * 2;          // bytes of one 128 x 128 bf16 tile
     constexpr uint32_t T1 = 128 * K1 * 2;          // bytes of one 128 x K1 tile
-    constexpr int NG = NT / 128;                   // warps per TMEM lane quarter
-    constexpr int CW = N / NG;                     // epilogue columns per thread
-    static_assert(NT == 256 || NT == 512, "two or four warps per lane quarter");
     extern __shared__ __align__(128) unsigned char s_raw[];
     unsigned char* sw1 = s_raw;                    // W1^T, N x K1
     unsigned char* sw2 = sw1 + T1;                 // W2^T, N x N
-    unsigned char* spz0 = sw2 + T;                 // z (encoder); 2 x P[src] rows, then z (layer)
-    unsigned char* sq = spz0 + (ENC ? T : 2 * T);  // Q[dst] rows (layer only)
-    unsigned char* sa0 = sq + (ENC ? 0 : T);       // 2 x e tile
+    unsigned char* sz = sw2 + T;                   // z tile
+    unsigned char* sa0 = sz + T;                   // 2 x x tile
     __shared__ __align__(16) float s_b1[128], s_b2[128];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
@@ -465,37 +426,19 @@ __global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) 
         s_b1[tid] = g.b1[tid];
         s_b2[tid] = g.b2[tid];
     }
-    // gather row of this thread (issue_gather's row mapping) and the table
-    // rows of the next tile (loaded one tile ahead)
-    const uint32_t gr = (uint32_t)(tid & 127);
-    uint32_t nsrc = 0, ndst = 0;
-    if (blockIdx.x < ntiles) {
-        issue_rows<K1, NT>(sa0, g.E, blockIdx.x * 128, g.M, K1);
-        if (!ENC) {
-            const uint32_t m0 = blockIdx.x * 128 + gr;
-            const bool ok0 = m0 < g.M;
-            issue_gather<NT>(spz0, g.P, ok0 ? g.src[m0] : 0u, ok0);
-            issue_gather<NT>(sq, g.Q, ok0 ? g.dst[m0] : 0u, ok0);
-            const uint32_t m1 = m0 + gridDim.x * 128;
-            if (m1 < g.M) {
-                nsrc = g.src[m1];
-                ndst = g.dst[m1];
-            }
-        }
-    }
+    if (blockIdx.x < ntiles) issue_rows<K1, NT>(sa0, g.E, blockIdx.x * 128, g.M, K1);
     cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int wq = w & 3, part = w >> 2;                 // lane quarter, column part
+    const int wq = w & 3, part = w >> 2;                 // lane quarter, column half
     const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
     uint32_t phase = 0, buf = 0;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, buf ^= 1u) {
         unsigned char* sa = sa0 + buf * T1;
-        unsigned char* spz = spz0 + (ENC ? 0u : buf * T);
-        cp_async_wait_all();                       // e (and P, Q) of this tile
+        cp_async_wait_all();                       // x of this tile (and the weights)
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
@@ -508,23 +451,11 @@ __global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) 
             }
             tc_commit(&s_bar);
         }
-        // the next tile's e and P[src] rows into the other buffers (their last
-        // readers, the previous tile's MMAs, have completed)
+        // the next tile's x into the other buffer (its last reader, the
+        // previous tile's MMA 1, has completed)
         const uint32_t next = tile + gridDim.x;
-        const bool ok_next = next * 128 + gr < g.M;
-        if (next < ntiles) {
-            issue_rows<K1, NT>(sa0 + (buf ^ 1u) * T1, g.E, next * 128, g.M, K1);
-            if (!ENC) issue_gather<NT>(spz0 + (buf ^ 1u) * T, g.P, nsrc, ok_next);
-        }
+        if (next < ntiles) issue_rows<K1, NT>(sa0 + (buf ^ 1u) * T1, g.E, next * 128, g.M, K1);
         cp_async_commit();
-        uint32_t nsrc2 = 0, ndst2 = 0;             // rows of the tile after next
-        if (!ENC) {
-            const uint32_t m2 = (next + gridDim.x) * 128 + gr;
-            if (next + gridDim.x < ntiles && m2 < g.M) {
-                nsrc2 = __ldg(g.src + m2);
-                ndst2 = __ldg(g.dst + m2);
-            }
-        }
         const int r = wq * 32 + lane;              // this thread's row of the tile
         const uint32_t m = tile * 128 + r;
         const bool valid = m < g.M;
@@ -533,26 +464,223 @@ __global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) 
         if (!ok) break;
         phase ^= 1u;
         tc_fence_after();
-        // epilogue 1: z = relu(acc + b1 [+ P[src] + Q[dst]]) -> shared (MMA 2; in
-        // a layer over the P[src] rows just read) and global
+        // epilogue 1: z = relu(acc + b1) -> shared (MMA 2) and global
 #pragma unroll 2
         for (int c0 = part * CW; c0 < part * CW + CW; c0 += 16) {
-            // ((acc + b1) + P) + Q per element, two elements per packed FP32 add
-            float v[16], t[16], u[16];
+            float v[16];
             tmem_ld16(lane_base + c0, v);
-            if (!ENC) {
-                lds16(spz, r, c0, t);
-                lds16(sq, r, c0, u);
+            const float2* b2v = reinterpret_cast<const float2*>(s_b1 + c0);
+            __nv_bfloat162 hh[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
+                hh[q] = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
             }
+            const uint4 z0 = *reinterpret_cast<uint4*>(&hh[0]);
+            const uint4 z1 = *reinterpret_cast<uint4*>(&hh[4]);
+            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0, N)) = z0;
+            *reinterpret_cast<uint4*>(sz + kmajor_offset(r, c0 + 8, N)) = z1;
+            if (g.Z && valid) {
+                uint4* o = reinterpret_cast<uint4*>(g.Z + (size_t)m * N + c0);
+                o[0] = z0;
+                o[1] = z1;
+            }
+        }
+        fence_async_shared();
+        tc_fence_before();
+        __syncthreads();                           // z complete
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < N / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(sz) + s * 256, kLBO, (N / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw2) + s * 256, kLBO, (N / 8) * 128);
+                tc_mma(tmem + 128, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
+            }
+            tc_commit(&s_bar);
+        }
+        got = mbar_wait(&s_bar, phase);
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 2: e0 = acc + b2
+#pragma unroll 2
+        for (int c0 = part * CW; c0 < part * CW + CW; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_base + 128 + c0, v);
+            if (!valid) continue;
+            const float2* b2v = reinterpret_cast<const float2*>(s_b2 + c0);
+            __nv_bfloat162 hh[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
+                hh[q] = __floats2bfloat162_rn(a.x, a.y);
+            }
+            uint4* o = reinterpret_cast<uint4*>(g.Eout + (size_t)m * N + c0);
+            o[0] = *reinterpret_cast<uint4*>(&hh[0]);
+            o[1] = *reinterpret_cast<uint4*>(&hh[4]);
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0 && g.status) atomicOr(g.status, 1u);
+    cp_async_wait_all();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, 256);
+}
+
+// Named barrier of one half of a 512-thread block (ids 1 and 2, 256 threads),
+// and its AND-reduction over a predicate.
+__device__ __forceinline__ void half_sync(int h) {
+    asm volatile("bar.sync %0, 256;" ::"r"(h + 1) : "memory");
+}
+
+__device__ __forceinline__ bool half_and(int h, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 256, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(h + 1)
+        : "memory");
+    return r != 0;
+}
+
+// The fused edge update of a message-passing layer, per 128-edge tile:
+//   z = relu(e W1c + b1 + P[src] + Q[dst]),  e' = e + z W2 + b2
+// (MMA 1 into TMEM, z written as MMA 2's K-major operand in shared memory and
+// to Z when training, MMA 2, the residual e read back from the staged tile),
+// as two independent halves of 256 threads that share the weights: half h
+// takes the tiles 2 b + h, 2 b + h + 2 grid, ... of block b with its own
+// mbarrier, its own 256 TMEM columns (accumulators of MMA 1 and MMA 2) and
+// its own named barrier, so one half's MMAs, copies and barriers overlap the
+// other half's epilogues.  Per half: the e tile, and the P[src] rows that z
+// overwrites; the Q[dst] rows go to registers (each thread's row and 64
+// columns), loaded while MMA 2 and the second epilogue run.  The next tile's
+// e and P[src] copies are issued at the end of a tile, the row indices a
+// tile ahead.
+constexpr size_t kEdgePPSmem = (size_t)6 * 128 * 128 * 2;   // W1c, W2, 2 x (e, P/z)
+
+__global__ void __launch_bounds__(512, 1) k_edge_pp(const EdgeArgs g) {
+    constexpr int N = 128;
+    constexpr uint32_t T = 128 * 128 * 2;
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    __shared__ __align__(16) float s_b1[128], s_b2[128];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int h = tid >> 8, lt = tid & 255;              // half, thread within the half
+    unsigned char* sw1 = s_raw;                          // W1c^T
+    unsigned char* sw2 = s_raw + T;                      // W2^T
+    unsigned char* se = s_raw + (2 + h) * T;             // e tile of this half
+    unsigned char* spz = s_raw + (4 + h) * T;            // P[src] rows, then z
+    if (w == 0) tmem_alloc(&s_tmem, 512);
+    if (tid == 0) {
+        mbar_init1(&s_bar[0]);
+        mbar_init1(&s_bar[1]);
+    }
+    for (int c = tid; c < N * (N / 8); c += 512) {
+        const int r = c % N, gk = c / N;
+        cp_async16(sw1 + kmajor_offset(r, gk * 8, N), g.W1t + (size_t)r * N + gk * 8, true);
+        cp_async16(sw2 + kmajor_offset(r, gk * 8, N), g.W2t + (size_t)r * N + gk * 8, true);
+    }
+    if (tid < 128) {
+        s_b1[tid] = g.b1[tid];
+        s_b2[tid] = g.b2[tid];
+    }
+    const uint32_t ntiles = (g.M + 127) / 128;
+    const uint32_t stride = 2 * gridDim.x;
+    const int wq = w & 3, part = (w >> 2) & 1;           // lane quarter, column half
+    const int r = wq * 32 + lane;                        // epilogue row of this thread
+    const uint32_t gr = (uint32_t)(lt & 127);            // gather row of this thread
+    const int gh = lt >> 7;                              // its half of the row's pieces
+    // copies of one tile's e and P[src] rows by this half
+    auto issue_tile = [&](uint32_t t, uint32_t srow) {
+#pragma unroll
+        for (int c = lt; c < 128 * (N / 8); c += 256) {
+            const int rr = c & 127, gk = c >> 7;
+            const bool ok = t * 128 + rr < g.M;
+            const __nv_bfloat16* p = ok ? g.E + (size_t)(t * 128 + rr) * N + gk * 8 : g.E;
+            cp_async16(se + kmajor_offset(rr, gk * 8, N), p, ok);
+        }
+        const bool ok = t * 128 + gr < g.M;
+        const __nv_bfloat16* p = ok ? g.P + (size_t)srow * N : g.P;
+#pragma unroll
+        for (int gk = 8 * gh; gk < 8 * gh + 8; ++gk)
+            cp_async16(spz + kmajor_offset(gr, gk * 8, N), p + gk * 8, ok);
+    };
+    // this thread's 64 columns of one Q[dst] row
+    uint4 qv[8];
+    auto load_q = [&](uint32_t t, uint32_t drow) {
+        const bool ok = t * 128 + r < g.M;
+        const uint4* q = reinterpret_cast<const uint4*>(g.Q + (size_t)(ok ? drow : 0u) * N + part * 64);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) qv[k] = ok ? __ldg(q + k) : make_uint4(0u, 0u, 0u, 0u);
+    };
+    uint32_t tile = 2 * blockIdx.x + (uint32_t)h;
+    uint32_t nsrc = 0, ndst = 0;                         // rows of the half's next tile
+    if (tile < ntiles) {
+        const uint32_t mg = tile * 128 + gr, me = tile * 128 + (uint32_t)r;
+        issue_tile(tile, mg < g.M ? g.src[mg] : 0u);
+        load_q(tile, me < g.M ? g.dst[me] : 0u);
+        const uint32_t nt = tile + stride;
+        if (nt < ntiles) {
+            if (nt * 128 + gr < g.M) nsrc = g.src[nt * 128 + gr];
+            if (nt * 128 + (uint32_t)r < g.M) ndst = g.dst[nt * 128 + r];
+        }
+    }
+    cp_async_commit();
+    cp_async_wait_all();                                 // weights of both halves, first tiles
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem + (uint32_t)(h * 256);
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (; tile < ntiles && ok; tile += stride) {
+        cp_async_wait_all();                             // e, P[src] of this tile
+        fence_async_shared();
+        tc_fence_before();
+        half_sync(h);
+        if (lt == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < N / 16; ++s) {
+                const uint64_t ad = smem_desc(sm_addr(se) + s * 256, kLBO, (N / 8) * 128);
+                const uint64_t bd = smem_desc(sm_addr(sw1) + s * 256, kLBO, (N / 8) * 128);
+                tc_mma(tmem, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
+            }
+            tc_commit(&s_bar[h]);
+        }
+        const uint32_t m = tile * 128 + (uint32_t)r;
+        const bool valid = m < g.M;
+        const uint32_t next = tile + stride;
+        bool got = mbar_wait(&s_bar[h], phase);
+        ok = half_and(h, got);
+        if (!ok) break;
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 1: z = relu(((acc + b1) + P[src]) + Q[dst]) over the P rows, and to Z
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c0 = part * 64 + 16 * k;
+            float v[16];
+            tmem_ld16(lane_base + c0, v);
+            float t[16], u[16];
+            unpack8(*reinterpret_cast<const uint4*>(spz + kmajor_offset(r, c0, N)), t);
+            unpack8(*reinterpret_cast<const uint4*>(spz + kmajor_offset(r, c0 + 8, N)), t + 8);
+            unpack8(qv[2 * k], u);
+            unpack8(qv[2 * k + 1], u + 8);
             const float2* b2v = reinterpret_cast<const float2*>(s_b1 + c0);
             __nv_bfloat162 hh[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
-                if (!ENC) {
-                    a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
-                    a = __fadd2_rn(a, make_float2(u[2 * q], u[2 * q + 1]));
-                }
+                a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
+                a = __fadd2_rn(a, make_float2(u[2 * q], u[2 * q + 1]));
                 hh[q] = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
             }
             const uint4 z0 = *reinterpret_cast<uint4*>(&hh[0]);
@@ -567,8 +695,8 @@ __global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) 
         }
         fence_async_shared();
         tc_fence_before();
-        __syncthreads();                           // z complete; the Q tile free
-        if (tid == 0) {
+        half_sync(h);                                    // z complete
+        if (lt == 0) {
             tc_fence_after();
 #pragma unroll
             for (int s = 0; s < N / 16; ++s) {
@@ -576,44 +704,56 @@ __global__ void __launch_bounds__(NT, ENC ? 2 : 1) k_edge_mlp(const EdgeArgs g) 
                 const uint64_t bd = smem_desc(sm_addr(sw2) + s * 256, kLBO, (N / 8) * 128);
                 tc_mma(tmem + 128, ad, bd, idesc_bf16(N), s > 0 ? 1u : 0u);
             }
-            tc_commit(&s_bar);
+            tc_commit(&s_bar[h]);
         }
-        if (!ENC && next < ntiles) issue_gather<NT>(sq, g.Q, ndst, ok_next);
-        cp_async_commit();
-        got = mbar_wait(&s_bar, phase);
-        ok = __syncthreads_and(got) != 0;
+        // the next tile's Q[dst] rows into registers, the rows of the one after
+        uint32_t nsrc2 = 0, ndst2 = 0;
+        if (next < ntiles) {
+            load_q(next, ndst);
+            const uint32_t n2 = next + stride;
+            if (n2 < ntiles) {
+                if (n2 * 128 + gr < g.M) nsrc2 = __ldg(g.src + n2 * 128 + gr);
+                if (n2 * 128 + (uint32_t)r < g.M) ndst2 = __ldg(g.dst + n2 * 128 + r);
+            }
+        }
+        got = mbar_wait(&s_bar[h], phase);
+        ok = half_and(h, got);
         if (!ok) break;
         phase ^= 1u;
         tc_fence_after();
-        // epilogue 2: e' = acc + b2 [+ e, from the staged tile]
-#pragma unroll 2
-        for (int c0 = part * CW; c0 < part * CW + CW; c0 += 16) {
-            // (acc + b2) + e per element, two elements per packed FP32 add
-            float v[16], t[16];
+        // epilogue 2: e' = (acc + b2) + e
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c0 = part * 64 + 16 * k;
+            float v[16];
             tmem_ld16(lane_base + 128 + c0, v);
             if (!valid) continue;
-            if (!ENC) lds16(sa, r, c0, t);
+            float t[16];
+            unpack8(*reinterpret_cast<const uint4*>(se + kmajor_offset(r, c0, N)), t);
+            unpack8(*reinterpret_cast<const uint4*>(se + kmajor_offset(r, c0 + 8, N)), t + 8);
             const float2* b2v = reinterpret_cast<const float2*>(s_b2 + c0);
             __nv_bfloat162 hh[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 float2 a = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2v[q]);
-                if (!ENC) a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
+                a = __fadd2_rn(a, make_float2(t[2 * q], t[2 * q + 1]));
                 hh[q] = __floats2bfloat162_rn(a.x, a.y);
             }
             uint4* o = reinterpret_cast<uint4*>(g.Eout + (size_t)m * N + c0);
             o[0] = *reinterpret_cast<uint4*>(&hh[0]);
             o[1] = *reinterpret_cast<uint4*>(&hh[4]);
         }
+        tc_fence_before();
+        half_sync(h);                                    // e and z tiles free
+        if (next < ntiles) issue_tile(next, nsrc);
+        cp_async_commit();
         nsrc = nsrc2;
         ndst = ndst2;
-        tc_fence_before();
-        __syncthreads();
     }
-    if (!ok && tid == 0 && g.status) atomicOr(g.status, 1u);
+    if (!ok && lt == 0 && g.status) atomicOr(g.status, 1u);
     cp_async_wait_all();
     __syncthreads();
-    if (w == 0) tmem_dealloc(tmem, 256);
+    if (w == 0) tmem_dealloc(s_tmem, 512);
 }
 
 template <int K, int N>
@@ -689,27 +829,34 @@ bool launch_linear(int K, int N, const LinearArgs& g, cudaStream_t st) {
     return true;
 }
 
-// The layer form: one 512-thread block per SM (its 224 KB of shared memory);
-// the encoder form: two 256-thread blocks per SM (76 KB each, 256 of the
-// SM's 512 TMEM columns each).
-template <bool ENC, int NT, int PER_SM>
-void launch_edge_mlp(const EdgeArgs& g, cudaStream_t st) {
+// The layer: two halves per block, one block per SM (192 KB of shared memory,
+// the SM's 512 TMEM columns).
+void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) {
     static bool init = false;
-    constexpr size_t smem = edge_smem<ENC>();
     if (!init) {
-        cudaFuncSetAttribute(k_edge_mlp<ENC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_edge_pp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEdgePPSmem);
         init = true;
     }
     if (g.M == 0) return;
     const uint32_t tiles = (g.M + 127) / 128;
-    uint32_t grid = (uint32_t)(num_sms() * PER_SM);
-    if (grid > tiles) grid = tiles;
-    k_edge_mlp<ENC, NT><<<grid, NT, smem, st>>>(g);
+    uint32_t grid = (uint32_t)num_sms();
+    if (grid > (tiles + 1) / 2) grid = (tiles + 1) / 2;
+    k_edge_pp<<<grid, 512, kEdgePPSmem, st>>>(g);
 }
 
-void launch_edge_layer(const EdgeArgs& g, cudaStream_t st) { launch_edge_mlp<false, 512, 1>(g, st); }
-
-void launch_edge_encoder(const EdgeArgs& g, cudaStream_t st) { launch_edge_mlp<true, 256, 2>(g, st); }
+// The encoder: two 256-thread blocks per SM.
+void launch_edge_encoder(const EdgeArgs& g, cudaStream_t st) {
+    static bool init = false;
+    if (!init) {
+        cudaFuncSetAttribute(k_edge_encoder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEncSmem);
+        init = true;
+    }
+    if (g.M == 0) return;
+    const uint32_t tiles = (g.M + 127) / 128;
+    uint32_t grid = (uint32_t)(num_sms() * 2);
+    if (grid > tiles) grid = tiles;
+    k_edge_encoder<<<grid, 256, kEncSmem, st>>>(g);
+}
 
 bool launch_wgrad(int N, const WgradArgs& g, cudaStream_t st) {
     if (N == 128) launch_wgrad_t<128>(g, num_sms(), st);
