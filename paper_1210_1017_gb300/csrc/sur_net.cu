@@ -203,13 +203,28 @@ __global__ void k_rowsum(uint32_t n, const uint32_t* __restrict__ rowptr, const 
     const uint32_t node = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (node >= n) return;
+    // each lane sums its 4 columns over the node's edges in edge order; one
+    // 8-byte (bf16) or 16-byte (fp32) load per edge and lane, several edges
+    // in flight
     float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (uint32_t k = rowptr[node]; k < rowptr[node + 1]; ++k) {
+    const uint32_t k0 = rowptr[node], k1 = rowptr[node + 1];
+#pragma unroll 4
+    for (uint32_t k = k0; k < k1; ++k) {
         const uint32_t ed = perm ? perm[k] : k;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if constexpr (sizeof(T) == 2) s[q] += __bfloat162float(e[(size_t)ed * L + lane * 4 + q]);
-            else s[q] += e[(size_t)ed * L + lane * 4 + q];
+        if constexpr (sizeof(T) == 2) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2*>(e + (size_t)ed * L) + lane);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+            s[0] += a.x;
+            s[1] += a.y;
+            s[2] += b.x;
+            s[3] += b.y;
+        } else {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(e + (size_t)ed * L) + lane);
+            s[0] += u.x;
+            s[1] += u.y;
+            s[2] += u.z;
+            s[3] += u.w;
         }
     }
 #pragma unroll

@@ -91,11 +91,14 @@ def test_wgrad_matches_numpy(torch, N, M):
     assert torch.equal(dW, dW2)
 
 
-@pytest.mark.parametrize("M", [1, 300, 5000, 70001])
+@pytest.mark.parametrize("M", [1, 300, 5000, 70001, 600011])
 def test_fused_edge_layer_matches_numpy(torch, M):
     """z = relu(E W1 + b1 + P[src] + Q[dst]) (bf16), E' = E + z W2 + b2 (bf16),
     against numpy in float64 on the same bf16 inputs; z within one bf16
-    rounding of the reference, E' within its rounding plus the effect of z's."""
+    rounding of the reference, E' within its rounding plus the effect of z's.
+    The sizes cover one tile, a grid smaller than the SMs with a half-block
+    idle, a ragged last tile, and (600011 edges) many tiles per half-block,
+    so the row indices loaded a tile ahead are used on every path."""
     rng = np.random.default_rng(M)
     nodes = max(2, M // 7)
     E = _bf16(torch, rng.normal(size=(M, 128)))
@@ -132,7 +135,7 @@ def test_fused_edge_layer_matches_numpy(torch, M):
     assert torch.equal(Eo, Eo2)
 
 
-@pytest.mark.parametrize("M", [1, 300, 5000, 100003])
+@pytest.mark.parametrize("M", [1, 300, 5000, 100003, 600011])
 def test_fused_edge_encoder_equals_two_linear_calls(torch, M):
     """The fused edge encoder, z = relu(X W1 + b1) (bf16), E0 = z W2 + b2
     (bf16), bit for bit against the same two layers as separate sur_linear
