@@ -557,9 +557,9 @@ __device__ __forceinline__ bool half_and(int h, bool v) {
 // its own named barrier, so one half's MMAs, copies and barriers overlap the
 // other half's epilogues.  Per half: the e tile, and the P[src] rows that z
 // overwrites; the Q[dst] rows go to registers (each thread's row and 64
-// columns), loaded while MMA 2 and the second epilogue run.  The next tile's
-// e and P[src] copies are issued at the end of a tile, the row indices a
-// tile ahead.
+// columns): the next tile's are loaded while this tile's MMA 2 and second
+// epilogue run.  The next tile's e and P[src] copies are issued at the end
+// of a tile, the row indices a tile ahead.
 constexpr size_t kEdgePPSmem = (size_t)6 * 128 * 128 * 2;   // W1c, W2, 2 x (e, P/z)
 
 __global__ void __launch_bounds__(512, 1) k_edge_pp(const EdgeArgs g) {
